@@ -1,0 +1,448 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: closed
+forms, a numerically differentiated projection, the literal product form of
+Eq. 1, invariants of Eq. 1 / Eq. 3, central finite differences, and brute
+force on tiny inputs.  None of these needs a GPU.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2506_00225_gb300.scenes import Camera, Scene, scene_plain, look_camera
+
+ALPHA_MIN = np.float32(1.0) / np.float32(255.0)
+
+
+def ident_cam(W, H, f, near=0.2):
+    w2c = np.zeros((3, 4), np.float32)
+    w2c[:, :3] = np.eye(3, dtype=np.float32)
+    return Camera(W, H, float(f), float(f), W / 2.0, H / 2.0, near, w2c)
+
+
+def mk_scene(means, scales, quats, opacity, rgb=None, ids=None, w=None, m=4, unc=None):
+    n = len(means)
+    rgb = np.full((n, 3), 0.5) if rgb is None else rgb
+    ids = np.zeros((n, 1), np.int32) if ids is None else ids
+    w = np.ones((n, ids.shape[1])) if w is None else w
+    f = lambda a: np.ascontiguousarray(np.asarray(a, np.float64).astype(np.float32))
+    return Scene(f(means), f(scales), f(quats), f(opacity), f(rgb), np.ascontiguousarray(ids, np.int32), f(w), m,
+                 None if unc is None else f(unc))
+
+
+def rand_quat(rng, n):
+    q = rng.normal(size=(n, 4))
+    return q / np.linalg.norm(q, axis=1, keepdims=True)
+
+
+def quat_to_rot(q):
+    """Rotation matrix of a unit quaternion (w, x, y, z) via the axis-angle
+    (Rodrigues) formula -- an independent route from the oracle's."""
+    q = np.asarray(q, np.float64)
+    q = q / np.linalg.norm(q)
+    w, v = q[0], q[1:]
+    s = np.linalg.norm(v)
+    if s < 1e-15:
+        return np.eye(3)
+    axis = v / s
+    ang = 2.0 * math.atan2(s, w)
+    K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+    return np.eye(3) + math.sin(ang) * K + (1 - math.cos(ang)) * (K @ K)
+
+
+# --------------------------------------------------------------------------
+# projection
+# --------------------------------------------------------------------------
+
+def test_isotropic_on_axis_closed_form():
+    """A single isotropic Gaussian on the optical axis renders
+    alpha(p) = o exp(-rho^2 / (2 ((f s / z)^2 + 0.3))) (Eq. 1 with one term,
+    pinhole projection of an isotropic 3D Gaussian), for any rotation."""
+    rng = np.random.default_rng(7)
+    W = H = 41
+    f, z, s, o = 40.0, 2.0, 0.15, 0.8
+    cam = ident_cam(W, H, f)
+    for q in [np.array([1.0, 0, 0, 0]), rand_quat(rng, 1)[0], rand_quat(rng, 1)[0]]:
+        sc = mk_scene([[0.0, 0.0, z]], [[s, s, s]], [q], [o], rgb=[[1.0, 0.25, 0.5]])
+        r = oracle.render(sc, cam, prec="f64")
+        # the scene stores float32 values; the closed form uses those
+        s32, z32, o32 = float(np.float32(s)), float(np.float32(z)), float(np.float32(o))
+        var = (f * s32 / z32) ** 2 + 0.3
+        lam = var + math.sqrt(0.1)  # eigenvalue floor of the radius rule
+        rad = math.ceil(3 * math.sqrt(lam))
+        ys, xs = np.mgrid[0:H, 0:W]
+        dx = xs + 0.5 - W / 2.0
+        dy = ys + 0.5 - H / 2.0
+        a = np.minimum(0.99, o32 * np.exp(-0.5 * (dx ** 2 + dy ** 2) / var))
+        inside = (np.abs(dx) <= rad) & (np.abs(dy) <= rad) & (a >= 1 / 255)
+        expect = np.where(inside, a, 0.0)
+        np.testing.assert_allclose(r["sil"], expect, rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(r["rgb"][..., 1], 0.25 * expect, rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(r["depth"], z32 * expect, rtol=1e-12, atol=1e-14)
+
+
+def _proj_numeric(mean, scale, q, cam):
+    """EWA linearisation by numerical differentiation of the pinhole map
+    (world point -> pixel) at the mean, in float64."""
+    w2c = cam.w2c.astype(np.float64)
+
+    def pix(X):
+        t = w2c[:, :3] @ X + w2c[:, 3]
+        return np.array([cam.fx * t[0] / t[2] + cam.cx, cam.fy * t[1] / t[2] + cam.cy])
+
+    h = 1e-6
+    J = np.zeros((2, 3))
+    for i in range(3):
+        e = np.zeros(3); e[i] = h
+        J[:, i] = (pix(mean + e) - pix(mean - e)) / (2 * h)
+    R = quat_to_rot(q)
+    S3 = R @ np.diag(np.asarray(scale, np.float64) ** 2) @ R.T
+    S2 = J @ S3 @ J.T + 0.3 * np.eye(2)
+    return pix(mean), S2
+
+
+def test_projection_matches_numeric_jacobian():
+    rng = np.random.default_rng(11)
+    cam = look_camera((0.3, -0.2, 1.4), 25.0, 96, 64, 70.0, pitch_deg=-10.0)
+    n = 200
+    c2w_r = cam.w2c[:, :3].astype(np.float64).T
+    pos = cam.position()
+    # points in front of the camera, inside the frustum clamp
+    tc = np.stack([rng.uniform(-0.5, 0.5, n), rng.uniform(-0.35, 0.35, n), rng.uniform(1.0, 4.0, n)], 1)
+    tc[:, 0] *= tc[:, 2]
+    tc[:, 1] *= tc[:, 2]
+    means = tc @ c2w_r.T + pos
+    scales = np.exp(rng.normal(-2.5, 0.6, size=(n, 3)))
+    quats = rand_quat(rng, n) * rng.uniform(0.5, 2.0, size=(n, 1))  # not unit
+    sc = mk_scene(means, scales, quats, np.full(n, 0.5))
+    p = oracle.project(sc, cam, prec="f64")
+    checked = 0
+    for i in range(n):
+        if not p["visible"][i]:
+            continue
+        uv, S2 = _proj_numeric(sc.means[i].astype(np.float64), sc.scales[i], sc.quats[i], cam)
+        np.testing.assert_allclose(p["uv"][i], uv, rtol=0, atol=1e-6)
+        conic = np.linalg.inv(S2)
+        np.testing.assert_allclose(p["conic"][i], [conic[0, 0], conic[0, 1], conic[1, 1]], rtol=2e-6, atol=1e-9)
+        ev = np.linalg.eigvalsh(S2)
+        mid = 0.5 * (ev[0] + ev[1])
+        lam = mid + math.sqrt(max(0.1, (0.5 * (ev[1] - ev[0])) ** 2))
+        assert p["radius"][i] == math.ceil(3 * math.sqrt(lam)) or abs(3 * math.sqrt(lam) - round(3 * math.sqrt(lam))) < 1e-6
+        t = cam.w2c[:, :3].astype(np.float64) @ sc.means[i] + cam.w2c[:, 3]
+        assert abs(p["depth"][i] - t[2]) < 1e-12
+        checked += 1
+    assert checked > 150
+
+
+def test_rect_rule_bruteforce_and_tiles():
+    """Pixel rectangle = bounding set of pixels whose centre lies within the
+    radius of the 2D mean (per axis); tile rectangle = tiles it touches."""
+    sc = scene_plain(0, n=3000)
+    cam = look_camera((0.0, 0.0, 1.5), 0.0, 100, 70, 80.0)
+    for tile in [(16, 16), (8, 8), (32, 8)]:
+        p = oracle.project(sc, cam, tile=tile, prec="f32")
+        for i in np.nonzero(p["visible"])[0][:400]:
+            u, v = p["uv"][i].astype(np.float64)
+            r = float(p["radius"][i])
+            xs = np.arange(cam.width)
+            ys = np.arange(cam.height)
+            okx = xs[np.abs(xs + 0.5 - u) <= r]
+            oky = ys[np.abs(ys + 0.5 - v) <= r]
+            x0, x1, y0, y1 = p["rect"][i]
+            assert (okx.min(), okx.max(), oky.min(), oky.max()) == (x0, x1, y0, y1)
+            tx0, tx1, ty0, ty1 = p["trect"][i]
+            assert (tx0, tx1, ty0, ty1) == (x0 // tile[0], x1 // tile[0], y0 // tile[1], y1 // tile[1])
+            assert p["ntiles"][i] == (tx1 - tx0 + 1) * (ty1 - ty0 + 1)
+        assert not p["visible"][p["depth"] <= cam.near].any()
+
+
+def test_tile_lists_bruteforce_and_tiebreak():
+    """Each tile's list = Gaussians whose tile rectangle holds the tile,
+    front to back by depth, ties by gid (Sec. 3.1 front-to-back sort)."""
+    rng = np.random.default_rng(3)
+    n = 300
+    cam = ident_cam(64, 48, 50.0)
+    z = rng.choice([1.5, 2.0, 2.5], size=n)  # many exactly equal depths
+    means = np.stack([rng.uniform(-0.6, 0.6, n) * z, rng.uniform(-0.45, 0.45, n) * z, z], 1)
+    sc = mk_scene(means, np.exp(rng.normal(-3, 0.4, (n, 3))), rand_quat(rng, n), np.full(n, 0.5))
+    p = oracle.project(sc, cam, prec="f32")
+    ranges, gids, offs = oracle.tile_lists([p], [cam])
+    gx, gy = oracle.tiles_of(cam)
+    for t in range(gx * gy):
+        tx, ty = t % gx, t // gx
+        members = [g for g in range(n) if p["visible"][g] and p["trect"][g][0] <= tx <= p["trect"][g][1]
+                   and p["trect"][g][2] <= ty <= p["trect"][g][3]]
+        members.sort(key=lambda g: (float(p["depth"][g]), g))
+        s, e = ranges[t]
+        assert list(gids[s:e]) == members
+
+
+# --------------------------------------------------------------------------
+# compositing (Eq. 1, Eq. 3)
+# --------------------------------------------------------------------------
+
+def _tiny_scene(rng, n, m=6, k=2, omax=0.8):
+    cam = ident_cam(16, 16, 14.0)
+    z = rng.uniform(1.0, 3.0, n)
+    means = np.stack([rng.uniform(-0.4, 0.4, n) * z, rng.uniform(-0.4, 0.4, n) * z, z], 1)
+    scales = np.exp(rng.normal(-1.6, 0.4, (n, 3)))
+    ids = np.stack([rng.choice(m, k, replace=False) for _ in range(n)]).astype(np.int32)
+    w = rng.dirichlet(np.ones(k), n)
+    sc = mk_scene(means, scales, rand_quat(rng, n), rng.uniform(0.2, omax, n), rgb=rng.uniform(0, 1, (n, 3)),
+                  ids=ids, w=w, m=m)
+    return sc, cam
+
+
+def test_product_form_tiny_scenes():
+    """Eq. 1 and Eq. 3 evaluated literally -- sum_i z_i f_i prod_{j<i}(1-f_j)
+    over the depth-sorted candidates -- match the oracle on tiny scenes."""
+    rng = np.random.default_rng(5)
+    for trial in range(6):
+        sc, cam = _tiny_scene(rng, 5)
+        p = oracle.project(sc, cam, prec="f64")
+        r = oracle.render(sc, cam, prec="f64")
+        order = sorted(np.nonzero(p["visible"])[0], key=lambda g: (p["depth"][g], g))
+        for y in range(cam.height):
+            for x in range(cam.width):
+                fs, zs = [], []
+                for g in order:
+                    x0, x1, y0, y1 = p["rect"][g]
+                    if not (x0 <= x <= x1 and y0 <= y <= y1):
+                        continue
+                    dx, dy = p["uv"][g][0] - (x + 0.5), p["uv"][g][1] - (y + 0.5)
+                    a, b, c = p["conic"][g]
+                    pw = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy
+                    al = min(0.99, float(sc.opacity[g]) * math.exp(pw))
+                    if pw > 0 or al < 1 / 255:
+                        continue
+                    fs.append(al)
+                    zs.append(g)
+                wts = [fs[i] * np.prod([1 - fs[j] for j in range(i)]) for i in range(len(fs))]
+                assert np.prod([1 - f for f in fs]) >= 1e-4  # no early stop in these scenes
+                sil = sum(wts)
+                col = sum(wi * sc.rgb[g].astype(np.float64) for wi, g in zip(wts, zs)) if zs else np.zeros(3)
+                dep = sum(wi * p["depth"][g] for wi, g in zip(wts, zs))
+                sem = np.zeros(sc.m)
+                for wi, g in zip(wts, zs):
+                    for j in range(sc.k):
+                        sem[sc.sem_ids[g, j]] += wi * float(sc.sem_w[g, j])
+                assert abs(r["sil"][y, x] - sil) < 1e-12
+                np.testing.assert_allclose(r["rgb"][y, x], col, atol=1e-12)
+                assert abs(r["depth"][y, x] - dep) < 1e-12
+                np.testing.assert_allclose(r["sem"][y, x], sem, atol=1e-12)
+
+
+def test_transmittance_stop_rule():
+    """Stacked Gaussians with alpha = 0.95 each: T after 3 is 1.25e-4, the
+    4th would take it below 1e-4, so exactly 3 contribute and
+    S = 1 - 0.05^3 at the centre pixel."""
+    cam = ident_cam(3, 3, 10.0)
+    n = 6
+    means = [[0.0, 0.0, 1.0 + 0.1 * i] for i in range(n)]
+    sc = mk_scene(means, [[1.0, 1.0, 1.0]] * n, [[1, 0, 0, 0]] * n, [0.95] * n)
+    r = oracle.render(sc, cam, prec="f64")
+    # centre pixel: dx = dy = 0 -> alpha = opacity exactly
+    assert r["n_contrib"][1, 1] == 3
+    o32 = float(np.float32(0.95))
+    assert abs(r["sil"][1, 1] - (1 - (1 - o32) ** 3)) < 1e-12
+
+
+def test_white_gaussians_colour_equals_silhouette():
+    """With c_i = 1, Eq. 1 for colour equals Eq. 1 for silhouette, which the
+    oracle computes separately as 1 - prod(1 - alpha_i)."""
+    sc = scene_plain(0, n=4000)
+    sc.rgb[:] = 1.0
+    cam = look_camera((0.0, 0.0, 1.5), 0.0, 64, 64, 55.0)
+    r = oracle.render(sc, cam, prec="f32")
+    for c in range(3):
+        np.testing.assert_allclose(r["rgb"][..., c], r["sil"], atol=2e-6)
+    r64 = oracle.render(sc, cam, prec="f64")
+    np.testing.assert_allclose(r64["rgb"][..., 0], r64["sil"], atol=1e-12)
+
+
+def test_semantics_sum_and_per_class_channel():
+    """Eq. 3: weights summing to 1 give sum_m P_m = S; and P_m equals Eq. 1
+    with z_i = p_{i,m} rendered through the colour channel."""
+    sc = scene_plain(0, n=4000, m=16, k=3)
+    cam = look_camera((0.0, 0.0, 1.5), 0.0, 64, 64, 55.0)
+    r = oracle.render(sc, cam, prec="f32")
+    np.testing.assert_allclose(r["sem"].sum(-1), r["sil"], atol=5e-6)
+    for classes in [(0, 5, 9), (15, 3, 7)]:
+        dense = np.zeros((sc.n, 3), np.float32)
+        for c, m_ in enumerate(classes):
+            hit = sc.sem_ids == m_
+            dense[:, c] = (sc.sem_w * hit).sum(1)
+        sc2 = Scene(sc.means, sc.scales, sc.quats, sc.opacity, dense, sc.sem_ids, sc.sem_w, sc.m)
+        r2 = oracle.render(sc2, cam, prec="f32", sem=False)
+        for c, m_ in enumerate(classes):
+            np.testing.assert_allclose(r2["rgb"][..., c], r["sem"][..., m_], atol=1e-6)
+
+
+def test_isotropic_independent_of_rotation():
+    rng = np.random.default_rng(2)
+    sc = scene_plain(1, n=800)
+    sc.scales[:] = sc.scales[:, :1]
+    cam = look_camera((0.0, 0.0, 1.5), 0.0, 48, 48, 40.0)
+    r0 = oracle.render(sc, cam, prec="f64")
+    sc.quats[:] = rand_quat(rng, sc.n).astype(np.float32)
+    r1 = oracle.render(sc, cam, prec="f64")
+    np.testing.assert_allclose(r0["rgb"], r1["rgb"], atol=1e-9)
+    np.testing.assert_allclose(r0["sem"], r1["sem"], atol=1e-9)
+
+
+def test_pixel_list_equals_full_image():
+    sc = scene_plain(0, n=3000)
+    cam = look_camera((0.0, 0.0, 1.5), 0.0, 40, 30, 35.0)
+    r = oracle.render(sc, cam, prec="f32")
+    rng = np.random.default_rng(0)
+    xs = rng.integers(0, 40, 50)
+    ys = rng.integers(0, 30, 50)
+    rp = oracle.render_pixels(sc, cam, xs, ys, prec="f32")
+    np.testing.assert_array_equal(rp["rgb"], r["rgb"][ys, xs])
+    np.testing.assert_array_equal(rp["sem"], r["sem"][ys, xs])
+    np.testing.assert_array_equal(rp["sil"], r["sil"][ys, xs])
+
+
+# --------------------------------------------------------------------------
+# adjoint
+# --------------------------------------------------------------------------
+
+def _fd_scene(seed):
+    rng = np.random.default_rng(seed)
+    n, m, k = 5, 5, 2
+    cam = look_camera((0.0, 0.0, 0.0), 0.0, 20, 18, 24.0, pitch_deg=5.0)
+    cam.near = 0.2
+    c2w = cam.w2c[:, :3].astype(np.float64).T
+    z = rng.uniform(1.5, 3.0, n)
+    tc = np.stack([rng.uniform(-0.25, 0.25, n) * z, rng.uniform(-0.25, 0.25, n) * z, z], 1)
+    means = tc @ c2w.T + cam.position()
+    scales = np.exp(rng.normal(-1.9, 0.3, (n, 3)))
+    ids = np.stack([rng.choice(m, k, replace=False) for _ in range(n)]).astype(np.int32)
+    sc = mk_scene(means, scales, rand_quat(rng, n) * 1.3, rng.uniform(0.3, 0.85, n),
+                  rgb=rng.uniform(0, 1, (n, 3)), ids=ids, w=rng.uniform(0.1, 0.9, (n, k)), m=m)
+    W, H = cam.width, cam.height
+    up = dict(d_rgb=rng.normal(size=(H, W, 3)), d_depth=rng.normal(size=(H, W)), d_sil=rng.normal(size=(H, W)),
+              d_sem=rng.normal(size=(H, W, m)))
+    return sc, cam, up
+
+
+def _loss(sc, cam, up, with_sem=True):
+    r = oracle.render(sc, cam, prec="f64")
+    L = (r["rgb"] * up["d_rgb"]).sum() + (r["depth"] * up["d_depth"]).sum() + (r["sil"] * up["d_sil"]).sum()
+    if with_sem:
+        L += (r["sem"] * up["d_sem"]).sum()
+    return L, r["n_contrib"].copy(), r["flag"].copy()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_adjoint_matches_central_differences(seed):
+    sc, cam, up = _fd_scene(seed)
+    g = oracle.render_bwd(sc, cam, **up, sem_detach=False, prec="f64")
+    fields = ["means", "scales", "quats", "opacity", "rgb", "sem_w"]
+    skipped = 0
+    total = 0
+    for fld in fields:
+        arr = getattr(sc, fld)
+        flat = arr.reshape(-1)
+        ga = g[fld].reshape(-1)
+        scale = np.abs(ga).max() + 1e-12
+        for j in range(flat.size):
+            x0 = float(flat[j])
+            # the scene is float32; perturb in double by editing a float64 copy
+            h = 1e-6 * max(1.0, abs(x0))
+            vals = []
+            sigs = []
+            for sgn in (1, -1):
+                sc2 = Scene(*[np.array(getattr(sc, a), dtype=np.float64) for a in ["means", "scales", "quats",
+                                                                                      "opacity", "rgb"]],
+                            sc.sem_ids, np.array(sc.sem_w, np.float64), sc.m)
+                getattr(sc2, fld).reshape(-1)[j] = x0 + sgn * h
+                L, nc, fl = _loss(sc2, cam, up)
+                vals.append(L)
+                sigs.append(nc)
+            total += 1
+            if not np.array_equal(sigs[0], sigs[1]):
+                skipped += 1
+                continue
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert abs(fd - ga[j]) <= 1e-5 * abs(ga[j]) + 1e-6 * scale, (fld, j, fd, ga[j])
+    assert skipped <= total // 20
+
+
+def test_semantic_gradient_block():
+    """With the block on, geometric gradients do not depend on the semantic
+    upstream gradient, and semantic-weight gradients do not change."""
+    sc, cam, up = _fd_scene(4)
+    g1 = oracle.render_bwd(sc, cam, **up, sem_detach=True, prec="f64")
+    up0 = dict(up)
+    up0["d_sem"] = np.zeros_like(up["d_sem"])
+    g0 = oracle.render_bwd(sc, cam, **up0, sem_detach=True, prec="f64")
+    for fld in ["means", "scales", "quats", "opacity", "rgb"]:
+        np.testing.assert_array_equal(g1[fld], g0[fld])
+    g2 = oracle.render_bwd(sc, cam, **up, sem_detach=False, prec="f64")
+    np.testing.assert_array_equal(g1["sem_w"], g2["sem_w"])
+    assert np.abs(g1["opacity"] - g2["opacity"]).max() > 0
+
+
+# --------------------------------------------------------------------------
+# candidate-view reductions (Eq. 6, Eq. 7 with Eq. 4)
+# --------------------------------------------------------------------------
+
+def test_candidate_empty_view():
+    sc = scene_plain(0, n=500, m=16)
+    sc.geo_unc = np.ones(sc.n, np.float32)
+    cam = look_camera((0.0, 0.0, 1.5), 0.0, 30, 20, 25.0)
+    cam.w2c[:, 3] += np.float32(100.0) * cam.w2c[:, 2]  # push everything behind the camera
+    cam.w2c[2, 3] = np.float32(-100.0)
+    su, sh, ns, nf = oracle.candidate(sc, cam)
+    assert ns == 30 * 20
+    assert su == 0.0
+    assert abs(sh - 30 * 20 * math.log(16)) < 1e-9
+
+
+def test_candidate_single_class_closed_form():
+    """One Gaussian, one class with weight 1: P_0 = S, other classes 0, so
+    after clipping to [0.001, 1] and renormalising the entropy per pixel has
+    a closed form in S; u_i = 1 gives U = S."""
+    cam = ident_cam(24, 20, 18.0)
+    m = 10
+    sc = mk_scene([[0.1, -0.05, 2.0]], [[0.4, 0.25, 0.3]], [[0.9, 0.1, 0.2, 0.3]], [0.9], ids=np.array([[3]]),
+                  w=np.array([[1.0]]), m=m, unc=[1.0])
+    su, sh, ns, nf = oracle.candidate(sc, cam, prec="f64")
+    r = oracle.render(sc, cam, prec="f64")
+    s = r["sil"].reshape(-1)
+    p0 = np.clip(s, 0.001, 1.0)
+    z = p0 + 0.001 * (m - 1)
+    h = -(p0 / z) * np.log(p0 / z) - (m - 1) * (0.001 / z) * np.log(0.001 / z)
+    assert abs(sh - h.sum()) < 1e-9 * h.sum()
+    assert abs(su - s.sum()) < 1e-9
+    assert ns == int((s == 0).sum()) and 0 < ns < s.size
+
+
+def test_entropy_uniform_k_is_log_k():
+    """Sec. 3.1: tau = log k is the entropy of a uniform distribution over k
+    classes.  A pixel whose semantic map is uniform over k classes with mass
+    well above the clip floor has entropy close to log k."""
+    cam = ident_cam(1, 1, 10.0)
+    for k in (2, 3, 8):
+        m = k
+        sc = mk_scene([[0.0, 0.0, 1.0]], [[1.0, 1.0, 1.0]], [[1, 0, 0, 0]], [0.99], ids=np.arange(k)[None, :],
+                      w=np.full((1, k), 1.0 / k), m=m)
+        su, sh, ns, nf = oracle.candidate(sc, cam, prec="f64")
+        assert abs(sh - math.log(k)) < 1e-12
+
+
+def test_golden_closed_forms():
+    import json
+    import os
+    d = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "closed_forms.json")))
+    cam = ident_cam(1, 1, 10.0)
+    for k, v in zip(d["entropy_uniform_k"]["k"], d["entropy_uniform_k"]["value"]):
+        sc = mk_scene([[0.0, 0.0, 1.0]], [[1.0, 1.0, 1.0]], [[1, 0, 0, 0]], [0.99], ids=np.arange(k)[None, :],
+                      w=np.full((1, k), 1.0 / k), m=k)
+        assert abs(oracle.candidate(sc, cam, prec="f64")[1] - v) < 1e-12
+    for m, v in zip(d["entropy_empty_pixel"]["m"], d["entropy_empty_pixel"]["value"]):
+        sc = mk_scene([[0.0, 0.0, -1.0]], [[1.0, 1.0, 1.0]], [[1, 0, 0, 0]], [0.5], m=m)
+        assert abs(oracle.candidate(sc, cam, prec="f64")[1] - v) < 1e-12
