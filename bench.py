@@ -1,0 +1,449 @@
+#!/usr/bin/env python
+"""Benchmark of the semantic Gaussian rasterizer's mapping step.
+
+Workload (default ``room300k``): one 680x1200 view (fx=fy=600) of a seeded
+300k-Gaussian synthetic 6x6x3 m room, 102 classes, sparse top-3 semantics.
+One step = project + bin/sort + forward render fused with the mean-L1 loss
+(colour, depth and semantic map against a target render of a perturbed copy)
++ adjoint to all Gaussian parameters through the autograd Function
+``raster.render_l1``.  ``value`` = mapping fwd+bwd iterations/s, summed over
+GPUs (replicas).  The same step with the semantic map materialised, a
+separate L1 kernel and the map-sized gradient (``raster.rasterize``) is timed
+too and reported under ``unfused_step``.
+
+Also measured in the same run (key ``candidates``): batched candidate-view
+rendering of 96 poses of mixed resolution (views/s), and the same views
+issued as one plain launch chain per view.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+L2_BYTES = 129 * 1024 * 1024
+ORACLE_ROW_STEP = 6       # CPU baseline: every 6th pixel row of the view (~10 s)
+ORACLE_ROW_STEP_REF = 40  # reference arm: every 40th row per step (~1.5 s)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="room300k")
+    ap.add_argument("--no-candidates", action="store_true")
+    ap.add_argument("--cand-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only: no data-path collective)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend)
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, path: str):
+        self.path = path
+        self.proc = None
+        try:
+            self.fh = open(path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not mhz:
+            return None
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline (the oracle as it stands)
+# ---------------------------------------------------------------------------
+
+def bench_config(world: int) -> dict:
+    return {"workload": "room300k: 300k-Gaussian synthetic room, one 680x1200 view (fx=fy=600), M=102 classes, "
+                        "top-3 semantics; step = project + bin/sort + forward fused with the mean-L1 loss on "
+                        "colour/depth/semantics + adjoint to all parameters (torch.autograd.Function)",
+            "tile": "16x16",
+            "l2": "inputs larger than L2 (333 MB target semantic map) and a 258 MB L2 flush between timed steps "
+                  "(outside the per-step events)",
+            "parallelism": f"replicas x{world}"}
+
+
+def cpu_baseline(wl, row_step=ORACLE_ROW_STEP) -> dict:
+    """Times the CPU oracle's forward + backward of the mapping step on every
+    row_step-th pixel row and scales to a full step."""
+    import oracle
+    sc, cam = wl["scene"], wl["cams"][0]
+    H, W, m = cam.height, cam.width, sc.m
+    rng = np.random.default_rng(0)
+    up = dict(d_rgb=np.sign(rng.normal(size=(H, W, 3))).astype(np.float32) / (3 * H * W),
+              d_depth=np.sign(rng.normal(size=(H, W))).astype(np.float32) / (H * W),
+              d_sem=np.sign(rng.normal(size=(H, W, m))).astype(np.float32) / (H * W * m))
+    rows = (0, H, row_step)
+    nrows = len(range(*rows))
+    t0 = time.perf_counter()
+    oracle.render(sc, cam, prec="f32", rows=rows)
+    oracle.render_bwd(sc, cam, **up, prec="f32", rows=rows)
+    dt = time.perf_counter() - t0
+    per_step = dt * H / nrows
+    return {"value": 1.0 / per_step, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"forward (OpenMP over rows, {os.cpu_count()} threads) + backward (1 thread) of the CPU "
+                      f"oracle on {nrows} of {H} pixel rows (every {row_step}th) of the 680x1200 view, "
+                      f"{dt:.2f} s measured, scaled by {H / nrows:.2f} to one step"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2506_00225_gb300 import scenes
+    wl = scenes.workload(args.workload)
+    times = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(wl, ORACLE_ROW_STEP_REF)
+        if i >= args.warmup:
+            times.append(1.0 / cb["value"])
+    ms = 1000.0 * statistics.mean(times)
+    value = 1000.0 / ms
+    line = {"metric": "mapping fwd+bwd iters/s @680x1200", "value": value, "unit": "iters/s",
+            "n_gpus": max(1, world), "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "impl": "reference",
+            "config": bench_config(max(1, world)),
+            "cpu_baseline": dict(cb, value=value),
+            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+FP32_LANES_PER_SM = 128
+N_SM = 152
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_init(world, "nccl")
+    dev = torch.device("cuda", local)
+
+    from paper_2506_00225_gb300 import build, raster, scenes
+    build.build()
+
+    wl = scenes.workload(args.workload)
+    sc, cam = wl["scene"], wl["cams"][0]
+    H, W, m, k = cam.height, cam.width, sc.m, sc.k
+    g = raster.Gaussians.from_scene(sc, dev)
+    gt = raster.Gaussians.from_scene(wl["target"], dev)
+    rast = raster.Rasterizer(device=dev)
+    with torch.no_grad():
+        t_rgb, t_depth, _, t_sem = rast.forward(gt, cam, check=True)
+        t_rgb, t_depth, t_sem = t_rgb.clone(), t_depth.clone(), t_sem.clone()
+    params = [t.clone().requires_grad_(True) for t in (g.means, g.scales, g.quats, g.opacity, g.rgb, g.sem_w)]
+    rast.forward(g, cam, check=True)  # sizes the workspace capacities
+    cnt = rast.counters()
+    n_records, n_pairs, n_contrib = int(cnt.n_records), int(cnt.n_pairs), int(cnt.n_contrib)
+
+    def step_fused(tr, td, ts):
+        for p in params:
+            p.grad = None
+        loss = raster.render_l1(rast, g, cam, tr, td, ts, *params, check=False)
+        loss.backward()
+        return loss
+
+    def step_unfused(tr, td, ts):
+        for p in params:
+            p.grad = None
+        rgb, depth, sil, sem = raster.rasterize(rast, g, cam, *params, check=False)
+        rast._mark("loss")
+        loss, d_rgb, d_depth, d_sem = raster.l1_loss_and_grads(rgb, depth, sem, tr, td, ts)
+        torch.autograd.backward([rgb, depth, sem], [d_rgb, d_depth, d_sem])
+        return loss
+
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+
+    def timed(step, steps):
+        starts, ends, phases = [], [], []
+        for _ in range(steps):
+            flush.zero_()
+            rast.phase_events = []
+            s_ = torch.cuda.Event(enable_timing=True)
+            e_ = torch.cuda.Event(enable_timing=True)
+            s_.record()
+            step(t_rgb, t_depth, t_sem)
+            e_.record()
+            starts.append(s_)
+            ends.append(e_)
+            phases.append(rast.phase_events)
+            rast.phase_events = None
+        torch.cuda.synchronize()
+        step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+        ph = {}
+        for evs in phases:
+            for (n0, e0), (_, e1) in zip(evs[:-1], evs[1:]):
+                ph.setdefault(n0, []).append(e0.elapsed_time(e1))
+        return step_ms, {k_: statistics.mean(v) for k_, v in ph.items()}
+
+    for _ in range(args.warmup):
+        step_unfused(t_rgb, t_depth, t_sem)
+        step_fused(t_rgb, t_depth, t_sem)
+    torch.cuda.synchronize()
+
+    # ---- timed region (headline: fused step) ---------------------------------
+    clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")) \
+        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ClockSampler(local, f"/tmp/clocks_rank{rank}.csv")
+    barrier(world)
+    torch.cuda.synchronize()
+    step_ms, ph_ms = timed(step_fused, args.steps)
+    barrier(world)
+    clk = clocks.stop()
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
+    ms_per_step = total_ms / args.steps
+    value = world * 1000.0 / ms_per_step
+
+    # the same step with the semantic map written, a separate L1 kernel and
+    # the map-sized gradient read back by the adjoint
+    un_ms, un_ph = timed(step_unfused, max(3, args.steps // 2))
+    un_total = max_over_ranks(sum(un_ms), world, dev) / len(un_ms)
+
+    # ---- roofline ---------------------------------------------------------------
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        peaks = json.load(open(pp))
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    clock_ghz = (clk["sm_mhz"] / 1000.0) if clk else 2.07
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * clock_ghz / 1000.0  # TFLOP/s at the sampled clock
+    nwc = (m + 31) // 32
+    code_b = 4 * 2 * (1 + nwc)
+    rec_b = 48 + 12 + 8 * k
+    grads_b = sc.n * (17 + k) * 4
+    bytes_fwd = H * W * (m + 4) * 4 + H * W * (8 + code_b) + n_pairs * 4 + n_records * rec_b
+    bytes_bwd = H * W * (8 + code_b) + n_pairs * 4 + n_records * (rec_b + 32) + grads_b
+    # flops per contribution of the adjoint (alpha 10, transmittance 2, g 8,
+    # semantic 3k, dalpha 3, accumulate 2, conic/mean/opacity terms 16)
+    flops_bwd = n_contrib * (41 + 3 * k)
+    kern = {"render_fwd": ph_ms.get("render_fwd", 0.0), "render_bwd": ph_ms.get("render_bwd", 0.0),
+            "project": ph_ms.get("project", 0.0)}
+    frac_fwd = (bytes_fwd / (kern["render_fwd"] * 1e-3) / 1e9) / hbm_peak if kern["render_fwd"] else 0.0
+    dom = max(kern, key=lambda n: kern[n])
+    if dom == "render_bwd":
+        t = kern["render_bwd"] * 1e-3
+        hbm_frac = (bytes_bwd / t / 1e9) / hbm_peak
+        alu = flops_bwd / t / 1e12
+        roofline = {"bound": "alu", "kernel": "k_render_bwd (codes mode; + zero, project_bwd)", "achieved": alu,
+                    "peak": fp32_peak, "unit": "TFLOP/s", "frac": alu / fp32_peak,
+                    "peak_source": f"FP32 pipe: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {clock_ghz:.3f} "
+                                   f"GHz (sampled SM clock)",
+                    "traffic": None, "algorithmic_flops": flops_bwd, "hbm_frac_of_" + peak_src: hbm_frac}
+    else:
+        name = {"render_fwd": ("k_render_fwd (fused L1)", bytes_fwd), "project": ("project + bin/sort", None)}[dom]
+        t = kern[dom] * 1e-3
+        b = name[1] if name[1] is not None else sc.n * 88 + n_records * 52 + n_pairs * 16
+        roofline = {"bound": "hbm", "kernel": name[0], "achieved": b / t / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": (b / t / 1e9) / hbm_peak, "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json)",
+                    "traffic": None, "algorithmic_bytes": b}
+    roofline["phases_ms"] = {k_: round(v, 4) for k_, v in ph_ms.items()}
+    roofline["render_fwd_hbm_frac"] = frac_fwd
+
+    # ---- e2e through the public API with host buffers ------------------------
+    pin = lambda t_: t_.detach().cpu().pin_memory()
+    h_rgb, h_depth, h_sem = pin(t_rgb), pin(t_depth), pin(t_sem)
+    d_tr, d_td, d_ts = torch.empty_like(t_rgb), torch.empty_like(t_depth), torch.empty_like(t_sem)
+    h_loss = torch.empty((), dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, args.steps // 2)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(e2e_steps):
+        d_tr.copy_(h_rgb, non_blocking=True)
+        d_td.copy_(h_depth, non_blocking=True)
+        d_ts.copy_(h_sem, non_blocking=True)
+        loss = step_fused(d_tr, d_td, d_ts)
+        h_loss.copy_(loss, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev) / e2e_steps
+    h2d = (h_rgb.numel() + h_depth.numel() + h_sem.numel()) * 4
+
+    st = rast.counters()
+    if st.status != 0:
+        raise RuntimeError(f"device status {st.status} after the timed region")
+
+    cand = None
+    if not args.no_candidates:
+        cand = bench_candidates(args, dev, flush)
+
+    # launches of our kernels per fused step: project 4, depth sort 3/pass,
+    # emit 3, tile sort 3/pass, ranges 1, fused fwd 1 + loss final 1, bwd 3
+    passes = lambda bits: (bits + 7) // 8
+    tiles = ((W + 15) // 16) * ((H + 15) // 16)
+    per_step = 4 + 3 * passes(31) + 3 + 3 * passes(max(1, (tiles - 1).bit_length())) + 1 + 2 + 3
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl)
+
+    if rank == 0:
+        line = {"metric": "mapping fwd+bwd iters/s @680x1200", "value": value, "unit": "iters/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": bench_config(world),
+                "counts": {"visible_records": n_records, "tile_gaussian_pairs": n_pairs, "contributions": n_contrib},
+                "roofline": roofline,
+                "cpu_baseline": cpu,
+                "e2e": {"value": world * 1000.0 / e2e_ms, "unit": "iters/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": 4},
+                "gpu_launches": per_step * args.steps,
+                "clocks": clk,
+                "unfused_step": {"value": world * 1000.0 / un_total, "unit": "iters/s", "ms_per_step": un_total,
+                                 "phases_ms": {k_: round(v, 4) for k_, v in un_ph.items()},
+                                 "what": "rasterize (writes the HxWxM map) + separate L1 kernel + adjoint reading "
+                                         "the HxWxM gradient"},
+                "candidates": cand}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def bench_candidates(args, dev, flush):
+    import torch
+    from paper_2506_00225_gb300 import raster, scenes
+    wl = scenes.workload("cand96")
+    sc, cams = wl["scene"], wl["cams"]
+    g = raster.Gaussians.from_scene(sc, dev)
+    rast = raster.Rasterizer(device=dev)
+    out = rast.candidates(g, cams, check=True)
+    cnt = rast.counters()
+    for _ in range(2):
+        rast.candidates(g, cams, check=False, out=out)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.cand_steps):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        rast.candidates(g, cams, check=False, out=out)
+        e.record()
+        ts.append((s, e))
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ts)
+    # the same views, one plain launch chain per view
+    singles = [raster.Rasterizer(device=dev) for _ in range(3)]
+    outs = []
+    for v, c in enumerate(cams[:3]):
+        outs.append(singles[v % 3].candidates(g, [c], check=True))
+    torch.cuda.synchronize()
+    flush.zero_()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for v, c in enumerate(cams):
+        singles[v % 3].candidates(g, [c], check=False)
+    e.record()
+    torch.cuda.synchronize()
+    per_view_ms = s.elapsed_time(e)
+    npix = sum(c.width * c.height for c in cams)
+    return {"metric": "candidate views/s", "value": 1000.0 * len(cams) / ms, "unit": "views/s",
+            "ms_per_batch": ms, "mpix_per_s": npix / (ms * 1e-3) / 1e6,
+            "workload": "cand96: the 300k room + Gamma(2,0.5) uncertainty, 96 poses (4x4 grid at 0.5 m x 6 yaws), "
+                        "resolutions cycling 170x300 / 340x600 / 680x1200",
+            "n_records": int(cnt.n_records), "n_pairs": int(cnt.n_pairs),
+            "per_view_launches": {"value": 1000.0 * len(cams) / per_view_ms, "unit": "views/s",
+                                  "ms": per_view_ms},
+            "batched_speedup": per_view_ms / ms}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

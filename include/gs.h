@@ -1,0 +1,247 @@
+/*
+ * gs.h -- C ABI of the GB300 (sm_103a) semantic Gaussian-splatting rasterizer.
+ *
+ * The library implements the data-parallel hot path of ActiveSGM's mapping
+ * backbone (arXiv 2506.00225): tile-based differentiable rasterization of
+ * anisotropic 3D Gaussians with colour, depth, silhouette (Sec. 3.1, Eq. 1)
+ * and the sparse top-k semantic distribution (Sec. 3.1, Eq. 3), its adjoint,
+ * and batched candidate-view rendering of the exploration criteria
+ * (Sec. 3.2, Eq. 6 and Eq. 7 with Eq. 4).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * - All array arguments are DEVICE pointers owned by the caller, except the
+ *   structs themselves (host memory, read during the call only) and the
+ *   explicit host buffers of gs_read_counters / gs_status_string.
+ * - The library allocates nothing.  Scratch memory is a caller-allocated
+ *   device workspace of gs_workspace_size() bytes (256-byte aligned); it
+ *   carries state from gs_project to gs_bin_sort to gs_render_fwd to
+ *   gs_render_bwd, so these calls must receive the same scene sizes, cameras,
+ *   config and workspace.
+ * - Every call is asynchronous and stream-ordered on `stream` (a
+ *   cudaStream_t; NULL = legacy default stream).  No call synchronises the
+ *   host except gs_read_counters.  No call reads data-dependent sizes back to
+ *   the host, so a chain of calls can be captured in a CUDA graph.
+ * - Host-detectable argument errors return GS_ERR_ARG before anything is
+ *   enqueued.  Launch failures return GS_ERR_CUDA.  Data-dependent device
+ *   errors (more visible Gaussians or more (tile, Gaussian) pairs than the
+ *   workspace holds) set a sticky status word in the workspace; later kernels
+ *   of the chain skip their work and gs_read_counters reports it.  Nothing
+ *   traps.
+ * - Floating point is IEEE FP32.  Projection and binning use no fused
+ *   multiply-add, so tile lists are reproducible bit for bit.
+ */
+#ifndef GS_H_
+#define GS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same handle as cudaStream_t. */
+typedef struct CUstream_st *gs_stream_t;
+
+typedef enum gs_status {
+  GS_OK = 0,
+  GS_ERR_ARG = 1,         /* invalid argument (host check) */
+  GS_ERR_CAPACITY = 2,    /* workspace capacity exceeded (device status) */
+  GS_ERR_CUDA = 3,        /* CUDA launch or runtime error */
+  GS_ERR_TIMEOUT = 4,     /* a bounded device wait gave up (device status) */
+  GS_ERR_UNSUPPORTED = 5  /* configuration not compiled in */
+} gs_status;
+
+/* Gaussian map, structure of arrays (Sec. 3.1 "Gaussian Mapping" and
+ * "Sparse Semantic Representation").  n Gaussians, top-k semantics over m
+ * classes (m includes the "unknown" class).
+ *   means   [n,3]  world position (metres)
+ *   scales  [n,3]  linear axis scales (already exponentiated)
+ *   quats   [n,4]  rotation (w,x,y,z); normalised inside, need not be unit
+ *   opacity [n]    in (0,1) (already through the sigmoid)
+ *   rgb     [n,3]  view-independent colour
+ *   sem_ids [n,k]  class ids in [0,m), fixed after initialisation
+ *   sem_w   [n,k]  class probabilities (blended as given, not renormalised)
+ *   geo_unc [n]    per-Gaussian scalar uncertainty, or NULL (candidates only)
+ * Limits: 1 <= k <= 16, 1 <= m <= 1024, 0 <= n < 2^28. */
+typedef struct gs_scene {
+  int32_t n, k, m;
+  const float *means, *scales, *quats, *opacity, *rgb;
+  const int32_t *sem_ids;
+  const float *sem_w;
+  const float *geo_unc;
+} gs_scene;
+
+/* Pinhole camera, OpenCV axes (x right, y down, z forward).  w2c is the
+ * row-major 3x4 world-to-camera [R | t].  Pixel (x, y) has centre
+ * (x + 0.5, y + 0.5).  Limits: 1 <= width, height <= 16384, near > 0. */
+typedef struct gs_camera {
+  int32_t width, height;
+  float fx, fy, cx, cy;
+  float near_plane;
+  float w2c[12];
+} gs_camera;
+
+/* Launch configuration.
+ *   tile_w, tile_h       screen tile (compiled shapes: 16x16, 16x8, 8x8, 32x8)
+ *   sem_detach_geometry  1 (default in the Python layer): the semantic
+ *                        upstream gradient reaches sem_w only, never the
+ *                        geometric attributes (Sec. 3.1 "Semantic Loss",
+ *                        last paragraph; Sec. 6 "Limited Joint Optimization")
+ *   record_capacity      max visible (view, Gaussian) records in the
+ *                        workspace; <= 0 means n * n_views (never overflows)
+ *   pair_capacity        max (tile, Gaussian) pairs; <= 0 means
+ *                        8 * record_capacity */
+typedef struct gs_config {
+  int32_t tile_w, tile_h;
+  int32_t sem_detach_geometry;
+  int32_t reserved;
+  int64_t record_capacity;
+  int64_t pair_capacity;
+} gs_config;
+
+/* Counters read back by gs_read_counters. */
+typedef struct gs_counters {
+  uint32_t status;      /* bit set of gs_status codes raised on the device (1 << code) */
+  uint32_t n_records;   /* visible (view, Gaussian) records (may exceed capacity) */
+  uint32_t n_pairs;     /* (tile, Gaussian) pairs (may exceed capacity) */
+  uint32_t n_contrib;   /* (pixel, Gaussian) contributions blended by the last forward render */
+} gs_counters;
+
+/* Device pointers into a workspace (for inspection and parity tests).  Only
+ * host arithmetic: nothing is read from the GPU. */
+typedef struct gs_workspace_map {
+  void *counters;      /* gs_counters */
+  void *rec_uv;        /* float2 [record_capacity]  2D mean (pixels) */
+  void *rec_conic;     /* float4 [record_capacity]  (a, b, c, opacity) */
+  void *rec_depth;     /* float  [record_capacity]  camera-space z */
+  void *rec_rect;      /* short4 [record_capacity]  (x0, x1, y0, y1) inclusive pixels */
+  void *rec_gid;       /* int32  [record_capacity]  Gaussian index */
+  void *rec_view;      /* int32  [record_capacity]  view index */
+  void *pair_tile;     /* uint32 [pair_capacity]    sorted global tile id */
+  void *pair_rec;      /* uint32 [pair_capacity]    sorted record index */
+  void *tile_ranges;   /* uint2  [total_tiles]      [start, end) into the pair list */
+  void *tile_offset;   /* uint32 [n_views + 1]      first global tile id of each view */
+  int64_t record_capacity, pair_capacity, total_tiles;
+} gs_workspace_map;
+
+/* Workspace bytes for `n_views` cameras (1 for mapping; up to 256 for
+ * candidates).  Returns 0 on invalid arguments. */
+size_t gs_workspace_size(const gs_scene *scene, const gs_camera *cams, int n_views, const gs_config *cfg);
+
+/* Fills *map from the workspace base pointer (no device access). */
+gs_status gs_workspace_layout(const gs_scene *scene, const gs_camera *cams, int n_views, const gs_config *cfg,
+                              void *ws, gs_workspace_map *map);
+
+/* Projection (Sec. 3.1 "Gaussian Mapping": transform the Gaussians to camera
+ * space and project them to the image plane; EWA projection of 3DGS, the
+ * prior art the paper adopts).  For every (view, Gaussian) computes the
+ * camera-space mean, the 2D mean, the dilated 2D covariance (+0.3 px^2) and
+ * its inverse (the conic), the radius ceil(3 sqrt(lambda_max)) and the pixel
+ * rectangle of pixels whose centre lies within that radius per axis.  Culls
+ * z <= near, non-positive determinant and rectangles outside the image.
+ * Visible records are compacted in (view, Gaussian index) order into the
+ * workspace.  Resets the workspace status word. */
+gs_status gs_project(const gs_scene *scene, const gs_camera *cams, int n_views, const gs_config *cfg, void *ws,
+                     gs_stream_t stream);
+
+/* Binning and front-to-back sort (Sec. 3.1: "sorting them front-to-back";
+ * supplement "Sparse Rendering": per tile, batches of the frustum's
+ * Gaussians).  Emits one pair per tile of each record's tile rectangle and
+ * orders pairs by (view, tile, depth bits, Gaussian index); writes per-tile
+ * [start, end) ranges.  Requires a preceding gs_project with the same
+ * arguments. */
+gs_status gs_bin_sort(const gs_scene *scene, const gs_camera *cams, int n_views, const gs_config *cfg, void *ws,
+                      gs_stream_t stream);
+
+/* Forward render of one view (Eq. 1 with z_i in {c_i, d_i, 1}; Eq. 3 for the
+ * sparse top-k semantics; supplement "Sparse Rendering").  Per pixel, the
+ * Gaussians whose pixel rectangle holds the pixel are composited front to
+ * back with alpha = min(0.99, o exp(-0.5 d^T conic d)), skipped when
+ * alpha < 1/255, and the pixel stops before a Gaussian that would take the
+ * transmittance below 1e-4.  Outputs (caller-owned device buffers):
+ *   rgb [H,W,3], depth [H,W], sil [H,W] (= 1 - final transmittance),
+ *   sem [H,W,m] or NULL.
+ * Keeps the per-pixel final transmittance and last-contributor index in the
+ * workspace for gs_render_bwd.  Requires gs_project + gs_bin_sort with
+ * n_views = 1 and the same camera. */
+gs_status gs_render_fwd(const gs_scene *scene, const gs_camera *cam, const gs_config *cfg, void *ws, float *rgb,
+                        float *depth, float *sil, float *sem, gs_stream_t stream);
+
+/* Adjoint of gs_render_fwd and gs_project (Sec. 3.1: the rendering is
+ * differentiable and optimised end to end; Sec. 6: semantic gradients
+ * blocked from geometry).  Upstream gradients with the output shapes of
+ * gs_render_fwd (any may be NULL = zero).  Gradients are ACCUMULATED (+=)
+ * into g_means [n,3], g_scales [n,3] (w.r.t. linear scales), g_quats [n,4]
+ * (w.r.t. the unnormalised quaternion), g_opacity [n], g_rgb [n,3],
+ * g_sem_w [n,k].  The transmittance before each contributor is recovered from
+ * the stored final transmittance; no per-pixel lists are kept.  Must follow
+ * the gs_render_fwd whose outputs it differentiates, with the same workspace. */
+gs_status gs_render_bwd(const gs_scene *scene, const gs_camera *cam, const gs_config *cfg, void *ws,
+                        const float *d_rgb, const float *d_depth, const float *d_sil, const float *d_sem,
+                        float *g_means, float *g_scales, float *g_quats, float *g_opacity, float *g_rgb,
+                        float *g_sem_w, gs_stream_t stream);
+
+/* Forward render of one view fused with the mean-L1 mapping loss (Sec. 3.1:
+ * Eq. 1 / Eq. 3 rendering, the L1 colour and depth terms of Eq. 2 without the
+ * silhouette mask, plus an L1 term on the semantic distribution):
+ *   *loss = mean|rgb - t_rgb| + mean|depth - t_depth| + mean|sem - t_sem|
+ * with the targets in the output layouts of gs_render_fwd (t_sem may be NULL
+ * to drop the semantic term).  The comparison happens inside the tile kernel:
+ * the semantic map need not be written (rgb, depth, sil, sem outputs are
+ * optional, NULL to skip).  Per rendered value the workspace keeps two bits
+ * (nonzero, negative) of the sign of (rendered - target) for
+ * gs_render_bwd_l1, so the per-pixel gradient maps are never materialised.
+ * *loss is a device float.  Same preconditions as gs_render_fwd. */
+gs_status gs_render_fwd_l1(const gs_scene *scene, const gs_camera *cam, const gs_config *cfg, void *ws,
+                           const float *t_rgb, const float *t_depth, const float *t_sem, float *rgb, float *depth,
+                           float *sil, float *sem, float *loss, gs_stream_t stream);
+
+/* Adjoint of gs_render_fwd_l1: accumulates (+=) the gradients of
+ * (*loss_scale) * loss into g_* exactly as gs_render_bwd would for upstream
+ * gradients sign(x - t) / count.  loss_scale is a DEVICE float (dL/dloss,
+ * e.g. the autograd grad_output), read on the stream, so no host
+ * synchronisation is needed.  Must follow the gs_render_fwd_l1 it
+ * differentiates, with the same workspace. */
+gs_status gs_render_bwd_l1(const gs_scene *scene, const gs_camera *cam, const gs_config *cfg, void *ws,
+                           const float *loss_scale, float *g_means, float *g_scales, float *g_quats,
+                           float *g_opacity, float *g_rgb, float *g_sem_w, gs_stream_t stream);
+
+/* Batched candidate-view rendering for next-best-view scoring (Sec. 3.2:
+ * geometric criterion Eq. 6 from the rendered silhouette, semantic criterion
+ * Eq. 7 from the entropy Eq. 4 of the rendered semantic map clipped to
+ * [0.001, 1] and renormalised).  Runs projection and binning for all views
+ * and one blend launch over every (view, tile); per-pixel maps are never
+ * written.  out is a caller-owned device array double[n_views][3]:
+ *   out[v][0] = sum_p U(p), U composited by Eq. 1 with z_i = geo_unc[i]
+ *               (0 if geo_unc is NULL),
+ *   out[v][1] = sum_p H(p) (natural log),
+ *   out[v][2] = N_S = number of pixels with S(p) = 0.
+ * The softmax normalisations of Eq. 6-8 over candidates are left to the
+ * caller.  1 <= n_views <= 256. */
+gs_status gs_render_candidates(const gs_scene *scene, const gs_camera *views, int n_views, const gs_config *cfg,
+                               void *ws, double *out, gs_stream_t stream);
+
+/* Mean-L1 mapping loss and its gradient (the per-pixel photometric/depth
+ * L1 terms of Sec. 3.1 Eq. 2, without the silhouette mask, plus an L1 term on
+ * the semantic map): loss = mean|rgb - t_rgb| + mean|depth - t_depth| +
+ * mean|sem - t_sem| over npix pixels (sem terms skipped when sem is NULL).
+ * Writes d_* = sign(x - t) / count (0 where equal) and *loss (device float).
+ * partial is caller scratch of at least 2048 doubles. */
+gs_status gs_l1_loss(int64_t npix, int m, const float *rgb, const float *t_rgb, const float *depth,
+                     const float *t_depth, const float *sem, const float *t_sem, float *d_rgb, float *d_depth,
+                     float *d_sem, float *loss, double *partial, gs_stream_t stream);
+
+/* Synchronises `stream`, then copies the workspace counters to *out (host).
+ * Returns the first device error recorded (GS_ERR_CAPACITY, GS_ERR_TIMEOUT)
+ * or GS_OK. */
+gs_status gs_read_counters(void *ws, gs_counters *out, gs_stream_t stream);
+
+/* Static description of a status code. */
+const char *gs_status_string(gs_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H_ */

@@ -127,7 +127,7 @@ def tile_lists(projs, cams, tile=(16, 16)):
     return np.stack([start, end], axis=1).astype(np.int64), gids.astype(np.int64), np.asarray(offs, np.int64)
 
 
-def render(scene, cam, prec="f32", sem=True, unc=False) -> dict:
+def render(scene, cam, prec="f32", sem=True, unc=False, rows=None) -> dict:
     """Full-image brute-force forward render (Eq. 1 for colour / depth /
     silhouette, Eq. 3 for the sparse semantic map; optional uncertainty
     channel composited as Eq. 1).  Also returns T_final, contributor counts,
@@ -152,7 +152,7 @@ def render(scene, cam, prec="f32", sem=True, unc=False) -> dict:
        _ptr(a["opacity"]), _ptr(a["rgb"]), _ptr(a["sem_ids"]), _ptr(a["sem_w"]),
        _ptr(a["unc"]) if out["unc"] is not None else None, _ptr(cam_array(cam, prec)), _I(W), _I(H),
        _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["sil"]), _ptr(out["unc"]), _ptr(out["sem"]),
-       _ptr(out["T"]), _ptr(out["n_contrib"]), _ptr(out["flag"]), _ptr(stats))
+       _ptr(out["T"]), _ptr(out["n_contrib"]), _ptr(out["flag"]), _ptr(stats), *_rows(rows, H))
     out["n_eval"], out["n_contrib_total"] = int(stats[0]), int(stats[1])
     return out
 
@@ -180,8 +180,16 @@ def render_pixels(scene, cam, xs, ys, prec="f32", sem=True) -> dict:
     return out
 
 
+def _rows(rows, H):
+    """(y_begin, y_end, y_step) of a row sample; None = every row."""
+    if rows is None:
+        return _I(0), _I(H), _I(1)
+    b, e, s = rows
+    return _I(b), _I(e), _I(s)
+
+
 def render_bwd(scene, cam, d_rgb=None, d_depth=None, d_sil=None, d_sem=None, sem_detach=True,
-               prec="f64") -> dict:
+               prec="f64", rows=None) -> dict:
     """Hand-derived adjoint of render(): gradients of sum(d_out * out) w.r.t.
     means, scales, quats, opacity, rgb and sem_w.  With sem_detach the
     semantic upstream gradient reaches sem_w only (Sec. 3.1, semantic loss
@@ -203,7 +211,7 @@ def render_bwd(scene, cam, d_rgb=None, d_depth=None, d_sil=None, d_sem=None, sem
        _ptr(a["rgb"]), _ptr(a["sem_ids"]), _ptr(a["sem_w"]), _ptr(cam_array(cam, prec)), _I(cam.width),
        _I(cam.height), _ptr(ups[0]), _ptr(ups[1]), _ptr(ups[2]), _ptr(ups[3]), _I(1 if sem_detach else 0),
        _ptr(g["means"]), _ptr(g["scales"]), _ptr(g["quats"]), _ptr(g["opacity"]), _ptr(g["rgb"]),
-       _ptr(g["sem_w"]))
+       _ptr(g["sem_w"]), *_rows(rows, cam.height))
     return g
 
 

@@ -323,7 +323,8 @@ static void composite_pixel(const scene_t *sc, const view_t *vw, int x, int y, r
 #define SCENE_FROM_ARGS                                                           \
   scene_t sc = {n, k, m, means, scales, quats, opacity, rgb, sem_w, unc, sem_ids};
 
-/* Full-image forward render.  Outputs: rgb[H,W,3], depth[H,W], sil[H,W]
+/* Forward render of rows y_begin, y_begin + y_step, ... < y_end (the full
+ * image for 0, H, 1).  Outputs: rgb[H,W,3], depth[H,W], sil[H,W]
  * (= 1 - T_final), unc_img[H,W] (if unc given and unc_img non-NULL),
  * sem[H,W,m] (if non-NULL), T_final[H,W], n_contrib[H,W], flag[H,W].
  * stats[2] = {N_eval, N_contrib} summed over pixels. */
@@ -331,13 +332,15 @@ void SFX(orc_render)(int n, int k, int m, const real *means, const real *scales,
                      const real *opacity, const real *rgb, const int *sem_ids, const real *sem_w,
                      const real *unc, const real *cam, int W, int H,
                      real *out_rgb, real *out_depth, real *out_sil, real *out_unc, real *out_sem,
-                     real *out_T, int *out_nc, int *out_flag, long *stats) {
+                     real *out_T, int *out_nc, int *out_flag, long *stats, int y_begin, int y_end, int y_step) {
   SCENE_FROM_ARGS
   view_t vw;
   view_build(&sc, cam, W, H, &vw);
   long ne = 0, ncs = 0;
+  if (y_step < 1) y_step = 1;
+  if (y_end > H || y_end < 0) y_end = H;
 #pragma omp parallel for schedule(dynamic, 1) reduction(+ : ne, ncs)
-  for (int y = 0; y < H; ++y) {
+  for (int y = y_begin; y < y_end; y += y_step) {
     for (int x = 0; x < W; ++x) {
       size_t pid = (size_t)y * W + x;
       real *sem = out_sem ? out_sem + pid * m : NULL;
@@ -472,7 +475,8 @@ static void project_adjoint(const proj_t *p, const real *s, const real *cam, rea
   gm[2] += V[2] * dtx + V[6] * dty + V[10] * dtz;
 }
 
-/* Backward of the full-image render.  Upstream gradients (any may be NULL):
+/* Backward of the render over rows y_begin, y_begin + y_step, ... < y_end
+ * (the full image for 0, H, 1).  Upstream gradients (any may be NULL):
  * d_rgb[H,W,3], d_depth[H,W], d_sil[H,W], d_sem[H,W,m].  Gradients are
  * ACCUMULATED into g_means[n,3], g_scales[n,3], g_quats[n,4], g_opacity[n],
  * g_rgb[n,3], g_sem_w[n,k].  When sem_detach != 0 the semantic upstream
@@ -482,7 +486,8 @@ void SFX(orc_render_bwd)(int n, int k, int m, const real *means, const real *sca
                          const real *opacity, const real *rgb, const int *sem_ids, const real *sem_w,
                          const real *cam, int W, int H, const real *d_rgb, const real *d_depth,
                          const real *d_sil, const real *d_sem, int sem_detach, real *g_means,
-                         real *g_scales, real *g_quats, real *g_opacity, real *g_rgb, real *g_sem_w) {
+                         real *g_scales, real *g_quats, real *g_opacity, real *g_rgb, real *g_sem_w,
+                         int y_begin, int y_end, int y_step) {
   const real *unc = NULL;
   SCENE_FROM_ARGS
   view_t vw;
@@ -491,7 +496,9 @@ void SFX(orc_render_bwd)(int n, int k, int m, const real *means, const real *sca
   real *g2 = (real *)calloc((size_t)(n > 0 ? n : 1) * 6, sizeof(real)); /* du dv dca dcb dcc dz */
   int cap = vw.nv > 0 ? vw.nv : 1;
   contrib_t *list = (contrib_t *)malloc(sizeof(contrib_t) * (size_t)cap);
-  for (int y = 0; y < H; ++y)
+  if (y_step < 1) y_step = 1;
+  if (y_end > H || y_end < 0) y_end = H;
+  for (int y = y_begin; y < y_end; y += y_step)
     for (int x = 0; x < W; ++x) {
       size_t pid = (size_t)y * W + x;
       pix_t o;

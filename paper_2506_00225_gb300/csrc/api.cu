@@ -1,0 +1,351 @@
+// api.cu -- the extern "C" entry points declared in include/gs.h: argument
+// validation, workspace layout and the launch chains.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "gs_internal.cuh"
+#include "render_common.cuh"
+
+namespace gs {
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+static int bits_for(uint64_t max_value) {
+  int b = 1;
+  while (b < 64 && (max_value >> b) != 0) ++b;
+  return b;
+}
+
+static bool cam_ok(const gs_camera &c) {
+  if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384) return false;
+  if (!(c.fx > 0.f) || !(c.fy > 0.f) || !isfinite(c.fx) || !isfinite(c.fy)) return false;
+  if (!isfinite(c.cx) || !isfinite(c.cy)) return false;
+  if (!(c.near_plane > 0.f) || !isfinite(c.near_plane)) return false;
+  for (int i = 0; i < 12; ++i)
+    if (!isfinite(c.w2c[i])) return false;
+  return true;
+}
+
+static gs_config default_config() {
+  gs_config c{};
+  c.tile_w = 16;
+  c.tile_h = 16;
+  c.sem_detach_geometry = 1;
+  return c;
+}
+
+bool make_layout(const gs_scene *scene, const gs_camera *cams, int n_views, const gs_config *cfg_in, Layout *L) {
+  if (!scene || !cams || n_views < 1 || n_views > kMaxViews) return false;
+  const gs_config cfg = cfg_in ? *cfg_in : default_config();
+  if (scene->n < 0 || scene->n >= (1 << 28) || scene->k < 1 || scene->k > kMaxK || scene->m < 1 ||
+      scene->m > kMaxM)
+    return false;
+  if (cfg.tile_w < 1 || cfg.tile_h < 1 || cfg.tile_w > 64 || cfg.tile_h > 64) return false;
+  memset(L, 0, sizeof(*L));
+  L->n = scene->n; L->k = scene->k; L->m = scene->m; L->n_views = n_views;
+  L->tile_w = cfg.tile_w; L->tile_h = cfg.tile_h;
+  uint64_t tiles = 0;
+  for (int v = 0; v < n_views; ++v) {
+    if (!cam_ok(cams[v])) return false;
+    const uint64_t gx = (uint64_t)(cams[v].width + cfg.tile_w - 1) / cfg.tile_w;
+    const uint64_t gy = (uint64_t)(cams[v].height + cfg.tile_h - 1) / cfg.tile_h;
+    tiles += gx * gy;
+  }
+  if (tiles >= (1ull << 31)) return false;
+  L->total_tiles = (int64_t)tiles;
+  L->cam0_w = cams[0].width;
+  L->cam0_h = cams[0].height;
+  L->npix = n_views == 1 ? (int64_t)cams[0].width * cams[0].height : 0;
+  const int64_t max_cap = (1ll << 31) - 1;
+  int64_t rcap = cfg.record_capacity > 0 ? cfg.record_capacity : (int64_t)scene->n * n_views;
+  if (rcap > max_cap) rcap = max_cap;
+  int64_t pcap = cfg.pair_capacity > 0 ? cfg.pair_capacity : 8 * rcap;
+  if (pcap > max_cap) pcap = max_cap;
+  L->rcap = rcap;
+  L->pcap = pcap;
+  L->proj_blocks = ((int64_t)scene->n + kProjBlock - 1) / kProjBlock;
+  L->key_bits_depth = 31 + (n_views > 1 ? bits_for((uint64_t)(n_views - 1)) : 0);
+  L->key_bits_tile = bits_for(tiles > 0 ? tiles - 1 : 0);
+  const size_t A = 256;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, A); return o; };
+  L->off_counters = take(sizeof(Counters));
+  L->off_cams = take(sizeof(DevCam) * n_views);
+  L->off_tile_off = take(sizeof(uint32_t) * (n_views + 1));
+  L->off_blockcnt = take(sizeof(uint32_t) * (size_t)(L->proj_blocks * n_views + 1));
+  L->off_rec_uv = take(8 * (size_t)rcap);
+  L->off_rec_conic = take(16 * (size_t)rcap);
+  L->off_rec_depth = take(4 * (size_t)rcap);
+  L->off_rec_rect = take(8 * (size_t)rcap);
+  L->off_rec_gid = take(4 * (size_t)rcap);
+  L->off_rec_view = take(4 * (size_t)rcap);
+  for (int i = 0; i < 2; ++i) L->off_dkeys[i] = take(8 * (size_t)rcap);
+  for (int i = 0; i < 2; ++i) L->off_dvals[i] = take(4 * (size_t)rcap);
+  L->off_epart = take(sizeof(uint32_t) * (kEmitCtas + 1));
+  for (int i = 0; i < 2; ++i) L->off_pkeys[i] = take(4 * (size_t)pcap);
+  for (int i = 0; i < 2; ++i) L->off_pvals[i] = take(4 * (size_t)pcap);
+  L->off_hist = take(sizeof(uint32_t) * (size_t)kRadix * kSortCtas);
+  L->off_ranges = take(8 * (size_t)(tiles > 0 ? tiles : 1));
+  L->off_tfinal = take(4 * (size_t)(L->npix > 0 ? L->npix : 1));
+  L->off_nlast = take(4 * (size_t)(L->npix > 0 ? L->npix : 1));
+  L->off_grad2d = take(n_views == 1 ? 32 * (size_t)rcap : 32);
+  L->nwc = (scene->m + 31) / 32;
+  L->off_codes = take(n_views == 1 ? 4 * (size_t)L->npix * (2 * (1 + L->nwc)) : 32);
+  L->off_lpart = take(n_views == 1 ? 3 * sizeof(double) * (size_t)(tiles > 0 ? tiles : 1) : 32);
+  L->total = off;
+  return true;
+}
+
+WsPtrs ws_ptrs(const Layout &L, void *ws) {
+  char *b = static_cast<char *>(ws);
+  WsPtrs P;
+  P.counters = reinterpret_cast<Counters *>(b + L.off_counters);
+  P.cams = reinterpret_cast<DevCam *>(b + L.off_cams);
+  P.tile_off = reinterpret_cast<uint32_t *>(b + L.off_tile_off);
+  P.blockcnt = reinterpret_cast<uint32_t *>(b + L.off_blockcnt);
+  P.rec_uv = reinterpret_cast<float2 *>(b + L.off_rec_uv);
+  P.rec_conic = reinterpret_cast<float4 *>(b + L.off_rec_conic);
+  P.rec_depth = reinterpret_cast<float *>(b + L.off_rec_depth);
+  P.rec_rect = reinterpret_cast<short4 *>(b + L.off_rec_rect);
+  P.rec_gid = reinterpret_cast<int32_t *>(b + L.off_rec_gid);
+  P.rec_view = reinterpret_cast<int32_t *>(b + L.off_rec_view);
+  for (int i = 0; i < 2; ++i) {
+    P.dkeys[i] = reinterpret_cast<unsigned long long *>(b + L.off_dkeys[i]);
+    P.dvals[i] = reinterpret_cast<uint32_t *>(b + L.off_dvals[i]);
+    P.pkeys[i] = reinterpret_cast<uint32_t *>(b + L.off_pkeys[i]);
+    P.pvals[i] = reinterpret_cast<uint32_t *>(b + L.off_pvals[i]);
+  }
+  P.epart = reinterpret_cast<uint32_t *>(b + L.off_epart);
+  P.hist = reinterpret_cast<uint32_t *>(b + L.off_hist);
+  P.ranges = reinterpret_cast<uint2 *>(b + L.off_ranges);
+  P.tfinal = reinterpret_cast<float *>(b + L.off_tfinal);
+  P.nlast = reinterpret_cast<uint32_t *>(b + L.off_nlast);
+  P.grad2d = reinterpret_cast<float4 *>(b + L.off_grad2d);
+  P.codes = reinterpret_cast<uint32_t *>(b + L.off_codes);
+  P.lpart = reinterpret_cast<double *>(b + L.off_lpart);
+  return P;
+}
+
+static void fill_cam_table(const gs_camera *cams, int n_views, int tw, int th, CamTable *tab) {
+  uint32_t off = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const gs_camera &c = cams[v];
+    DevCam &d = tab->cam[v];
+    d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy; d.near_plane = c.near_plane;
+    d.r[0] = c.w2c[0]; d.r[1] = c.w2c[1]; d.r[2] = c.w2c[2];
+    d.r[3] = c.w2c[4]; d.r[4] = c.w2c[5]; d.r[5] = c.w2c[6];
+    d.r[6] = c.w2c[8]; d.r[7] = c.w2c[9]; d.r[8] = c.w2c[10];
+    d.t[0] = c.w2c[3]; d.t[1] = c.w2c[7]; d.t[2] = c.w2c[11];
+    d.width = c.width; d.height = c.height;
+    d.tiles_x = (c.width + tw - 1) / tw;
+    d.tiles_y = (c.height + th - 1) / th;
+    d.tile_off = off;
+    off += (uint32_t)(d.tiles_x * d.tiles_y);
+  }
+}
+
+static bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+static bool scene_ptrs_ok(const gs_scene *s, bool need_sem) {
+  if (s->n == 0) return true;
+  if (!s->means || !s->scales || !s->quats || !s->opacity) return false;
+  if (!aligned(s->quats, 16)) return false;
+  if (need_sem && (!s->sem_ids || !s->sem_w)) return false;
+  return true;
+}
+
+static bool shape_compiled(int tw, int th) {
+  return (tw == 16 && th == 16) || (tw == 16 && th == 8) || (tw == 8 && th == 8) || (tw == 32 && th == 8);
+}
+
+#define GS_CHECK_CUDA(expr)                      \
+  do {                                           \
+    cudaError_t _e = (expr);                     \
+    if (_e != cudaSuccess) return GS_ERR_CUDA;   \
+  } while (0)
+
+static gs_status run_project(const Layout &L, const WsPtrs &P, const gs_scene &sc, const gs_camera *cams,
+                             cudaStream_t s) {
+  std::vector<unsigned char> buf(sizeof(CamTable));
+  CamTable *tab = reinterpret_cast<CamTable *>(buf.data());
+  memset(tab, 0, sizeof(CamTable));
+  fill_cam_table(cams, L.n_views, L.tile_w, L.tile_h, tab);
+  GS_CHECK_CUDA(launch_setup_views(*tab, L.n_views, P, (uint32_t)L.total_tiles, true, s));
+  GS_CHECK_CUDA(launch_project(L, P, sc, s));
+  return GS_OK;
+}
+
+static gs_status run_bin_sort(const Layout &L, const WsPtrs &P, cudaStream_t s) {
+  int dbuf = 0, pbuf = 0;
+  GS_CHECK_CUDA(launch_radix_sort_u64(L, P, L.key_bits_depth, &dbuf, s));
+  GS_CHECK_CUDA(launch_emit_pairs(L, P, dbuf, s));
+  GS_CHECK_CUDA(launch_radix_sort_u32(L, P, L.key_bits_tile, &pbuf, s));
+  GS_CHECK_CUDA(launch_tile_ranges(L, P, pbuf, s));
+  return GS_OK;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" {
+
+size_t gs_workspace_size(const gs_scene *scene, const gs_camera *cams, int n_views, const gs_config *cfg) {
+  Layout L;
+  if (!make_layout(scene, cams, n_views, cfg, &L)) return 0;
+  return L.total;
+}
+
+gs_status gs_workspace_layout(const gs_scene *scene, const gs_camera *cams, int n_views, const gs_config *cfg,
+                              void *ws, gs_workspace_map *map) {
+  Layout L;
+  if (!map || !ws || !make_layout(scene, cams, n_views, cfg, &L)) return GS_ERR_ARG;
+  WsPtrs P = ws_ptrs(L, ws);
+  map->counters = P.counters;
+  map->rec_uv = P.rec_uv;
+  map->rec_conic = P.rec_conic;
+  map->rec_depth = P.rec_depth;
+  map->rec_rect = P.rec_rect;
+  map->rec_gid = P.rec_gid;
+  map->rec_view = P.rec_view;
+  map->pair_tile = P.pkeys[pair_sort_buffer(L)];
+  map->pair_rec = P.pvals[pair_sort_buffer(L)];
+  map->tile_ranges = P.ranges;
+  map->tile_offset = P.tile_off;
+  map->record_capacity = L.rcap;
+  map->pair_capacity = L.pcap;
+  map->total_tiles = L.total_tiles;
+  return GS_OK;
+}
+
+gs_status gs_project(const gs_scene *scene, const gs_camera *cams, int n_views, const gs_config *cfg, void *ws,
+                     gs_stream_t stream) {
+  Layout L;
+  if (!ws || !aligned(ws, 256) || !make_layout(scene, cams, n_views, cfg, &L)) return GS_ERR_ARG;
+  if (!scene_ptrs_ok(scene, false)) return GS_ERR_ARG;
+  return run_project(L, ws_ptrs(L, ws), *scene, cams, (cudaStream_t)stream);
+}
+
+gs_status gs_bin_sort(const gs_scene *scene, const gs_camera *cams, int n_views, const gs_config *cfg, void *ws,
+                      gs_stream_t stream) {
+  Layout L;
+  if (!ws || !aligned(ws, 256) || !make_layout(scene, cams, n_views, cfg, &L)) return GS_ERR_ARG;
+  return run_bin_sort(L, ws_ptrs(L, ws), (cudaStream_t)stream);
+}
+
+gs_status gs_render_fwd(const gs_scene *scene, const gs_camera *cam, const gs_config *cfg, void *ws, float *rgb,
+                        float *depth, float *sil, float *sem, gs_stream_t stream) {
+  Layout L;
+  if (!ws || !aligned(ws, 256) || !make_layout(scene, cam, 1, cfg, &L)) return GS_ERR_ARG;
+  if (!scene_ptrs_ok(scene, true) || (scene->n > 0 && !scene->rgb)) return GS_ERR_ARG;
+  if (!shape_compiled(L.tile_w, L.tile_h)) return GS_ERR_UNSUPPORTED;
+  WsPtrs P = ws_ptrs(L, ws);
+  GS_CHECK_CUDA(launch_render_fwd(L, P, pair_sort_buffer(L), *scene, rgb, depth, sil, sem, (cudaStream_t)stream));
+  return GS_OK;
+}
+
+gs_status gs_render_bwd(const gs_scene *scene, const gs_camera *cam, const gs_config *cfg, void *ws,
+                        const float *d_rgb, const float *d_depth, const float *d_sil, const float *d_sem,
+                        float *g_means, float *g_scales, float *g_quats, float *g_opacity, float *g_rgb,
+                        float *g_sem_w, gs_stream_t stream) {
+  Layout L;
+  if (!ws || !aligned(ws, 256) || !make_layout(scene, cam, 1, cfg, &L)) return GS_ERR_ARG;
+  if (!scene_ptrs_ok(scene, true) || (scene->n > 0 && !scene->rgb)) return GS_ERR_ARG;
+  if (scene->n > 0 && (!g_means || !g_scales || !g_quats || !g_opacity || !g_rgb || !g_sem_w)) return GS_ERR_ARG;
+  if (!shape_compiled(L.tile_w, L.tile_h)) return GS_ERR_UNSUPPORTED;
+  const gs_config c = cfg ? *cfg : default_config();
+  WsPtrs P = ws_ptrs(L, ws);
+  cudaStream_t s = (cudaStream_t)stream;
+  GS_CHECK_CUDA(launch_render_bwd(L, P, pair_sort_buffer(L), *scene, d_rgb, d_depth, d_sil, d_sem,
+                                  c.sem_detach_geometry ? 1 : 0, g_rgb, g_sem_w, s));
+  GS_CHECK_CUDA(launch_project_bwd(L, P, *scene, g_means, g_scales, g_quats, g_opacity, s));
+  return GS_OK;
+}
+
+gs_status gs_render_fwd_l1(const gs_scene *scene, const gs_camera *cam, const gs_config *cfg, void *ws,
+                           const float *t_rgb, const float *t_depth, const float *t_sem, float *rgb, float *depth,
+                           float *sil, float *sem, float *loss, gs_stream_t stream) {
+  Layout L;
+  if (!ws || !aligned(ws, 256) || !make_layout(scene, cam, 1, cfg, &L)) return GS_ERR_ARG;
+  if (!scene_ptrs_ok(scene, true) || (scene->n > 0 && !scene->rgb)) return GS_ERR_ARG;
+  if (!t_rgb || !t_depth || !loss) return GS_ERR_ARG;
+  if (!shape_compiled(L.tile_w, L.tile_h)) return GS_ERR_UNSUPPORTED;
+  WsPtrs P = ws_ptrs(L, ws);
+  GS_CHECK_CUDA(launch_render_fwd_l1(L, P, pair_sort_buffer(L), *scene, t_rgb, t_depth, t_sem, rgb, depth, sil, sem,
+                                     loss, (cudaStream_t)stream));
+  return GS_OK;
+}
+
+gs_status gs_render_bwd_l1(const gs_scene *scene, const gs_camera *cam, const gs_config *cfg, void *ws,
+                           const float *loss_scale, float *g_means, float *g_scales, float *g_quats,
+                           float *g_opacity, float *g_rgb, float *g_sem_w, gs_stream_t stream) {
+  Layout L;
+  if (!ws || !aligned(ws, 256) || !make_layout(scene, cam, 1, cfg, &L)) return GS_ERR_ARG;
+  if (!scene_ptrs_ok(scene, true) || (scene->n > 0 && !scene->rgb) || !loss_scale) return GS_ERR_ARG;
+  if (scene->n > 0 && (!g_means || !g_scales || !g_quats || !g_opacity || !g_rgb || !g_sem_w)) return GS_ERR_ARG;
+  if (!shape_compiled(L.tile_w, L.tile_h)) return GS_ERR_UNSUPPORTED;
+  const gs_config c = cfg ? *cfg : default_config();
+  WsPtrs P = ws_ptrs(L, ws);
+  cudaStream_t s = (cudaStream_t)stream;
+  GS_CHECK_CUDA(launch_render_bwd(L, P, pair_sort_buffer(L), *scene, nullptr, nullptr, nullptr, nullptr,
+                                  c.sem_detach_geometry ? 1 : 0, g_rgb, g_sem_w, s, loss_scale));
+  GS_CHECK_CUDA(launch_project_bwd(L, P, *scene, g_means, g_scales, g_quats, g_opacity, s));
+  return GS_OK;
+}
+
+gs_status gs_render_candidates(const gs_scene *scene, const gs_camera *views, int n_views, const gs_config *cfg,
+                               void *ws, double *out, gs_stream_t stream) {
+  Layout L;
+  if (!ws || !aligned(ws, 256) || !out || !make_layout(scene, views, n_views, cfg, &L)) return GS_ERR_ARG;
+  if (!scene_ptrs_ok(scene, true)) return GS_ERR_ARG;
+  if (!shape_compiled(L.tile_w, L.tile_h)) return GS_ERR_UNSUPPORTED;
+  WsPtrs P = ws_ptrs(L, ws);
+  cudaStream_t s = (cudaStream_t)stream;
+  gs_status st = run_project(L, P, *scene, views, s);
+  if (st != GS_OK) return st;
+  st = run_bin_sort(L, P, s);
+  if (st != GS_OK) return st;
+  GS_CHECK_CUDA(launch_candidates(L, P, pair_sort_buffer(L), *scene, out, s));
+  return GS_OK;
+}
+
+gs_status gs_l1_loss(int64_t npix, int m, const float *rgb, const float *t_rgb, const float *depth,
+                     const float *t_depth, const float *sem, const float *t_sem, float *d_rgb, float *d_depth,
+                     float *d_sem, float *loss, double *partial, gs_stream_t stream) {
+  if (npix < 1 || !loss || !partial) return GS_ERR_ARG;
+  if ((rgb && !t_rgb) || (depth && !t_depth) || (sem && (!t_sem || m < 1))) return GS_ERR_ARG;
+  if (sem && (!aligned(sem, 16) || !aligned(t_sem, 16) || (d_sem && !aligned(d_sem, 16)))) return GS_ERR_ARG;
+  GS_CHECK_CUDA(launch_l1_loss(npix, m, rgb, t_rgb, depth, t_depth, sem, t_sem, d_rgb, d_depth, d_sem, loss, partial,
+                               (cudaStream_t)stream));
+  return GS_OK;
+}
+
+gs_status gs_read_counters(void *ws, gs_counters *out, gs_stream_t stream) {
+  if (!ws || !out) return GS_ERR_ARG;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return GS_ERR_CUDA;
+  Counters c;
+  if (cudaMemcpy(&c, ws, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return GS_ERR_CUDA;
+  out->status = c.status;
+  out->n_records = c.n_records;
+  out->n_pairs = c.n_pairs;
+  out->n_contrib = c.n_contrib;
+  if (c.status & kStatusCapacity) return GS_ERR_CAPACITY;
+  if (c.status & kStatusTimeout) return GS_ERR_TIMEOUT;
+  return GS_OK;
+}
+
+const char *gs_status_string(gs_status s) {
+  switch (s) {
+    case GS_OK: return "ok";
+    case GS_ERR_ARG: return "invalid argument";
+    case GS_ERR_CAPACITY: return "workspace capacity exceeded (records or pairs)";
+    case GS_ERR_CUDA: return "CUDA error";
+    case GS_ERR_TIMEOUT: return "bounded device wait timed out";
+    case GS_ERR_UNSUPPORTED: return "configuration not compiled in";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

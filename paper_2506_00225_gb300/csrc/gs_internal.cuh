@@ -1,0 +1,192 @@
+// gs_internal.cuh -- workspace layout, device camera table and small device
+// helpers shared by the kernels of the rasterizer library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gs.h"
+
+namespace gs {
+
+constexpr int kMaxViews = 256;
+constexpr int kMaxK = 16;
+constexpr int kMaxM = 1024;
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kSortCtas = 4 * 152;        // fixed grid of the radix-sort kernels
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;             // keys per thread per tile
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kProjThreads = 256;
+constexpr int kProjItems = 4;
+constexpr int kProjBlock = kProjThreads * kProjItems;  // Gaussians per projection CTA
+constexpr int kEmitCtas = 2 * 152;
+constexpr int kEmitThreads = 256;
+
+// Status bits in the workspace counters (1 << gs_status code).
+constexpr uint32_t kStatusCapacity = 1u << GS_ERR_CAPACITY;
+constexpr uint32_t kStatusTimeout = 1u << GS_ERR_TIMEOUT;
+
+// Per-view camera as the kernels read it (written once per call into the
+// workspace by k_setup_views).
+struct DevCam {
+  float fx, fy, cx, cy, near_plane;
+  float r[9];
+  float t[3];
+  int width, height;
+  int tiles_x, tiles_y;
+  uint32_t tile_off;   // first global tile id of this view
+};
+
+// Kernel-parameter carrier for up to kMaxViews cameras (kernel parameters up
+// to 32 KB are legal on sm_70+ with CUDA 12.1+; 256 * 84 B fits).
+struct CamTable {
+  DevCam cam[kMaxViews];
+};
+
+struct Counters {
+  uint32_t status;
+  uint32_t n_records;
+  uint32_t n_pairs;
+  uint32_t n_contrib;  // (pixel, Gaussian) contributions of the last forward render
+};
+
+// Host-computed workspace layout (offsets in bytes from the base pointer).
+struct Layout {
+  int n, k, m, n_views, tile_w, tile_h;
+  int cam0_w, cam0_h;                      // first camera (the single view of mapping calls)
+  int64_t rcap, pcap, total_tiles, npix;  // npix: pixels of view 0 when n_views == 1
+  int64_t proj_blocks;                     // projection CTAs per view
+  int key_bits_depth;                      // bits of the (view, depth) record key
+  int key_bits_tile;                       // bits of the global tile id
+  size_t off_counters, off_cams, off_tile_off, off_blockcnt;
+  size_t off_rec_uv, off_rec_conic, off_rec_depth, off_rec_rect, off_rec_gid, off_rec_view;
+  size_t off_dkeys[2], off_dvals[2];
+  size_t off_epart;
+  size_t off_pkeys[2], off_pvals[2];
+  size_t off_hist;
+  size_t off_ranges;
+  size_t off_tfinal, off_nlast;
+  size_t off_grad2d;
+  int nwc;                                 // 32-class sign words per plane (fused L1 mode)
+  size_t off_codes, off_lpart;
+  size_t total;
+};
+
+struct WsPtrs {
+  Counters *counters;
+  DevCam *cams;
+  uint32_t *tile_off;
+  uint32_t *blockcnt;
+  float2 *rec_uv;
+  float4 *rec_conic;
+  float *rec_depth;
+  short4 *rec_rect;
+  int32_t *rec_gid;
+  int32_t *rec_view;
+  unsigned long long *dkeys[2];
+  uint32_t *dvals[2];
+  uint32_t *epart;
+  uint32_t *pkeys[2];
+  uint32_t *pvals[2];
+  uint32_t *hist;
+  uint2 *ranges;
+  float *tfinal;
+  uint32_t *nlast;
+  float4 *grad2d;  // [rcap][2]: (du, dv, da, db), (dc, dopacity, dz, 0)
+  uint32_t *codes; // [npix][2 * (1 + nwc)] sign codes of the fused L1 mode
+  double *lpart;   // [tiles of view 0][3] per-tile L1 sums
+};
+
+// Host side (api.cu).
+bool make_layout(const gs_scene *scene, const gs_camera *cams, int n_views, const gs_config *cfg, Layout *L);
+WsPtrs ws_ptrs(const Layout &L, void *ws);
+
+// Number of radix passes over `bits` key bits.
+inline int radix_passes(int bits) { return (bits + kRadixBits - 1) / kRadixBits; }
+
+// ---------------------------------------------------------------------------
+// Launchers implemented in the kernel translation units.
+// ---------------------------------------------------------------------------
+cudaError_t launch_setup_views(const CamTable &tab, int n_views, const WsPtrs &P, uint32_t total_tiles,
+                               bool reset_status, cudaStream_t s);
+cudaError_t launch_project(const Layout &L, const WsPtrs &P, const gs_scene &sc, cudaStream_t s);
+cudaError_t launch_scan_single(uint32_t *data, uint32_t n, uint32_t *total_out, uint32_t capacity,
+                               Counters *counters, cudaStream_t s);
+cudaError_t launch_radix_sort_u64(const Layout &L, const WsPtrs &P, int bits, int *final_buf, cudaStream_t s);
+cudaError_t launch_radix_sort_u32(const Layout &L, const WsPtrs &P, int bits, int *final_buf, cudaStream_t s);
+cudaError_t launch_emit_pairs(const Layout &L, const WsPtrs &P, int dbuf, cudaStream_t s);
+cudaError_t launch_tile_ranges(const Layout &L, const WsPtrs &P, int pbuf, cudaStream_t s);
+cudaError_t launch_render_fwd(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc, float *rgb,
+                              float *depth, float *sil, float *sem, cudaStream_t s);
+cudaError_t launch_render_fwd_l1(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc,
+                                 const float *t_rgb, const float *t_depth, const float *t_sem, float *rgb,
+                                 float *depth, float *sil, float *sem, float *loss, cudaStream_t s);
+// loss_scale != nullptr selects the fused-L1 adjoint (upstream from sign codes)
+cudaError_t launch_render_bwd(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc, const float *d_rgb,
+                              const float *d_depth, const float *d_sil, const float *d_sem, int sem_detach,
+                              float *g_rgb, float *g_sem_w, cudaStream_t s, const float *loss_scale = nullptr);
+cudaError_t launch_project_bwd(const Layout &L, const WsPtrs &P, const gs_scene &sc, float *g_means,
+                               float *g_scales, float *g_quats, float *g_opacity, cudaStream_t s);
+cudaError_t launch_candidates(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc, double *out,
+                              cudaStream_t s);
+cudaError_t launch_l1_loss(int64_t npix, int m, const float *rgb, const float *t_rgb, const float *depth,
+                           const float *t_depth, const float *sem, const float *t_sem, float *d_rgb, float *d_depth,
+                           float *d_sem, float *loss, double *partial, cudaStream_t s);
+
+// Which of the two ping-pong buffers holds the sorted data after the passes.
+inline int depth_sort_buffer(const Layout &L) { return radix_passes(L.key_bits_depth) & 1; }
+inline int pair_sort_buffer(const Layout &L) { return radix_passes(L.key_bits_tile) & 1; }
+
+}  // namespace gs
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+namespace gs {
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Inclusive warp scan of a u32.
+__device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t v) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    uint32_t o = __shfl_up_sync(0xffffffffu, v, d);
+    if ((int)lane_id() >= d) v += o;
+  }
+  return v;
+}
+
+// Exclusive block scan of one u32 per thread (blockDim.x a multiple of 32,
+// at most 1024).  `tmp` needs 33 words of shared memory.  Returns the
+// exclusive prefix; *total receives the block sum.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *tmp, uint32_t *total) {
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t inc = warp_inclusive_scan(v);
+  if (lane == 31) tmp[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < nw ? tmp[lane] : 0u;
+    uint32_t wi = warp_inclusive_scan(w);
+    if (lane < nw) tmp[lane] = wi - w;
+    if (lane == nw - 1) tmp[32] = wi;
+  }
+  __syncthreads();
+  uint32_t r = tmp[warp] + inc - v;
+  *total = tmp[32];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ void set_status(Counters *c, uint32_t bits) { atomicOr(&c->status, bits); }
+
+}  // namespace gs
+#endif

@@ -1,0 +1,245 @@
+// project.cu -- per-(view, Gaussian) EWA projection, visibility compaction
+// and the single-CTA exclusive scan used for compaction offsets.
+//
+// Sec. 3.1 "Gaussian Mapping" (transform to camera space, project to the
+// image plane); the EWA projection with 0.3 px^2 dilation, 3-sigma radius and
+// frustum clamp is the 3DGS prior art the paper adopts via SplaTAM.
+//
+// This translation unit is compiled with -fmad=false: every expression below
+// is evaluated as written (one rounding per operation), so the pixel and tile
+// rectangles -- and therefore the tile lists -- are reproducible bit for bit.
+#include "gs_internal.cuh"
+
+namespace gs {
+
+struct Proj {
+  float u, v, ca, cb, cc, depth;
+  int x0, x1, y0, y1;
+};
+
+// Projects one Gaussian into camera `c`; returns false when culled.
+__device__ __forceinline__ bool project_gaussian(float mx, float my, float mz, float sx, float sy, float sz,
+                                                 float4 q, const DevCam &c, Proj &o) {
+  const float tx = ((c.r[0] * mx + c.r[1] * my) + c.r[2] * mz) + c.t[0];
+  const float ty = ((c.r[3] * mx + c.r[4] * my) + c.r[5] * mz) + c.t[1];
+  const float tz = ((c.r[6] * mx + c.r[7] * my) + c.r[8] * mz) + c.t[2];
+  if (!(isfinite(tx) && isfinite(ty) && isfinite(tz))) return false;
+  if (!(tz > c.near_plane)) return false;
+  const float n2 = ((q.x * q.x + q.y * q.y) + q.z * q.z) + q.w * q.w;
+  if (!(n2 > 0.f) || !isfinite(n2)) return false;
+  const float qn = sqrtf(n2);
+  const float w = q.x / qn, x = q.y / qn, y = q.z / qn, z = q.w / qn;
+  const float xx = x * x, yy = y * y, zz = z * z, xy = x * y, xz = x * z, yz = y * z;
+  const float wx = w * x, wy = w * y, wz = w * z;
+  const float R0 = 1.f - 2.f * (yy + zz), R1 = 2.f * (xy - wz), R2 = 2.f * (xz + wy);
+  const float R3 = 2.f * (xy + wz), R4 = 1.f - 2.f * (xx + zz), R5 = 2.f * (yz - wx);
+  const float R6 = 2.f * (xz - wy), R7 = 2.f * (yz + wx), R8 = 1.f - 2.f * (xx + yy);
+  // M = R diag(s)
+  const float M0 = R0 * sx, M1 = R1 * sy, M2 = R2 * sz;
+  const float M3 = R3 * sx, M4 = R4 * sy, M5 = R5 * sz;
+  const float M6 = R6 * sx, M7 = R7 * sy, M8 = R8 * sz;
+  // Sigma3 = M M^T (rows i <= j)
+  const float s00 = (M0 * M0 + M1 * M1) + M2 * M2;
+  const float s01 = (M0 * M3 + M1 * M4) + M2 * M5;
+  const float s02 = (M0 * M6 + M1 * M7) + M2 * M8;
+  const float s11 = (M3 * M3 + M4 * M4) + M5 * M5;
+  const float s12 = (M3 * M6 + M4 * M7) + M5 * M8;
+  const float s22 = (M6 * M6 + M7 * M7) + M8 * M8;
+  // pinhole Jacobian at the frustum-clamped mean
+  const float limx = 1.3f * ((0.5f * (float)c.width) / c.fx);
+  const float limy = 1.3f * ((0.5f * (float)c.height) / c.fy);
+  const float rx = tx / tz, ry = ty / tz;
+  const float rxc = rx < -limx ? -limx : (rx > limx ? limx : rx);
+  const float ryc = ry < -limy ? -limy : (ry > limy ? limy : ry);
+  const float txc = rxc * tz, tyc = ryc * tz;
+  const float tz2 = tz * tz;
+  const float J00 = c.fx / tz;
+  const float J02 = -(c.fx * txc) / tz2;
+  const float J11 = c.fy / tz;
+  const float J12 = -(c.fy * tyc) / tz2;
+  // T = J W
+  const float T0 = J00 * c.r[0] + J02 * c.r[6];
+  const float T1 = J00 * c.r[1] + J02 * c.r[7];
+  const float T2 = J00 * c.r[2] + J02 * c.r[8];
+  const float T3 = J11 * c.r[3] + J12 * c.r[6];
+  const float T4 = J11 * c.r[4] + J12 * c.r[7];
+  const float T5 = J11 * c.r[5] + J12 * c.r[8];
+  // U = T Sigma3 (Sigma3 column j = (s0j, s1j, s2j) with the mirrored entries)
+  const float U0 = (T0 * s00 + T1 * s01) + T2 * s02;
+  const float U1 = (T0 * s01 + T1 * s11) + T2 * s12;
+  const float U2 = (T0 * s02 + T1 * s12) + T2 * s22;
+  const float U3 = (T3 * s00 + T4 * s01) + T5 * s02;
+  const float U4 = (T3 * s01 + T4 * s11) + T5 * s12;
+  const float U5 = (T3 * s02 + T4 * s12) + T5 * s22;
+  const float A = ((U0 * T0 + U1 * T1) + U2 * T2) + 0.3f;
+  const float B = (U0 * T3 + U1 * T4) + U2 * T5;
+  const float C = ((U3 * T3 + U4 * T4) + U5 * T5) + 0.3f;
+  if (!(isfinite(A) && isfinite(B) && isfinite(C))) return false;
+  const float det = A * C - B * B;
+  if (!(det > 0.f)) return false;
+  const float inv = 1.f / det;
+  o.ca = C * inv;
+  o.cb = -B * inv;
+  o.cc = A * inv;
+  const float mid = 0.5f * (A + C);
+  const float disc = mid * mid - det;
+  const float lam = mid + sqrtf(disc > 0.1f ? disc : 0.1f);
+  const float rad = ceilf(3.f * sqrtf(lam));
+  o.u = (c.fx * tx) / tz + c.cx;
+  o.v = (c.fy * ty) / tz + c.cy;
+  if (!(isfinite(o.u) && isfinite(o.v))) return false;
+  float xlo = ceilf((o.u - 0.5f) - rad);
+  float xhi = floorf((o.u - 0.5f) + rad);
+  float ylo = ceilf((o.v - 0.5f) - rad);
+  float yhi = floorf((o.v - 0.5f) + rad);
+  if (xlo < 0.f) xlo = 0.f;
+  if (ylo < 0.f) ylo = 0.f;
+  if (xhi > (float)(c.width - 1)) xhi = (float)(c.width - 1);
+  if (yhi > (float)(c.height - 1)) yhi = (float)(c.height - 1);
+  if (!(xlo <= xhi) || !(ylo <= yhi)) return false;
+  o.x0 = (int)xlo; o.x1 = (int)xhi; o.y0 = (int)ylo; o.y1 = (int)yhi;
+  o.depth = tz;
+  return true;
+}
+
+__global__ void k_setup_views(CamTable tab, int n_views, DevCam *cams, uint32_t *tile_off, uint32_t total_tiles,
+                              Counters *counters, int reset_status) {
+  int i = threadIdx.x;
+  if (i < n_views) {
+    cams[i] = tab.cam[i];
+    tile_off[i] = tab.cam[i].tile_off;
+  }
+  if (i == 0) {
+    tile_off[n_views] = total_tiles;
+    if (reset_status) counters->status = 0u;
+    counters->n_records = 0u;
+    counters->n_pairs = 0u;
+    counters->n_contrib = 0u;
+  }
+}
+
+// Loads Gaussian g's projection inputs.
+struct GIn {
+  float mx, my, mz, sx, sy, sz;
+  float4 q;
+};
+__device__ __forceinline__ GIn load_gaussian(const gs_scene &sc, int g) {
+  GIn r;
+  r.mx = __ldg(sc.means + 3 * g); r.my = __ldg(sc.means + 3 * g + 1); r.mz = __ldg(sc.means + 3 * g + 2);
+  r.sx = __ldg(sc.scales + 3 * g); r.sy = __ldg(sc.scales + 3 * g + 1); r.sz = __ldg(sc.scales + 3 * g + 2);
+  r.q = __ldg(reinterpret_cast<const float4 *>(sc.quats) + g);
+  return r;
+}
+
+// Pass 1: count visible Gaussians per projection block.
+__global__ void __launch_bounds__(kProjThreads) k_project_count(gs_scene sc, const DevCam *cams, int nb,
+                                                                uint32_t *blockcnt) {
+  __shared__ uint32_t tmp[33];
+  const int v = blockIdx.x / nb, b = blockIdx.x % nb;
+  const DevCam c = cams[v];
+  const int g0 = b * kProjBlock + threadIdx.x * kProjItems;
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int i = 0; i < kProjItems; ++i) {
+    const int g = g0 + i;
+    if (g < sc.n) {
+      GIn in = load_gaussian(sc, g);
+      Proj p;
+      cnt += project_gaussian(in.mx, in.my, in.mz, in.sx, in.sy, in.sz, in.q, c, p) ? 1u : 0u;
+    }
+  }
+  uint32_t total;
+  block_exclusive_scan(cnt, tmp, &total);
+  if (threadIdx.x == 0) blockcnt[blockIdx.x] = total;
+}
+
+// Pass 2: recompute (bit-identical) and write compacted records in
+// (view, Gaussian index) order, plus the (view, depth) sort keys.
+__global__ void __launch_bounds__(kProjThreads) k_project_emit(gs_scene sc, const DevCam *cams, int nb,
+                                                               const uint32_t *blockoff, uint32_t rcap,
+                                                               WsPtrs P) {
+  __shared__ uint32_t tmp[33];
+  const int v = blockIdx.x / nb, b = blockIdx.x % nb;
+  const DevCam c = cams[v];
+  const int g0 = b * kProjBlock + threadIdx.x * kProjItems;
+  Proj p[kProjItems];
+  bool vis[kProjItems];
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int i = 0; i < kProjItems; ++i) {
+    const int g = g0 + i;
+    vis[i] = false;
+    if (g < sc.n) {
+      GIn in = load_gaussian(sc, g);
+      vis[i] = project_gaussian(in.mx, in.my, in.mz, in.sx, in.sy, in.sz, in.q, c, p[i]);
+    }
+    cnt += vis[i] ? 1u : 0u;
+  }
+  uint32_t total;
+  uint32_t rank = blockoff[blockIdx.x] + block_exclusive_scan(cnt, tmp, &total);
+#pragma unroll
+  for (int i = 0; i < kProjItems; ++i) {
+    if (!vis[i]) continue;
+    const uint32_t r = rank++;
+    if (r >= rcap) continue;
+    P.rec_uv[r] = make_float2(p[i].u, p[i].v);
+    P.rec_conic[r] = make_float4(p[i].ca, p[i].cb, p[i].cc, __ldg(sc.opacity + g0 + i));
+    P.rec_depth[r] = p[i].depth;
+    P.rec_rect[r] = make_short4((short)p[i].x0, (short)p[i].x1, (short)p[i].y0, (short)p[i].y1);
+    P.rec_gid[r] = g0 + i;
+    P.rec_view[r] = v;
+    P.dkeys[0][r] = ((unsigned long long)v << 31) | (unsigned long long)__float_as_uint(p[i].depth);
+    P.dvals[0][r] = r;
+  }
+}
+
+// Exclusive scan of n u32 in place by one CTA of 1024 threads (each thread
+// owns a contiguous segment).  Writes the sum to *total_out and raises the
+// capacity status when it exceeds `capacity`.
+__global__ void __launch_bounds__(1024) k_scan_single(uint32_t *data, uint32_t n, uint32_t *total_out,
+                                                      uint32_t capacity, Counters *counters) {
+  __shared__ uint32_t tmp[33];
+  const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
+  const uint32_t lo = min(n, threadIdx.x * per), hi = min(n, lo + per);
+  uint32_t s = 0;
+  for (uint32_t i = lo; i < hi; ++i) s += data[i];
+  uint32_t total;
+  uint32_t run = block_exclusive_scan(s, tmp, &total);
+  for (uint32_t i = lo; i < hi; ++i) {
+    uint32_t x = data[i];
+    data[i] = run;
+    run += x;
+  }
+  if (threadIdx.x == 0) {
+    if (total_out) *total_out = total;
+    if (total > capacity) set_status(counters, kStatusCapacity);
+  }
+}
+
+cudaError_t launch_setup_views(const CamTable &tab, int n_views, const WsPtrs &P, uint32_t total_tiles,
+                               bool reset_status, cudaStream_t s) {
+  k_setup_views<<<1, kMaxViews, 0, s>>>(tab, n_views, P.cams, P.tile_off, total_tiles, P.counters,
+                                        reset_status ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_single(uint32_t *data, uint32_t n, uint32_t *total_out, uint32_t capacity,
+                               Counters *counters, cudaStream_t s) {
+  k_scan_single<<<1, 1024, 0, s>>>(data, n, total_out, capacity, counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project(const Layout &L, const WsPtrs &P, const gs_scene &sc, cudaStream_t s) {
+  const int nb = (int)L.proj_blocks;
+  const int grid = nb * L.n_views;
+  if (grid == 0) return cudaSuccess;
+  k_project_count<<<grid, kProjThreads, 0, s>>>(sc, P.cams, nb, P.blockcnt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_scan_single(P.blockcnt, (uint32_t)grid, &P.counters->n_records, (uint32_t)L.rcap, P.counters, s);
+  if (e != cudaSuccess) return e;
+  k_project_emit<<<grid, kProjThreads, 0, s>>>(sc, P.cams, nb, P.blockcnt, (uint32_t)L.rcap, P);
+  return cudaGetLastError();
+}
+
+}  // namespace gs

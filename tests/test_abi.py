@@ -1,0 +1,134 @@
+"""The C ABI library builds, loads and exports every symbol declared in
+include/gs.h; host-side argument validation works without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2506_00225_gb300 import _native as N
+from paper_2506_00225_gb300 import build as B
+from paper_2506_00225_gb300 import raster, scenes
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "gs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(gs_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return N.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = header_functions()
+    assert len(names) >= 10
+    assert sorted(N.EXPORTS) == names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    for code in range(6):
+        assert lib.gs_status_string(code)
+    assert b"capacity" in lib.gs_status_string(N.GS_ERR_CAPACITY)
+
+
+def _structs(n=100, views=1, w=64, h=48, tile=(16, 16)):
+    sc = N.GsScene()
+    sc.n, sc.k, sc.m = n, 3, 16
+    cams = raster.cameras_array([scenes.look_camera((0, 0, 1.5), 0.0, w, h, 50.0)] * views)
+    cfg = N.GsConfig()
+    cfg.tile_w, cfg.tile_h = tile
+    cfg.sem_detach_geometry = 1
+    return sc, cams, cfg
+
+
+def test_workspace_size_and_layout_host_only(lib):
+    sc, cams, cfg = _structs()
+    size = lib.gs_workspace_size(ctypes.byref(sc), cams, 1, ctypes.byref(cfg))
+    assert size > 0 and size % 256 == 0
+    mp = N.GsWorkspaceMap()
+    base = 1 << 40  # a fake, never dereferenced device address
+    assert lib.gs_workspace_layout(ctypes.byref(sc), cams, 1, ctypes.byref(cfg), ctypes.c_void_p(base),
+                                   ctypes.byref(mp)) == N.GS_OK
+    ptrs = [mp.counters, mp.rec_uv, mp.rec_conic, mp.rec_depth, mp.rec_rect, mp.rec_gid, mp.rec_view, mp.pair_tile,
+            mp.pair_rec, mp.tile_ranges, mp.tile_offset]
+    assert all(base <= p < base + size for p in ptrs)
+    assert mp.record_capacity == 100 and mp.total_tiles == 4 * 3
+    # more views -> more tiles and records
+    sc2, cams2, cfg2 = _structs(views=5)
+    assert lib.gs_workspace_size(ctypes.byref(sc2), cams2, 5, ctypes.byref(cfg2)) > size
+
+
+@pytest.mark.parametrize("bad", ["k0", "k17", "m0", "views0", "views257", "tile0", "width0", "near0", "fx_nan"])
+def test_invalid_arguments_rejected_on_host(lib, bad):
+    sc, cams, cfg = _structs()
+    views = 1
+    if bad == "k0":
+        sc.k = 0
+    elif bad == "k17":
+        sc.k = 17
+    elif bad == "m0":
+        sc.m = 0
+    elif bad == "views0":
+        views = 0
+    elif bad == "views257":
+        views = 257
+    elif bad == "tile0":
+        cfg.tile_w = 0
+    elif bad == "width0":
+        cams[0].width = 0
+    elif bad == "near0":
+        cams[0].near_plane = 0.0
+    elif bad == "fx_nan":
+        cams[0].fx = float("nan")
+    assert lib.gs_workspace_size(ctypes.byref(sc), cams, views, ctypes.byref(cfg)) == 0
+    # every entry point refuses before touching the GPU
+    fake = ctypes.c_void_p(1 << 40)
+    assert lib.gs_project(ctypes.byref(sc), cams, views, ctypes.byref(cfg), fake, None) == N.GS_ERR_ARG
+    assert lib.gs_bin_sort(ctypes.byref(sc), cams, views, ctypes.byref(cfg), fake, None) == N.GS_ERR_ARG
+
+
+def test_null_workspace_and_misaligned_rejected(lib):
+    sc, cams, cfg = _structs()
+    assert lib.gs_project(ctypes.byref(sc), cams, 1, ctypes.byref(cfg), None, None) == N.GS_ERR_ARG
+    assert lib.gs_project(ctypes.byref(sc), cams, 1, ctypes.byref(cfg), ctypes.c_void_p((1 << 40) + 8),
+                          None) == N.GS_ERR_ARG
+    out = ctypes.c_void_p(1 << 41)
+    assert lib.gs_render_candidates(ctypes.byref(sc), cams, 1, ctypes.byref(cfg), None, out, None) == N.GS_ERR_ARG
+    assert lib.gs_l1_loss(0, 1, None, None, None, None, None, None, None, None, None, None, None,
+                          None) == N.GS_ERR_ARG
+
+
+def test_scene_pointer_checks(lib):
+    sc, cams, cfg = _structs()
+    fake = ctypes.c_void_p(1 << 40)
+    # n > 0 with NULL means -> refused
+    assert lib.gs_project(ctypes.byref(sc), cams, 1, ctypes.byref(cfg), fake, None) == N.GS_ERR_ARG
+    # quaternions must be 16-byte aligned
+    sc.means = sc.scales = sc.opacity = ctypes.c_void_p(1 << 40)
+    sc.quats = ctypes.c_void_p((1 << 40) + 4)
+    assert lib.gs_project(ctypes.byref(sc), cams, 1, ctypes.byref(cfg), fake, None) == N.GS_ERR_ARG
+
+
+def test_unsupported_tile_shape(lib):
+    sc, cams, cfg = _structs(n=0, tile=(12, 12))
+    fake = ctypes.c_void_p(1 << 40)
+    assert lib.gs_render_fwd(ctypes.byref(sc), cams, ctypes.byref(cfg), fake, None, None, None, None,
+                             None) == N.GS_ERR_UNSUPPORTED
+
+
+def test_product_has_no_oracle_dependency():
+    """The product package never imports or links the oracle."""
+    pkg = os.path.join(ROOT, "paper_2506_00225_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt and "gs_oracle" not in txt, f
