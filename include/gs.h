@@ -50,7 +50,8 @@ typedef enum gs_status {
   GS_ERR_CAPACITY = 2,    /* workspace capacity exceeded (device status) */
   GS_ERR_CUDA = 3,        /* CUDA launch or runtime error */
   GS_ERR_TIMEOUT = 4,     /* a bounded device wait gave up (device status) */
-  GS_ERR_UNSUPPORTED = 5  /* configuration not compiled in */
+  GS_ERR_UNSUPPORTED = 5, /* configuration not compiled in */
+  GS_ERR_TOO_LARGE = 6    /* sizes need more scratch than gs_render_fwd_noalloc has */
 } gs_status;
 
 /* Gaussian map, structure of arrays (Sec. 3.1 "Gaussian Mapping" and
@@ -232,6 +233,38 @@ gs_status gs_render_candidates(const gs_scene *scene, const gs_camera *views, in
 gs_status gs_l1_loss(int64_t npix, int m, const float *rgb, const float *t_rgb, const float *depth,
                      const float *t_depth, const float *sem, const float *t_sem, float *d_rgb, float *d_depth,
                      float *d_sem, float *loss, double *partial, gs_stream_t stream);
+
+/* Bytes of the fixed device scratch array used by gs_render_fwd_noalloc. */
+#define GS_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* No-allocation variant of one forward render (the paper has no counterpart:
+ * this is an interface for callers of this library).
+ *
+ * Some callers cannot allocate device memory: code running while a CUDA graph
+ * is being captured, real-time loops that must never block inside an
+ * allocator, and plug-in hosts that own all device memory.  This entry point
+ * runs the same kernels as gs_project + gs_bin_sort + gs_render_fwd for one
+ * view, but its workspace is a fixed device array of
+ * GS_NOALLOC_SCRATCH_BYTES inside the library, so it calls no cudaMalloc,
+ * cudaFree or other allocating routine.  Every GPU that loads the library
+ * holds that array until the process exits.
+ *   - Arguments are those of gs_render_fwd without the workspace; outputs
+ *     (rgb, depth, sil, sem; any may be NULL) are caller-owned device buffers.
+ *   - Returns GS_ERR_TOO_LARGE, before any GPU work, when the workspace these
+ *     sizes and capacities need (gs_workspace_size with n_views = 1) exceeds
+ *     GS_NOALLOC_SCRATCH_BYTES.
+ *   - The first call on each device looks up the array's device address
+ *     (with that device current) and caches it; make that first call before
+ *     any stream capture.
+ *   - All calls share the one array, which keeps the previous call's
+ *     contents; the chain clears what must start at zero (counters, status).
+ *     Calls that overlap on the GPU (other streams, other host threads) race
+ *     on the array and must be serialised by the caller.
+ *   - counters_out (optional DEVICE pointer) receives the chain's counters,
+ *     including the capacity status bit, at the end of the chain. */
+gs_status gs_render_fwd_noalloc(const gs_scene *scene, const gs_camera *cam, const gs_config *cfg, float *rgb,
+                                float *depth, float *sil, float *sem, gs_counters *counters_out,
+                                gs_stream_t stream);
 
 /* Synchronises `stream`, then copies the workspace counters to *out (host).
  * Returns the first device error recorded (GS_ERR_CAPACITY, GS_ERR_TIMEOUT)

@@ -30,6 +30,7 @@ SOURCES = {
     "candidates.cu": [],
     "loss.cu": [],
     "api.cu": [],
+    "noalloc.cu": [],
 }
 HEADERS = ["gs_internal.cuh", "render_common.cuh"]
 

@@ -344,6 +344,7 @@ const char *gs_status_string(gs_status s) {
     case GS_ERR_CUDA: return "CUDA error";
     case GS_ERR_TIMEOUT: return "bounded device wait timed out";
     case GS_ERR_UNSUPPORTED: return "configuration not compiled in";
+    case GS_ERR_TOO_LARGE: return "sizes need more workspace than the fixed no-allocation scratch array holds";
   }
   return "unknown status";
 }

@@ -34,7 +34,7 @@ def test_exports_every_declared_symbol(lib):
 
 
 def test_status_strings(lib):
-    for code in range(6):
+    for code in range(7):
         assert lib.gs_status_string(code)
     assert b"capacity" in lib.gs_status_string(N.GS_ERR_CAPACITY)
 
