@@ -142,9 +142,10 @@ def bench_config(world: int) -> dict:
     return {"workload": "room300k: 300k-Gaussian synthetic room, one 680x1200 view (fx=fy=600), M=102 classes, "
                         "top-3 semantics; step = project + bin/sort + forward fused with the mean-L1 loss on "
                         "colour/depth/semantics + adjoint to all parameters (torch.autograd.Function)",
-            "tile": "16x16",
             "l2": "inputs larger than L2 (333 MB target semantic map) and a 258 MB L2 flush between timed steps "
                   "(outside the per-step events)",
+            "timing": "each step replayed as one CUDA graph (forward, loss, autograd backward); CUDA events "
+                      "around each replay",
             "parallelism": f"replicas x{world}"}
 
 
@@ -221,10 +222,15 @@ def main():
     H, W, m, k = cam.height, cam.width, sc.m, sc.k
     g = raster.Gaussians.from_scene(sc, dev)
     gt = raster.Gaussians.from_scene(wl["target"], dev)
-    rast = raster.Rasterizer(device=dev)
+    rast0 = raster.Rasterizer(device=dev)
     with torch.no_grad():
-        t_rgb, t_depth, _, t_sem = rast.forward(gt, cam, check=True)
+        t_rgb, t_depth, _, t_sem = rast0.forward(gt, cam, check=True)
         t_rgb, t_depth, t_sem = t_rgb.clone(), t_depth.clone(), t_sem.clone()
+    del rast0
+    # launch configuration picked by the autotuner (outside the timed region)
+    from paper_2506_00225_gb300 import autotune
+    best, tune_table = autotune.tune_mapping(g, cam, t_rgb, t_depth, t_sem)
+    rast = raster.Rasterizer(tile=best["tile"], px_per_thread=best["px_per_thread"], device=dev)
     params = [t.clone().requires_grad_(True) for t in (g.means, g.scales, g.quats, g.opacity, g.rgb, g.sem_w)]
     rast.forward(g, cam, check=True)  # sizes the workspace capacities
     cnt = rast.counters()
@@ -248,39 +254,67 @@ def main():
 
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
 
-    def timed(step, steps):
-        starts, ends, phases = [], [], []
+    def phase_times(step, steps):
+        """Eager steps; a device-side sleep before each step lets the host
+        enqueue the whole step first, so the phase events bracket GPU work
+        only.  Returns mean per-phase device times (ms)."""
+        ph = {}
         for _ in range(steps):
             flush.zero_()
+            torch.cuda._sleep(4_000_000)
             rast.phase_events = []
+            step(t_rgb, t_depth, t_sem)
+            evs = rast.phase_events
+            rast.phase_events = None
+            torch.cuda.synchronize()
+            for (n0, e0), (_, e1) in zip(evs[:-1], evs[1:]):
+                ph.setdefault(n0, []).append(e0.elapsed_time(e1))
+        return {k_: statistics.mean(v) for k_, v in ph.items()}
+
+    def capture(step):
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(2):
+                step(t_rgb, t_depth, t_sem)
+        torch.cuda.current_stream().wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            out = step(t_rgb, t_depth, t_sem)
+        return graph, out
+
+    def timed_graph(graph, steps):
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
             s_ = torch.cuda.Event(enable_timing=True)
             e_ = torch.cuda.Event(enable_timing=True)
             s_.record()
-            step(t_rgb, t_depth, t_sem)
+            graph.replay()
             e_.record()
-            starts.append(s_)
-            ends.append(e_)
-            phases.append(rast.phase_events)
-            rast.phase_events = None
+            ms.append((s_, e_))
         torch.cuda.synchronize()
-        step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-        ph = {}
-        for evs in phases:
-            for (n0, e0), (_, e1) in zip(evs[:-1], evs[1:]):
-                ph.setdefault(n0, []).append(e0.elapsed_time(e1))
-        return step_ms, {k_: statistics.mean(v) for k_, v in ph.items()}
+        return [a.elapsed_time(b) for a, b in ms]
 
     for _ in range(args.warmup):
         step_unfused(t_rgb, t_depth, t_sem)
         step_fused(t_rgb, t_depth, t_sem)
     torch.cuda.synchronize()
 
-    # ---- timed region (headline: fused step) ---------------------------------
     clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")) \
         if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ClockSampler(local, f"/tmp/clocks_rank{rank}.csv")
+    ph_ms = phase_times(step_fused, max(3, args.steps // 3))
+    un_ph = phase_times(step_unfused, max(3, args.steps // 3))
+    g_fused, g_loss = capture(step_fused)
+    g_unfused, _ = capture(step_unfused)
+    for _ in range(args.warmup):
+        g_fused.replay()
+    torch.cuda.synchronize()
+
+    # ---- timed region (headline: fused step, whole step replayed as one CUDA graph)
     barrier(world)
     torch.cuda.synchronize()
-    step_ms, ph_ms = timed(step_fused, args.steps)
+    step_ms = timed_graph(g_fused, args.steps)
     barrier(world)
     clk = clocks.stop()
     total_ms = max_over_ranks(sum(step_ms), world, dev)
@@ -289,7 +323,7 @@ def main():
 
     # the same step with the semantic map written, a separate L1 kernel and
     # the map-sized gradient read back by the adjoint
-    un_ms, un_ph = timed(step_unfused, max(3, args.steps // 2))
+    un_ms = timed_graph(g_unfused, max(3, args.steps // 2))
     un_total = max_over_ranks(sum(un_ms), world, dev) / len(un_ms)
 
     # ---- roofline ---------------------------------------------------------------
@@ -334,9 +368,10 @@ def main():
     roofline["render_fwd_hbm_frac"] = frac_fwd
 
     # ---- e2e through the public API with host buffers ------------------------
+    # every step copies its target frame from pinned host memory into the
+    # graph's input buffers, replays the step and reads the loss back
     pin = lambda t_: t_.detach().cpu().pin_memory()
     h_rgb, h_depth, h_sem = pin(t_rgb), pin(t_depth), pin(t_sem)
-    d_tr, d_td, d_ts = torch.empty_like(t_rgb), torch.empty_like(t_depth), torch.empty_like(t_sem)
     h_loss = torch.empty((), dtype=torch.float32).pin_memory()
     e2e_steps = max(3, args.steps // 2)
     barrier(world)
@@ -345,11 +380,11 @@ def main():
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(e2e_steps):
-        d_tr.copy_(h_rgb, non_blocking=True)
-        d_td.copy_(h_depth, non_blocking=True)
-        d_ts.copy_(h_sem, non_blocking=True)
-        loss = step_fused(d_tr, d_td, d_ts)
-        h_loss.copy_(loss, non_blocking=True)
+        t_rgb.copy_(h_rgb, non_blocking=True)
+        t_depth.copy_(h_depth, non_blocking=True)
+        t_sem.copy_(h_sem, non_blocking=True)
+        g_fused.replay()
+        h_loss.copy_(g_loss, non_blocking=True)
     e1.record()
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev) / e2e_steps
@@ -363,11 +398,14 @@ def main():
     if not args.no_candidates:
         cand = bench_candidates(args, dev, flush)
 
-    # launches of our kernels per fused step: project 4, depth sort 3/pass,
-    # emit 3, tile sort 3/pass, ranges 1, fused fwd 1 + loss final 1, bwd 3
+    # launches of our kernels per fused step: project 4 (setup, count, scan,
+    # emit); depth sort: reset, histogram, one per pass; pair emission 3;
+    # tile sort: reset, histogram, one per pass; ranges 2; fused forward +
+    # loss reduction 2; backward 3 (zero, blend adjoint, projection adjoint)
     passes = lambda bits: (bits + 7) // 8
-    tiles = ((W + 15) // 16) * ((H + 15) // 16)
-    per_step = 4 + 3 * passes(31) + 3 + 3 * passes(max(1, (tiles - 1).bit_length())) + 1 + 2 + 3
+    tw_, th_ = best["tile"]
+    tiles = ((W + tw_ - 1) // tw_) * ((H + th_ - 1) // th_)
+    per_step = 4 + (2 + passes(31)) + 3 + (2 + passes(max(1, (tiles - 1).bit_length()))) + 2 + 2 + 3
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -380,6 +418,8 @@ def main():
                 "data": "synthetic",
                 "config": bench_config(world),
                 "counts": {"visible_records": n_records, "tile_gaussian_pairs": n_pairs, "contributions": n_contrib},
+                "autotune": {"chosen": {"tile": "%dx%d" % best["tile"], "px_per_thread": best["px_per_thread"]},
+                             "fused_step_ms": tune_table},
                 "roofline": roofline,
                 "cpu_baseline": cpu,
                 "e2e": {"value": world * 1000.0 / e2e_ms, "unit": "iters/s", "h2d_bytes_per_step": h2d,

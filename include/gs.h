@@ -86,6 +86,8 @@ typedef struct gs_camera {
 
 /* Launch configuration.
  *   tile_w, tile_h       screen tile (compiled shapes: 16x16, 16x8, 8x8, 32x8)
+ *   px_per_thread        pixels per thread in the blend kernels: 1 or 2
+ *                        (0 = default 2); results do not depend on it
  *   sem_detach_geometry  1 (default in the Python layer): the semantic
  *                        upstream gradient reaches sem_w only, never the
  *                        geometric attributes (Sec. 3.1 "Semantic Loss",
@@ -97,7 +99,7 @@ typedef struct gs_camera {
 typedef struct gs_config {
   int32_t tile_w, tile_h;
   int32_t sem_detach_geometry;
-  int32_t reserved;
+  int32_t px_per_thread;
   int64_t record_capacity;
   int64_t pair_capacity;
 } gs_config;

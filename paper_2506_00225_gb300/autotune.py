@@ -1,0 +1,60 @@
+"""Launch-configuration autotuner for the tile kernels.
+
+Times the fused mapping step (project, bin/sort, forward + mean-L1, adjoint)
+for every compiled tile shape and pixels-per-thread mapping on the caller's
+own scene, view and targets, and returns the fastest.  The rendered values
+and gradients do not depend on the choice (every pixel sees the same
+Gaussians in the same order); only the time does.  Results are cached per
+(Gaussians, image size, k, m).
+"""
+from __future__ import annotations
+
+import statistics
+
+import torch
+
+from . import raster
+
+SHAPES = ((16, 16), (16, 8), (32, 8), (8, 8))
+PPTS = (2, 1)
+
+_CACHE: dict = {}
+
+
+def _time_config(g, cam, targets, tile, ppt, reps, device):
+    rast = raster.Rasterizer(tile=tile, px_per_thread=ppt, device=device)
+    loss = rast.forward_l1(g, cam, *targets, check=True)  # sizes the workspace
+    rast.backward_l1(g, cam, torch.ones((), device=device))
+    ones = torch.ones((), device=device)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        torch.cuda._sleep(2_000_000)  # let the host enqueue the whole step first
+        s.record()
+        rast.forward_l1(g, cam, *targets, check=False)
+        rast.backward_l1(g, cam, ones)
+        e.record()
+        torch.cuda.synchronize()
+        times.append(s.elapsed_time(e))
+    del loss
+    return statistics.median(times), rast
+
+
+def tune_mapping(g: raster.Gaussians, cam, t_rgb, t_depth, t_sem, reps: int = 5, device=None):
+    """Returns (best {tile, px_per_thread, ms}, table of all timings)."""
+    key = (g.n, cam.width, cam.height, g.k, g.m)
+    if key in _CACHE:
+        return _CACHE[key]
+    device = device or g.means.device
+    table = []
+    for tile in SHAPES:
+        for ppt in PPTS:
+            ms, _ = _time_config(g, cam, (t_rgb, t_depth, t_sem), tile, ppt, reps, device)
+            table.append({"tile": f"{tile[0]}x{tile[1]}", "px_per_thread": ppt, "ms": round(ms, 4)})
+    best = min(table, key=lambda r: r["ms"])
+    w, h = (int(x) for x in best["tile"].split("x"))
+    res = ({"tile": (w, h), "px_per_thread": best["px_per_thread"], "ms": best["ms"]}, table)
+    _CACHE[key] = res
+    return res

@@ -46,6 +46,8 @@ bool make_layout(const gs_scene *scene, const gs_camera *cams, int n_views, cons
   memset(L, 0, sizeof(*L));
   L->n = scene->n; L->k = scene->k; L->m = scene->m; L->n_views = n_views;
   L->tile_w = cfg.tile_w; L->tile_h = cfg.tile_h;
+  if (cfg.px_per_thread < 0 || cfg.px_per_thread > 2) return false;
+  L->ppt = cfg.px_per_thread == 0 ? 2 : cfg.px_per_thread;
   uint64_t tiles = 0;
   for (int v = 0; v < n_views; ++v) {
     if (!cam_ok(cams[v])) return false;
@@ -81,12 +83,19 @@ bool make_layout(const gs_scene *scene, const gs_camera *cams, int n_views, cons
   L->off_rec_rect = take(8 * (size_t)rcap);
   L->off_rec_gid = take(4 * (size_t)rcap);
   L->off_rec_view = take(4 * (size_t)rcap);
+  L->off_rec_box = take(8 * (size_t)rcap);
+  L->off_rec_cd = take(16 * (size_t)rcap);
+  L->off_rec_unc = take(4 * (size_t)rcap);
+  L->off_rec_sem = take(8 * (size_t)rcap * scene->k);
   for (int i = 0; i < 2; ++i) L->off_dkeys[i] = take(8 * (size_t)rcap);
   for (int i = 0; i < 2; ++i) L->off_dvals[i] = take(4 * (size_t)rcap);
   L->off_epart = take(sizeof(uint32_t) * (kEmitCtas + 1));
   for (int i = 0; i < 2; ++i) L->off_pkeys[i] = take(4 * (size_t)pcap);
   for (int i = 0; i < 2; ++i) L->off_pvals[i] = take(4 * (size_t)pcap);
-  L->off_hist = take(sizeof(uint32_t) * (size_t)kRadix * kSortCtas);
+  L->off_tickets = take(sizeof(uint32_t) * 2 * kMaxRadixPasses);
+  L->off_ghist = take(sizeof(uint32_t) * 2 * kMaxRadixPasses * kRadix);
+  L->off_lb_depth = take(8 * (size_t)kRadix * sort_tiles(rcap) * radix_passes(L->key_bits_depth));
+  L->off_lb_pairs = take(8 * (size_t)kRadix * sort_tiles(pcap) * radix_passes(L->key_bits_tile));
   L->off_ranges = take(8 * (size_t)(tiles > 0 ? tiles : 1));
   L->off_tfinal = take(4 * (size_t)(L->npix > 0 ? L->npix : 1));
   L->off_nlast = take(4 * (size_t)(L->npix > 0 ? L->npix : 1));
@@ -111,6 +120,10 @@ WsPtrs ws_ptrs(const Layout &L, void *ws) {
   P.rec_rect = reinterpret_cast<short4 *>(b + L.off_rec_rect);
   P.rec_gid = reinterpret_cast<int32_t *>(b + L.off_rec_gid);
   P.rec_view = reinterpret_cast<int32_t *>(b + L.off_rec_view);
+  P.rec_box = reinterpret_cast<short4 *>(b + L.off_rec_box);
+  P.rec_cd = reinterpret_cast<float4 *>(b + L.off_rec_cd);
+  P.rec_unc = reinterpret_cast<float *>(b + L.off_rec_unc);
+  P.rec_sem = reinterpret_cast<int2 *>(b + L.off_rec_sem);
   for (int i = 0; i < 2; ++i) {
     P.dkeys[i] = reinterpret_cast<unsigned long long *>(b + L.off_dkeys[i]);
     P.dvals[i] = reinterpret_cast<uint32_t *>(b + L.off_dvals[i]);
@@ -118,7 +131,10 @@ WsPtrs ws_ptrs(const Layout &L, void *ws) {
     P.pvals[i] = reinterpret_cast<uint32_t *>(b + L.off_pvals[i]);
   }
   P.epart = reinterpret_cast<uint32_t *>(b + L.off_epart);
-  P.hist = reinterpret_cast<uint32_t *>(b + L.off_hist);
+  P.tickets = reinterpret_cast<uint32_t *>(b + L.off_tickets);
+  P.ghist = reinterpret_cast<uint32_t *>(b + L.off_ghist);
+  P.lb_depth = reinterpret_cast<unsigned long long *>(b + L.off_lb_depth);
+  P.lb_pairs = reinterpret_cast<unsigned long long *>(b + L.off_lb_pairs);
   P.ranges = reinterpret_cast<uint2 *>(b + L.off_ranges);
   P.tfinal = reinterpret_cast<float *>(b + L.off_tfinal);
   P.nlast = reinterpret_cast<uint32_t *>(b + L.off_nlast);

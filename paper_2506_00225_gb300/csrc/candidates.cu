@@ -21,8 +21,6 @@ struct CandArgs {
   const uint32_t *pvals;
   RecPtrs rec;
   const float *unc;
-  const int32_t *sem_ids;
-  const float *sem_w;
   const DevCam *cams;
   const uint32_t *tile_off;
   int n_views, k, m;
@@ -34,7 +32,8 @@ constexpr float kClipLo = 0.001f;
 
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW *TH) k_candidates(CandArgs a) {
-  constexpr int THREADS = TW * TH;
+  using FP = Footprint<TW, TH>;
+  constexpr int THREADS = FP::kThreads;
   extern __shared__ float4 smem4[];
   BatchSmem bs = batch_smem(smem4, a.k);
   float *sP = bs.tail;
@@ -51,12 +50,15 @@ __global__ void __launch_bounds__(TW *TH) k_candidates(CandArgs a) {
   const int v = lo;
   const DevCam &c = a.cams[v];
   const uint32_t local = tile - c.tile_off;
-  const int tx = (int)(local % (uint32_t)c.tiles_x), ty = (int)(local / (uint32_t)c.tiles_x);
+  const int ox = (int)(local % (uint32_t)c.tiles_x) * TW, oy = (int)(local / (uint32_t)c.tiles_x) * TH;
   const uint2 rg = a.ranges[tile];
-  const int px = tx * TW + (int)(threadIdx.x % TW), py = ty * TH + (int)(threadIdx.x / TW);
+  const int px = ox + FP::lx(), py = oy + FP::ly(0);
   const bool inside = px < c.width && py < c.height;
   const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
   float *myP = sP + threadIdx.x * a.mstride;
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  const int k = a.k;
+  const bool use_unc = a.unc != nullptr;
 
   float T = 1.f, U = 0.f, Z = 0.f, Aacc = 0.f;
   uint32_t nfloor = 0;
@@ -68,25 +70,31 @@ __global__ void __launch_bounds__(TW *TH) k_candidates(CandArgs a) {
     for (uint32_t b = rg.x; b < rg.y; b += kBatch) {
       const int n = (int)min((uint32_t)kBatch, rg.y - b);
       __syncthreads();
-      if ((int)threadIdx.x < n) load_batch_entry(a.rec, a.pvals[b + threadIdx.x], threadIdx.x, a.k, bs, nullptr,
-                                                 a.sem_ids, a.sem_w, a.unc);
+      for (int t = threadIdx.x; t < n; t += THREADS)
+        stage_record<TW, TH>(a.rec, a.pvals[b + t], t, k, ox, oy, bs, true, use_unc);
       __syncthreads();
-      if (!done) {
-        for (int j = 0; j < n; ++j) {
-          if (!rect_holds(bs.rect[j], px, py)) continue;
-          float alpha, G, araw, dx, dy;
-          if (!gauss_alpha(bs.uv[j], bs.co[j], fpx, fpy, alpha, G, araw, dx, dy)) continue;
-          const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
-          if (Tn < kTStop) { done = true; break; }
-          const float w = __fmul_rn(alpha, T);
-          U = fmaf(w, bs.cd[j].x, U);
-          const int *sid = bs.sid + j * a.k;
-          const float *sw = bs.sw + j * a.k;
-          for (int l = 0; l < a.k; ++l) {
-            const int id = sid[l] - c_lo;
-            if ((unsigned)id < (unsigned)mc) myP[id] = fmaf(w, sw[l], myP[id]);
+      if (!__all_sync(0xffffffffu, done)) {
+        for (int base = 0; base < n; base += 32) {
+          const int jj = base + (int)lane;
+          uint32_t vis = __ballot_sync(0xffffffffu, jj < n && ((bs.wmask[jj] >> warp) & 1u));
+          while (vis) {
+            const int j = base + __ffs(vis) - 1;
+            vis &= vis - 1;
+            if (done || !box_holds(bs.box[j], px, py)) continue;
+            float alpha, G, araw, dx, dy;
+            if (!gauss_alpha(bs.uv[j], bs.co[j], fpx, fpy, alpha, G, araw, dx, dy)) continue;
+            const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
+            if (Tn < kTStop) { done = true; continue; }
+            const float w = __fmul_rn(alpha, T);
+            U = fmaf(w, bs.cd[j].x, U);
+            const int2 *sp = bs.sem + j * k;
+            for (int l = 0; l < k; ++l) {
+              const int2 e = sp[l];
+              const int id = e.x - c_lo;
+              if ((unsigned)id < (unsigned)mc) myP[id] = fmaf(w, __int_as_float(e.y), myP[id]);
+            }
+            T = Tn;
           }
-          T = Tn;
         }
       }
       if (__syncthreads_count(done) == THREADS) break;
@@ -111,11 +119,10 @@ __global__ void __launch_bounds__(TW *TH) k_candidates(CandArgs a) {
     Z += zf;
     Aacc = fmaf(zf, logf(kClipLo), Aacc);
     h = logf(Z) - Aacc / Z;
-    u = a.unc ? U : 0.f;
+    u = use_unc ? U : 0.f;
     ns = (T == 1.f) ? 1u : 0u;
   }
   // block reduction
-  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     h += __shfl_xor_sync(0xffffffffu, h, o);
@@ -162,7 +169,6 @@ cudaError_t launch_candidates(const Layout &L, const WsPtrs &P, int pbuf, const 
   a.pvals = P.pvals[pbuf];
   a.rec = rec_ptrs(P);
   a.unc = sc.geo_unc;
-  a.sem_ids = sc.sem_ids; a.sem_w = sc.sem_w;
   a.cams = P.cams; a.tile_off = P.tile_off;
   a.n_views = L.n_views; a.k = sc.k; a.m = sc.m;
   a.out = out;

@@ -14,10 +14,7 @@ constexpr int kMaxK = 16;
 constexpr int kMaxM = 1024;
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
-constexpr int kSortCtas = 4 * 152;        // fixed grid of the radix-sort kernels
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 8;             // keys per thread per tile
-constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kMaxRadixPasses = 8;       // 64-bit keys at most
 constexpr int kProjThreads = 256;
 constexpr int kProjItems = 4;
 constexpr int kProjBlock = kProjThreads * kProjItems;  // Gaussians per projection CTA
@@ -56,16 +53,18 @@ struct Counters {
 struct Layout {
   int n, k, m, n_views, tile_w, tile_h;
   int cam0_w, cam0_h;                      // first camera (the single view of mapping calls)
+  int ppt;                                 // pixels per thread in the tile kernels (1 or 2)
   int64_t rcap, pcap, total_tiles, npix;  // npix: pixels of view 0 when n_views == 1
   int64_t proj_blocks;                     // projection CTAs per view
   int key_bits_depth;                      // bits of the (view, depth) record key
   int key_bits_tile;                       // bits of the global tile id
   size_t off_counters, off_cams, off_tile_off, off_blockcnt;
   size_t off_rec_uv, off_rec_conic, off_rec_depth, off_rec_rect, off_rec_gid, off_rec_view;
+  size_t off_rec_box, off_rec_cd, off_rec_unc, off_rec_sem;
   size_t off_dkeys[2], off_dvals[2];
   size_t off_epart;
   size_t off_pkeys[2], off_pvals[2];
-  size_t off_hist;
+  size_t off_tickets, off_ghist, off_lb_depth, off_lb_pairs;
   size_t off_ranges;
   size_t off_tfinal, off_nlast;
   size_t off_grad2d;
@@ -85,12 +84,19 @@ struct WsPtrs {
   short4 *rec_rect;
   int32_t *rec_gid;
   int32_t *rec_view;
+  short4 *rec_box;   // alpha box (pixels outside have alpha < 1/255), within rec_rect
+  float4 *rec_cd;    // r, g, b, depth
+  float *rec_unc;    // per-Gaussian uncertainty (0 when absent)
+  int2 *rec_sem;     // [rcap][k] (class id, weight bits)
   unsigned long long *dkeys[2];
   uint32_t *dvals[2];
   uint32_t *epart;
   uint32_t *pkeys[2];
   uint32_t *pvals[2];
-  uint32_t *hist;
+  uint32_t *tickets;                 // [2][kMaxRadixPasses] tile tickets (depth sort, pair sort)
+  uint32_t *ghist;                   // [2][kMaxRadixPasses][256] digit histograms
+  unsigned long long *lb_depth;      // look-back words of the depth sort
+  unsigned long long *lb_pairs;      // look-back words of the pair sort
   uint2 *ranges;
   float *tfinal;
   uint32_t *nlast;
@@ -105,6 +111,8 @@ WsPtrs ws_ptrs(const Layout &L, void *ws);
 
 // Number of radix passes over `bits` key bits.
 inline int radix_passes(int bits) { return (bits + kRadixBits - 1) / kRadixBits; }
+// Tiles of the radix-sort pass kernel for `capacity` elements.
+int sort_tiles(int64_t capacity);
 
 // ---------------------------------------------------------------------------
 // Launchers implemented in the kernel translation units.

@@ -15,7 +15,26 @@ namespace gs {
 struct Proj {
   float u, v, ca, cb, cc, depth;
   int x0, x1, y0, y1;
+  float A, C;  // dilated 2D covariance diagonal (for the alpha box)
 };
+
+// Pixel box outside which alpha < 1/255 for sure: the axis-aligned box of the
+// ellipse q(d) <= 2 ln(255 o) (half-extents sqrt(2 ln(255 o) Sigma_xx),
+// sqrt(.. Sigma_yy)), widened by 0.1 % plus one pixel, clipped to the pixel
+// rectangle.  Inside the rectangle but outside this box every pixel would be
+// skipped by the alpha < 1/255 rule, so the blend kernels may skip it without
+// evaluating alpha; tile lists still use the pixel rectangle.  Empty when
+// x0 > x1.
+__device__ __forceinline__ short4 alpha_box(const Proj &p, float opacity) {
+  if (!(opacity >= 1.f / 255.f)) return make_short4(1, 0, 1, 0);
+  const float L = 2.f * logf(255.f * opacity);
+  const float hx = sqrtf(fmaxf(L, 0.f) * p.A) * 1.001f + 1.f;
+  const float hy = sqrtf(fmaxf(L, 0.f) * p.C) * 1.001f + 1.f;
+  const float bx0 = fmaxf((float)p.x0, floorf(p.u - 0.5f - hx)), bx1 = fminf((float)p.x1, ceilf(p.u - 0.5f + hx));
+  const float by0 = fmaxf((float)p.y0, floorf(p.v - 0.5f - hy)), by1 = fminf((float)p.y1, ceilf(p.v - 0.5f + hy));
+  if (!(bx0 <= bx1) || !(by0 <= by1)) return make_short4(1, 0, 1, 0);
+  return make_short4((short)bx0, (short)bx1, (short)by0, (short)by1);
+}
 
 // Projects one Gaussian into camera `c`; returns false when culled.
 __device__ __forceinline__ bool project_gaussian(float mx, float my, float mz, float sx, float sy, float sz,
@@ -99,6 +118,8 @@ __device__ __forceinline__ bool project_gaussian(float mx, float my, float mz, f
   if (!(xlo <= xhi) || !(ylo <= yhi)) return false;
   o.x0 = (int)xlo; o.x1 = (int)xhi; o.y0 = (int)ylo; o.y1 = (int)yhi;
   o.depth = tz;
+  o.A = A;
+  o.C = C;
   return true;
 }
 
@@ -188,6 +209,17 @@ __global__ void __launch_bounds__(kProjThreads) k_project_emit(gs_scene sc, cons
     P.rec_rect[r] = make_short4((short)p[i].x0, (short)p[i].x1, (short)p[i].y0, (short)p[i].y1);
     P.rec_gid[r] = g0 + i;
     P.rec_view[r] = v;
+    // blend record: alpha box, colour + depth, uncertainty, sparse semantics
+    const int g = g0 + i;
+    const float op = __ldg(sc.opacity + g);
+    P.rec_box[r] = alpha_box(p[i], op);
+    P.rec_cd[r] = make_float4(sc.rgb ? __ldg(sc.rgb + 3 * g) : 0.f, sc.rgb ? __ldg(sc.rgb + 3 * g + 1) : 0.f,
+                              sc.rgb ? __ldg(sc.rgb + 3 * g + 2) : 0.f, p[i].depth);
+    P.rec_unc[r] = sc.geo_unc ? __ldg(sc.geo_unc + g) : 0.f;
+    if (sc.sem_ids)
+      for (int l = 0; l < sc.k; ++l)
+        P.rec_sem[(size_t)r * sc.k + l] = make_int2(__ldg(sc.sem_ids + (size_t)g * sc.k + l),
+                                                    __float_as_int(__ldg(sc.sem_w + (size_t)g * sc.k + l)));
     P.dkeys[0][r] = ((unsigned long long)v << 31) | (unsigned long long)__float_as_uint(p[i].depth);
     P.dvals[0][r] = r;
   }

@@ -25,9 +25,6 @@ struct BwdArgs {
   const uint2 *ranges;
   const uint32_t *pvals;
   RecPtrs rec;
-  const float *rgb;
-  const int32_t *sem_ids;
-  const float *sem_w;
   int k, m, width, height, tiles_x;
   const float *tfinal;
   const uint32_t *nlast;
@@ -46,145 +43,162 @@ __device__ __forceinline__ float sign_code(uint32_t nz, uint32_t ng, int bit, fl
   return ((nz >> bit) & 1u) ? (((ng >> bit) & 1u) ? -s : s) : 0.f;
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-template <int TW, int TH, bool CODES>
-__global__ void __launch_bounds__(TW *TH) k_render_bwd(BwdArgs a) {
+// Per contributing (pixel, Gaussian) the thread forms NV values
+//   0..6  du, dv, da, db, dc, dopacity, ddepth   (2D gradients of the record)
+//   7..9  drgb                                   (colour of the Gaussian)
+//   10..  dsem_w (k values)
+// which a transposed warp reduction sums over the warp's 32 pixels; each lane
+// then adds one of the totals with a single scalar atomic.
+template <int TW, int TH, bool CODES, int NV, int PPT>
+__global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
+  using FP = Footprint<TW, TH, PPT>;
   extern __shared__ float4 smem4[];
   BatchSmem bs = batch_smem(smem4, a.k);
   __shared__ uint32_t s_maxnl;
-  // CODES: per-thread copy of its pixel's class sign words (odd stride)
-  uint32_t *myc = reinterpret_cast<uint32_t *>(bs.tail) + threadIdx.x * (2 * a.nwc + 1);
 
   const int tile = blockIdx.x;
   const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+  const int ox = tx * TW, oy = ty * TH;
   const uint2 rg = a.ranges[tile];
-  const int lx = threadIdx.x % TW, ly = threadIdx.x / TW;
-  const int px = tx * TW + lx, py = ty * TH + ly;
-  const bool inside = px < a.width && py < a.height;
-  const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
-  const size_t pix = inside ? (size_t)py * a.width + px : 0;
+  const int lx = FP::lx();
+  const int px = ox + lx;
+  const float fpx = (float)px + 0.5f;
   const int k = a.k;
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   // warp-uniform: every lane takes the same branches around the shuffles
   const bool has_dsem = CODES || a.d_sem != nullptr;
   float s_sem = 0.f;
 
-  float T = 1.f, dR = 0.f, dG = 0.f, dB = 0.f, dD = 0.f, dS = 0.f;
-  uint32_t nl = 0;
-  const float *dP = nullptr;
-  if (inside) {
-    T = a.tfinal[pix];
-    nl = a.nlast[pix];
-    if (CODES) {
-      const float ls = *a.loss_scale;
-      const float s_rgb = (float)(ls / (3.0 * a.npix)), s_d = (float)(ls / a.npix);
-      s_sem = (float)(ls / (a.npix * a.m));
-      const uint32_t *cp = a.codes + pix * code_words(a.nwc);
-      const uint32_t nz = cp[0], ng = cp[1 + a.nwc];
-      dR = sign_code(nz, ng, 0, s_rgb); dG = sign_code(nz, ng, 1, s_rgb); dB = sign_code(nz, ng, 2, s_rgb);
-      dD = sign_code(nz, ng, 3, s_d);
-      for (int wd = 0; wd < a.nwc; ++wd) { myc[wd] = cp[1 + wd]; myc[a.nwc + wd] = cp[2 + a.nwc + wd]; }
-    } else {
-      if (a.d_rgb) { dR = a.d_rgb[3 * pix]; dG = a.d_rgb[3 * pix + 1]; dB = a.d_rgb[3 * pix + 2]; }
-      if (a.d_depth) dD = a.d_depth[pix];
-      if (a.d_sil) dS = a.d_sil[pix];
-      if (a.d_sem) dP = a.d_sem + pix * a.m;
+  int py[PPT];
+  float fpy[PPT], T[PPT], acc[PPT], dR[PPT], dG[PPT], dB[PPT], dD[PPT], dS[PPT];
+  uint32_t nl[PPT];
+  const float *dP[PPT];
+  uint32_t *myc[PPT];  // CODES: this pixel's class sign words (odd stride)
+  uint32_t my_max = 0;
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    const int ly = FP::ly(i);
+    py[i] = oy + ly;
+    fpy[i] = (float)py[i] + 0.5f;
+    T[i] = 1.f; acc[i] = 0.f; dR[i] = dG[i] = dB[i] = dD[i] = dS[i] = 0.f;
+    nl[i] = 0;
+    dP[i] = nullptr;
+    myc[i] = reinterpret_cast<uint32_t *>(bs.tail) + (ly * TW + lx) * (2 * a.nwc + 1);
+    if (px < a.width && py[i] < a.height) {
+      const size_t pix = (size_t)py[i] * a.width + px;
+      T[i] = a.tfinal[pix];
+      nl[i] = a.nlast[pix];
+      if (CODES) {
+        const float ls = *a.loss_scale;
+        const float s_rgb = (float)(ls / (3.0 * a.npix)), s_d = (float)(ls / a.npix);
+        s_sem = (float)(ls / (a.npix * a.m));
+        const uint32_t *cp = a.codes + pix * code_words(a.nwc);
+        const uint32_t nz = cp[0], ng = cp[1 + a.nwc];
+        dR[i] = sign_code(nz, ng, 0, s_rgb); dG[i] = sign_code(nz, ng, 1, s_rgb); dB[i] = sign_code(nz, ng, 2, s_rgb);
+        dD[i] = sign_code(nz, ng, 3, s_d);
+        for (int wd = 0; wd < a.nwc; ++wd) { myc[i][wd] = cp[1 + wd]; myc[i][a.nwc + wd] = cp[2 + a.nwc + wd]; }
+      } else {
+        if (a.d_rgb) { dR[i] = a.d_rgb[3 * pix]; dG[i] = a.d_rgb[3 * pix + 1]; dB[i] = a.d_rgb[3 * pix + 2]; }
+        if (a.d_depth) dD[i] = a.d_depth[pix];
+        if (a.d_sil) dS[i] = a.d_sil[pix];
+        if (a.d_sem) dP[i] = a.d_sem + pix * a.m;
+      }
+      my_max = max(my_max, nl[i]);
     }
   }
   if (threadIdx.x == 0) s_maxnl = 0;
   __syncthreads();
-  if (nl) atomicMax(&s_maxnl, nl);
+  if (my_max) atomicMax(&s_maxnl, my_max);
   __syncthreads();
   const uint32_t maxnl = s_maxnl;
-  float acc = 0.f;  // sum over later contributors of w_j g_j
+  const int my_idx = reduced_index<NV>();
 
   for (uint32_t hi = rg.x + maxnl; hi > rg.x;) {
     const uint32_t lo = hi - min((uint32_t)kBatch, hi - rg.x);
     const int n = (int)(hi - lo);
     __syncthreads();
-    if ((int)threadIdx.x < n) load_batch_entry(a.rec, a.pvals[lo + threadIdx.x], threadIdx.x, k, bs, a.rgb,
-                                               a.sem_ids, a.sem_w, nullptr);
+    for (int t = threadIdx.x; t < n; t += FP::kThreads)
+      stage_record<TW, TH, PPT>(a.rec, a.pvals[lo + t], t, k, ox, oy, bs, has_dsem, false);
     __syncthreads();
-    for (int j = n - 1; j >= 0; --j) {
-      const uint32_t idx = lo - rg.x + j;
-      bool contrib = inside && idx < nl && rect_holds(bs.rect[j], px, py);
-      float alpha = 0.f, G = 0.f, araw = 0.f, dx = 0.f, dy = 0.f;
-      if (contrib) contrib = gauss_alpha(bs.uv[j], bs.co[j], fpx, fpy, alpha, G, araw, dx, dy);
-      float v[7];  // du, dv, da, db, dc, dopacity, ddepth
-      float vc[3];
-      float vs[kMaxK];
-#pragma unroll
-      for (int i = 0; i < 7; ++i) v[i] = 0.f;
-      vc[0] = vc[1] = vc[2] = 0.f;
-#pragma unroll
-      for (int l = 0; l < kMaxK; ++l) vs[l] = 0.f;
-      if (contrib) {
+    for (int base = ((n - 1) / 32) * 32; base >= 0; base -= 32) {
+      const int jj = base + (int)lane;
+      uint32_t vis = __ballot_sync(0xffffffffu, jj < n && ((bs.wmask[jj] >> warp) & 1u));
+      while (vis) {
+        const int bit = 31 - __clz(vis);
+        vis &= ~(1u << bit);
+        const int j = base + bit;
+        const uint32_t idx = lo - rg.x + j;
+        const int2 bb = bs.box[j];
+        const float2 uv = bs.uv[j];
         const float4 co = bs.co[j];
+        bool contrib[PPT];
+        float alpha[PPT], G[PPT], araw[PPT], dx[PPT], dy[PPT];
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < PPT; ++i) {
+          contrib[i] = idx < nl[i] && box_holds(bb, px, py[i]);
+          if (contrib[i]) contrib[i] = gauss_alpha(uv, co, fpx, fpy[i], alpha[i], G[i], araw[i], dx[i], dy[i]);
+          any = any || contrib[i];
+        }
+        if (!__any_sync(0xffffffffu, any)) continue;
+        float v[NV];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q] = 0.f;
         const float4 cdp = bs.cd[j];
-        const float om = 1.f - alpha;
-        const float Ti = T / om;
-        const float w = alpha * Ti;
-        float gi = dR * cdp.x + dG * cdp.y + dB * cdp.z + dD * cdp.w + dS;
-        if (has_dsem) {
-          const int *sid = bs.sid + j * k;
-          const float *sw = bs.sw + j * k;
-          float gs = 0.f;
+        const int2 *sp = bs.sem + j * k;
 #pragma unroll
-          for (int l = 0; l < kMaxK; ++l) {
-            if (l < k && (unsigned)sid[l] < (unsigned)a.m) {
-              float dp;
-              if (CODES) {
-                const int wd = sid[l] >> 5, bit = sid[l] & 31;
-                dp = sign_code(myc[wd], myc[a.nwc + wd], bit, s_sem);
-              } else {
-                dp = __ldg(dP + sid[l]);
+        for (int i = 0; i < PPT; ++i) {
+          if (!contrib[i]) continue;
+          const float om = 1.f - alpha[i];
+          const float Ti = T[i] / om;
+          const float w = alpha[i] * Ti;
+          float gi = dR[i] * cdp.x + dG[i] * cdp.y + dB[i] * cdp.z + dD[i] * cdp.w + dS[i];
+          if (has_dsem) {
+            float gs = 0.f;
+#pragma unroll
+            for (int l = 0; l < NV - 10; ++l) {
+              if (l < k) {
+                const int2 e = sp[l];
+                float dp = 0.f;
+                if ((unsigned)e.x < (unsigned)a.m) {
+                  if (CODES) {
+                    dp = sign_code(myc[i][e.x >> 5], myc[i][a.nwc + (e.x >> 5)], e.x & 31, s_sem);
+                  } else {
+                    dp = __ldg(dP[i] + e.x);
+                  }
+                }
+                v[10 + l] = fmaf(dp, w, v[10 + l]);
+                gs = fmaf(dp, __int_as_float(e.y), gs);
               }
-              vs[l] = dp * w;
-              gs = fmaf(dp, sw[l], gs);
             }
+            if (!a.sem_detach) gi += gs;
           }
-          if (!a.sem_detach) gi += gs;
-        }
-        vc[0] = dR * w; vc[1] = dG * w; vc[2] = dB * w;
-        v[6] = dD * w;
-        const float dalpha = Ti * gi - acc / om;
-        acc = fmaf(w, gi, acc);
-        T = Ti;
-        if (araw < kAlphaMax) {
-          v[5] = dalpha * G;
-          const float dpow = dalpha * araw;
-          v[2] = dpow * (-0.5f * dx * dx);
-          v[3] = dpow * (-dx * dy);
-          v[4] = dpow * (-0.5f * dy * dy);
-          v[0] = dpow * (-(co.x * dx + co.y * dy));
-          v[1] = dpow * (-(co.z * dy + co.y * dx));
-        }
-      }
-      if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-        for (int i = 0; i < 7; ++i) v[i] = warp_sum(v[i]);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) vc[i] = warp_sum(vc[i]);
-        if (has_dsem) {
-#pragma unroll
-          for (int l = 0; l < kMaxK; ++l)
-            if (l < k) vs[l] = warp_sum(vs[l]);
-        }
-        if (lane_id() == 0) {
-          const int r = bs.rec[j], g = bs.gid[j];
-          atomicAdd(a.grad2d + 2 * (size_t)r, make_float4(v[0], v[1], v[2], v[3]));
-          atomicAdd(a.grad2d + 2 * (size_t)r + 1, make_float4(v[4], v[5], v[6], 0.f));
-          if (a.g_rgb) {
-            atomicAdd(a.g_rgb + 3 * (size_t)g, vc[0]);
-            atomicAdd(a.g_rgb + 3 * (size_t)g + 1, vc[1]);
-            atomicAdd(a.g_rgb + 3 * (size_t)g + 2, vc[2]);
+          v[7] = fmaf(dR[i], w, v[7]); v[8] = fmaf(dG[i], w, v[8]); v[9] = fmaf(dB[i], w, v[9]);
+          v[6] = fmaf(dD[i], w, v[6]);
+          const float dalpha = Ti * gi - acc[i] / om;
+          acc[i] = fmaf(w, gi, acc[i]);
+          T[i] = Ti;
+          if (araw[i] < kAlphaMax) {
+            v[5] = fmaf(dalpha, G[i], v[5]);
+            const float dpow = dalpha * araw[i];
+            const float ddx = dx[i], ddy = dy[i];
+            v[2] = fmaf(dpow, -0.5f * ddx * ddx, v[2]);
+            v[3] = fmaf(dpow, -ddx * ddy, v[3]);
+            v[4] = fmaf(dpow, -0.5f * ddy * ddy, v[4]);
+            v[0] = fmaf(dpow, -(co.x * ddx + co.y * ddy), v[0]);
+            v[1] = fmaf(dpow, -(co.z * ddy + co.y * ddx), v[1]);
           }
-          if (has_dsem && a.g_sem_w)
-            for (int l = 0; l < k; ++l) atomicAdd(a.g_sem_w + (size_t)g * k + l, vs[l]);
+        }
+        const float tot = warp_reduce_scatter<NV>(v);
+        if (my_idx == (int)lane || NV == 32) {
+          // lanes 0..15 (NV = 16) or all lanes (NV = 32) own one value each
+          if (my_idx < 7) {
+            if (tot != 0.f) atomicAdd(reinterpret_cast<float *>(a.grad2d) + 8 * (size_t)bs.rec[j] + my_idx, tot);
+          } else if (my_idx < 10) {
+            if (a.g_rgb && tot != 0.f) atomicAdd(a.g_rgb + 3 * (size_t)bs.gid[j] + (my_idx - 7), tot);
+          } else if (my_idx < 10 + k) {
+            if (has_dsem && a.g_sem_w && tot != 0.f) atomicAdd(a.g_sem_w + (size_t)bs.gid[j] * k + (my_idx - 10), tot);
+          }
         }
       }
     }
@@ -198,19 +212,29 @@ __global__ void k_zero_grad2d(float4 *g, const Counters *cnt, uint32_t rcap) {
     g[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-template <int TW, int TH, bool CODES>
+template <int TW, int TH, bool CODES, int NV, int PPT>
 static cudaError_t launch_bwd_shape(const BwdArgs &a, int grid, size_t smem, cudaStream_t s) {
-  k_render_bwd<TW, TH, CODES><<<grid, TW * TH, smem, s>>>(a);
+  k_render_bwd<TW, TH, CODES, NV, PPT><<<grid, TW * TH / PPT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <bool CODES>
-static cudaError_t dispatch_bwd(int tw, int th, const BwdArgs &a, int grid, size_t smem, cudaStream_t s) {
-  if (tw == 16 && th == 16) return launch_bwd_shape<16, 16, CODES>(a, grid, smem, s);
-  if (tw == 16 && th == 8) return launch_bwd_shape<16, 8, CODES>(a, grid, smem, s);
-  if (tw == 8 && th == 8) return launch_bwd_shape<8, 8, CODES>(a, grid, smem, s);
-  if (tw == 32 && th == 8) return launch_bwd_shape<32, 8, CODES>(a, grid, smem, s);
+template <bool CODES, int NV, int PPT>
+static cudaError_t dispatch_bwd_shape(int tw, int th, const BwdArgs &a, int grid, size_t smem, cudaStream_t s) {
+  if (tw == 16 && th == 16) return launch_bwd_shape<16, 16, CODES, NV, PPT>(a, grid, smem, s);
+  if (tw == 16 && th == 8) return launch_bwd_shape<16, 8, CODES, NV, PPT>(a, grid, smem, s);
+  if (tw == 8 && th == 8) return launch_bwd_shape<8, 8, CODES, NV, PPT>(a, grid, smem, s);
+  if (tw == 32 && th == 8) return launch_bwd_shape<32, 8, CODES, NV, PPT>(a, grid, smem, s);
   return cudaErrorInvalidConfiguration;
+}
+
+template <bool CODES>
+static cudaError_t dispatch_bwd(const Layout &L, const BwdArgs &a, int grid, size_t smem, cudaStream_t s) {
+  if (L.ppt == 2) {
+    if (a.k <= 6) return dispatch_bwd_shape<CODES, 16, 2>(L.tile_w, L.tile_h, a, grid, smem, s);
+    return dispatch_bwd_shape<CODES, 32, 2>(L.tile_w, L.tile_h, a, grid, smem, s);
+  }
+  if (a.k <= 6) return dispatch_bwd_shape<CODES, 16, 1>(L.tile_w, L.tile_h, a, grid, smem, s);
+  return dispatch_bwd_shape<CODES, 32, 1>(L.tile_w, L.tile_h, a, grid, smem, s);
 }
 
 cudaError_t launch_render_bwd(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc, const float *d_rgb,
@@ -223,7 +247,6 @@ cudaError_t launch_render_bwd(const Layout &L, const WsPtrs &P, int pbuf, const 
   a.ranges = P.ranges;
   a.pvals = P.pvals[pbuf];
   a.rec = rec_ptrs(P);
-  a.rgb = sc.rgb; a.sem_ids = sc.sem_ids; a.sem_w = sc.sem_w;
   a.k = sc.k; a.m = sc.m;
   a.width = L.cam0_w; a.height = L.cam0_h;
   a.tiles_x = (L.cam0_w + L.tile_w - 1) / L.tile_w;
@@ -241,10 +264,10 @@ cudaError_t launch_render_bwd(const Layout &L, const WsPtrs &P, int pbuf, const 
     a.loss_scale = loss_scale;
     a.npix = (double)L.npix;
     const size_t smem = batch_smem_bytes(sc.k) + (size_t)L.tile_w * L.tile_h * (2 * L.nwc + 1) * 4;
-    return dispatch_bwd<true>(L.tile_w, L.tile_h, a, grid, smem, s);
+    return dispatch_bwd<true>(L, a, grid, smem, s);
   }
   const size_t smem = batch_smem_bytes(sc.k);
-  return dispatch_bwd<false>(L.tile_w, L.tile_h, a, grid, smem, s);
+  return dispatch_bwd<false>(L, a, grid, smem, s);
 }
 
 // ---------------------------------------------------------------------------

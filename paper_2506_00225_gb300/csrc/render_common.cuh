@@ -1,6 +1,7 @@
 // render_common.cuh -- pieces shared by the forward, backward and candidate
-// blend kernels: shared-memory batch staging of a tile's sorted Gaussians,
-// the pixel-rectangle test and the per-pixel opacity rule.
+// blend kernels: warp footprints inside a tile, shared-memory batch staging
+// of a tile's sorted Gaussians with per-warp visibility masks, the per-pixel
+// opacity rule and a transposed warp reduction.
 #pragma once
 
 #include "gs_internal.cuh"
@@ -13,32 +14,62 @@ constexpr float kAlphaMin = 1.0f / 255.0f;       // skip threshold
 constexpr float kAlphaMax = 0.99f;               // opacity cap
 constexpr size_t kSmemBudget = 112 * 1024;       // per CTA: two 256-thread CTAs per SM
 
+// Each warp owns an 8 x (4 PPT) pixel block of the tile; lane l sits at
+// column l % 8 and rows l / 8 + 4 i (i < PPT) of its block, so a thread
+// handles PPT pixels that share every staged load.
+template <int TW, int TH, int PPT = 1>
+struct Footprint {
+  static constexpr int kPix = TW * TH;
+  static constexpr int kThreads = kPix / PPT;
+  static constexpr int kWarps = kThreads / 32;
+  static constexpr int kBH = 4 * PPT;  // warp block height
+  static constexpr int kWX = TW / 8;   // warp blocks per tile row
+  static_assert(TW % 8 == 0 && TH % kBH == 0, "tile must be a multiple of the warp block");
+  // tile-local pixel i of this thread
+  __device__ static int lx() { return ((threadIdx.x >> 5) % kWX) * 8 + (threadIdx.x & 7); }
+  __device__ static int ly(int i) { return ((threadIdx.x >> 5) / kWX) * kBH + ((threadIdx.x & 31) >> 3) + 4 * i; }
+  // bit w set when box [bx0,bx1] x [by0,by1] (tile-local pixels) meets warp w's block
+  __device__ static uint32_t warp_mask(int bx0, int bx1, int by0, int by1) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const int x0 = (w % kWX) * 8, y0 = (w / kWX) * kBH;
+      if (bx0 <= x0 + 7 && bx1 >= x0 && by0 <= y0 + kBH - 1 && by1 >= y0) m |= 1u << w;
+    }
+    return m;
+  }
+};
+
 struct RecPtrs {
   const float2 *uv;
-  const float4 *co;
-  const float *depth;
-  const short4 *rect;
+  const float4 *co;    // conic a, b, c, opacity
+  const short4 *box;   // alpha box
+  const float4 *cd;    // r, g, b, depth
+  const float *unc;
+  const int2 *sem;     // [k] (id, weight bits)
   const int32_t *gid;
 };
 
-inline RecPtrs rec_ptrs(const WsPtrs &P) { return RecPtrs{P.rec_uv, P.rec_conic, P.rec_depth, P.rec_rect, P.rec_gid}; }
+inline RecPtrs rec_ptrs(const WsPtrs &P) {
+  return RecPtrs{P.rec_uv, P.rec_conic, P.rec_box, P.rec_cd, P.rec_unc, P.rec_sem, P.rec_gid};
+}
 
-// Shared-memory view of one staged batch (struct-of-arrays) plus the tail
-// region after it (per-pixel class accumulators).
+// Shared-memory view of one staged batch (struct of arrays) plus the tail
+// region after it.
 struct BatchSmem {
-  float4 *co;   // conic a, b, c, opacity
-  float4 *cd;   // colour r, g, b, depth (candidates: uncertainty in .x)
-  float2 *uv;   // 2D mean
-  int2 *rect;   // packed pixel rectangle (x0 | x1 << 16, y0 | y1 << 16)
+  float4 *co;
+  float4 *cd;      // r, g, b, depth (candidates: uncertainty in .x)
+  float2 *uv;
+  int2 *box;       // packed alpha box (x0 | x1 << 16, y0 | y1 << 16), image pixels
+  int2 *sem;       // [kBatch][k]
+  uint32_t *wmask; // warps whose block meets the box
   int *gid;
   int *rec;
-  int *sid;     // [kBatch][k] class ids
-  float *sw;    // [kBatch][k] class weights
   float *tail;
 };
 
 __host__ __device__ inline size_t batch_smem_bytes(int k) {
-  size_t b = (size_t)kBatch * (16 + 16 + 8 + 8 + 4 + 4) + (size_t)kBatch * k * 8;
+  size_t b = (size_t)kBatch * (16 + 16 + 8 + 8 + 4 + 4 + 4) + (size_t)kBatch * k * 8;
   return (b + 15) & ~(size_t)15;
 }
 
@@ -48,66 +79,118 @@ __device__ __forceinline__ BatchSmem batch_smem(float4 *base, int k) {
   s.co = reinterpret_cast<float4 *>(p); p += kBatch * 16;
   s.cd = reinterpret_cast<float4 *>(p); p += kBatch * 16;
   s.uv = reinterpret_cast<float2 *>(p); p += kBatch * 8;
-  s.rect = reinterpret_cast<int2 *>(p); p += kBatch * 8;
+  s.box = reinterpret_cast<int2 *>(p); p += kBatch * 8;
+  s.sem = reinterpret_cast<int2 *>(p); p += (size_t)kBatch * k * 8;
+  s.wmask = reinterpret_cast<uint32_t *>(p); p += kBatch * 4;
   s.gid = reinterpret_cast<int *>(p); p += kBatch * 4;
-  s.rec = reinterpret_cast<int *>(p); p += kBatch * 4;
-  s.sid = reinterpret_cast<int *>(p); p += kBatch * k * 4;
-  s.sw = reinterpret_cast<float *>(p);
+  s.rec = reinterpret_cast<int *>(p);
   s.tail = reinterpret_cast<float *>(reinterpret_cast<char *>(base) + batch_smem_bytes(k));
   return s;
 }
 
-// Stage record r in batch slot `slot`.  If unc != nullptr the .x of the
-// colour/depth slot carries unc[gid] instead of red.
-__device__ __forceinline__ void load_batch_entry(const RecPtrs &rec, uint32_t r, int slot, int k,
-                                                 const BatchSmem &bs, const float *__restrict__ rgb,
-                                                 const int32_t *__restrict__ sem_ids,
-                                                 const float *__restrict__ sem_w, const float *__restrict__ unc) {
-  const int g = __ldg(rec.gid + r);
+// Stage record r in batch slot `slot` of the tile whose top-left pixel is
+// (ox, oy).  With use_unc the .x of the colour slot carries the uncertainty.
+template <int TW, int TH, int PPT = 1>
+__device__ __forceinline__ void stage_record(const RecPtrs &rec, uint32_t r, int slot, int k, int ox, int oy,
+                                             const BatchSmem &bs, bool use_sem, bool use_unc) {
+  const short4 b = __ldg(rec.box + r);
   bs.uv[slot] = __ldg(rec.uv + r);
   bs.co[slot] = __ldg(rec.co + r);
-  const short4 rc = __ldg(rec.rect + r);
-  bs.rect[slot] = make_int2((int)(uint16_t)rc.x | ((int)(uint16_t)rc.y << 16),
-                            (int)(uint16_t)rc.z | ((int)(uint16_t)rc.w << 16));
-  const float d = __ldg(rec.depth + r);
-  if (unc) {
-    bs.cd[slot] = make_float4(__ldg(unc + g), 0.f, 0.f, d);
-  } else {
-    bs.cd[slot] = make_float4(__ldg(rgb + 3 * g), __ldg(rgb + 3 * g + 1), __ldg(rgb + 3 * g + 2), d);
-  }
-  bs.gid[slot] = g;
+  float4 cd = __ldg(rec.cd + r);
+  if (use_unc) cd.x = __ldg(rec.unc + r);
+  bs.cd[slot] = cd;
+  bs.box[slot] = make_int2((int)(uint16_t)b.x | ((int)(uint16_t)b.y << 16),
+                           (int)(uint16_t)b.z | ((int)(uint16_t)b.w << 16));
+  bs.wmask[slot] = b.x > b.y ? 0u : Footprint<TW, TH, PPT>::warp_mask(b.x - ox, b.y - ox, b.z - oy, b.w - oy);
+  bs.gid[slot] = __ldg(rec.gid + r);
   bs.rec[slot] = (int)r;
-  if (sem_ids) {
-    for (int l = 0; l < k; ++l) {
-      bs.sid[slot * k + l] = __ldg(sem_ids + (size_t)g * k + l);
-      bs.sw[slot * k + l] = __ldg(sem_w + (size_t)g * k + l);
-    }
+  if (use_sem) {
+    const int2 *src = rec.sem + (size_t)r * k;
+    for (int l = 0; l < k; ++l) bs.sem[slot * k + l] = __ldg(src + l);
   }
 }
 
-__device__ __forceinline__ bool rect_holds(int2 rr, int px, int py) {
-  const int x0 = rr.x & 0xffff, x1 = (int)((unsigned)rr.x >> 16);
-  const int y0 = rr.y & 0xffff, y1 = (int)((unsigned)rr.y >> 16);
-  return px >= x0 && px <= x1 && py >= y0 && py <= y1;
+// Pixel inside the packed box (x0 | x1 << 16, y0 | y1 << 16).
+__device__ __forceinline__ bool box_holds(int2 bb, int px, int py) {
+  const int x0 = bb.x & 0xffff, x1 = (int)((unsigned)bb.x >> 16);
+  const int y0 = bb.y & 0xffff, y1 = (int)((unsigned)bb.y >> 16);
+  return (unsigned)(px - x0) <= (unsigned)(x1 - x0) && (unsigned)(py - y0) <= (unsigned)(y1 - y0);
 }
 
 // The per-pixel opacity of one Gaussian at pixel centre (fpx, fpy):
-// alpha = min(0.99, o exp(-0.5 d^T conic d)), d = mean - centre.  Evaluated
-// with one rounding per operation (no contraction) so the skip / stop
-// decisions match a plain IEEE evaluation of the same expression.  Returns
-// false when the Gaussian is skipped (power > 0 or alpha < 1/255).
+// alpha = min(0.99, o exp(-0.5 d^T conic d)), d = mean - centre, evaluated
+// in a fixed fused order (the same instructions in every kernel, so the
+// forward, backward and candidate kernels take identical decisions).
+// Returns false when skipped (power > 0 or alpha < 1/255).
 __device__ __forceinline__ bool gauss_alpha(float2 uv, float4 co, float fpx, float fpy, float &alpha, float &G,
                                             float &araw, float &dx, float &dy) {
   dx = __fsub_rn(uv.x, fpx);
   dy = __fsub_rn(uv.y, fpy);
-  const float t1 = __fmul_rn(dx, dx), t2 = __fmul_rn(dy, dy), t3 = __fmul_rn(dx, dy);
-  const float s = __fadd_rn(__fmul_rn(co.x, t1), __fmul_rn(co.z, t2));
-  const float power = __fsub_rn(__fmul_rn(-0.5f, s), __fmul_rn(co.y, t3));
+  const float q = __fmaf_rn(co.x, __fmul_rn(dx, dx), __fmul_rn(co.z, __fmul_rn(dy, dy)));
+  const float power = __fmaf_rn(-0.5f, q, -__fmul_rn(co.y, __fmul_rn(dx, dy)));
   if (power > 0.f) return false;
-  G = expf(power);
+  G = __expf(power);
   araw = __fmul_rn(co.w, G);
   alpha = araw < kAlphaMax ? araw : kAlphaMax;
   return !(alpha < kAlphaMin);
+}
+
+// Transposed warp sum of NV values per lane (NV = 16 or 32): exchange halves
+// of the value set at each butterfly level, so NV - 1 (+1 for NV = 16)
+// shuffles replace 5 NV.  Afterwards lane l holds the warp total of value
+// reduced_index<NV>() (l & 15 for NV = 16, l for NV = 32).
+template <int NV>
+__device__ __forceinline__ float warp_reduce_scatter(float (&v)[NV]) {
+  const uint32_t lane = lane_id();
+  if constexpr (NV == 32) {
+    const bool hi = lane & 16;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const float send = hi ? v[i] : v[i + 16];
+      const float keep = hi ? v[i + 16] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+  }
+  {
+    const bool hi = lane & 8;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float send = hi ? v[i] : v[i + 8];
+      const float keep = hi ? v[i + 8] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+  }
+  {
+    const bool hi = lane & 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float send = hi ? v[i] : v[i + 4];
+      const float keep = hi ? v[i + 4] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+  }
+  {
+    const bool hi = lane & 2;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const float send = hi ? v[i] : v[i + 2];
+      const float keep = hi ? v[i + 2] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+  }
+  {
+    const bool hi = lane & 1;
+    const float send = hi ? v[0] : v[1];
+    const float keep = hi ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+  }
+  if constexpr (NV == 16) v[0] += __shfl_xor_sync(0xffffffffu, v[0], 16);
+  return v[0];
+}
+
+template <int NV>
+__device__ __forceinline__ int reduced_index() {
+  return NV == 32 ? (int)lane_id() : (int)(lane_id() & 15);
 }
 
 // Class chunking of the per-pixel accumulator: the stride is odd so that
@@ -131,9 +214,6 @@ struct FwdArgs {
   const uint2 *ranges;
   const uint32_t *pvals;
   RecPtrs rec;
-  const float *rgb;
-  const int32_t *sem_ids;
-  const float *sem_w;
   int k, m, width, height, tiles_x;
   float *rgb_out, *depth_out, *sil_out, *sem;
   float *tfinal;
@@ -142,7 +222,7 @@ struct FwdArgs {
   // fused mean-L1 mode
   const float *t_rgb, *t_depth, *t_sem;
   uint32_t *codes;   // per pixel: 2 planes (nonzero, negative) x (1 head word + nwc class words)
-  int nwc;           // class words per plane = ceil(m / 32) when t_sem is given, else 0
+  int nwc;           // class words per plane = ceil(m / 32)
   double *lpart;     // per tile: sum|d rgb|, sum|d depth|, sum|d sem|
   Counters *counters;
 };

@@ -1,32 +1,48 @@
 // render_fwd.cu -- forward tile blend: Eq. 1 (colour, depth, silhouette) and
 // Eq. 3 (sparse top-k semantics), supplement "Sparse Rendering".
 //
-// One CTA per screen tile, one thread per pixel.  The tile's depth-sorted
-// pair range is walked in batches staged in shared memory; each thread
-// composites the Gaussians whose pixel rectangle holds its pixel, front to
-// back, and stops before the Gaussian that would take the transmittance
-// below 1e-4.  The CTA leaves the loop when every pixel is done
-// (__syncthreads_count).  Semantic probabilities are scattered into a
-// per-pixel M-class accumulator in shared memory (k adds per contributor
-// instead of M, the point of the sparse representation), then written out
-// with coalesced stores.  When M does not fit the shared-memory budget the
-// classes are processed in chunks of 32-class multiples, recompositing per
-// chunk.
+// One CTA per screen tile, one thread per pixel, each warp an 8 x 4 pixel
+// block.  The tile's depth-sorted pair range is walked in batches staged in
+// shared memory; for every staged Gaussian the stager records which warps'
+// blocks meet its alpha box (the pixels where alpha can reach 1/255), and
+// each warp visits only those Gaussians.  A thread composites a Gaussian
+// whose box holds its pixel, front to back, and stops before the Gaussian
+// that would take the transmittance below 1e-4; the CTA leaves when every
+// pixel is done (__syncthreads_count).  Semantic probabilities are scattered
+// into a per-pixel M-class accumulator in shared memory (k adds per
+// contributor instead of M, the point of the sparse representation), then
+// written out with coalesced stores.  When M does not fit, classes are
+// processed in chunks of 32-class multiples, recompositing per chunk.
 //
 // Fused mean-L1 mode (L1 = true): the rendered colour, depth and semantic
 // distribution are compared with the targets inside the tile; the kernel
 // keeps per-tile sums of |rendered - target| and, per value, two bits
 // (nonzero, negative) of the sign of the difference for the adjoint.  The
-// semantic map itself need not be written.
+// tile's target rows are prefetched into L2 with bulk-copy prefetches when
+// the CTA starts, so the comparison reads them from L2.
 #include "gs_internal.cuh"
 #include "render_common.cuh"
 
 namespace gs {
 
-template <int TW, int TH, bool L1>
-__global__ void __launch_bounds__(TW *TH) k_render_fwd(FwdArgs a) {
-  constexpr int THREADS = TW * TH;
-  constexpr int WARPS = THREADS / 32;
+// L2 prefetch of [p, p + bytes) clipped to 16-byte granules inside
+// [base, base + total).
+__device__ __forceinline__ void prefetch_l2(const void *base, size_t total, const void *p, size_t bytes) {
+  const uintptr_t b = reinterpret_cast<uintptr_t>(base);
+  const uintptr_t lo = (reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15;
+  uintptr_t hi = (reinterpret_cast<uintptr_t>(p) + bytes) & ~(uintptr_t)15;
+  const uintptr_t end = (b + total) & ~(uintptr_t)15;
+  if (hi > end) hi = end;
+  if (lo < b || hi <= lo) return;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((uint32_t)(hi - lo)) : "memory");
+}
+
+template <int TW, int TH, bool L1, int PPT>
+__global__ void __launch_bounds__(TW *TH / PPT) k_render_fwd(FwdArgs a) {
+  using FP = Footprint<TW, TH, PPT>;
+  constexpr int THREADS = FP::kThreads;
+  constexpr int WARPS = FP::kWarps;
+  constexpr int NPIX = FP::kPix;
   extern __shared__ float4 smem4[];
   BatchSmem bs = batch_smem(smem4, a.k);
   float *sP = bs.tail;
@@ -34,69 +50,119 @@ __global__ void __launch_bounds__(TW *TH) k_render_fwd(FwdArgs a) {
 
   const int tile = blockIdx.x;
   const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+  const int ox = tx * TW, oy = ty * TH;
   const uint2 rg = a.ranges[tile];
-  const int lx = threadIdx.x % TW, ly = threadIdx.x / TW;
-  const int px = tx * TW + lx, py = ty * TH + ly;
-  const bool inside = px < a.width && py < a.height;
-  const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+  const int lx = FP::lx();
+  const int px = ox + lx;
+  const float fpx = (float)px + 0.5f;
+  int py[PPT];
+  bool inside[PPT];
+  float fpy[PPT];
+  float *myP[PPT];
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    const int ly = FP::ly(i);
+    py[i] = oy + ly;
+    inside[i] = px < a.width && py[i] < a.height;
+    fpy[i] = (float)py[i] + 0.5f;
+    myP[i] = sP + (ly * TW + lx) * a.mstride;
+  }
   const bool acc_sem = a.sem != nullptr || (L1 && a.t_sem != nullptr);
-  float *myP = sP + threadIdx.x * a.mstride;
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   const int cw = code_words(a.nwc);
+  const int k = a.k;
   float l1_sem = 0.f;
 
-  float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, cd = 0.f;
-  uint32_t last = 0, ncontrib = 0;
+  if (L1 && a.t_sem && (int)threadIdx.x < TH) {
+    const int y = oy + (int)threadIdx.x;
+    if (y < a.height) {
+      const int vw = min(TW, a.width - ox);
+      prefetch_l2(a.t_sem, (size_t)a.width * a.height * a.m * 4, a.t_sem + ((size_t)y * a.width + ox) * a.m,
+                  (size_t)vw * a.m * 4);
+    }
+  }
+
+  float T[PPT], cr[PPT], cg[PPT], cb[PPT], cd[PPT];
+  uint32_t last[PPT];
+  uint32_t ncontrib = 0;
   for (int c = 0; c < a.nchunks; ++c) {
     const int c_lo = c * a.mchunk, c_hi = min(a.m, c_lo + a.mchunk);
     const int mc = c_hi - c_lo;
-    if (acc_sem)
-      for (int i = 0; i < mc; ++i) myP[i] = 0.f;
-    T = 1.f; cr = cg = cb = cd = 0.f; last = 0; ncontrib = 0;
-    bool done = !inside;
+    bool done[PPT];
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+      if (acc_sem)
+        for (int q = 0; q < mc; ++q) myP[i][q] = 0.f;
+      T[i] = 1.f; cr[i] = cg[i] = cb[i] = cd[i] = 0.f; last[i] = 0;
+      done[i] = !inside[i];
+    }
+    ncontrib = 0;
     for (uint32_t b = rg.x; b < rg.y; b += kBatch) {
       const int n = (int)min((uint32_t)kBatch, rg.y - b);
       __syncthreads();
-      if ((int)threadIdx.x < n) load_batch_entry(a.rec, a.pvals[b + threadIdx.x], threadIdx.x, a.k, bs, a.rgb,
-                                                 a.sem_ids, a.sem_w, nullptr);
+      for (int t = threadIdx.x; t < n; t += THREADS)
+        stage_record<TW, TH, PPT>(a.rec, a.pvals[b + t], t, k, ox, oy, bs, acc_sem, false);
       __syncthreads();
-      if (!done) {
-        for (int j = 0; j < n; ++j) {
-          const int2 rr = bs.rect[j];
-          if (!rect_holds(rr, px, py)) continue;
-          const float2 uv = bs.uv[j];
-          const float4 co = bs.co[j];
-          float alpha, G, araw, dx, dy;
-          if (!gauss_alpha(uv, co, fpx, fpy, alpha, G, araw, dx, dy)) continue;
-          const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
-          if (Tn < kTStop) { done = true; break; }
-          const float w = __fmul_rn(alpha, T);
-          const float4 cdp = bs.cd[j];
-          cr = fmaf(w, cdp.x, cr); cg = fmaf(w, cdp.y, cg); cb = fmaf(w, cdp.z, cb); cd = fmaf(w, cdp.w, cd);
-          if (acc_sem) {
-            const int *sid = bs.sid + j * a.k;
-            const float *sw = bs.sw + j * a.k;
-            for (int l = 0; l < a.k; ++l) {
-              const int id = sid[l] - c_lo;
-              if ((unsigned)id < (unsigned)mc) myP[id] = fmaf(w, sw[l], myP[id]);
+      bool all_done = true;
+#pragma unroll
+      for (int i = 0; i < PPT; ++i) all_done = all_done && done[i];
+      if (!__all_sync(0xffffffffu, all_done)) {
+        for (int base = 0; base < n; base += 32) {
+          const int jj = base + (int)lane;
+          uint32_t vis = __ballot_sync(0xffffffffu, jj < n && ((bs.wmask[jj] >> warp) & 1u));
+          while (vis) {
+            const int j = base + __ffs(vis) - 1;
+            vis &= vis - 1;
+            const int2 bb = bs.box[j];
+            bool hold[PPT];
+            bool any = false;
+#pragma unroll
+            for (int i = 0; i < PPT; ++i) {
+              hold[i] = !done[i] && box_holds(bb, px, py[i]);
+              any = any || hold[i];
+            }
+            if (!any) continue;
+            const float2 uv = bs.uv[j];
+            const float4 co = bs.co[j];
+            const float4 cdp = bs.cd[j];
+#pragma unroll
+            for (int i = 0; i < PPT; ++i) {
+              if (!hold[i]) continue;
+              float alpha, G, araw, dx, dy;
+              if (!gauss_alpha(uv, co, fpx, fpy[i], alpha, G, araw, dx, dy)) continue;
+              const float Tn = __fmul_rn(T[i], __fsub_rn(1.f, alpha));
+              if (Tn < kTStop) { done[i] = true; continue; }
+              const float w = __fmul_rn(alpha, T[i]);
+              cr[i] = fmaf(w, cdp.x, cr[i]); cg[i] = fmaf(w, cdp.y, cg[i]); cb[i] = fmaf(w, cdp.z, cb[i]);
+              cd[i] = fmaf(w, cdp.w, cd[i]);
+              if (acc_sem) {
+                const int2 *sp = bs.sem + j * k;
+                for (int l = 0; l < k; ++l) {
+                  const int2 e = sp[l];
+                  const int id = e.x - c_lo;
+                  if ((unsigned)id < (unsigned)mc) myP[i][id] = fmaf(w, __int_as_float(e.y), myP[i][id]);
+                }
+              }
+              T[i] = Tn;
+              last[i] = b - rg.x + j + 1;
+              ++ncontrib;
             }
           }
-          T = Tn;
-          last = b - rg.x + j + 1;
-          ++ncontrib;
         }
       }
-      if (__syncthreads_count(done) == THREADS) break;
+      bool my_done = true;
+#pragma unroll
+      for (int i = 0; i < PPT; ++i) my_done = my_done && done[i];
+      if (__syncthreads_count(my_done) == THREADS) break;
     }
     if (acc_sem) {
       __syncthreads();
-      const int x0 = tx * TW;
-      const int vw = min(TW, a.width - x0);
+      const int vw = min(TW, a.width - ox);
       if (a.sem) {
         for (int r = 0; r < TH; ++r) {
-          const int y = ty * TH + r;
+          const int y = oy + r;
           if (y >= a.height) break;
-          float *dst = a.sem + ((size_t)y * a.width + x0) * a.m + c_lo;
+          float *dst = a.sem + ((size_t)y * a.width + ox) * a.m + c_lo;
           const float *src = sP + (r * TW) * a.mstride;
           for (int e = threadIdx.x; e < vw * mc; e += THREADS) {
             const int p = e / mc, cl = e - p * mc;
@@ -105,25 +171,49 @@ __global__ void __launch_bounds__(TW *TH) k_render_fwd(FwdArgs a) {
         }
       }
       if (L1 && a.t_sem) {
-        // one warp per (pixel, 32-class word): coalesced target reads, ballots
-        // assemble the sign words
-        const int w_lo = c_lo >> 5, nwt = (c_hi + 31) / 32 - w_lo;
-        for (int task = warp; task < THREADS * nwt; task += WARPS) {
-          const int p = task / nwt, wd = w_lo + task % nwt;
-          const int qx = x0 + p % TW, qy = ty * TH + p / TW;
-          if (qx >= a.width || qy >= a.height) continue;
-          const size_t pix = (size_t)qy * a.width + qx;
-          const int mcl = wd * 32 + (int)lane;
-          const bool valid = mcl < c_hi;
-          float d = 0.f;
-          if (valid) d = sP[p * a.mstride + (mcl - c_lo)] - __ldcs(a.t_sem + pix * a.m + mcl);
-          const uint32_t nz = __ballot_sync(0xffffffffu, d != 0.f);
-          const uint32_t ng = __ballot_sync(0xffffffffu, d < 0.f);
-          l1_sem += fabsf(d);
-          if (lane == 0) {
-            uint32_t *cp = a.codes + pix * cw;
-            cp[1 + wd] = nz;
-            cp[1 + a.nwc + 1 + wd] = ng;
+        // each warp takes kG pixels x kWG 32-class words per round: all kG*kWG
+        // coalesced target reads (L2 hits after the prefetch) are issued before
+        // any is consumed; ballots assemble the sign words
+        constexpr int kG = 4, kWG = 4;
+        const int w_lo = c_lo >> 5, w_hi = (c_hi + 31) >> 5;
+        for (int p0 = (int)warp * kG; p0 < NPIX; p0 += WARPS * kG) {
+          for (int wb = w_lo; wb < w_hi; wb += kWG) {
+            float tv[kG][kWG];
+            const float *row[kG];
+            bool okp[kG];
+#pragma unroll
+            for (int g = 0; g < kG; ++g) {
+              const int p = p0 + g;
+              const int qx = ox + p % TW, qy = oy + p / TW;
+              okp[g] = qx < a.width && qy < a.height;
+              row[g] = a.t_sem + (okp[g] ? ((size_t)qy * a.width + qx) * a.m : 0);
+#pragma unroll
+              for (int u = 0; u < kWG; ++u) {
+                const int mcl = (wb + u) * 32 + (int)lane;
+                tv[g][u] = (okp[g] && mcl < c_hi) ? __ldcs(row[g] + mcl) : 0.f;
+              }
+            }
+#pragma unroll
+            for (int g = 0; g < kG; ++g) {
+              if (!okp[g]) continue;  // uniform over the warp
+              const int p = p0 + g;
+#pragma unroll
+              for (int u = 0; u < kWG; ++u) {
+                const int wd = wb + u;
+                if (wd >= w_hi) break;
+                const int mcl = wd * 32 + (int)lane;
+                float d = 0.f;
+                if (mcl < c_hi) d = sP[p * a.mstride + (mcl - c_lo)] - tv[g][u];
+                const uint32_t nz = __ballot_sync(0xffffffffu, d != 0.f);
+                const uint32_t ng = __ballot_sync(0xffffffffu, d < 0.f);
+                l1_sem += fabsf(d);
+                if (lane == 0) {
+                  uint32_t *cp = a.codes + (size_t)((row[g] - a.t_sem) / a.m) * cw;
+                  cp[1 + wd] = nz;
+                  cp[2 + a.nwc + wd] = ng;
+                }
+              }
+            }
           }
         }
       }
@@ -131,23 +221,25 @@ __global__ void __launch_bounds__(TW *TH) k_render_fwd(FwdArgs a) {
     }
   }
   {
-    // diagnostics: total contributions (one atomic per CTA)
+    // diagnostics: total contributions (one atomic per warp)
     uint32_t nc = ncontrib;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nc += __shfl_xor_sync(0xffffffffu, nc, o);
     if (lane == 0 && nc) atomicAdd(&a.counters->n_contrib, nc);
   }
   float l1_rgb = 0.f, l1_d = 0.f;
-  if (inside) {
-    const size_t pix = (size_t)py * a.width + px;
-    if (a.rgb_out) { a.rgb_out[3 * pix] = cr; a.rgb_out[3 * pix + 1] = cg; a.rgb_out[3 * pix + 2] = cb; }
-    if (a.depth_out) a.depth_out[pix] = cd;
-    if (a.sil_out) a.sil_out[pix] = 1.f - T;
-    a.tfinal[pix] = T;
-    a.nlast[pix] = last;
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    if (!inside[i]) continue;
+    const size_t pix = (size_t)py[i] * a.width + px;
+    if (a.rgb_out) { a.rgb_out[3 * pix] = cr[i]; a.rgb_out[3 * pix + 1] = cg[i]; a.rgb_out[3 * pix + 2] = cb[i]; }
+    if (a.depth_out) a.depth_out[pix] = cd[i];
+    if (a.sil_out) a.sil_out[pix] = 1.f - T[i];
+    a.tfinal[pix] = T[i];
+    a.nlast[pix] = last[i];
     if (L1) {
-      const float d0 = cr - a.t_rgb[3 * pix], d1 = cg - a.t_rgb[3 * pix + 1], d2 = cb - a.t_rgb[3 * pix + 2];
-      const float d3 = cd - a.t_depth[pix];
+      const float d0 = cr[i] - a.t_rgb[3 * pix], d1 = cg[i] - a.t_rgb[3 * pix + 1], d2 = cb[i] - a.t_rgb[3 * pix + 2];
+      const float d3 = cd[i] - a.t_depth[pix];
       const uint32_t nz = (d0 != 0.f ? 1u : 0u) | (d1 != 0.f ? 2u : 0u) | (d2 != 0.f ? 4u : 0u) | (d3 != 0.f ? 8u : 0u);
       const uint32_t ng = (d0 < 0.f ? 1u : 0u) | (d1 < 0.f ? 2u : 0u) | (d2 < 0.f ? 4u : 0u) | (d3 < 0.f ? 8u : 0u);
       uint32_t *cp = a.codes + pix * cw;
@@ -155,8 +247,8 @@ __global__ void __launch_bounds__(TW *TH) k_render_fwd(FwdArgs a) {
       cp[1 + a.nwc] = ng;
       if (!a.t_sem)
         for (int wd = 0; wd < a.nwc; ++wd) { cp[1 + wd] = 0u; cp[2 + a.nwc + wd] = 0u; }
-      l1_rgb = fabsf(d0) + fabsf(d1) + fabsf(d2);
-      l1_d = fabsf(d3);
+      l1_rgb += fabsf(d0) + fabsf(d1) + fabsf(d2);
+      l1_d += fabsf(d3);
     }
   }
   if (L1) {
@@ -198,26 +290,32 @@ __global__ void k_l1_tiles_final(const double *lpart, int ntiles, double npix, d
   }
 }
 
-template <int TW, int TH, bool L1>
+template <int TW, int TH, bool L1, int PPT>
 static cudaError_t launch_fwd_shape(const FwdArgs &a, int grid, size_t smem, cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_render_fwd<TW, TH, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemBudget);
+    cudaError_t e = cudaFuncSetAttribute(k_render_fwd<TW, TH, L1, PPT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_render_fwd<TW, TH, L1><<<grid, TW * TH, smem, s>>>(a);
+  k_render_fwd<TW, TH, L1, PPT><<<grid, TW * TH / PPT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <bool L1>
-static cudaError_t dispatch_fwd(int tw, int th, const FwdArgs &a, int grid, size_t smem, cudaStream_t s) {
-  if (tw == 16 && th == 16) return launch_fwd_shape<16, 16, L1>(a, grid, smem, s);
-  if (tw == 16 && th == 8) return launch_fwd_shape<16, 8, L1>(a, grid, smem, s);
-  if (tw == 8 && th == 8) return launch_fwd_shape<8, 8, L1>(a, grid, smem, s);
-  if (tw == 32 && th == 8) return launch_fwd_shape<32, 8, L1>(a, grid, smem, s);
+template <bool L1, int PPT>
+static cudaError_t dispatch_fwd_ppt(int tw, int th, const FwdArgs &a, int grid, size_t smem, cudaStream_t s) {
+  if (tw == 16 && th == 16) return launch_fwd_shape<16, 16, L1, PPT>(a, grid, smem, s);
+  if (tw == 16 && th == 8) return launch_fwd_shape<16, 8, L1, PPT>(a, grid, smem, s);
+  if (tw == 8 && th == 8) return launch_fwd_shape<8, 8, L1, PPT>(a, grid, smem, s);
+  if (tw == 32 && th == 8) return launch_fwd_shape<32, 8, L1, PPT>(a, grid, smem, s);
   return cudaErrorInvalidConfiguration;
+}
+
+template <bool L1>
+static cudaError_t dispatch_fwd(const Layout &L, const FwdArgs &a, int grid, size_t smem, cudaStream_t s) {
+  if (L.ppt == 2) return dispatch_fwd_ppt<L1, 2>(L.tile_w, L.tile_h, a, grid, smem, s);
+  return dispatch_fwd_ppt<L1, 1>(L.tile_w, L.tile_h, a, grid, smem, s);
 }
 
 static FwdArgs fwd_args(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc) {
@@ -225,7 +323,6 @@ static FwdArgs fwd_args(const Layout &L, const WsPtrs &P, int pbuf, const gs_sce
   a.ranges = P.ranges;
   a.pvals = P.pvals[pbuf];
   a.rec = rec_ptrs(P);
-  a.rgb = sc.rgb; a.sem_ids = sc.sem_ids; a.sem_w = sc.sem_w;
   a.k = sc.k; a.m = sc.m;
   a.width = L.cam0_w; a.height = L.cam0_h;
   a.tiles_x = (L.cam0_w + L.tile_w - 1) / L.tile_w;
@@ -239,12 +336,12 @@ cudaError_t launch_render_fwd(const Layout &L, const WsPtrs &P, int pbuf, const 
   FwdArgs a = fwd_args(L, P, pbuf, sc);
   const int tiles_y = (L.cam0_h + L.tile_h - 1) / L.tile_h;
   a.rgb_out = rgb; a.depth_out = depth; a.sil_out = sil; a.sem = sem;
-  const int threads = L.tile_w * L.tile_h;
-  chunk_classes(sc.m, threads, sc.k, sem != nullptr, &a.mchunk, &a.mstride, &a.nchunks);
-  const size_t smem = batch_smem_bytes(sc.k) + (sem ? (size_t)threads * a.mstride * sizeof(float) : 0);
+  const int npix = L.tile_w * L.tile_h;  // accumulator rows: one per pixel of the tile
+  chunk_classes(sc.m, npix, sc.k, sem != nullptr, &a.mchunk, &a.mstride, &a.nchunks);
+  const size_t smem = batch_smem_bytes(sc.k) + (sem ? (size_t)npix * a.mstride * sizeof(float) : 0);
   const int grid = a.tiles_x * tiles_y;
   if (grid == 0) return cudaSuccess;
-  return dispatch_fwd<false>(L.tile_w, L.tile_h, a, grid, smem, s);
+  return dispatch_fwd<false>(L, a, grid, smem, s);
 }
 
 cudaError_t launch_render_fwd_l1(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc,
@@ -258,12 +355,12 @@ cudaError_t launch_render_fwd_l1(const Layout &L, const WsPtrs &P, int pbuf, con
   a.nwc = L.nwc;
   a.lpart = P.lpart;
   const bool acc = sem != nullptr || t_sem != nullptr;
-  const int threads = L.tile_w * L.tile_h;
-  chunk_classes(sc.m, threads, sc.k, acc, &a.mchunk, &a.mstride, &a.nchunks);
-  const size_t smem = batch_smem_bytes(sc.k) + (acc ? (size_t)threads * a.mstride * sizeof(float) : 0);
+  const int npix = L.tile_w * L.tile_h;
+  chunk_classes(sc.m, npix, sc.k, acc, &a.mchunk, &a.mstride, &a.nchunks);
+  const size_t smem = batch_smem_bytes(sc.k) + (acc ? (size_t)npix * a.mstride * sizeof(float) : 0);
   const int grid = a.tiles_x * tiles_y;
   if (grid == 0) return cudaSuccess;
-  cudaError_t e = dispatch_fwd<true>(L.tile_w, L.tile_h, a, grid, smem, s);
+  cudaError_t e = dispatch_fwd<true>(L, a, grid, smem, s);
   if (e != cudaSuccess) return e;
   k_l1_tiles_final<<<1, 1024, 0, s>>>(P.lpart, grid, (double)L.npix, (double)sc.m, t_sem ? 1 : 0, loss);
   return cudaGetLastError();

@@ -11,129 +11,214 @@
 //      bits only.
 // Stability carries the depth order (and the gid tie-break) into each tile.
 //
-// The radix sort is a reduce-then-scan LSD sort with 8-bit digits and a
-// fixed grid: per pass, (1) per-CTA digit histograms, (2) one-CTA exclusive
-// scan of the digit-major histogram matrix, (3) per-CTA stable scatter using
-// warp match-based ranking.  There are no inter-CTA waits; element counts
-// are read from device memory, so the whole sort is graph-capturable.
+// Radix sort: 8-bit digits, one histogram kernel for all digit passes, then
+// one kernel per pass.  Each CTA takes a tile ticket from an atomic counter,
+// ranks its keys stably (warp match + per-warp counters), publishes its
+// per-digit counts and looks back over earlier tiles for their prefixes
+// (decoupled look-back).  A CTA only waits on tiles whose tickets were taken
+// earlier, i.e. by CTAs already running; every wait is bounded and, if the
+// bound is hit, raises the timeout status instead of hanging.  Keys are then
+// reordered in shared memory so that the global writes of each digit run are
+// contiguous.  Element counts are read from device memory, so the sort is
+// graph-capturable.
 #include "gs_internal.cuh"
 
 namespace gs {
+
+constexpr int kOsThreads = 256;
+constexpr int kOsWarps = kOsThreads / 32;
+constexpr int kOsItems = 16;
+constexpr int kOsTile = kOsThreads * kOsItems;
+constexpr int kHistCtas = 2 * 152;
+constexpr unsigned long long kFlagA = 1ull << 62;   // tile aggregate published
+constexpr unsigned long long kFlagP = 2ull << 62;   // inclusive prefix published
+constexpr unsigned long long kValMask = (1ull << 62) - 1;
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+int sort_tiles(int64_t capacity) { return (int)((capacity + kOsTile - 1) / kOsTile); }
 
 template <typename K>
 __device__ __forceinline__ uint32_t digit_of(K key, int shift) {
   return (uint32_t)(key >> shift) & (kRadix - 1);
 }
 
-__device__ __forceinline__ void chunk_range(uint32_t count, uint32_t &begin, uint32_t &end) {
-  const uint32_t tiles = (count + kSortTile - 1) / kSortTile;
-  const uint32_t per = (tiles + gridDim.x - 1) / gridDim.x;
-  begin = min(count, blockIdx.x * per * kSortTile);
-  end = min(count, begin + per * kSortTile);
-}
-
-template <typename K>
-__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const K *__restrict__ keys, const uint32_t *count_p,
-                                                             uint32_t cap, int shift, uint32_t *hist) {
-  __shared__ uint32_t h[kSortThreads / 32][kRadix];
-  const uint32_t warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < (kSortThreads / 32) * kRadix; i += kSortThreads) (&h[0][0])[i] = 0;
-  __syncthreads();
+// Clears the tickets, the global histograms and the look-back words of the
+// tiles the current element count needs.
+__global__ void k_os_reset(const uint32_t *count_p, uint32_t cap, int passes, uint32_t *tickets, uint32_t *ghist,
+                           unsigned long long *lookback, uint32_t lb_tiles) {
   const uint32_t count = min(*count_p, cap);
-  uint32_t begin, end;
-  chunk_range(count, begin, end);
-  for (uint32_t i = begin + threadIdx.x; i < end; i += kSortThreads) atomicAdd(&h[warp][digit_of(keys[i], shift)], 1u);
-  __syncthreads();
-  for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
-    uint32_t s = 0;
-#pragma unroll
-    for (int w = 0; w < kSortThreads / 32; ++w) s += h[w][d];
-    hist[d * gridDim.x + blockIdx.x] = s;
+  const uint32_t tiles = (count + kOsTile - 1) / kOsTile;
+  const size_t words = (size_t)tiles * kRadix;
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  if (tid < (size_t)passes) tickets[tid] = 0u;
+  if (tid < (size_t)passes * kRadix) ghist[tid] = 0u;
+  for (int p = 0; p < passes; ++p) {
+    unsigned long long *lb = lookback + (size_t)p * lb_tiles * kRadix;
+    for (size_t i = tid; i < words; i += stride) lb[i] = 0ull;
   }
 }
 
 template <typename K>
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const K *__restrict__ keys_in,
-                                                                const uint32_t *__restrict__ vals_in,
-                                                                K *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
-                                                                const uint32_t *count_p, uint32_t cap, int shift,
-                                                                const uint32_t *__restrict__ hist) {
-  constexpr int kWarps = kSortThreads / 32;
-  __shared__ uint32_t digit_off[kRadix];
-  __shared__ uint32_t wcnt[kWarps][kRadix];
-  __shared__ uint32_t tile_tot[kRadix];
-  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+__global__ void __launch_bounds__(256) k_os_hist(const K *__restrict__ keys, const uint32_t *count_p, uint32_t cap,
+                                                 int passes, uint32_t *ghist) {
+  __shared__ uint32_t h[kMaxRadixPasses][kRadix];
+  for (int i = threadIdx.x; i < kMaxRadixPasses * kRadix; i += blockDim.x) (&h[0][0])[i] = 0u;
+  __syncthreads();
   const uint32_t count = min(*count_p, cap);
-  uint32_t begin, end;
-  chunk_range(count, begin, end);
-  for (int d = threadIdx.x; d < kRadix; d += kSortThreads) digit_off[d] = hist[d * gridDim.x + blockIdx.x];
   const uint32_t lt = lanemask_lt();
-  for (uint32_t base = begin; base < end; base += kSortTile) {
-    for (int i = threadIdx.x; i < kWarps * kRadix; i += kSortThreads) (&wcnt[0][0])[i] = 0;
-    __syncthreads();
-    K key[kSortItems];
-    uint32_t val[kSortItems], dig[kSortItems], loc[kSortItems];
-#pragma unroll
-    for (int i = 0; i < kSortItems; ++i) {
-      const uint32_t idx = base + warp * (32 * kSortItems) + i * 32 + lane;
-      const bool ok = idx < end;
-      key[i] = ok ? keys_in[idx] : (K)0;
-      val[i] = ok ? vals_in[idx] : 0u;
-      dig[i] = ok ? digit_of(key[i], shift) : (uint32_t)kRadix;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  // uniform trip count so that every lane takes part in the match
+  for (uint32_t base = blockIdx.x * blockDim.x; base < count; base += stride) {
+    const uint32_t i = base + threadIdx.x;
+    const bool ok = i < count;
+    const K k = ok ? keys[i] : (K)0;
+    for (int p = 0; p < passes; ++p) {
+      const uint32_t d = ok ? digit_of(k, p * kRadixBits) : (uint32_t)kRadix;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      if (ok && (peers & lt) == 0u) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
     }
-#pragma unroll
-    for (int i = 0; i < kSortItems; ++i) {
-      const uint32_t peers = __match_any_sync(0xffffffffu, dig[i]);
-      const uint32_t rank = __popc(peers & lt);
-      const bool leader = (peers & lt) == 0u;
-      uint32_t b = 0;
-      if (dig[i] < (uint32_t)kRadix) b = wcnt[warp][dig[i]];
-      loc[i] = b + rank;
-      __syncwarp();
-      if (leader && dig[i] < (uint32_t)kRadix) wcnt[warp][dig[i]] = b + __popc(peers);
-      __syncwarp();
-    }
-    __syncthreads();
-    // exclusive scan over warps, per digit
-    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
-      uint32_t run = 0;
-#pragma unroll
-      for (int w = 0; w < kWarps; ++w) {
-        const uint32_t c = wcnt[w][d];
-        wcnt[w][d] = run;
-        run += c;
-      }
-      tile_tot[d] = run;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < kSortItems; ++i) {
-      if (dig[i] < (uint32_t)kRadix) {
-        const uint32_t pos = digit_off[dig[i]] + wcnt[warp][dig[i]] + loc[i];
-        keys_out[pos] = key[i];
-        vals_out[pos] = val[i];
-      }
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) digit_off[d] += tile_tot[d];
-    __syncthreads();
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) {
+    const uint32_t v = (&h[0][0])[i];
+    if (v) atomicAdd(ghist + i, v);
   }
 }
 
 template <typename K>
-static cudaError_t radix_sort(K *keys[2], uint32_t *vals[2], const uint32_t *count_p, uint32_t cap, int bits,
-                              uint32_t *hist, Counters *counters, cudaStream_t s) {
+__global__ void __launch_bounds__(kOsThreads) k_os_pass(const K *__restrict__ keys_in,
+                                                        const uint32_t *__restrict__ vals_in,
+                                                        K *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
+                                                        const uint32_t *count_p, uint32_t cap, int shift,
+                                                        const uint32_t *__restrict__ ghist,
+                                                        unsigned long long *lookback, uint32_t *ticket,
+                                                        Counters *counters) {
+  extern __shared__ unsigned long long os_smem[];
+  K *skey = reinterpret_cast<K *>(os_smem);
+  uint32_t *sval = reinterpret_cast<uint32_t *>(skey + kOsTile);
+  __shared__ uint32_t wcnt[kOsWarps][kRadix];
+  __shared__ uint32_t tile_pre[kRadix];
+  __shared__ uint32_t out_base[kRadix];
+  __shared__ uint32_t scan_tmp[33];
+  __shared__ uint32_t s_tile;
+
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, d = threadIdx.x;
+  const uint32_t count = min(*count_p, cap);
+  if (threadIdx.x == 0) s_tile = atomicAdd(ticket, 1u);
+  for (int i = threadIdx.x; i < kOsWarps * kRadix; i += kOsThreads) (&wcnt[0][0])[i] = 0u;
+  __syncthreads();
+  const uint32_t t = s_tile;
+  const uint32_t base = t * kOsTile;
+  if (base >= count) return;  // uniform: tiles past the data
+  const uint32_t n_tile = min((uint32_t)kOsTile, count - base);
+
+  // stable ranking: warp-striped items, in index order within each warp
+  const uint32_t lt = lanemask_lt();
+  K key[kOsItems];
+  uint32_t val[kOsItems], dig[kOsItems], loc[kOsItems];
+#pragma unroll
+  for (int i = 0; i < kOsItems; ++i) {
+    const uint32_t off = warp * (32 * kOsItems) + i * 32 + lane;
+    const bool ok = off < n_tile;
+    key[i] = ok ? keys_in[base + off] : (K)0;
+    val[i] = ok ? vals_in[base + off] : 0u;
+    dig[i] = ok ? digit_of(key[i], shift) : (uint32_t)kRadix;
+  }
+#pragma unroll
+  for (int i = 0; i < kOsItems; ++i) {
+    const uint32_t peers = __match_any_sync(0xffffffffu, dig[i]);
+    uint32_t b = 0;
+    if (dig[i] < (uint32_t)kRadix) b = wcnt[warp][dig[i]];
+    loc[i] = b + __popc(peers & lt);
+    __syncwarp();
+    if ((peers & lt) == 0u && dig[i] < (uint32_t)kRadix) wcnt[warp][dig[i]] = b + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit: exclusive prefix over warps, tile count
+  uint32_t run = 0;
+#pragma unroll
+  for (int w = 0; w < kOsWarps; ++w) {
+    const uint32_t c = wcnt[w][d];
+    wcnt[w][d] = run;
+    run += c;
+  }
+  const uint32_t tile_count = run;
+  // publish this tile's aggregate, then look back for the exclusive prefix
+  unsigned long long *lb = lookback + (size_t)t * kRadix;
+  if (t == 0) {
+    atomicExch(lb + d, kFlagP | (unsigned long long)tile_count);
+  } else {
+    atomicExch(lb + d, kFlagA | (unsigned long long)tile_count);
+  }
+  unsigned long long excl = 0ull;
+  if (t > 0) {
+    int j = (int)t - 1;
+    uint32_t spins = 0;
+    while (j >= 0) {
+      const unsigned long long v = *reinterpret_cast<volatile unsigned long long *>(lookback + (size_t)j * kRadix + d);
+      const unsigned long long flag = v & ~kValMask;
+      if (flag == 0ull) {
+        if (++spins > kSpinLimit) { set_status(counters, kStatusTimeout); break; }
+        __nanosleep(32);
+        continue;
+      }
+      excl += v & kValMask;
+      if (flag == kFlagP) break;
+      --j;
+    }
+    atomicExch(lb + d, kFlagP | (excl + tile_count));
+  }
+  // global start of digit d: all keys with a smaller digit + earlier tiles
+  const uint32_t gpre = block_exclusive_scan(ghist[d], scan_tmp, &run);
+  const uint32_t tpre = block_exclusive_scan(tile_count, scan_tmp, &run);
+  tile_pre[d] = tpre;
+  out_base[d] = gpre + (uint32_t)excl;
+  __syncthreads();
+  // local reorder by digit (stable), then contiguous global writes
+#pragma unroll
+  for (int i = 0; i < kOsItems; ++i) {
+    if (dig[i] < (uint32_t)kRadix) {
+      const uint32_t lp = tile_pre[dig[i]] + wcnt[warp][dig[i]] + loc[i];
+      skey[lp] = key[i];
+      sval[lp] = val[i];
+    }
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < n_tile; i += kOsThreads) {
+    const K k = skey[i];
+    const uint32_t dd = digit_of(k, shift);
+    const uint32_t pos = out_base[dd] + (i - tile_pre[dd]);
+    keys_out[pos] = k;
+    vals_out[pos] = sval[i];
+  }
+}
+
+template <typename K>
+static cudaError_t os_sort(K *keys[2], uint32_t *vals[2], const uint32_t *count_p, uint32_t cap, int bits,
+                           uint32_t *tickets, uint32_t *ghist, unsigned long long *lookback, Counters *counters,
+                           cudaStream_t s) {
   const int passes = radix_passes(bits);
+  const uint32_t lb_tiles = (uint32_t)sort_tiles(cap);
+  if (passes < 1 || passes > kMaxRadixPasses || lb_tiles == 0) return cudaErrorInvalidValue;
+  k_os_reset<<<2 * 152, 256, 0, s>>>(count_p, cap, passes, tickets, ghist, lookback, lb_tiles);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_os_hist<K><<<kHistCtas, 256, 0, s>>>(keys[0], count_p, cap, passes, ghist);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = (size_t)kOsTile * (sizeof(K) + sizeof(uint32_t));
+  static bool attr_set = false;
+  if (!attr_set) {
+    e = cudaFuncSetAttribute(k_os_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
   for (int p = 0; p < passes; ++p) {
     const int src = p & 1, dst = src ^ 1;
-    const int shift = p * kRadixBits;
-    k_radix_hist<K><<<kSortCtas, kSortThreads, 0, s>>>(keys[src], count_p, cap, shift, hist);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    e = launch_scan_single(hist, (uint32_t)(kRadix * kSortCtas), nullptr, 0xffffffffu, counters, s);
-    if (e != cudaSuccess) return e;
-    k_radix_scatter<K><<<kSortCtas, kSortThreads, 0, s>>>(keys[src], vals[src], keys[dst], vals[dst], count_p, cap,
-                                                         shift, hist);
+    k_os_pass<K><<<lb_tiles, kOsThreads, smem, s>>>(keys[src], vals[src], keys[dst], vals[dst], count_p, cap,
+                                                   p * kRadixBits, ghist + p * kRadix,
+                                                   lookback + (size_t)p * lb_tiles * kRadix, tickets + p, counters);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -144,14 +229,16 @@ cudaError_t launch_radix_sort_u64(const Layout &L, const WsPtrs &P, int bits, in
   unsigned long long *k[2] = {P.dkeys[0], P.dkeys[1]};
   uint32_t *v[2] = {P.dvals[0], P.dvals[1]};
   *final_buf = radix_passes(bits) & 1;
-  return radix_sort<unsigned long long>(k, v, &P.counters->n_records, (uint32_t)L.rcap, bits, P.hist, P.counters, s);
+  return os_sort<unsigned long long>(k, v, &P.counters->n_records, (uint32_t)L.rcap, bits, P.tickets, P.ghist,
+                                     P.lb_depth, P.counters, s);
 }
 
 cudaError_t launch_radix_sort_u32(const Layout &L, const WsPtrs &P, int bits, int *final_buf, cudaStream_t s) {
   uint32_t *k[2] = {P.pkeys[0], P.pkeys[1]};
   uint32_t *v[2] = {P.pvals[0], P.pvals[1]};
   *final_buf = radix_passes(bits) & 1;
-  return radix_sort<uint32_t>(k, v, &P.counters->n_pairs, (uint32_t)L.pcap, bits, P.hist, P.counters, s);
+  return os_sort<uint32_t>(k, v, &P.counters->n_pairs, (uint32_t)L.pcap, bits, P.tickets + kMaxRadixPasses,
+                           P.ghist + kMaxRadixPasses * kRadix, P.lb_pairs, P.counters, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -182,6 +269,10 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_count(const uint32_t *__r
   if (threadIdx.x == 0) epart[blockIdx.x] = total;
 }
 
+// Each warp takes 32 consecutive (depth-sorted) records and writes all their
+// pairs cooperatively: lane i of each round writes pair i of the warp's run,
+// finding its record by a search over the warp's prefix sums, so consecutive
+// lanes write consecutive addresses.
 __global__ void __launch_bounds__(kEmitThreads) k_emit_write(const uint32_t *__restrict__ sorted_rec,
                                                              const short4 *__restrict__ rect,
                                                              const int32_t *__restrict__ rview,
@@ -191,34 +282,61 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_write(const uint32_t *__r
                                                              uint32_t *__restrict__ pkeys,
                                                              uint32_t *__restrict__ pvals) {
   __shared__ uint32_t tmp[33];
+  __shared__ uint32_t wpre[kEmitThreads / 32][33];
+  __shared__ int4 wrec[kEmitThreads / 32][32];  // tx0, width, ty0, tile_off | view info packed below
+  __shared__ uint32_t wrid[kEmitThreads / 32][32];
+  __shared__ int wtx[kEmitThreads / 32][32];
   const uint32_t count = min(cnt->n_records, rcap);
   uint32_t begin, end;
   emit_chunk(count, begin, end);
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   uint32_t run = epart[blockIdx.x];
   for (uint32_t q0 = begin; q0 < end; q0 += kEmitThreads) {
     const uint32_t q = q0 + threadIdx.x;
     uint32_t r = 0, nt = 0;
-    short4 rc = make_short4(0, 0, 0, 0);
+    int tx0 = 0, gw = 1, ty0 = 0, tiles_x = 1;
+    uint32_t toff = 0;
     if (q < end) {
       r = sorted_rec[q];
-      rc = rect[r];
+      const short4 rc = rect[r];
       nt = record_ntiles(rc, tw, th);
+      const DevCam &c = cams[rview[r]];
+      tx0 = rc.x / tw;
+      gw = rc.y / tw - tx0 + 1;
+      ty0 = rc.z / th;
+      tiles_x = c.tiles_x;
+      toff = c.tile_off;
     }
     uint32_t total;
-    uint32_t pos = run + block_exclusive_scan(nt, tmp, &total);
+    const uint32_t pos = run + block_exclusive_scan(nt, tmp, &total);
     run += total;
-    if (nt) {
-      const DevCam &c = cams[rview[r]];
-      const int tx0 = rc.x / tw, tx1 = rc.y / tw, ty0 = rc.z / th, ty1 = rc.w / th;
-      for (int ty = ty0; ty <= ty1; ++ty)
-        for (int tx = tx0; tx <= tx1; ++tx) {
-          if (pos < pcap) {
-            pkeys[pos] = c.tile_off + (uint32_t)(ty * c.tiles_x + tx);
-            pvals[pos] = r;
-          }
-          ++pos;
-        }
+    // warp-local prefix of pair counts
+    const uint32_t inc = warp_inclusive_scan(nt);
+    wpre[warp][lane + 1] = inc;
+    if (lane == 0) wpre[warp][0] = 0;
+    wrec[warp][lane] = make_int4(tx0, gw, ty0, (int)toff);
+    wtx[warp][lane] = tiles_x;
+    wrid[warp][lane] = r;
+    __syncwarp();
+    const uint32_t wbase = __shfl_sync(0xffffffffu, pos, 0);
+    const uint32_t wtotal = wpre[warp][32];
+    for (uint32_t i = lane; i < wtotal; i += 32) {
+      // record of pair i: largest l with wpre[l] <= i
+      int lo = 0, hi = 31;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (wpre[warp][mid] <= i) lo = mid; else hi = mid - 1;
+      }
+      const int4 rr = wrec[warp][lo];
+      const uint32_t j = i - wpre[warp][lo];
+      const int ty = rr.z + (int)(j / (uint32_t)rr.y), tx = rr.x + (int)(j % (uint32_t)rr.y);
+      const uint32_t p = wbase + i;
+      if (p < pcap) {
+        pkeys[p] = (uint32_t)rr.w + (uint32_t)(ty * wtx[warp][lo] + tx);
+        pvals[p] = wrid[warp][lo];
+      }
     }
+    __syncwarp();
   }
 }
 
@@ -236,30 +354,34 @@ cudaError_t launch_emit_pairs(const Layout &L, const WsPtrs &P, int dbuf, cudaSt
 }
 
 // ---------------------------------------------------------------------------
-// Per-tile [start, end) ranges by binary search over the sorted tile ids.
+// Per-tile [start, end) ranges from the sorted tile ids: every pair that
+// starts or ends a run writes its tile's bound; tiles with no pair keep the
+// empty range written first.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ uint32_t lower_bound_u32(const uint32_t *a, uint32_t n, uint32_t x) {
-  uint32_t lo = 0, hi = n;
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (a[mid] < x) lo = mid + 1; else hi = mid;
-  }
-  return lo;
+__global__ void k_ranges_clear(uint2 *ranges, uint32_t total_tiles) {
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total_tiles; t += gridDim.x * blockDim.x)
+    ranges[t] = make_uint2(0u, 0u);
 }
 
-__global__ void k_tile_ranges(const uint32_t *__restrict__ pkeys, const Counters *cnt, uint32_t pcap,
+__global__ void k_ranges_mark(const uint32_t *__restrict__ pkeys, const Counters *cnt, uint32_t pcap,
                               uint32_t total_tiles, uint2 *ranges) {
-  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= total_tiles) return;
   const uint32_t k = min(cnt->n_pairs, pcap);
-  ranges[t] = make_uint2(lower_bound_u32(pkeys, k, t), lower_bound_u32(pkeys, k, t + 1));
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
+    const uint32_t t = pkeys[i];
+    if (t >= total_tiles) continue;
+    if (i == 0 || pkeys[i - 1] != t) ranges[t].x = i;
+    if (i + 1 == k || pkeys[i + 1] != t) ranges[t].y = i + 1;
+  }
 }
 
 cudaError_t launch_tile_ranges(const Layout &L, const WsPtrs &P, int pbuf, cudaStream_t s) {
   const uint32_t T = (uint32_t)L.total_tiles;
   if (T == 0) return cudaSuccess;
-  k_tile_ranges<<<(T + 255) / 256, 256, 0, s>>>(P.pkeys[pbuf], P.counters, (uint32_t)L.pcap, T, P.ranges);
+  k_ranges_clear<<<min((T + 255) / 256, 4u * 152u), 256, 0, s>>>(P.ranges, T);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_ranges_mark<<<4 * 152, 256, 0, s>>>(P.pkeys[pbuf], P.counters, (uint32_t)L.pcap, T, P.ranges);
   return cudaGetLastError();
 }
 

@@ -110,8 +110,9 @@ class Rasterizer:
     """
 
     def __init__(self, tile=(16, 16), sem_detach_geometry=True, record_capacity=0, pair_capacity=0,
-                 device=None):
+                 device=None, px_per_thread=0):
         self.tile = tuple(tile)
+        self.px_per_thread = int(px_per_thread)
         self.sem_detach_geometry = bool(sem_detach_geometry)
         self.record_capacity = int(record_capacity)
         self.pair_capacity = int(pair_capacity)
@@ -133,6 +134,7 @@ class Rasterizer:
         c = N.GsConfig()
         c.tile_w, c.tile_h = self.tile
         c.sem_detach_geometry = 1 if self.sem_detach_geometry else 0
+        c.px_per_thread = self.px_per_thread
         # capacities start at a bound that never overflows for small problems
         # and grow on reported overflow (check=True)
         c.record_capacity = self.record_capacity if self.record_capacity > 0 else max(1, min(n_gauss * n_views,

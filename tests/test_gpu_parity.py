@@ -96,9 +96,9 @@ def test_binning_bitexact_multi_view_equal_depths():
 # forward render
 # ---------------------------------------------------------------------------
 
-def _fwd(sc, cam, tile=(16, 16)):
+def _fwd(sc, cam, tile=(16, 16), ppt=0):
     g = raster.Gaussians.from_scene(sc)
-    rast = raster.Rasterizer(tile=tile)
+    rast = raster.Rasterizer(tile=tile, px_per_thread=ppt)
     with torch.no_grad():
         out = rast.forward(g, cam)
     return [t.cpu().numpy() if t is not None else None for t in out]
@@ -136,13 +136,42 @@ def test_forward_plain10k_workload():
     _img_close(sem, r["sem"], ok)
 
 
-def test_forward_independent_of_tile_shape():
+def test_forward_independent_of_tile_shape_and_mapping():
     sc, cam = small_case(w=100, h=70)
-    base = _fwd(sc, cam, (16, 16))
-    for tile in [(16, 8), (8, 8), (32, 8)]:
-        other = _fwd(sc, cam, tile)
-        for a, b in zip(base, other):
-            np.testing.assert_array_equal(a, b)
+    base = _fwd(sc, cam, (16, 16), 1)
+    for tile in [(16, 16), (16, 8), (8, 8), (32, 8)]:
+        for ppt in (1, 2):
+            other = _fwd(sc, cam, tile, ppt)
+            for a, b in zip(base, other):
+                np.testing.assert_array_equal(a, b)
+
+
+def test_backward_independent_of_mapping():
+    """Pixels per thread changes only the order of the float atomics."""
+    sc, cam = small_case(n=2500, w=45, h=37, seed=2)
+    g = raster.Gaussians.from_scene(sc)
+    H, W = cam.height, cam.width
+    torch.manual_seed(0)
+    ups = [torch.randn(H, W, 3, device="cuda"), torch.randn(H, W, device="cuda"), torch.randn(H, W, device="cuda"),
+           torch.randn(H, W, sc.m, device="cuda")]
+    res = []
+    for tile, ppt in [((16, 16), 1), ((16, 16), 2), ((32, 8), 2)]:
+        rast = raster.Rasterizer(tile=tile, px_per_thread=ppt, sem_detach_geometry=False)
+        rast.forward(g, cam)
+        res.append({k: v.cpu().numpy() for k, v in rast.backward(g, cam, *ups).items()})
+    for other in res[1:]:
+        for name in res[0]:
+            _grad_close(other[name], res[0][name], rtol=1e-4, name=name)
+
+
+def test_autotune_picks_a_compiled_config():
+    from paper_2506_00225_gb300 import autotune
+    sc, cam, t, _ = _l1_case(seed=7)
+    g = raster.Gaussians.from_scene(sc)
+    tt = [torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda() for x in (t["rgb"], t["depth"], t["sem"])]
+    best, table = autotune.tune_mapping(g, cam, *tt, reps=2)
+    assert len(table) == len(autotune.SHAPES) * len(autotune.PPTS)
+    assert best["ms"] == min(r["ms"] for r in table) and best["px_per_thread"] in (1, 2)
 
 
 def test_forward_class_chunking_large_m():
