@@ -103,6 +103,10 @@ bool make_layout(const gs_scene *scene, const gs_camera *cams, int n_views, cons
   L->nwc = (scene->m + 31) / 32;
   L->off_codes = take(n_views == 1 ? 4 * (size_t)L->npix * (2 * (1 + L->nwc)) : 32);
   L->off_lpart = take(n_views == 1 ? 3 * sizeof(double) * (size_t)(tiles > 0 ? tiles : 1) : 32);
+  // one unit = one staged batch of one tile: 2 words per tile pixel
+  L->mask_units = n_views == 1 ? pcap / kBatch + (int64_t)tiles + 1 : 1;
+  L->off_mask_off = take(sizeof(uint32_t) * (size_t)(tiles + 1));
+  L->off_masks = take(n_views == 1 ? 8 * (size_t)L->mask_units * cfg.tile_w * cfg.tile_h : 32);
   L->total = off;
   return true;
 }
@@ -141,6 +145,8 @@ WsPtrs ws_ptrs(const Layout &L, void *ws) {
   P.grad2d = reinterpret_cast<float4 *>(b + L.off_grad2d);
   P.codes = reinterpret_cast<uint32_t *>(b + L.off_codes);
   P.lpart = reinterpret_cast<double *>(b + L.off_lpart);
+  P.mask_off = reinterpret_cast<uint32_t *>(b + L.off_mask_off);
+  P.masks = reinterpret_cast<uint32_t *>(b + L.off_masks);
   return P;
 }
 

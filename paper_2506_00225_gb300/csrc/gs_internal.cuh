@@ -70,6 +70,8 @@ struct Layout {
   size_t off_grad2d;
   int nwc;                                 // 32-class sign words per plane (fused L1 mode)
   size_t off_codes, off_lpart;
+  size_t off_mask_off, off_masks;          // contributor bitmasks of the mapping view
+  int64_t mask_units;                      // capacity in (tile, batch) units
   size_t total;
 };
 
@@ -102,6 +104,8 @@ struct WsPtrs {
   uint32_t *nlast;
   float4 *grad2d;  // [rcap][2]: (du, dv, da, db), (dc, dopacity, dz, 0)
   uint32_t *codes; // [npix][2 * (1 + nwc)] sign codes of the fused L1 mode
+  uint32_t *mask_off;  // [tiles + 1] first (tile, batch) unit of each tile
+  uint32_t *masks;     // [unit][2][tile pixels] contributor bits of each staged batch
   double *lpart;   // [tiles of view 0][3] per-tile L1 sums
 };
 

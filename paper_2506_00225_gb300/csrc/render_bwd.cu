@@ -37,6 +37,8 @@ struct BwdArgs {
   int nwc;
   const float *loss_scale;  // device dL/dloss
   double npix;
+  const uint32_t *mask_off;  // contributor bitmasks of the forward pass
+  const uint32_t *masks;
 };
 
 __device__ __forceinline__ float sign_code(uint32_t nz, uint32_t ng, int bit, float s) {
@@ -113,22 +115,34 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
   const uint32_t maxnl = s_maxnl;
   const int my_idx = reduced_index<NV>();
 
-  for (uint32_t hi = rg.x + maxnl; hi > rg.x;) {
-    const uint32_t lo = hi - min((uint32_t)kBatch, hi - rg.x);
-    const int n = (int)(hi - lo);
+  // the forward's batches, last to first (batch bi covers rg.x + 64 bi ...)
+  for (int bi = maxnl ? (int)((maxnl - 1) / kBatch) : -1; bi >= 0; --bi) {
+    const uint32_t lo = rg.x + (uint32_t)bi * kBatch;
+    const int n = (int)min((uint32_t)kBatch, rg.y - lo);
     __syncthreads();
     for (int t = threadIdx.x; t < n; t += FP::kThreads)
       stage_record<TW, TH, PPT>(a.rec, a.pvals[lo + t], t, k, ox, oy, bs, has_dsem, false);
     __syncthreads();
-    for (int base = ((n - 1) / 32) * 32; base >= 0; base -= 32) {
-      const int jj = base + (int)lane;
-      uint32_t vis = __ballot_sync(0xffffffffu, jj < n && ((bs.wmask[jj] >> warp) & 1u));
+    // contributor bits of this batch (written by the forward pass 1)
+    const uint32_t unit = a.mask_off[tile] + (uint32_t)bi;
+    const uint32_t *mw = a.masks + (size_t)unit * 2 * FP::kPix;
+    uint32_t mb[PPT][2];
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+      const int lp = FP::ly(i) * TW + lx;
+      const bool ok = px < a.width && py[i] < a.height;
+      mb[i][0] = ok ? mw[lp] : 0u;
+      mb[i][1] = ok ? mw[FP::kPix + lp] : 0u;
+    }
+    for (int h = 1; h >= 0; --h) {
+      uint32_t mine = 0u;
+#pragma unroll
+      for (int i = 0; i < PPT; ++i) mine |= mb[i][h];
+      uint32_t vis = __reduce_or_sync(0xffffffffu, mine);
       while (vis) {
         const int bit = 31 - __clz(vis);
         vis &= ~(1u << bit);
-        const int j = base + bit;
-        const uint32_t idx = lo - rg.x + j;
-        const int2 bb = bs.box[j];
+        const int j = h * 32 + bit;
         const float2 uv = bs.uv[j];
         const float4 co = bs.co[j];
         bool contrib[PPT];
@@ -136,11 +150,11 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
         bool any = false;
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
-          contrib[i] = idx < nl[i] && box_holds(bb, px, py[i]);
-          if (contrib[i]) contrib[i] = gauss_alpha(uv, co, fpx, fpy[i], alpha[i], G[i], araw[i], dx[i], dy[i]);
+          contrib[i] = (mb[i][h] >> bit) & 1u;
+          if (contrib[i]) gauss_alpha(uv, co, fpx, fpy[i], alpha[i], G[i], araw[i], dx[i], dy[i]);
           any = any || contrib[i];
         }
-        if (!__any_sync(0xffffffffu, any)) continue;
+        (void)any;
         float v[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) v[q] = 0.f;
@@ -202,7 +216,6 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
         }
       }
     }
-    hi = lo;
   }
 }
 
@@ -256,6 +269,8 @@ cudaError_t launch_render_bwd(const Layout &L, const WsPtrs &P, int pbuf, const 
   a.sem_detach = sem_detach;
   a.grad2d = P.grad2d;
   a.g_rgb = g_rgb; a.g_sem_w = g_sem_w;
+  a.mask_off = P.mask_off;
+  a.masks = P.masks;
   const int grid = a.tiles_x * tiles_y;
   if (grid == 0) return cudaSuccess;
   if (loss_scale) {

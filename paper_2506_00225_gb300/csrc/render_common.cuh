@@ -225,6 +225,10 @@ struct FwdArgs {
   int nwc;           // class words per plane = ceil(m / 32)
   double *lpart;     // per tile: sum|d rgb|, sum|d depth|, sum|d sem|
   Counters *counters;
+  // contributor bitmasks (pass 1 writes, pass 2 and the adjoint read)
+  const uint32_t *mask_off;
+  uint32_t *masks;
+  uint32_t mask_units;
 };
 
 // Per-pixel sign-code layout of the fused L1 mode.

@@ -1,25 +1,28 @@
 // render_fwd.cu -- forward tile blend: Eq. 1 (colour, depth, silhouette) and
 // Eq. 3 (sparse top-k semantics), supplement "Sparse Rendering".
 //
-// One CTA per screen tile, one thread per pixel, each warp an 8 x 4 pixel
-// block.  The tile's depth-sorted pair range is walked in batches staged in
-// shared memory; for every staged Gaussian the stager records which warps'
-// blocks meet its alpha box (the pixels where alpha can reach 1/255), and
-// each warp visits only those Gaussians.  A thread composites a Gaussian
-// whose box holds its pixel, front to back, and stops before the Gaussian
-// that would take the transmittance below 1e-4; the CTA leaves when every
-// pixel is done (__syncthreads_count).  Semantic probabilities are scattered
-// into a per-pixel M-class accumulator in shared memory (k adds per
-// contributor instead of M, the point of the sparse representation), then
-// written out with coalesced stores.  When M does not fit, classes are
-// processed in chunks of 32-class multiples, recompositing per chunk.
+// Two passes over each screen tile (one CTA per tile, one thread per pixel,
+// each warp an 8 x 4 pixel block):
 //
-// Fused mean-L1 mode (L1 = true): the rendered colour, depth and semantic
-// distribution are compared with the targets inside the tile; the kernel
-// keeps per-tile sums of |rendered - target| and, per value, two bits
-// (nonzero, negative) of the sign of the difference for the adjoint.  The
-// tile's target rows are prefetched into L2 with bulk-copy prefetches when
-// the CTA starts, so the comparison reads them from L2.
+// Pass 1 (k_blend) walks the tile's depth-sorted pair range in batches
+// staged in shared memory.  For every staged Gaussian the stager records
+// which warps' blocks meet its alpha box (the pixels where alpha can reach
+// 1/255), and each warp visits only those Gaussians.  A thread composites a
+// Gaussian whose box holds its pixel, front to back, and stops before the
+// Gaussian that would take the transmittance below 1e-4.  Besides colour,
+// depth, silhouette, the final transmittance and the last contributor, it
+// writes one bit per (pixel, staged Gaussian) that contributed.  Pass 1 keeps
+// no per-pixel class accumulator, so many CTAs share an SM.
+//
+// Pass 2 (k_semantic) rebuilds Eq. 3: it walks only each pixel's
+// contributor bits, recomputes alpha with the same function (bit-identical)
+// and the transmittance from the contributors alone, and scatters the k
+// (class, weight) pairs into a per-pixel M-class accumulator in shared memory
+// (k adds per contributor instead of M, the point of the sparse
+// representation).  Then it writes the semantic map, or, in the fused mean-L1
+// mode, compares it with the target map (read from L2 after a bulk prefetch)
+// and keeps per-value sign bits and per-tile sums.  When M does not fit,
+// classes are processed in chunks of 32-class multiples.
 #include "gs_internal.cuh"
 #include "render_common.cuh"
 
@@ -37,209 +40,93 @@ __device__ __forceinline__ void prefetch_l2(const void *base, size_t total, cons
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((uint32_t)(hi - lo)) : "memory");
 }
 
-template <int TW, int TH, bool L1, int PPT>
-__global__ void __launch_bounds__(TW *TH / PPT) k_render_fwd(FwdArgs a) {
-  using FP = Footprint<TW, TH, PPT>;
+// Per tile: number of staged batches of its pair range.
+__global__ void k_tile_batches(const uint2 *__restrict__ ranges, uint32_t ntiles, uint32_t *units) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < ntiles) units[t] = (ranges[t].y - ranges[t].x + kBatch - 1) / kBatch;
+}
+
+template <int TW, int TH, bool L1>
+__global__ void __launch_bounds__(TW *TH) k_blend(FwdArgs a) {
+  using FP = Footprint<TW, TH, 1>;
   constexpr int THREADS = FP::kThreads;
   constexpr int WARPS = FP::kWarps;
   constexpr int NPIX = FP::kPix;
   extern __shared__ float4 smem4[];
-  BatchSmem bs = batch_smem(smem4, a.k);
-  float *sP = bs.tail;
-  __shared__ float red[3][WARPS];
+  BatchSmem bs = batch_smem(smem4, 0);
+  __shared__ float red[2][WARPS];
 
   const int tile = blockIdx.x;
   const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
   const int ox = tx * TW, oy = ty * TH;
   const uint2 rg = a.ranges[tile];
-  const int lx = FP::lx();
-  const int px = ox + lx;
-  const float fpx = (float)px + 0.5f;
-  int py[PPT];
-  bool inside[PPT];
-  float fpy[PPT];
-  float *myP[PPT];
-#pragma unroll
-  for (int i = 0; i < PPT; ++i) {
-    const int ly = FP::ly(i);
-    py[i] = oy + ly;
-    inside[i] = px < a.width && py[i] < a.height;
-    fpy[i] = (float)py[i] + 0.5f;
-    myP[i] = sP + (ly * TW + lx) * a.mstride;
-  }
-  const bool acc_sem = a.sem != nullptr || (L1 && a.t_sem != nullptr);
+  const int lx = FP::lx(), ly = FP::ly(0);
+  const int px = ox + lx, py = oy + ly;
+  const int lp = ly * TW + lx;
+  const bool inside = px < a.width && py < a.height;
+  const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-  const int cw = code_words(a.nwc);
-  const int k = a.k;
-  float l1_sem = 0.f;
+  const uint32_t unit0 = a.mask_off[tile];
 
-  if (L1 && a.t_sem && (int)threadIdx.x < TH) {
-    const int y = oy + (int)threadIdx.x;
-    if (y < a.height) {
-      const int vw = min(TW, a.width - ox);
-      prefetch_l2(a.t_sem, (size_t)a.width * a.height * a.m * 4, a.t_sem + ((size_t)y * a.width + ox) * a.m,
-                  (size_t)vw * a.m * 4);
-    }
-  }
-
-  float T[PPT], cr[PPT], cg[PPT], cb[PPT], cd[PPT];
-  uint32_t last[PPT];
-  uint32_t ncontrib = 0;
-  for (int c = 0; c < a.nchunks; ++c) {
-    const int c_lo = c * a.mchunk, c_hi = min(a.m, c_lo + a.mchunk);
-    const int mc = c_hi - c_lo;
-    bool done[PPT];
-#pragma unroll
-    for (int i = 0; i < PPT; ++i) {
-      if (acc_sem)
-        for (int q = 0; q < mc; ++q) myP[i][q] = 0.f;
-      T[i] = 1.f; cr[i] = cg[i] = cb[i] = cd[i] = 0.f; last[i] = 0;
-      done[i] = !inside[i];
-    }
-    ncontrib = 0;
-    for (uint32_t b = rg.x; b < rg.y; b += kBatch) {
-      const int n = (int)min((uint32_t)kBatch, rg.y - b);
-      __syncthreads();
-      for (int t = threadIdx.x; t < n; t += THREADS)
-        stage_record<TW, TH, PPT>(a.rec, a.pvals[b + t], t, k, ox, oy, bs, acc_sem, false);
-      __syncthreads();
-      bool all_done = true;
-#pragma unroll
-      for (int i = 0; i < PPT; ++i) all_done = all_done && done[i];
-      if (!__all_sync(0xffffffffu, all_done)) {
-        for (int base = 0; base < n; base += 32) {
-          const int jj = base + (int)lane;
-          uint32_t vis = __ballot_sync(0xffffffffu, jj < n && ((bs.wmask[jj] >> warp) & 1u));
-          while (vis) {
-            const int j = base + __ffs(vis) - 1;
-            vis &= vis - 1;
-            const int2 bb = bs.box[j];
-            bool hold[PPT];
-            bool any = false;
-#pragma unroll
-            for (int i = 0; i < PPT; ++i) {
-              hold[i] = !done[i] && box_holds(bb, px, py[i]);
-              any = any || hold[i];
-            }
-            if (!any) continue;
-            const float2 uv = bs.uv[j];
-            const float4 co = bs.co[j];
-            const float4 cdp = bs.cd[j];
-#pragma unroll
-            for (int i = 0; i < PPT; ++i) {
-              if (!hold[i]) continue;
-              float alpha, G, araw, dx, dy;
-              if (!gauss_alpha(uv, co, fpx, fpy[i], alpha, G, araw, dx, dy)) continue;
-              const float Tn = __fmul_rn(T[i], __fsub_rn(1.f, alpha));
-              if (Tn < kTStop) { done[i] = true; continue; }
-              const float w = __fmul_rn(alpha, T[i]);
-              cr[i] = fmaf(w, cdp.x, cr[i]); cg[i] = fmaf(w, cdp.y, cg[i]); cb[i] = fmaf(w, cdp.z, cb[i]);
-              cd[i] = fmaf(w, cdp.w, cd[i]);
-              if (acc_sem) {
-                const int2 *sp = bs.sem + j * k;
-                for (int l = 0; l < k; ++l) {
-                  const int2 e = sp[l];
-                  const int id = e.x - c_lo;
-                  if ((unsigned)id < (unsigned)mc) myP[i][id] = fmaf(w, __int_as_float(e.y), myP[i][id]);
-                }
-              }
-              T[i] = Tn;
-              last[i] = b - rg.x + j + 1;
-              ++ncontrib;
-            }
-          }
+  float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, cd = 0.f;
+  uint32_t last = 0, ncontrib = 0;
+  bool done = !inside;
+  uint32_t bi = 0;
+  for (uint32_t b = rg.x; b < rg.y; b += kBatch, ++bi) {
+    const int n = (int)min((uint32_t)kBatch, rg.y - b);
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += THREADS)
+      stage_record<TW, TH, 1>(a.rec, a.pvals[b + t], t, 0, ox, oy, bs, false, false);
+    __syncthreads();
+    uint32_t bits[2] = {0u, 0u};
+    if (!__all_sync(0xffffffffu, done)) {
+      for (int base = 0; base < n; base += 32) {
+        const int jj = base + (int)lane;
+        uint32_t vis = __ballot_sync(0xffffffffu, jj < n && ((bs.wmask[jj] >> warp) & 1u));
+        while (vis) {
+          const int bit = __ffs(vis) - 1;
+          vis &= vis - 1;
+          const int j = base + bit;
+          if (done || !box_holds(bs.box[j], px, py)) continue;
+          float alpha, G, araw, dx, dy;
+          if (!gauss_alpha(bs.uv[j], bs.co[j], fpx, fpy, alpha, G, araw, dx, dy)) continue;
+          const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
+          if (Tn < kTStop) { done = true; continue; }
+          const float w = __fmul_rn(alpha, T);
+          const float4 cdp = bs.cd[j];
+          cr = fmaf(w, cdp.x, cr); cg = fmaf(w, cdp.y, cg); cb = fmaf(w, cdp.z, cb); cd = fmaf(w, cdp.w, cd);
+          T = Tn;
+          last = b - rg.x + j + 1;
+          ++ncontrib;
+          bits[base >> 5] |= 1u << bit;
         }
       }
-      bool my_done = true;
-#pragma unroll
-      for (int i = 0; i < PPT; ++i) my_done = my_done && done[i];
-      if (__syncthreads_count(my_done) == THREADS) break;
     }
-    if (acc_sem) {
-      __syncthreads();
-      const int vw = min(TW, a.width - ox);
-      if (a.sem) {
-        for (int r = 0; r < TH; ++r) {
-          const int y = oy + r;
-          if (y >= a.height) break;
-          float *dst = a.sem + ((size_t)y * a.width + ox) * a.m + c_lo;
-          const float *src = sP + (r * TW) * a.mstride;
-          for (int e = threadIdx.x; e < vw * mc; e += THREADS) {
-            const int p = e / mc, cl = e - p * mc;
-            dst[(size_t)p * a.m + cl] = src[p * a.mstride + cl];
-          }
-        }
-      }
-      if (L1 && a.t_sem) {
-        // each warp takes kG pixels x kWG 32-class words per round: all kG*kWG
-        // coalesced target reads (L2 hits after the prefetch) are issued before
-        // any is consumed; ballots assemble the sign words
-        constexpr int kG = 4, kWG = 4;
-        const int w_lo = c_lo >> 5, w_hi = (c_hi + 31) >> 5;
-        for (int p0 = (int)warp * kG; p0 < NPIX; p0 += WARPS * kG) {
-          for (int wb = w_lo; wb < w_hi; wb += kWG) {
-            float tv[kG][kWG];
-            const float *row[kG];
-            bool okp[kG];
-#pragma unroll
-            for (int g = 0; g < kG; ++g) {
-              const int p = p0 + g;
-              const int qx = ox + p % TW, qy = oy + p / TW;
-              okp[g] = qx < a.width && qy < a.height;
-              row[g] = a.t_sem + (okp[g] ? ((size_t)qy * a.width + qx) * a.m : 0);
-#pragma unroll
-              for (int u = 0; u < kWG; ++u) {
-                const int mcl = (wb + u) * 32 + (int)lane;
-                tv[g][u] = (okp[g] && mcl < c_hi) ? __ldcs(row[g] + mcl) : 0.f;
-              }
-            }
-#pragma unroll
-            for (int g = 0; g < kG; ++g) {
-              if (!okp[g]) continue;  // uniform over the warp
-              const int p = p0 + g;
-#pragma unroll
-              for (int u = 0; u < kWG; ++u) {
-                const int wd = wb + u;
-                if (wd >= w_hi) break;
-                const int mcl = wd * 32 + (int)lane;
-                float d = 0.f;
-                if (mcl < c_hi) d = sP[p * a.mstride + (mcl - c_lo)] - tv[g][u];
-                const uint32_t nz = __ballot_sync(0xffffffffu, d != 0.f);
-                const uint32_t ng = __ballot_sync(0xffffffffu, d < 0.f);
-                l1_sem += fabsf(d);
-                if (lane == 0) {
-                  uint32_t *cp = a.codes + (size_t)((row[g] - a.t_sem) / a.m) * cw;
-                  cp[1 + wd] = nz;
-                  cp[2 + a.nwc + wd] = ng;
-                }
-              }
-            }
-          }
-        }
-      }
-      __syncthreads();  // the next chunk reuses the accumulator rows
+    if (unit0 + bi < a.mask_units) {
+      uint32_t *mw = a.masks + (size_t)(unit0 + bi) * 2 * NPIX;
+      mw[lp] = bits[0];
+      mw[NPIX + lp] = bits[1];
     }
+    if (__syncthreads_count(done) == THREADS) break;
   }
   {
-    // diagnostics: total contributions (one atomic per warp)
     uint32_t nc = ncontrib;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nc += __shfl_xor_sync(0xffffffffu, nc, o);
     if (lane == 0 && nc) atomicAdd(&a.counters->n_contrib, nc);
   }
   float l1_rgb = 0.f, l1_d = 0.f;
-#pragma unroll
-  for (int i = 0; i < PPT; ++i) {
-    if (!inside[i]) continue;
-    const size_t pix = (size_t)py[i] * a.width + px;
-    if (a.rgb_out) { a.rgb_out[3 * pix] = cr[i]; a.rgb_out[3 * pix + 1] = cg[i]; a.rgb_out[3 * pix + 2] = cb[i]; }
-    if (a.depth_out) a.depth_out[pix] = cd[i];
-    if (a.sil_out) a.sil_out[pix] = 1.f - T[i];
-    a.tfinal[pix] = T[i];
-    a.nlast[pix] = last[i];
+  if (inside) {
+    const size_t pix = (size_t)py * a.width + px;
+    if (a.rgb_out) { a.rgb_out[3 * pix] = cr; a.rgb_out[3 * pix + 1] = cg; a.rgb_out[3 * pix + 2] = cb; }
+    if (a.depth_out) a.depth_out[pix] = cd;
+    if (a.sil_out) a.sil_out[pix] = 1.f - T;
+    a.tfinal[pix] = T;
+    a.nlast[pix] = last;
     if (L1) {
-      const float d0 = cr[i] - a.t_rgb[3 * pix], d1 = cg[i] - a.t_rgb[3 * pix + 1], d2 = cb[i] - a.t_rgb[3 * pix + 2];
-      const float d3 = cd[i] - a.t_depth[pix];
+      const int cw = code_words(a.nwc);
+      const float d0 = cr - a.t_rgb[3 * pix], d1 = cg - a.t_rgb[3 * pix + 1], d2 = cb - a.t_rgb[3 * pix + 2];
+      const float d3 = cd - a.t_depth[pix];
       const uint32_t nz = (d0 != 0.f ? 1u : 0u) | (d1 != 0.f ? 2u : 0u) | (d2 != 0.f ? 4u : 0u) | (d3 != 0.f ? 8u : 0u);
       const uint32_t ng = (d0 < 0.f ? 1u : 0u) | (d1 < 0.f ? 2u : 0u) | (d2 < 0.f ? 4u : 0u) | (d3 < 0.f ? 8u : 0u);
       uint32_t *cp = a.codes + pix * cw;
@@ -247,8 +134,8 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_fwd(FwdArgs a) {
       cp[1 + a.nwc] = ng;
       if (!a.t_sem)
         for (int wd = 0; wd < a.nwc; ++wd) { cp[1 + wd] = 0u; cp[2 + a.nwc + wd] = 0u; }
-      l1_rgb += fabsf(d0) + fabsf(d1) + fabsf(d2);
-      l1_d += fabsf(d3);
+      l1_rgb = fabsf(d0) + fabsf(d1) + fabsf(d2);
+      l1_d = fabsf(d3);
     }
   }
   if (L1) {
@@ -256,14 +143,218 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_fwd(FwdArgs a) {
     for (int o = 16; o > 0; o >>= 1) {
       l1_rgb += __shfl_xor_sync(0xffffffffu, l1_rgb, o);
       l1_d += __shfl_xor_sync(0xffffffffu, l1_d, o);
-      l1_sem += __shfl_xor_sync(0xffffffffu, l1_sem, o);
     }
-    if (lane == 0) { red[0][warp] = l1_rgb; red[1][warp] = l1_d; red[2][warp] = l1_sem; }
+    if (lane == 0) { red[0][warp] = l1_rgb; red[1][warp] = l1_d; }
     __syncthreads();
     if (threadIdx.x < 3) {
       double s = 0.0;
-      for (int w = 0; w < WARPS; ++w) s += red[threadIdx.x][w];
-      a.lpart[3 * (size_t)tile + threadIdx.x] = s;
+      if (threadIdx.x < 2)
+        for (int w = 0; w < WARPS; ++w) s += red[threadIdx.x][w];
+      a.lpart[3 * (size_t)tile + threadIdx.x] = s;  // [2] (semantic) is set by pass 2
+    }
+  }
+}
+
+// Asynchronous global -> shared copies (sm_80+ cp.async), used to stage the
+// next batch while the current one is processed.
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Shared-memory layout of one pass-2 batch buffer: mean, conic, k sem pairs.
+__host__ __device__ inline size_t sem_batch_bytes(int k) {
+  return (size_t)kBatch * (8 + 16) + (size_t)kBatch * k * 8;
+}
+
+// Class chunking for pass 2, whose fixed part is two batch buffers.
+static void sem_chunks(int m, int npix, int k, bool acc, FwdArgs &a) {
+  const size_t fixed = 2 * sem_batch_bytes(k), base = batch_smem_bytes(k);
+  chunk_classes(m, npix, k, acc, &a.mchunk, &a.mstride, &a.nchunks, fixed > base ? fixed - base : 0);
+}
+
+template <int TW, int TH, bool L1>
+__global__ void __launch_bounds__(TW *TH) k_semantic(FwdArgs a) {
+  using FP = Footprint<TW, TH, 1>;
+  constexpr int THREADS = FP::kThreads;
+  constexpr int WARPS = FP::kWarps;
+  constexpr int NPIX = FP::kPix;
+  extern __shared__ float4 smem4[];
+  const int k = a.k;
+  // two batch buffers, then the accumulator rows
+  char *sbase = reinterpret_cast<char *>(smem4);
+  const size_t bbytes = sem_batch_bytes(k);
+  float *sP = reinterpret_cast<float *>(sbase + 2 * bbytes);
+  __shared__ float red[WARPS];
+  __shared__ uint32_t s_maxlast;
+
+  const int tile = blockIdx.x;
+  const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
+  const int ox = tx * TW, oy = ty * TH;
+  const uint2 rg = a.ranges[tile];
+  const int lx = FP::lx(), ly = FP::ly(0);
+  const int px = ox + lx, py = oy + ly;
+  const int lp = ly * TW + lx;
+  const bool inside = px < a.width && py < a.height;
+  const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+  float *myP = sP + lp * a.mstride;
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  const uint32_t unit0 = a.mask_off[tile];
+  const int cw = code_words(a.nwc);
+
+  if (L1 && a.t_sem && (int)threadIdx.x < TH) {
+    // warm L2 with the tile's target rows while the accumulation runs
+    const int y = oy + (int)threadIdx.x;
+    if (y < a.height) {
+      const int vw = min(TW, a.width - ox);
+      prefetch_l2(a.t_sem, (size_t)a.width * a.height * a.m * 4, a.t_sem + ((size_t)y * a.width + ox) * a.m,
+                  (size_t)vw * a.m * 4);
+    }
+  }
+  const uint32_t last = inside ? a.nlast[(size_t)py * a.width + px] : 0u;
+  if (threadIdx.x == 0) s_maxlast = 0;
+  __syncthreads();
+  if (last) atomicMax(&s_maxlast, last);
+  __syncthreads();
+  const uint32_t maxlast = s_maxlast;
+  const int nbatch = (int)((maxlast + kBatch - 1) / kBatch);
+  float l1_sem = 0.f;
+
+  auto buf_uv = [&](int q) { return reinterpret_cast<float2 *>(sbase + q * bbytes); };
+  auto buf_co = [&](int q) { return reinterpret_cast<float4 *>(sbase + q * bbytes + kBatch * 8); };
+  auto buf_sem = [&](int q) { return reinterpret_cast<int2 *>(sbase + q * bbytes + kBatch * 24); };
+  auto batch_n = [&](int bi) { return (int)min((uint32_t)kBatch, rg.y - (rg.x + (uint32_t)bi * kBatch)); };
+  auto issue = [&](int bi, uint32_t r) {  // thread t < n copies record r into slot t of buffer bi & 1
+    const int q = bi & 1, t = threadIdx.x;
+    cp_async8(buf_uv(q) + t, a.rec.uv + r);
+    cp_async16(buf_co(q) + t, a.rec.co + r);
+    const int2 *src = a.rec.sem + (size_t)r * k;
+    for (int l = 0; l < k; ++l) cp_async8(buf_sem(q) + t * k + l, src + l);
+  };
+
+  for (int c = 0; c < a.nchunks; ++c) {
+    const int c_lo = c * a.mchunk, c_hi = min(a.m, c_lo + a.mchunk);
+    const int mc = c_hi - c_lo;
+    for (int q = 0; q < mc; ++q) myP[q] = 0.f;
+    float T = 1.f;
+    // pipeline: copies of batch bi + 1 fly while batch bi is processed; the
+    // pair indices are fetched one batch further ahead
+    const int t = threadIdx.x;
+    if (nbatch > 0 && t < batch_n(0)) issue(0, a.pvals[rg.x + t]);
+    cp_async_commit();
+    uint32_t pv = (nbatch > 1 && t < batch_n(1)) ? a.pvals[rg.x + kBatch + t] : 0u;
+    cp_async_wait_all();
+    __syncthreads();
+    for (int bi = 0; bi < nbatch; ++bi) {
+      if (bi + 1 < nbatch && t < batch_n(bi + 1)) issue(bi + 1, pv);
+      cp_async_commit();
+      if (bi + 2 < nbatch && t < batch_n(bi + 2)) pv = a.pvals[rg.x + (uint32_t)(bi + 2) * kBatch + t];
+      const uint32_t b0 = (uint32_t)bi * kBatch;
+      if (b0 < last) {
+        const float2 *suv = buf_uv(bi & 1);
+        const float4 *sco = buf_co(bi & 1);
+        const int2 *ssem = buf_sem(bi & 1);
+        const uint32_t *mw = a.masks + (size_t)(unit0 + bi) * 2 * NPIX;
+        uint32_t bits[2] = {mw[lp], mw[NPIX + lp]};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          while (bits[h]) {
+            const int j = h * 32 + __ffs(bits[h]) - 1;
+            bits[h] &= bits[h] - 1;
+            float alpha, G, araw, dx, dy;
+            gauss_alpha(suv[j], sco[j], fpx, fpy, alpha, G, araw, dx, dy);
+            const float w = __fmul_rn(alpha, T);
+            const int2 *sp = ssem + j * k;
+            for (int l = 0; l < k; ++l) {
+              const int2 e = sp[l];
+              const int id = e.x - c_lo;
+              if ((unsigned)id < (unsigned)mc) myP[id] = fmaf(w, __int_as_float(e.y), myP[id]);
+            }
+            T = __fmul_rn(T, __fsub_rn(1.f, alpha));
+          }
+        }
+      }
+      cp_async_wait_all();
+      __syncthreads();
+    }
+    __syncthreads();
+    const int vw = min(TW, a.width - ox);
+    if (a.sem) {
+      for (int r = 0; r < TH; ++r) {
+        const int y = oy + r;
+        if (y >= a.height) break;
+        float *dst = a.sem + ((size_t)y * a.width + ox) * a.m + c_lo;
+        const float *src = sP + (r * TW) * a.mstride;
+        for (int e = threadIdx.x; e < vw * mc; e += THREADS) {
+          const int p = e / mc, cl = e - p * mc;
+          dst[(size_t)p * a.m + cl] = src[p * a.mstride + cl];
+        }
+      }
+    }
+    if (L1 && a.t_sem) {
+      // each warp takes kG pixels x kWG 32-class words per round: all kG*kWG
+      // coalesced target reads (L2 hits after the prefetch) are issued before
+      // any is consumed; ballots assemble the sign words
+      constexpr int kG = 4, kWG = 4;
+      const int w_lo = c_lo >> 5, w_hi = (c_hi + 31) >> 5;
+      for (int p0 = (int)warp * kG; p0 < NPIX; p0 += WARPS * kG) {
+        for (int wb = w_lo; wb < w_hi; wb += kWG) {
+          float tv[kG][kWG];
+          const float *row[kG];
+          bool okp[kG];
+#pragma unroll
+          for (int g = 0; g < kG; ++g) {
+            const int p = p0 + g;
+            const int qx = ox + p % TW, qy = oy + p / TW;
+            okp[g] = qx < a.width && qy < a.height;
+            row[g] = a.t_sem + (okp[g] ? ((size_t)qy * a.width + qx) * a.m : 0);
+#pragma unroll
+            for (int u = 0; u < kWG; ++u) {
+              const int mcl = (wb + u) * 32 + (int)lane;
+              tv[g][u] = (okp[g] && mcl < c_hi) ? __ldcs(row[g] + mcl) : 0.f;
+            }
+          }
+#pragma unroll
+          for (int g = 0; g < kG; ++g) {
+            if (!okp[g]) continue;  // uniform over the warp
+            const int p = p0 + g;
+#pragma unroll
+            for (int u = 0; u < kWG; ++u) {
+              const int wd = wb + u;
+              if (wd >= w_hi) break;
+              const int mcl = wd * 32 + (int)lane;
+              float d = 0.f;
+              if (mcl < c_hi) d = sP[p * a.mstride + (mcl - c_lo)] - tv[g][u];
+              const uint32_t nz = __ballot_sync(0xffffffffu, d != 0.f);
+              const uint32_t ng = __ballot_sync(0xffffffffu, d < 0.f);
+              l1_sem += fabsf(d);
+              if (lane == 0) {
+                uint32_t *cp = a.codes + (size_t)((row[g] - a.t_sem) / a.m) * cw;
+                cp[1 + wd] = nz;
+                cp[2 + a.nwc + wd] = ng;
+              }
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();  // the next chunk reuses the accumulator rows
+  }
+  if (L1 && a.t_sem) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l1_sem += __shfl_xor_sync(0xffffffffu, l1_sem, o);
+    if (lane == 0) red[warp] = l1_sem;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < WARPS; ++w) s += red[w];
+      a.lpart[3 * (size_t)tile + 2] = s;
     }
   }
 }
@@ -290,32 +381,30 @@ __global__ void k_l1_tiles_final(const double *lpart, int ntiles, double npix, d
   }
 }
 
-template <int TW, int TH, bool L1, int PPT>
-static cudaError_t launch_fwd_shape(const FwdArgs &a, int grid, size_t smem, cudaStream_t s) {
+template <int TW, int TH, bool L1>
+static cudaError_t launch_shape(const FwdArgs &a, int grid, size_t smem_sem, bool run_sem, cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_render_fwd<TW, TH, L1, PPT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
+    cudaError_t e = cudaFuncSetAttribute(k_semantic<TW, TH, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemBudget);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_render_fwd<TW, TH, L1, PPT><<<grid, TW * TH / PPT, smem, s>>>(a);
+  k_blend<TW, TH, L1><<<grid, TW * TH, batch_smem_bytes(0), s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !run_sem) return e;
+  k_semantic<TW, TH, L1><<<grid, TW * TH, smem_sem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <bool L1, int PPT>
-static cudaError_t dispatch_fwd_ppt(int tw, int th, const FwdArgs &a, int grid, size_t smem, cudaStream_t s) {
-  if (tw == 16 && th == 16) return launch_fwd_shape<16, 16, L1, PPT>(a, grid, smem, s);
-  if (tw == 16 && th == 8) return launch_fwd_shape<16, 8, L1, PPT>(a, grid, smem, s);
-  if (tw == 8 && th == 8) return launch_fwd_shape<8, 8, L1, PPT>(a, grid, smem, s);
-  if (tw == 32 && th == 8) return launch_fwd_shape<32, 8, L1, PPT>(a, grid, smem, s);
-  return cudaErrorInvalidConfiguration;
-}
-
 template <bool L1>
-static cudaError_t dispatch_fwd(const Layout &L, const FwdArgs &a, int grid, size_t smem, cudaStream_t s) {
-  if (L.ppt == 2) return dispatch_fwd_ppt<L1, 2>(L.tile_w, L.tile_h, a, grid, smem, s);
-  return dispatch_fwd_ppt<L1, 1>(L.tile_w, L.tile_h, a, grid, smem, s);
+static cudaError_t dispatch_fwd(const Layout &L, const FwdArgs &a, int grid, size_t smem_sem, bool run_sem,
+                                cudaStream_t s) {
+  if (L.tile_w == 16 && L.tile_h == 16) return launch_shape<16, 16, L1>(a, grid, smem_sem, run_sem, s);
+  if (L.tile_w == 16 && L.tile_h == 8) return launch_shape<16, 8, L1>(a, grid, smem_sem, run_sem, s);
+  if (L.tile_w == 8 && L.tile_h == 8) return launch_shape<8, 8, L1>(a, grid, smem_sem, run_sem, s);
+  if (L.tile_w == 32 && L.tile_h == 8) return launch_shape<32, 8, L1>(a, grid, smem_sem, run_sem, s);
+  return cudaErrorInvalidConfiguration;
 }
 
 static FwdArgs fwd_args(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc) {
@@ -328,7 +417,21 @@ static FwdArgs fwd_args(const Layout &L, const WsPtrs &P, int pbuf, const gs_sce
   a.tiles_x = (L.cam0_w + L.tile_w - 1) / L.tile_w;
   a.tfinal = P.tfinal; a.nlast = P.nlast;
   a.counters = P.counters;
+  a.mask_off = P.mask_off;
+  a.masks = P.masks;
+  a.mask_units = (uint32_t)L.mask_units;
+  a.codes = P.codes;
+  a.nwc = L.nwc;
+  a.lpart = P.lpart;
   return a;
+}
+
+// First (tile, batch) unit of every tile: batches per tile, exclusive scan.
+static cudaError_t launch_mask_offsets(const Layout &L, const WsPtrs &P, int grid, cudaStream_t s) {
+  k_tile_batches<<<(grid + 255) / 256, 256, 0, s>>>(P.ranges, (uint32_t)grid, P.mask_off);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_scan_single(P.mask_off, (uint32_t)grid, nullptr, 0xffffffffu, P.counters, s);
 }
 
 cudaError_t launch_render_fwd(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc, float *rgb,
@@ -337,11 +440,13 @@ cudaError_t launch_render_fwd(const Layout &L, const WsPtrs &P, int pbuf, const 
   const int tiles_y = (L.cam0_h + L.tile_h - 1) / L.tile_h;
   a.rgb_out = rgb; a.depth_out = depth; a.sil_out = sil; a.sem = sem;
   const int npix = L.tile_w * L.tile_h;  // accumulator rows: one per pixel of the tile
-  chunk_classes(sc.m, npix, sc.k, sem != nullptr, &a.mchunk, &a.mstride, &a.nchunks);
-  const size_t smem = batch_smem_bytes(sc.k) + (sem ? (size_t)npix * a.mstride * sizeof(float) : 0);
+  sem_chunks(sc.m, npix, sc.k, sem != nullptr, a);
+  const size_t smem = 2 * sem_batch_bytes(sc.k) + (sem ? (size_t)npix * a.mstride * sizeof(float) : 0);
   const int grid = a.tiles_x * tiles_y;
   if (grid == 0) return cudaSuccess;
-  return dispatch_fwd<false>(L, a, grid, smem, s);
+  cudaError_t e = launch_mask_offsets(L, P, grid, s);
+  if (e != cudaSuccess) return e;
+  return dispatch_fwd<false>(L, a, grid, smem, sem != nullptr, s);
 }
 
 cudaError_t launch_render_fwd_l1(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc,
@@ -351,16 +456,15 @@ cudaError_t launch_render_fwd_l1(const Layout &L, const WsPtrs &P, int pbuf, con
   const int tiles_y = (L.cam0_h + L.tile_h - 1) / L.tile_h;
   a.rgb_out = rgb; a.depth_out = depth; a.sil_out = sil; a.sem = sem;
   a.t_rgb = t_rgb; a.t_depth = t_depth; a.t_sem = t_sem;
-  a.codes = P.codes;
-  a.nwc = L.nwc;
-  a.lpart = P.lpart;
   const bool acc = sem != nullptr || t_sem != nullptr;
   const int npix = L.tile_w * L.tile_h;
-  chunk_classes(sc.m, npix, sc.k, acc, &a.mchunk, &a.mstride, &a.nchunks);
-  const size_t smem = batch_smem_bytes(sc.k) + (acc ? (size_t)npix * a.mstride * sizeof(float) : 0);
+  sem_chunks(sc.m, npix, sc.k, acc, a);
+  const size_t smem = 2 * sem_batch_bytes(sc.k) + (acc ? (size_t)npix * a.mstride * sizeof(float) : 0);
   const int grid = a.tiles_x * tiles_y;
   if (grid == 0) return cudaSuccess;
-  cudaError_t e = dispatch_fwd<true>(L, a, grid, smem, s);
+  cudaError_t e = launch_mask_offsets(L, P, grid, s);
+  if (e != cudaSuccess) return e;
+  e = dispatch_fwd<true>(L, a, grid, smem, acc, s);
   if (e != cudaSuccess) return e;
   k_l1_tiles_final<<<1, 1024, 0, s>>>(P.lpart, grid, (double)L.npix, (double)sc.m, t_sem ? 1 : 0, loss);
   return cudaGetLastError();

@@ -61,9 +61,11 @@ def test_workspace_size_and_layout_host_only(lib):
             mp.pair_rec, mp.tile_ranges, mp.tile_offset]
     assert all(base <= p < base + size for p in ptrs)
     assert mp.record_capacity == 100 and mp.total_tiles == 4 * 3
-    # more views -> more tiles and records
-    sc2, cams2, cfg2 = _structs(views=5)
-    assert lib.gs_workspace_size(ctypes.byref(sc2), cams2, 5, ctypes.byref(cfg2)) > size
+    # more candidate views -> more tiles and records
+    sc2, cams2, cfg2 = _structs(views=2)
+    sc5, cams5, cfg5 = _structs(views=5)
+    assert lib.gs_workspace_size(ctypes.byref(sc5), cams5, 5, ctypes.byref(cfg5)) > \
+        lib.gs_workspace_size(ctypes.byref(sc2), cams2, 2, ctypes.byref(cfg2)) > 0
 
 
 @pytest.mark.parametrize("bad", ["k0", "k17", "m0", "views0", "views257", "tile0", "width0", "near0", "fx_nan"])
