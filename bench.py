@@ -40,13 +40,15 @@ ORACLE_ROW_STEP_REF = 40  # reference arm: every 40th row per step (~1.5 s)
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="room300k")
     ap.add_argument("--no-candidates", action="store_true")
     ap.add_argument("--cand-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", default=None, help="WxH: fixed tile shape instead of the autotuner's")
+    ap.add_argument("--ppt", type=int, default=2, help="pixels per thread of the adjoint with --tile")
     return ap.parse_args()
 
 
@@ -89,7 +91,7 @@ def max_over_ranks(x: float, world: int, device) -> float:
 # ---------------------------------------------------------------------------
 
 class ClockSampler:
-    """Samples nvidia-smi SM clocks and throttle reasons every 200 ms."""
+    """Samples nvidia-smi SM clocks and throttle reasons every 100 ms."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -100,10 +102,20 @@ class ClockSampler:
         try:
             self.fh = open(path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+
+    def wait_first(self, limit_s: float = 3.0) -> None:
+        """Blocks until the first sample is written (nvidia-smi start-up), so
+        that the samples fall inside the region timed next."""
+        t0 = time.time()
+        while self.proc is not None and time.time() - t0 < limit_s:
+            self.fh.flush()
+            if os.path.getsize(self.path) > 0:
+                return
+            time.sleep(0.02)
 
     def stop(self) -> dict | None:
         if self.proc is None:
@@ -229,7 +241,11 @@ def main():
     del rast0
     # launch configuration picked by the autotuner (outside the timed region)
     from paper_2506_00225_gb300 import autotune
-    best, tune_table = autotune.tune_mapping(g, cam, t_rgb, t_depth, t_sem)
+    if args.tile:
+        tw_, th_ = (int(x) for x in args.tile.lower().split("x"))
+        best, tune_table = {"tile": (tw_, th_), "px_per_thread": args.ppt}, None
+    else:
+        best, tune_table = autotune.tune_mapping(g, cam, t_rgb, t_depth, t_sem)
     rast = raster.Rasterizer(tile=best["tile"], px_per_thread=best["px_per_thread"], device=dev)
     params = [t.clone().requires_grad_(True) for t in (g.means, g.scales, g.quats, g.opacity, g.rgb, g.sem_w)]
     rast.forward(g, cam, check=True)  # sizes the workspace capacities
@@ -301,10 +317,9 @@ def main():
         step_fused(t_rgb, t_depth, t_sem)
     torch.cuda.synchronize()
 
-    clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")) \
-        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ClockSampler(local, f"/tmp/clocks_rank{rank}.csv")
-    ph_ms = phase_times(step_fused, max(3, args.steps // 3))
-    un_ph = phase_times(step_unfused, max(3, args.steps // 3))
+    ph_steps = min(20, max(3, args.steps // 3))
+    ph_ms = phase_times(step_fused, ph_steps)
+    un_ph = phase_times(step_unfused, ph_steps)
     g_fused, g_loss = capture(step_fused)
     g_unfused, _ = capture(step_unfused)
     for _ in range(args.warmup):
@@ -312,6 +327,9 @@ def main():
     torch.cuda.synchronize()
 
     # ---- timed region (headline: fused step, whole step replayed as one CUDA graph)
+    clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")) \
+        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ClockSampler(local, f"/tmp/clocks_rank{rank}.csv")
+    clocks.wait_first()
     barrier(world)
     torch.cuda.synchronize()
     step_ms = timed_graph(g_fused, args.steps)
@@ -323,7 +341,7 @@ def main():
 
     # the same step with the semantic map written, a separate L1 kernel and
     # the map-sized gradient read back by the adjoint
-    un_ms = timed_graph(g_unfused, max(3, args.steps // 2))
+    un_ms = timed_graph(g_unfused, min(50, max(3, args.steps // 2)))
     un_total = max_over_ranks(sum(un_ms), world, dev) / len(un_ms)
 
     # ---- roofline ---------------------------------------------------------------
@@ -373,7 +391,7 @@ def main():
     pin = lambda t_: t_.detach().cpu().pin_memory()
     h_rgb, h_depth, h_sem = pin(t_rgb), pin(t_depth), pin(t_sem)
     h_loss = torch.empty((), dtype=torch.float32).pin_memory()
-    e2e_steps = max(3, args.steps // 2)
+    e2e_steps = min(100, max(3, args.steps // 2))
     barrier(world)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -400,12 +418,13 @@ def main():
 
     # launches of our kernels per fused step: project 4 (setup, count, scan,
     # emit); depth sort: reset, histogram, one per pass; pair emission 3;
-    # tile sort: reset, histogram, one per pass; ranges 2; fused forward +
-    # loss reduction 2; backward 3 (zero, blend adjoint, projection adjoint)
+    # tile sort: reset, histogram, one per pass; ranges 2; fused forward 5
+    # (batches per tile, their scan, blend pass, semantic pass, loss
+    # reduction); backward 3 (zero, blend adjoint, projection adjoint)
     passes = lambda bits: (bits + 7) // 8
     tw_, th_ = best["tile"]
     tiles = ((W + tw_ - 1) // tw_) * ((H + th_ - 1) // th_)
-    per_step = 4 + (2 + passes(31)) + 3 + (2 + passes(max(1, (tiles - 1).bit_length()))) + 2 + 2 + 3
+    per_step = 4 + (2 + passes(31)) + 3 + (2 + passes(max(1, (tiles - 1).bit_length()))) + 2 + 5 + 3
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

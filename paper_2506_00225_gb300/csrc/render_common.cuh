@@ -28,6 +28,11 @@ struct Footprint {
   // tile-local pixel i of this thread
   __device__ static int lx() { return ((threadIdx.x >> 5) % kWX) * 8 + (threadIdx.x & 7); }
   __device__ static int ly(int i) { return ((threadIdx.x >> 5) / kWX) * kBH + ((threadIdx.x & 31) >> 3) + 4 * i; }
+  // thread holding tile-local pixel p (raster order); PPT = 1 only
+  __device__ static int thread_of(int p) {
+    const int x = p % TW, y = p / TW;
+    return ((y >> 2) * kWX + (x >> 3)) * 32 + (y & 3) * 8 + (x & 7);
+  }
   // bit w set when box [bx0,bx1] x [by0,by1] (tile-local pixels) meets warp w's block
   __device__ static uint32_t warp_mask(int bx0, int bx1, int by0, int by1) {
     uint32_t m = 0;

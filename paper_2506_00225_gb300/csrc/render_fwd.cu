@@ -179,7 +179,21 @@ static void sem_chunks(int m, int npix, int k, bool acc, FwdArgs &a) {
   chunk_classes(m, npix, k, acc, &a.mchunk, &a.mstride, &a.nchunks, fixed > base ? fixed - base : 0);
 }
 
-template <int TW, int TH, bool L1>
+// Adds w * weight to the accumulator slot of each of the Gaussian's k
+// (class, weight) entries that falls in the class chunk [c_lo, c_lo + mc).
+// K > 0 fixes k at compile time.
+template <int K>
+__device__ __forceinline__ void scatter_classes(float *row, const int2 *e, int k, int c_lo, int mc, float w) {
+  const int n = K > 0 ? K : k;
+#pragma unroll
+  for (int l = 0; l < n; ++l) {
+    const int2 v = e[l];
+    const int id = v.x - c_lo;
+    if ((unsigned)id < (unsigned)mc) row[id] = fmaf(w, __int_as_float(v.y), row[id]);
+  }
+}
+
+template <int TW, int TH, bool L1, int K>
 __global__ void __launch_bounds__(TW *TH) k_semantic(FwdArgs a) {
   using FP = Footprint<TW, TH, 1>;
   constexpr int THREADS = FP::kThreads;
@@ -203,7 +217,7 @@ __global__ void __launch_bounds__(TW *TH) k_semantic(FwdArgs a) {
   const int lp = ly * TW + lx;
   const bool inside = px < a.width && py < a.height;
   const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
-  float *myP = sP + lp * a.mstride;
+  float *myP = sP + threadIdx.x * a.mstride;  // accumulator row of this thread's pixel
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t unit0 = a.mask_off[tile];
   const int cw = code_words(a.nwc);
@@ -256,28 +270,32 @@ __global__ void __launch_bounds__(TW *TH) k_semantic(FwdArgs a) {
       cp_async_commit();
       if (bi + 2 < nbatch && t < batch_n(bi + 2)) pv = a.pvals[rg.x + (uint32_t)(bi + 2) * kBatch + t];
       const uint32_t b0 = (uint32_t)bi * kBatch;
+      // warp-uniform walk over the union of the warp's contributor bits: the
+      // Gaussian's entries are broadcast reads, lanes that it does not touch
+      // add zero weight, and the accumulator rows are indexed by thread so
+      // that the 32 lanes' adds to one class fall in 32 distinct banks
+      uint32_t mine[2] = {0u, 0u};
       if (b0 < last) {
-        const float2 *suv = buf_uv(bi & 1);
-        const float4 *sco = buf_co(bi & 1);
-        const int2 *ssem = buf_sem(bi & 1);
         const uint32_t *mw = a.masks + (size_t)(unit0 + bi) * 2 * NPIX;
-        uint32_t bits[2] = {mw[lp], mw[NPIX + lp]};
+        mine[0] = mw[lp];
+        mine[1] = mw[NPIX + lp];
+      }
+      const float2 *suv = buf_uv(bi & 1);
+      const float4 *sco = buf_co(bi & 1);
+      const int2 *ssem = buf_sem(bi & 1);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          while (bits[h]) {
-            const int j = h * 32 + __ffs(bits[h]) - 1;
-            bits[h] &= bits[h] - 1;
-            float alpha, G, araw, dx, dy;
-            gauss_alpha(suv[j], sco[j], fpx, fpy, alpha, G, araw, dx, dy);
-            const float w = __fmul_rn(alpha, T);
-            const int2 *sp = ssem + j * k;
-            for (int l = 0; l < k; ++l) {
-              const int2 e = sp[l];
-              const int id = e.x - c_lo;
-              if ((unsigned)id < (unsigned)mc) myP[id] = fmaf(w, __int_as_float(e.y), myP[id]);
-            }
-            T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-          }
+      for (int h = 0; h < 2; ++h) {
+        uint32_t un = __reduce_or_sync(0xffffffffu, mine[h]);
+        while (un) {
+          const int jb = __ffs(un) - 1;
+          un &= un - 1;
+          const int j = h * 32 + jb;
+          float alpha = 0.f, G, araw, dx, dy;
+          gauss_alpha(suv[j], sco[j], fpx, fpy, alpha, G, araw, dx, dy);
+          const bool on = (mine[h] >> jb) & 1u;
+          const float w = on ? __fmul_rn(alpha, T) : 0.f;
+          if (on) T = __fmul_rn(T, __fsub_rn(1.f, alpha));
+          scatter_classes<K>(myP, ssem + j * k, k, c_lo, mc, w);
         }
       }
       cp_async_wait_all();
@@ -290,10 +308,9 @@ __global__ void __launch_bounds__(TW *TH) k_semantic(FwdArgs a) {
         const int y = oy + r;
         if (y >= a.height) break;
         float *dst = a.sem + ((size_t)y * a.width + ox) * a.m + c_lo;
-        const float *src = sP + (r * TW) * a.mstride;
         for (int e = threadIdx.x; e < vw * mc; e += THREADS) {
           const int p = e / mc, cl = e - p * mc;
-          dst[(size_t)p * a.m + cl] = src[p * a.mstride + cl];
+          dst[(size_t)p * a.m + cl] = sP[FP::thread_of(r * TW + p) * a.mstride + cl];
         }
       }
     }
@@ -330,7 +347,7 @@ __global__ void __launch_bounds__(TW *TH) k_semantic(FwdArgs a) {
               if (wd >= w_hi) break;
               const int mcl = wd * 32 + (int)lane;
               float d = 0.f;
-              if (mcl < c_hi) d = sP[p * a.mstride + (mcl - c_lo)] - tv[g][u];
+              if (mcl < c_hi) d = sP[FP::thread_of(p) * a.mstride + (mcl - c_lo)] - tv[g][u];
               const uint32_t nz = __ballot_sync(0xffffffffu, d != 0.f);
               const uint32_t ng = __ballot_sync(0xffffffffu, d < 0.f);
               l1_sem += fabsf(d);
@@ -381,20 +398,28 @@ __global__ void k_l1_tiles_final(const double *lpart, int ntiles, double npix, d
   }
 }
 
-template <int TW, int TH, bool L1>
-static cudaError_t launch_shape(const FwdArgs &a, int grid, size_t smem_sem, bool run_sem, cudaStream_t s) {
+template <int TW, int TH, bool L1, int K>
+static cudaError_t launch_semantic(const FwdArgs &a, int grid, size_t smem, cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_semantic<TW, TH, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_semantic<TW, TH, L1, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kSmemBudget);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
+  k_semantic<TW, TH, L1, K><<<grid, TW * TH, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int TW, int TH, bool L1>
+static cudaError_t launch_shape(const FwdArgs &a, int grid, size_t smem_sem, bool run_sem, cudaStream_t s) {
   k_blend<TW, TH, L1><<<grid, TW * TH, batch_smem_bytes(0), s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !run_sem) return e;
-  k_semantic<TW, TH, L1><<<grid, TW * TH, smem_sem, s>>>(a);
-  return cudaGetLastError();
+  // the common top-k sizes get an unrolled scatter
+  if (a.k == 3) return launch_semantic<TW, TH, L1, 3>(a, grid, smem_sem, s);
+  if (a.k == 8) return launch_semantic<TW, TH, L1, 8>(a, grid, smem_sem, s);
+  return launch_semantic<TW, TH, L1, 0>(a, grid, smem_sem, s);
 }
 
 template <bool L1>
