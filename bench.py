@@ -13,7 +13,11 @@ too and reported under ``unfused_step``.
 
 Also measured in the same run (key ``candidates``): batched candidate-view
 rendering of 96 poses of mixed resolution (views/s), and the same views
-issued as one plain launch chain per view.
+issued as one plain launch chain per view.  Key ``large_scene``: the mapping
+step on 2M Gaussians (256 classes, top-8) with and without stored
+contributor bits, and its peak device memory.  Key ``mixed_stream``: one
+mapping step plus 128 candidate views captured as one CUDA graph, against
+the same work as plain per-view launches.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -47,6 +51,7 @@ def parse():
     ap.add_argument("--no-candidates", action="store_true")
     ap.add_argument("--cand-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the 2M-Gaussian mapping and mixed-stream runs")
     ap.add_argument("--tile", default=None, help="WxH: fixed tile shape instead of the autotuner's")
     ap.add_argument("--ppt", type=int, default=2, help="pixels per thread of the adjoint with --tile")
     return ap.parse_args()
@@ -288,29 +293,10 @@ def main():
         return {k_: statistics.mean(v) for k_, v in ph.items()}
 
     def capture(step):
-        side = torch.cuda.Stream()
-        side.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(side):
-            for _ in range(2):
-                step(t_rgb, t_depth, t_sem)
-        torch.cuda.current_stream().wait_stream(side)
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
-            out = step(t_rgb, t_depth, t_sem)
-        return graph, out
+        return capture_graph(lambda: step(t_rgb, t_depth, t_sem))
 
     def timed_graph(graph, steps):
-        ms = []
-        for _ in range(steps):
-            flush.zero_()
-            s_ = torch.cuda.Event(enable_timing=True)
-            e_ = torch.cuda.Event(enable_timing=True)
-            s_.record()
-            graph.replay()
-            e_.record()
-            ms.append((s_, e_))
-        torch.cuda.synchronize()
-        return [a.elapsed_time(b) for a, b in ms]
+        return time_graph(graph, steps, flush)
 
     for _ in range(args.warmup):
         step_unfused(t_rgb, t_depth, t_sem)
@@ -415,6 +401,9 @@ def main():
     cand = None
     if not args.no_candidates:
         cand = bench_candidates(args, dev, flush)
+    large = mixed = None
+    if not args.no_large:
+        large, mixed = bench_large(args, dev, flush, scenes.workload("mixed2m"))
 
     # launches of our kernels per fused step: project 4 (setup, count, scan,
     # emit); depth sort: reset, histogram, one per pass; pair emission 3;
@@ -449,12 +438,163 @@ def main():
                                  "phases_ms": {k_: round(v, 4) for k_, v in un_ph.items()},
                                  "what": "rasterize (writes the HxWxM map) + separate L1 kernel + adjoint reading "
                                          "the HxWxM gradient"},
-                "candidates": cand}
+                "candidates": cand,
+                "large_scene": large,
+                "mixed_stream": mixed}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def capture_graph(step):
+    """Captures step() as one CUDA graph after two eager runs on a side
+    stream; returns (graph, the captured call's return value)."""
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            step()
+    torch.cuda.current_stream().wait_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        out = step()
+    return graph, out
+
+
+def time_graph(graph, steps, flush):
+    """Per-replay device times (ms), L2 flushed before each replay (outside
+    the events)."""
+    import torch
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        s_ = torch.cuda.Event(enable_timing=True)
+        e_ = torch.cuda.Event(enable_timing=True)
+        s_.record()
+        graph.replay()
+        e_.record()
+        ms.append((s_, e_))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ms]
+
+
+def _mapping_step(rast, g, cam, params, t_rgb, t_depth, t_sem):
+    from paper_2506_00225_gb300 import raster
+
+    def step():
+        for p in params:
+            p.grad = None
+        loss = raster.render_l1(rast, g, cam, t_rgb, t_depth, t_sem, *params, check=False)
+        loss.backward()
+        return loss
+    return step
+
+
+def bench_large(args, dev, flush, wl):
+    """rooms2m: the mapping step on 2M Gaussians (M=256, top-8) in both
+    storage modes, with peak device memory; then the mixed stream (mapping
+    step + 128 batched candidate views, one graph) against the same work as
+    plain per-view launches."""
+    import torch
+    from paper_2506_00225_gb300 import autotune, raster
+    sc, cam = wl["scene"], wl["cams"][0]
+    g = raster.Gaussians.from_scene(sc, dev)
+    gt = raster.Gaussians.from_scene(wl["target"], dev)
+    with torch.no_grad():
+        t_rgb, t_depth, _, t_sem = raster.Rasterizer(device=dev).forward(gt, cam, check=True)
+        t_rgb, t_depth, t_sem = t_rgb.clone(), t_depth.clone(), t_sem.clone()
+    del gt
+    best, _ = autotune.tune_mapping(g, cam, t_rgb, t_depth, t_sem)
+    tile, ppt = best["tile"], best["px_per_thread"]
+    steps = max(3, min(20, args.steps))
+    modes = {}
+    rast_keep = None
+    for recompute in (True, False):
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        torch.cuda.reset_peak_memory_stats(dev)
+        base = torch.cuda.memory_allocated(dev)
+        rast = raster.Rasterizer(tile=tile, px_per_thread=ppt, recompute_bwd=recompute, device=dev)
+        params = [t.clone().requires_grad_(True) for t in (g.means, g.scales, g.quats, g.opacity, g.rgb, g.sem_w)]
+        rast.forward(g, cam, check=True)
+        step = _mapping_step(rast, g, cam, params, t_rgb, t_depth, t_sem)
+        for _ in range(3):
+            step()
+        graph, _ = capture_graph(step)
+        for _ in range(3):
+            graph.replay()
+        ms = statistics.mean(time_graph(graph, steps, flush))
+        cnt = rast.counters()
+        if cnt.status != 0:
+            raise RuntimeError(f"device status {cnt.status} (rooms2m)")
+        modes["recompute" if recompute else "stored_bits"] = {
+            "value": 1000.0 / ms, "unit": "iters/s", "ms_per_step": ms,
+            "peak_device_bytes": int(torch.cuda.max_memory_allocated(dev)),
+            "step_peak_bytes": int(torch.cuda.max_memory_allocated(dev) - base),
+            "resident_before_bytes": int(base),
+            "workspace_bytes": int(rast.ws.numel())}
+        if recompute:
+            rast_keep, params_keep = rast, params
+        del graph
+    large = {"metric": "mapping fwd+bwd iters/s @680x1200 (2M Gaussians, M=256, top-8)",
+             "workload": "rooms2m: 2M Gaussians in 2x2 adjoining 6x6x3 m rooms, 256 classes, top-8 semantics, "
+                         "one 680x1200 view (f=600), fused mean-L1 step through the autograd Function",
+             "value": modes["recompute"]["value"], "unit": "iters/s",
+             "autotune": {"tile": "%dx%d" % tile, "px_per_thread": ppt},
+             "counts": {"visible_records": int(cnt.n_records), "tile_gaussian_pairs": int(cnt.n_pairs),
+                        "contributions": int(cnt.n_contrib)},
+             "modes": modes}
+
+    # ---- mixed stream: mapping step + 128 candidates, one graph ----------
+    cams = wl["cand_cams"]
+    rc = raster.Rasterizer(tile=tile, device=dev)
+    cand_out = rc.candidates(g, cams, check=True)
+    step = _mapping_step(rast_keep, g, cam, params_keep, t_rgb, t_depth, t_sem)
+
+    def iteration():
+        loss = step()
+        rc.candidates(g, cams, check=False, out=cand_out)
+        return loss
+    graph, _ = capture_graph(iteration)
+    for _ in range(2):
+        graph.replay()
+    iters = max(3, min(8, args.steps))
+    ms_graph = statistics.mean(time_graph(graph, iters, flush))
+    # the same work as plain launches: the eager mapping step, then one
+    # projection / binning / render chain per candidate view
+    singles = {}
+    for c in cams:
+        key = (c.width, c.height)
+        if key not in singles:
+            singles[key] = raster.Rasterizer(tile=tile, device=dev)
+            singles[key].candidates(g, [c], check=True)
+    torch.cuda.synchronize()
+    plain = []
+    for _ in range(2):
+        flush.zero_()
+        s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s_.record()
+        step()
+        for c in cams:
+            singles[(c.width, c.height)].candidates(g, [c], check=False)
+        e_.record()
+        plain.append((s_, e_))
+    torch.cuda.synchronize()
+    ms_plain = statistics.mean(a.elapsed_time(b) for a, b in plain)
+    if rc.counters().status != 0:
+        raise RuntimeError("device status after the mixed stream")
+    mixed = {"metric": "mixed iterations/s (mapping step + 128 candidate views)",
+             "workload": "mixed2m: the rooms2m scene + Gamma(2,0.5) uncertainty; per iteration one fused mapping "
+                         "step (recompute mode) and 128 candidate views (64 @170x300, 48 @340x600, 16 @680x1200) "
+                         "sharing one projection/binning pass",
+             "value": 1000.0 / ms_graph, "unit": "iters/s", "ms_per_iter": ms_graph,
+             "candidate_views_per_s": 1000.0 * len(cams) / ms_graph,
+             "plain_per_view_launches": {"value": 1000.0 / ms_plain, "unit": "iters/s", "ms_per_iter": ms_plain},
+             "graph_batched_speedup": ms_plain / ms_graph}
+    return large, mixed
 
 
 def bench_candidates(args, dev, flush):

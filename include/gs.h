@@ -95,13 +95,21 @@ typedef struct gs_camera {
  *   record_capacity      max visible (view, Gaussian) records in the
  *                        workspace; <= 0 means n * n_views (never overflows)
  *   pair_capacity        max (tile, Gaussian) pairs; <= 0 means
- *                        8 * record_capacity */
+ *                        8 * record_capacity
+ *   recompute_bwd        0: the forward keeps one bit per (pixel, staged
+ *                        Gaussian) that contributed (pair_capacity / 8 bytes
+ *                        per tile pixel), read by the semantic pass and the
+ *                        adjoint; 1: no per-pixel storage besides the final
+ *                        transmittance and last contributor -- both re-test
+ *                        every (pixel, Gaussian) pair of the tile instead.
+ *                        Results are identical. */
 typedef struct gs_config {
   int32_t tile_w, tile_h;
   int32_t sem_detach_geometry;
   int32_t px_per_thread;
   int64_t record_capacity;
   int64_t pair_capacity;
+  int32_t recompute_bwd;
 } gs_config;
 
 /* Counters read back by gs_read_counters. */

@@ -47,6 +47,7 @@ bool make_layout(const gs_scene *scene, const gs_camera *cams, int n_views, cons
   L->n = scene->n; L->k = scene->k; L->m = scene->m; L->n_views = n_views;
   L->tile_w = cfg.tile_w; L->tile_h = cfg.tile_h;
   if (cfg.px_per_thread < 0 || cfg.px_per_thread > 2) return false;
+  if (cfg.recompute_bwd != 0 && cfg.recompute_bwd != 1) return false;
   L->ppt = cfg.px_per_thread == 0 ? 2 : cfg.px_per_thread;
   uint64_t tiles = 0;
   for (int v = 0; v < n_views; ++v) {
@@ -104,9 +105,10 @@ bool make_layout(const gs_scene *scene, const gs_camera *cams, int n_views, cons
   L->off_codes = take(n_views == 1 ? 4 * (size_t)L->npix * (2 * (1 + L->nwc)) : 32);
   L->off_lpart = take(n_views == 1 ? 3 * sizeof(double) * (size_t)(tiles > 0 ? tiles : 1) : 32);
   // one unit = one staged batch of one tile: 2 words per tile pixel
-  L->mask_units = n_views == 1 ? pcap / kBatch + (int64_t)tiles + 1 : 1;
+  // (none with recompute_bwd: pass 2 and the adjoint re-test the pairs)
+  L->mask_units = (n_views == 1 && !cfg.recompute_bwd) ? pcap / kBatch + (int64_t)tiles + 1 : 0;
   L->off_mask_off = take(sizeof(uint32_t) * (size_t)(tiles + 1));
-  L->off_masks = take(n_views == 1 ? 8 * (size_t)L->mask_units * cfg.tile_w * cfg.tile_h : 32);
+  L->off_masks = take(L->mask_units ? 8 * (size_t)L->mask_units * cfg.tile_w * cfg.tile_h : 32);
   L->total = off;
   return true;
 }

@@ -123,16 +123,32 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
     for (int t = threadIdx.x; t < n; t += FP::kThreads)
       stage_record<TW, TH, PPT>(a.rec, a.pvals[lo + t], t, k, ox, oy, bs, has_dsem, false);
     __syncthreads();
-    // contributor bits of this batch (written by the forward pass 1)
-    const uint32_t unit = a.mask_off[tile] + (uint32_t)bi;
-    const uint32_t *mw = a.masks + (size_t)unit * 2 * FP::kPix;
+    // contributor bits of this batch: written by the forward pass 1, or
+    // re-tested (pairs up to the last contributor whose pixel box holds the
+    // pixel and whose alpha passes 1/255)
     uint32_t mb[PPT][2];
+    if (a.masks) {
+      const uint32_t unit = a.mask_off[tile] + (uint32_t)bi;
+      const uint32_t *mw = a.masks + (size_t)unit * 2 * FP::kPix;
 #pragma unroll
-    for (int i = 0; i < PPT; ++i) {
-      const int lp = FP::ly(i) * TW + lx;
-      const bool ok = px < a.width && py[i] < a.height;
-      mb[i][0] = ok ? mw[lp] : 0u;
-      mb[i][1] = ok ? mw[FP::kPix + lp] : 0u;
+      for (int i = 0; i < PPT; ++i) {
+        const int lp = FP::ly(i) * TW + lx;
+        const bool ok = px < a.width && py[i] < a.height;
+        mb[i][0] = ok ? mw[lp] : 0u;
+        mb[i][1] = ok ? mw[FP::kPix + lp] : 0u;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < PPT; ++i) {
+        mb[i][0] = mb[i][1] = 0u;
+        const uint32_t b0 = (uint32_t)bi * kBatch;
+        const int nj = nl[i] > b0 ? min(n, (int)(nl[i] - b0)) : 0;
+        for (int j = 0; j < nj; ++j) {
+          if (!((bs.wmask[j] >> warp) & 1u) || !box_holds(bs.box[j], px, py[i])) continue;
+          float al, G_, ar, dx_, dy_;
+          if (gauss_alpha(bs.uv[j], bs.co[j], fpx, fpy[i], al, G_, ar, dx_, dy_)) mb[i][j >> 5] |= 1u << (j & 31);
+        }
+      }
     }
     for (int h = 1; h >= 0; --h) {
       uint32_t mine = 0u;
@@ -269,8 +285,8 @@ cudaError_t launch_render_bwd(const Layout &L, const WsPtrs &P, int pbuf, const 
   a.sem_detach = sem_detach;
   a.grad2d = P.grad2d;
   a.g_rgb = g_rgb; a.g_sem_w = g_sem_w;
-  a.mask_off = P.mask_off;
-  a.masks = P.masks;
+  a.mask_off = L.mask_units ? P.mask_off : nullptr;
+  a.masks = L.mask_units ? P.masks : nullptr;
   const int grid = a.tiles_x * tiles_y;
   if (grid == 0) return cudaSuccess;
   if (loss_scale) {

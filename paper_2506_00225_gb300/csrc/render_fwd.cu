@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(TW *TH) k_blend(FwdArgs a) {
   const bool inside = px < a.width && py < a.height;
   const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-  const uint32_t unit0 = a.mask_off[tile];
+  const uint32_t unit0 = a.masks ? a.mask_off[tile] : 0u;
 
   float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, cd = 0.f;
   uint32_t last = 0, ncontrib = 0;
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(TW *TH) k_blend(FwdArgs a) {
         }
       }
     }
-    if (unit0 + bi < a.mask_units) {
+    if (a.masks && unit0 + bi < a.mask_units) {
       uint32_t *mw = a.masks + (size_t)(unit0 + bi) * 2 * NPIX;
       mw[lp] = bits[0];
       mw[NPIX + lp] = bits[1];
@@ -168,9 +168,10 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// Shared-memory layout of one pass-2 batch buffer: mean, conic, k sem pairs.
+// Shared-memory layout of one pass-2 batch buffer: mean, conic, pixel box
+// (recomputation mode), k sem pairs.
 __host__ __device__ inline size_t sem_batch_bytes(int k) {
-  return (size_t)kBatch * (8 + 16) + (size_t)kBatch * k * 8;
+  return (size_t)kBatch * (8 + 16 + 8) + (size_t)kBatch * k * 8;
 }
 
 // Class chunking for pass 2, whose fixed part is two batch buffers.
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(TW *TH) k_semantic(FwdArgs a) {
   const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
   float *myP = sP + threadIdx.x * a.mstride;  // accumulator row of this thread's pixel
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-  const uint32_t unit0 = a.mask_off[tile];
+  const uint32_t unit0 = a.masks ? a.mask_off[tile] : 0u;
   const int cw = code_words(a.nwc);
 
   if (L1 && a.t_sem && (int)threadIdx.x < TH) {
@@ -242,12 +243,14 @@ __global__ void __launch_bounds__(TW *TH) k_semantic(FwdArgs a) {
 
   auto buf_uv = [&](int q) { return reinterpret_cast<float2 *>(sbase + q * bbytes); };
   auto buf_co = [&](int q) { return reinterpret_cast<float4 *>(sbase + q * bbytes + kBatch * 8); };
-  auto buf_sem = [&](int q) { return reinterpret_cast<int2 *>(sbase + q * bbytes + kBatch * 24); };
+  auto buf_box = [&](int q) { return reinterpret_cast<short4 *>(sbase + q * bbytes + kBatch * 24); };
+  auto buf_sem = [&](int q) { return reinterpret_cast<int2 *>(sbase + q * bbytes + kBatch * 32); };
   auto batch_n = [&](int bi) { return (int)min((uint32_t)kBatch, rg.y - (rg.x + (uint32_t)bi * kBatch)); };
   auto issue = [&](int bi, uint32_t r) {  // thread t < n copies record r into slot t of buffer bi & 1
     const int q = bi & 1, t = threadIdx.x;
     cp_async8(buf_uv(q) + t, a.rec.uv + r);
     cp_async16(buf_co(q) + t, a.rec.co + r);
+    if (!a.masks) cp_async8(buf_box(q) + t, a.rec.box + r);
     const int2 *src = a.rec.sem + (size_t)r * k;
     for (int l = 0; l < k; ++l) cp_async8(buf_sem(q) + t * k + l, src + l);
   };
@@ -275,14 +278,27 @@ __global__ void __launch_bounds__(TW *TH) k_semantic(FwdArgs a) {
       // add zero weight, and the accumulator rows are indexed by thread so
       // that the 32 lanes' adds to one class fall in 32 distinct banks
       uint32_t mine[2] = {0u, 0u};
-      if (b0 < last) {
-        const uint32_t *mw = a.masks + (size_t)(unit0 + bi) * 2 * NPIX;
-        mine[0] = mw[lp];
-        mine[1] = mw[NPIX + lp];
-      }
       const float2 *suv = buf_uv(bi & 1);
       const float4 *sco = buf_co(bi & 1);
       const int2 *ssem = buf_sem(bi & 1);
+      if (b0 < last) {
+        if (a.masks) {
+          const uint32_t *mw = a.masks + (size_t)(unit0 + bi) * 2 * NPIX;
+          mine[0] = mw[lp];
+          mine[1] = mw[NPIX + lp];
+        } else {
+          // recomputation: contributors are the pairs up to the last one
+          // whose pixel box holds the pixel and whose alpha passes 1/255
+          const short4 *sbox = buf_box(bi & 1);
+          const int n = min(batch_n(bi), (int)(last - b0));
+          for (int j = 0; j < n; ++j) {
+            const short4 bx = sbox[j];
+            if (px < bx.x || px > bx.y || py < bx.z || py > bx.w) continue;
+            float alpha, G, araw, dx, dy;
+            if (gauss_alpha(suv[j], sco[j], fpx, fpy, alpha, G, araw, dx, dy)) mine[j >> 5] |= 1u << (j & 31);
+          }
+        }
+      }
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         uint32_t un = __reduce_or_sync(0xffffffffu, mine[h]);
@@ -442,8 +458,8 @@ static FwdArgs fwd_args(const Layout &L, const WsPtrs &P, int pbuf, const gs_sce
   a.tiles_x = (L.cam0_w + L.tile_w - 1) / L.tile_w;
   a.tfinal = P.tfinal; a.nlast = P.nlast;
   a.counters = P.counters;
-  a.mask_off = P.mask_off;
-  a.masks = P.masks;
+  a.mask_off = L.mask_units ? P.mask_off : nullptr;
+  a.masks = L.mask_units ? P.masks : nullptr;
   a.mask_units = (uint32_t)L.mask_units;
   a.codes = P.codes;
   a.nwc = L.nwc;
@@ -453,6 +469,7 @@ static FwdArgs fwd_args(const Layout &L, const WsPtrs &P, int pbuf, const gs_sce
 
 // First (tile, batch) unit of every tile: batches per tile, exclusive scan.
 static cudaError_t launch_mask_offsets(const Layout &L, const WsPtrs &P, int grid, cudaStream_t s) {
+  if (!L.mask_units) return cudaSuccess;
   k_tile_batches<<<(grid + 255) / 256, 256, 0, s>>>(P.ranges, (uint32_t)grid, P.mask_off);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

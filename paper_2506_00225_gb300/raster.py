@@ -103,6 +103,10 @@ def _stream():
 class Rasterizer:
     """Owns one device workspace and a launch configuration.
 
+    ``recompute_bwd=True`` keeps no per-pixel contributor bits: the semantic
+    pass and the adjoint re-test each tile's pairs (less memory, same
+    results).
+
     ``check=True`` calls read the device counters after binning (a host
     synchronisation) and grow the pair capacity and rerun when the workspace
     overflowed; ``check=False`` never synchronises (use after warm-up, e.g.
@@ -110,8 +114,9 @@ class Rasterizer:
     """
 
     def __init__(self, tile=(16, 16), sem_detach_geometry=True, record_capacity=0, pair_capacity=0,
-                 device=None, px_per_thread=0):
+                 device=None, px_per_thread=0, recompute_bwd=False):
         self.tile = tuple(tile)
+        self.recompute_bwd = bool(recompute_bwd)
         self.px_per_thread = int(px_per_thread)
         self.sem_detach_geometry = bool(sem_detach_geometry)
         self.record_capacity = int(record_capacity)
@@ -135,6 +140,7 @@ class Rasterizer:
         c.tile_w, c.tile_h = self.tile
         c.sem_detach_geometry = 1 if self.sem_detach_geometry else 0
         c.px_per_thread = self.px_per_thread
+        c.recompute_bwd = 1 if self.recompute_bwd else 0
         # capacities start at a bound that never overflows for small problems
         # and grow on reported overflow (check=True)
         c.record_capacity = self.record_capacity if self.record_capacity > 0 else max(1, min(n_gauss * n_views,

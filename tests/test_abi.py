@@ -66,9 +66,17 @@ def test_workspace_size_and_layout_host_only(lib):
     sc5, cams5, cfg5 = _structs(views=5)
     assert lib.gs_workspace_size(ctypes.byref(sc5), cams5, 5, ctypes.byref(cfg5)) > \
         lib.gs_workspace_size(ctypes.byref(sc2), cams2, 2, ctypes.byref(cfg2)) > 0
+    # recomputation mode keeps no contributor bits: 8 bytes per tile pixel
+    # per 64 pairs of capacity less
+    cfg.pair_capacity = 1 << 16
+    keep = lib.gs_workspace_size(ctypes.byref(sc), cams, 1, ctypes.byref(cfg))
+    cfg.recompute_bwd = 1
+    lean = lib.gs_workspace_size(ctypes.byref(sc), cams, 1, ctypes.byref(cfg))
+    assert 0 < lean and keep - lean >= 8 * ((1 << 16) // 64) * 16 * 16
 
 
-@pytest.mark.parametrize("bad", ["k0", "k17", "m0", "views0", "views257", "tile0", "width0", "near0", "fx_nan"])
+@pytest.mark.parametrize("bad", ["k0", "k17", "m0", "views0", "views257", "tile0", "width0", "near0", "fx_nan",
+                                 "ppt3", "recompute2"])
 def test_invalid_arguments_rejected_on_host(lib, bad):
     sc, cams, cfg = _structs()
     views = 1
@@ -90,6 +98,10 @@ def test_invalid_arguments_rejected_on_host(lib, bad):
         cams[0].near_plane = 0.0
     elif bad == "fx_nan":
         cams[0].fx = float("nan")
+    elif bad == "ppt3":
+        cfg.px_per_thread = 3
+    elif bad == "recompute2":
+        cfg.recompute_bwd = 2
     assert lib.gs_workspace_size(ctypes.byref(sc), cams, views, ctypes.byref(cfg)) == 0
     # every entry point refuses before touching the GPU
     fake = ctypes.c_void_p(1 << 40)

@@ -1,0 +1,208 @@
+"""Parity at the full benchmark sizes (680x1200 mapping views of the 300k and
+2M-Gaussian rooms, the 96 and 128 mixed-resolution candidate sets), in every
+launch configuration the autotuner can pick, on outputs the oracle computes
+one by one:
+
+* forward: every 20th pixel row (offset 7, so sampled rows fall at every
+  position inside a 16-row tile), all pixels of those rows, 1e-5 max abs on
+  colour, depth, silhouette and the class distribution (pixels with a
+  threshold decision within a relative 1e-5 of its threshold excluded and
+  counted);
+* adjoint: upstream gradients that are non-zero on the sampled rows only,
+  so that the GPU's full-image adjoint and the oracle's row adjoint sum the
+  same per-pixel terms (1e-3 relative, scaled as in the small-case tests);
+* fused mean-L1 step: a property that holds at any size -- its gradients
+  equal the plain adjoint fed with sign(rendered - target) / count, and its
+  loss equals the mean absolute differences of the rendered maps;
+* candidates: the oracle's per-view sums on a sample of the views, taken
+  from the one batched launch over all views.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2506_00225_gb300 import raster, scenes
+
+pytestmark = pytest.mark.gpu
+
+ROWS = (7, None, 20)
+CONFIGS = [((16, 16), 2), ((16, 16), 1), ((32, 8), 2), ((16, 8), 2), ((8, 8), 1)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_00225_gb300 import build
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def room300k():
+    return scenes.workload("room300k")
+
+
+@pytest.fixture(scope="module")
+def rooms2m():
+    return scenes.workload("rooms2m")
+
+
+def _rows(cam):
+    b, _, s = ROWS
+    return (b, cam.height, s)
+
+
+def _grad_close(a, b, rtol=1e-3, name=""):
+    scale = np.abs(b).max() + 1e-30
+    err = np.abs(a - b) / (np.abs(b) + 0.01 * scale)
+    assert err.max() <= rtol, (name, err.max(), np.unravel_index(err.argmax(), err.shape))
+
+
+def _check_rows(out, ref, cam):
+    ys = np.arange(*_rows(cam))
+    ok = ref["flag"][ys] == 0
+    assert (~ok).sum() <= max(3, ok.size // 1000), (~ok).sum()  # at most 0.1 % flagged
+    names = ["rgb", "depth", "sil", "sem"]
+    for name, x in zip(names, out):
+        x = x.cpu().numpy()[ys]
+        r = ref[name][ys]
+        err = np.abs(x - r)
+        if err.ndim == 3:
+            err = err.max(-1)
+        assert err[ok].max() <= 1e-5, (name, err[ok].max())
+
+
+def _forward_rows(wl, configs, recompute=False):
+    sc, cam = wl["scene"], wl["cams"][0]
+    ref = oracle.render(sc, cam, prec="f32", rows=_rows(cam))
+    g = raster.Gaussians.from_scene(sc)
+    for tile, ppt in configs:
+        rast = raster.Rasterizer(tile=tile, px_per_thread=ppt, recompute_bwd=recompute)
+        with torch.no_grad():
+            out = rast.forward(g, cam, check=True)
+        _check_rows(out, ref, cam)
+        assert int(rast.counters().status) == 0
+    return ref
+
+
+def test_room300k_forward_rows_all_configs(room300k):
+    _forward_rows(room300k, CONFIGS)
+
+
+def _row_upstream(sc, cam, ref, seed):
+    H, W, m = cam.height, cam.width, sc.m
+    rng = np.random.default_rng(seed)
+    keep = np.zeros((H, W), bool)
+    keep[np.arange(*_rows(cam))] = True
+    keep &= ref["flag"] == 0
+    up = dict(d_rgb=rng.normal(size=(H, W, 3)).astype(np.float32), d_depth=rng.normal(size=(H, W)).astype(np.float32),
+              d_sil=rng.normal(size=(H, W)).astype(np.float32), d_sem=rng.normal(size=(H, W, m)).astype(np.float32))
+    for v in up.values():
+        v[~keep] = 0.0
+    return up
+
+
+def _backward_rows(wl, configs, recompute=False, seed=0):
+    sc, cam = wl["scene"], wl["cams"][0]
+    ref_f = oracle.render(sc, cam, prec="f32", rows=_rows(cam))
+    up = _row_upstream(sc, cam, ref_f, seed)
+    for sem_detach in (True, False):
+        ref = oracle.render_bwd(sc, cam, **up, sem_detach=sem_detach, prec="f32", rows=_rows(cam))
+        g = raster.Gaussians.from_scene(sc)
+        t = {k: torch.from_numpy(v).cuda() for k, v in up.items()}
+        for tile, ppt in configs:
+            rast = raster.Rasterizer(tile=tile, px_per_thread=ppt, sem_detach_geometry=sem_detach,
+                                     recompute_bwd=recompute)
+            with torch.no_grad():
+                rast.forward(g, cam, check=True)
+            grads = rast.backward(g, cam, t["d_rgb"], t["d_depth"], t["d_sil"], t["d_sem"])
+            for name in ["means", "scales", "quats", "opacity", "rgb", "sem_w"]:
+                _grad_close(grads[name].cpu().numpy(), ref[name], name=(name, tile, ppt, sem_detach))
+
+
+def test_room300k_backward_rows(room300k):
+    _backward_rows(room300k, [((16, 16), 2), ((32, 8), 1)])
+
+
+def test_room300k_recompute_mode_rows(room300k):
+    """No stored contributor bits: the semantic pass and the adjoint re-test
+    the pairs; outputs and gradients stay within the same bar."""
+    _forward_rows(room300k, [((16, 16), 2), ((16, 8), 1)], recompute=True)
+    _backward_rows(room300k, [((16, 16), 2)], recompute=True, seed=1)
+
+
+def _fused_vs_plain(wl, tile, ppt, recompute=False):
+    sc, cam = wl["scene"], wl["cams"][0]
+    g = raster.Gaussians.from_scene(sc)
+    gt = raster.Gaussians.from_scene(wl["target"])
+    with torch.no_grad():
+        t_rgb, t_depth, _, t_sem = raster.Rasterizer().forward(gt, cam, check=True)
+    rast = raster.Rasterizer(tile=tile, px_per_thread=ppt, recompute_bwd=recompute)
+    with torch.no_grad():
+        rgb, depth, sil, sem = rast.forward(g, cam, check=True)
+    # the plain path, fed with the L1 sign upstream
+    loss_ref, d_rgb, d_depth, d_sem = raster.l1_loss_and_grads(rgb, depth, sem, t_rgb, t_depth, t_sem)
+    plain = rast.backward(g, cam, d_rgb, d_depth, None, d_sem)
+    plain = {k: v.clone() for k, v in plain.items()}
+    # the fused path
+    loss = rast.forward_l1(g, cam, t_rgb, t_depth, t_sem)
+    fused = rast.backward_l1(g, cam, torch.ones((), device=loss.device))
+    n = rgb.shape[0] * rgb.shape[1]
+    direct = ((rgb - t_rgb).abs().double().sum() / (3 * n) + (depth - t_depth).abs().double().sum() / n
+              + (sem - t_sem).abs().double().sum() / (n * sc.m))
+    assert abs(float(loss) - float(direct)) <= 1e-5 * abs(float(direct))
+    assert abs(float(loss) - float(loss_ref)) <= 1e-5 * abs(float(loss_ref))
+    for name in ["means", "scales", "quats", "opacity", "rgb", "sem_w"]:
+        _grad_close(fused[name].cpu().numpy(), plain[name].cpu().numpy(), name=name)
+
+
+def test_room300k_fused_l1_matches_plain_adjoint(room300k):
+    _fused_vs_plain(room300k, (16, 16), 2)
+    _fused_vs_plain(room300k, (32, 8), 1, recompute=True)
+
+
+def test_rooms2m_forward_backward_rows(rooms2m):
+    """2M Gaussians, 256 classes (class words straddle 32-class boundaries),
+    top-8 semantics (the wide reduction), both storage modes."""
+    _forward_rows(rooms2m, [((16, 16), 2)])
+    _forward_rows(rooms2m, [((16, 16), 2)], recompute=True)
+    _backward_rows(rooms2m, [((16, 16), 2)], seed=2)
+    _backward_rows(rooms2m, [((16, 16), 1)], recompute=True, seed=3)
+
+
+def test_rooms2m_fused_l1_matches_plain_adjoint(rooms2m):
+    _fused_vs_plain(rooms2m, (16, 16), 2, recompute=True)
+
+
+def _candidates_sample(sc, cams, pick):
+    out = raster.Rasterizer().candidates(raster.Gaussians.from_scene(sc), cams).cpu().numpy()
+    assert np.isfinite(out).all()
+    for v in pick:
+        su, sh, ns, nf = oracle.candidate(sc, cams[v])
+        assert abs(out[v, 0] - su) <= 1e-5 * abs(su) + 1e-3, (v, out[v, 0], su)
+        assert abs(out[v, 1] - sh) <= 1e-5 * abs(sh), (v, out[v, 1], sh)
+        assert abs(out[v, 2] - ns) <= nf, (v, out[v, 2], ns, nf)
+    return out
+
+
+def test_cand96_batched_sampled_views():
+    """All 96 views in one batched launch; the oracle checks 12 of the
+    170x300 views, two 340x600 and one 680x1200 view."""
+    wl = scenes.workload("cand96")
+    cams = wl["cams"]
+    by_res = {}
+    for v, c in enumerate(cams):
+        by_res.setdefault(c.width, []).append(v)
+    pick = by_res[300][::3][:12] + by_res[600][:2] + by_res[1200][:1]
+    _candidates_sample(wl["scene"], cams, pick)
+
+
+def test_mixed2m_candidates_sampled_views():
+    """The 128 candidate views of the 2M-Gaussian scene (M=256, k=8) in one
+    batched launch; the oracle checks six 170x300 views and one 340x600."""
+    wl = scenes.workload("mixed2m")
+    cams = wl["cand_cams"]
+    small = [v for v, c in enumerate(cams) if c.width == 300][:6]
+    mid = [v for v, c in enumerate(cams) if c.width == 600][:1]
+    _candidates_sample(wl["scene"], cams, small + mid)
