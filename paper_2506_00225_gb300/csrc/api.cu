@@ -91,6 +91,7 @@ bool make_layout(const gs_scene *scene, const gs_camera *cams, int n_views, cons
   for (int i = 0; i < 2; ++i) L->off_dkeys[i] = take(8 * (size_t)rcap);
   for (int i = 0; i < 2; ++i) L->off_dvals[i] = take(4 * (size_t)rcap);
   L->off_epart = take(sizeof(uint32_t) * (kEmitCtas + 1));
+  L->off_rloc = take(4 * (size_t)rcap);
   for (int i = 0; i < 2; ++i) L->off_pkeys[i] = take(4 * (size_t)pcap);
   for (int i = 0; i < 2; ++i) L->off_pvals[i] = take(4 * (size_t)pcap);
   L->off_tickets = take(sizeof(uint32_t) * 2 * kMaxRadixPasses);
@@ -137,6 +138,7 @@ WsPtrs ws_ptrs(const Layout &L, void *ws) {
     P.pvals[i] = reinterpret_cast<uint32_t *>(b + L.off_pvals[i]);
   }
   P.epart = reinterpret_cast<uint32_t *>(b + L.off_epart);
+  P.rloc = reinterpret_cast<uint32_t *>(b + L.off_rloc);
   P.tickets = reinterpret_cast<uint32_t *>(b + L.off_tickets);
   P.ghist = reinterpret_cast<uint32_t *>(b + L.off_ghist);
   P.lb_depth = reinterpret_cast<unsigned long long *>(b + L.off_lb_depth);

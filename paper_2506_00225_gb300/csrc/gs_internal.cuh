@@ -62,7 +62,7 @@ struct Layout {
   size_t off_rec_uv, off_rec_conic, off_rec_depth, off_rec_rect, off_rec_gid, off_rec_view;
   size_t off_rec_box, off_rec_cd, off_rec_unc, off_rec_sem;
   size_t off_dkeys[2], off_dvals[2];
-  size_t off_epart;
+  size_t off_epart, off_rloc;
   size_t off_pkeys[2], off_pvals[2];
   size_t off_tickets, off_ghist, off_lb_depth, off_lb_pairs;
   size_t off_ranges;
@@ -93,6 +93,7 @@ struct WsPtrs {
   unsigned long long *dkeys[2];
   uint32_t *dvals[2];
   uint32_t *epart;
+  uint32_t *rloc;     // [rcap] pair offset of each depth-sorted record inside its emit chunk
   uint32_t *pkeys[2];
   uint32_t *pvals[2];
   uint32_t *tickets;                 // [2][kMaxRadixPasses] tile tickets (depth sort, pair sort)

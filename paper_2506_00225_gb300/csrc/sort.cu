@@ -255,101 +255,82 @@ __device__ __forceinline__ void emit_chunk(uint32_t count, uint32_t &begin, uint
   end = min(count, begin + per);
 }
 
+// Pass 1: per chunk of depth-sorted records, the exclusive prefix of their
+// tile counts inside the chunk (rloc) and the chunk total (epart).
 __global__ void __launch_bounds__(kEmitThreads) k_emit_count(const uint32_t *__restrict__ sorted_rec,
                                                              const short4 *__restrict__ rect, const Counters *cnt,
-                                                             uint32_t rcap, int tw, int th, uint32_t *epart) {
+                                                             uint32_t rcap, int tw, int th, uint32_t *epart,
+                                                             uint32_t *rloc) {
   __shared__ uint32_t tmp[33];
   const uint32_t count = min(cnt->n_records, rcap);
   uint32_t begin, end;
   emit_chunk(count, begin, end);
-  uint32_t s = 0;
-  for (uint32_t q = begin + threadIdx.x; q < end; q += kEmitThreads) s += record_ntiles(rect[sorted_rec[q]], tw, th);
-  uint32_t total;
-  block_exclusive_scan(s, tmp, &total);
-  if (threadIdx.x == 0) epart[blockIdx.x] = total;
+  uint32_t run = 0;
+  for (uint32_t q0 = begin; q0 < end; q0 += kEmitThreads) {
+    const uint32_t q = q0 + threadIdx.x;
+    const uint32_t nt = q < end ? record_ntiles(rect[sorted_rec[q]], tw, th) : 0u;
+    uint32_t total;
+    const uint32_t ex = block_exclusive_scan(nt, tmp, &total);
+    if (q < end) rloc[q] = run + ex;
+    run += total;
+  }
+  if (threadIdx.x == 0) epart[blockIdx.x] = run;
 }
 
-// Each warp takes 32 consecutive (depth-sorted) records and writes all their
-// pairs cooperatively: lane i of each round writes pair i of the warp's run,
-// finding its record by a search over the warp's prefix sums, so consecutive
-// lanes write consecutive addresses.
+// Pass 2, balanced over pairs: each thread takes pair indices, finds the
+// chunk (largest c with epart[c] <= p) and then the record (largest q of the
+// chunk with rloc[q] <= p - epart[c]) by binary search -- records with no
+// tile are never selected -- and writes the pair's tile id and record.
+// Consecutive threads write consecutive pairs, and the output equals the
+// depth-ordered, row-major-within-record emission.
 __global__ void __launch_bounds__(kEmitThreads) k_emit_write(const uint32_t *__restrict__ sorted_rec,
                                                              const short4 *__restrict__ rect,
                                                              const int32_t *__restrict__ rview,
                                                              const DevCam *__restrict__ cams, const Counters *cnt,
                                                              uint32_t rcap, uint32_t pcap, int tw, int th,
                                                              const uint32_t *__restrict__ epart,
+                                                             const uint32_t *__restrict__ rloc,
                                                              uint32_t *__restrict__ pkeys,
                                                              uint32_t *__restrict__ pvals) {
-  __shared__ uint32_t tmp[33];
-  __shared__ uint32_t wpre[kEmitThreads / 32][33];
-  __shared__ int4 wrec[kEmitThreads / 32][32];  // tx0, width, ty0, tile_off | view info packed below
-  __shared__ uint32_t wrid[kEmitThreads / 32][32];
-  __shared__ int wtx[kEmitThreads / 32][32];
+  __shared__ uint32_t s_epart[kEmitCtas];
+  for (int i = threadIdx.x; i < kEmitCtas; i += kEmitThreads) s_epart[i] = epart[i];
+  __syncthreads();
   const uint32_t count = min(cnt->n_records, rcap);
-  uint32_t begin, end;
-  emit_chunk(count, begin, end);
-  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-  uint32_t run = epart[blockIdx.x];
-  for (uint32_t q0 = begin; q0 < end; q0 += kEmitThreads) {
-    const uint32_t q = q0 + threadIdx.x;
-    uint32_t r = 0, nt = 0;
-    int tx0 = 0, gw = 1, ty0 = 0, tiles_x = 1;
-    uint32_t toff = 0;
-    if (q < end) {
-      r = sorted_rec[q];
-      const short4 rc = rect[r];
-      nt = record_ntiles(rc, tw, th);
-      const DevCam &c = cams[rview[r]];
-      tx0 = rc.x / tw;
-      gw = rc.y / tw - tx0 + 1;
-      ty0 = rc.z / th;
-      tiles_x = c.tiles_x;
-      toff = c.tile_off;
+  const uint32_t npairs = min(cnt->n_pairs, pcap);
+  const uint32_t per = (count + kEmitCtas - 1) / kEmitCtas;
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += gridDim.x * blockDim.x) {
+    int lo = 0, hi = kEmitCtas - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_epart[mid] <= p) lo = mid; else hi = mid - 1;
     }
-    uint32_t total;
-    const uint32_t pos = run + block_exclusive_scan(nt, tmp, &total);
-    run += total;
-    // warp-local prefix of pair counts
-    const uint32_t inc = warp_inclusive_scan(nt);
-    wpre[warp][lane + 1] = inc;
-    if (lane == 0) wpre[warp][0] = 0;
-    wrec[warp][lane] = make_int4(tx0, gw, ty0, (int)toff);
-    wtx[warp][lane] = tiles_x;
-    wrid[warp][lane] = r;
-    __syncwarp();
-    const uint32_t wbase = __shfl_sync(0xffffffffu, pos, 0);
-    const uint32_t wtotal = wpre[warp][32];
-    for (uint32_t i = lane; i < wtotal; i += 32) {
-      // record of pair i: largest l with wpre[l] <= i
-      int lo = 0, hi = 31;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (wpre[warp][mid] <= i) lo = mid; else hi = mid - 1;
-      }
-      const int4 rr = wrec[warp][lo];
-      const uint32_t j = i - wpre[warp][lo];
-      const int ty = rr.z + (int)(j / (uint32_t)rr.y), tx = rr.x + (int)(j % (uint32_t)rr.y);
-      const uint32_t p = wbase + i;
-      if (p < pcap) {
-        pkeys[p] = (uint32_t)rr.w + (uint32_t)(ty * wtx[warp][lo] + tx);
-        pvals[p] = wrid[warp][lo];
-      }
+    const uint32_t local = p - s_epart[lo];
+    uint32_t qlo = (uint32_t)lo * per, qhi = min(count, qlo + per) - 1;
+    while (qlo < qhi) {
+      const uint32_t mid = (qlo + qhi + 1) >> 1;
+      if (__ldg(rloc + mid) <= local) qlo = mid; else qhi = mid - 1;
     }
-    __syncwarp();
+    const uint32_t j = local - __ldg(rloc + qlo);
+    const uint32_t r = __ldg(sorted_rec + qlo);
+    const short4 rc = __ldg(rect + r);
+    const DevCam &c = cams[__ldg(rview + r)];
+    const int tx0 = rc.x / tw, gw = rc.y / tw - tx0 + 1, ty0 = rc.z / th;
+    const int ty = ty0 + (int)(j / (uint32_t)gw), tx = tx0 + (int)(j % (uint32_t)gw);
+    pkeys[p] = c.tile_off + (uint32_t)(ty * c.tiles_x + tx);
+    pvals[p] = r;
   }
 }
 
 cudaError_t launch_emit_pairs(const Layout &L, const WsPtrs &P, int dbuf, cudaStream_t s) {
   k_emit_count<<<kEmitCtas, kEmitThreads, 0, s>>>(P.dvals[dbuf], P.rec_rect, P.counters, (uint32_t)L.rcap, L.tile_w,
-                                                  L.tile_h, P.epart);
+                                                  L.tile_h, P.epart, P.rloc);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = launch_scan_single(P.epart, (uint32_t)kEmitCtas, &P.counters->n_pairs, (uint32_t)L.pcap, P.counters, s);
   if (e != cudaSuccess) return e;
-  k_emit_write<<<kEmitCtas, kEmitThreads, 0, s>>>(P.dvals[dbuf], P.rec_rect, P.rec_view, P.cams, P.counters,
-                                                  (uint32_t)L.rcap, (uint32_t)L.pcap, L.tile_w, L.tile_h, P.epart,
-                                                  P.pkeys[0], P.pvals[0]);
+  k_emit_write<<<8 * 152, kEmitThreads, 0, s>>>(P.dvals[dbuf], P.rec_rect, P.rec_view, P.cams, P.counters,
+                                                (uint32_t)L.rcap, (uint32_t)L.pcap, L.tile_w, L.tile_h, P.epart,
+                                                P.rloc, P.pkeys[0], P.pvals[0]);
   return cudaGetLastError();
 }
 
