@@ -165,6 +165,10 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
                "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
@@ -195,7 +199,7 @@ __device__ __forceinline__ void scatter_classes(float *row, const int2 *e, int k
 }
 
 template <int TW, int TH, bool L1, int K>
-__global__ void __launch_bounds__(TW *TH) k_semantic(FwdArgs a) {
+__global__ void __launch_bounds__(TW *TH, 2) k_semantic(FwdArgs a) {
   using FP = Footprint<TW, TH, 1>;
   constexpr int THREADS = FP::kThreads;
   constexpr int WARPS = FP::kWarps;
@@ -223,7 +227,11 @@ __global__ void __launch_bounds__(TW *TH) k_semantic(FwdArgs a) {
   const uint32_t unit0 = a.masks ? a.mask_off[tile] : 0u;
   const int cw = code_words(a.nwc);
 
-  if (L1 && a.t_sem && (int)threadIdx.x < TH) {
+  // fused mean-L1 without a semantic map output: the accumulator rows start
+  // as the target rows and the contributions are subtracted, so they end as
+  // target - rendered and the comparison needs no second read of the target
+  const bool tmode = L1 && a.t_sem && !a.sem;
+  if (L1 && a.t_sem && !tmode && (int)threadIdx.x < TH) {
     // warm L2 with the tile's target rows while the accumulation runs
     const int y = oy + (int)threadIdx.x;
     if (y < a.height) {
@@ -258,7 +266,22 @@ __global__ void __launch_bounds__(TW *TH) k_semantic(FwdArgs a) {
   for (int c = 0; c < a.nchunks; ++c) {
     const int c_lo = c * a.mchunk, c_hi = min(a.m, c_lo + a.mchunk);
     const int mc = c_hi - c_lo;
-    for (int q = 0; q < mc; ++q) myP[q] = 0.f;
+    if (tmode) {
+      // each warp copies whole target rows of its pixels (coalesced 128-byte
+      // runs), lanes over classes; rows of pixels outside the image start at 0
+      for (int p = (int)warp; p < NPIX; p += WARPS) {
+        float *row = sP + FP::thread_of(p) * a.mstride;
+        const int qx = ox + p % TW, qy = oy + p / TW;
+        if (qx < a.width && qy < a.height) {
+          const float *src = a.t_sem + ((size_t)qy * a.width + qx) * a.m + c_lo;
+          for (int e = (int)lane; e < mc; e += 32) cp_async4(row + e, src + e);
+        } else {
+          for (int e = (int)lane; e < mc; e += 32) row[e] = 0.f;
+        }
+      }
+    } else {
+      for (int q = 0; q < mc; ++q) myP[q] = 0.f;
+    }
     float T = 1.f;
     // pipeline: copies of batch bi + 1 fly while batch bi is processed; the
     // pair indices are fetched one batch further ahead
@@ -309,7 +332,8 @@ __global__ void __launch_bounds__(TW *TH) k_semantic(FwdArgs a) {
           float alpha = 0.f, G, araw, dx, dy;
           gauss_alpha(suv[j], sco[j], fpx, fpy, alpha, G, araw, dx, dy);
           const bool on = (mine[h] >> jb) & 1u;
-          const float w = on ? __fmul_rn(alpha, T) : 0.f;
+          float w = on ? __fmul_rn(alpha, T) : 0.f;
+          if (tmode) w = -w;
           if (on) T = __fmul_rn(T, __fsub_rn(1.f, alpha));
           scatter_classes<K>(myP, ssem + j * k, k, c_lo, mc, w);
         }
@@ -330,7 +354,28 @@ __global__ void __launch_bounds__(TW *TH) k_semantic(FwdArgs a) {
         }
       }
     }
-    if (L1 && a.t_sem) {
+    if (tmode) {
+      // rows hold target - rendered: per pixel (one warp), lanes over the
+      // classes of each 32-class word; ballots give the sign words
+      const int w_lo = c_lo >> 5, w_hi = (c_hi + 31) >> 5;
+      for (int p = (int)warp; p < NPIX; p += WARPS) {
+        const int qx = ox + p % TW, qy = oy + p / TW;
+        if (qx >= a.width || qy >= a.height) continue;  // uniform over the warp
+        const float *row = sP + FP::thread_of(p) * a.mstride - c_lo;
+        uint32_t *cp = a.codes + ((size_t)qy * a.width + qx) * cw;
+        for (int wd = w_lo; wd < w_hi; ++wd) {
+          const int mcl = wd * 32 + (int)lane;
+          const float v = mcl < c_hi ? row[mcl] : 0.f;
+          const uint32_t nz = __ballot_sync(0xffffffffu, v != 0.f);
+          const uint32_t ng = __ballot_sync(0xffffffffu, v > 0.f);  // rendered < target
+          l1_sem += fabsf(v);
+          if (lane == 0) {
+            cp[1 + wd] = nz;
+            cp[2 + a.nwc + wd] = ng;
+          }
+        }
+      }
+    } else if (L1 && a.t_sem) {
       // each warp takes kG pixels x kWG 32-class words per round: all kG*kWG
       // coalesced target reads (L2 hits after the prefetch) are issued before
       // any is consumed; ballots assemble the sign words
