@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
   float fpy[PPT], T[PPT], acc[PPT], dR[PPT], dG[PPT], dB[PPT], dD[PPT], dS[PPT];
   uint32_t nl[PPT];
   const float *dP[PPT];
-  uint32_t *myc[PPT];  // CODES: this pixel's class sign words (odd stride)
+  uint2 *myc[PPT];  // CODES: this pixel's (nonzero, negative) class sign word pairs (odd stride)
   uint32_t my_max = 0;
 #pragma unroll
   for (int i = 0; i < PPT; ++i) {
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
     T[i] = 1.f; acc[i] = 0.f; dR[i] = dG[i] = dB[i] = dD[i] = dS[i] = 0.f;
     nl[i] = 0;
     dP[i] = nullptr;
-    myc[i] = reinterpret_cast<uint32_t *>(bs.tail) + (ly * TW + lx) * (2 * a.nwc + 1);
+    myc[i] = reinterpret_cast<uint2 *>(bs.tail) + (ly * TW + lx) * (a.nwc | 1);
     if (px < a.width && py[i] < a.height) {
       const size_t pix = (size_t)py[i] * a.width + px;
       T[i] = a.tfinal[pix];
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
         const uint32_t nz = cp[0], ng = cp[1 + a.nwc];
         dR[i] = sign_code(nz, ng, 0, s_rgb); dG[i] = sign_code(nz, ng, 1, s_rgb); dB[i] = sign_code(nz, ng, 2, s_rgb);
         dD[i] = sign_code(nz, ng, 3, s_d);
-        for (int wd = 0; wd < a.nwc; ++wd) { myc[i][wd] = cp[1 + wd]; myc[i][a.nwc + wd] = cp[2 + a.nwc + wd]; }
+        for (int wd = 0; wd < a.nwc; ++wd) myc[i][wd] = make_uint2(cp[1 + wd], cp[2 + a.nwc + wd]);
       } else {
         if (a.d_rgb) { dR[i] = a.d_rgb[3 * pix]; dG[i] = a.d_rgb[3 * pix + 1]; dB[i] = a.d_rgb[3 * pix + 2]; }
         if (a.d_depth) dD[i] = a.d_depth[pix];
@@ -180,7 +180,8 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
         for (int i = 0; i < PPT; ++i) {
           if (!contrib[i]) continue;
           const float om = 1.f - alpha[i];
-          const float Ti = T[i] / om;
+          const float inv_om = __fdividef(1.f, om);  // approximate: 2 ulp, well inside the gradient bar
+          const float Ti = T[i] * inv_om;
           const float w = alpha[i] * Ti;
           float gi = dR[i] * cdp.x + dG[i] * cdp.y + dB[i] * cdp.z + dD[i] * cdp.w + dS[i];
           if (has_dsem) {
@@ -192,7 +193,8 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
                 float dp = 0.f;
                 if ((unsigned)e.x < (unsigned)a.m) {
                   if (CODES) {
-                    dp = sign_code(myc[i][e.x >> 5], myc[i][a.nwc + (e.x >> 5)], e.x & 31, s_sem);
+                    const uint2 cw = myc[i][e.x >> 5];
+                    dp = sign_code(cw.x, cw.y, e.x & 31, s_sem);
                   } else {
                     dp = __ldg(dP[i] + e.x);
                   }
@@ -205,7 +207,7 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
           }
           v[7] = fmaf(dR[i], w, v[7]); v[8] = fmaf(dG[i], w, v[8]); v[9] = fmaf(dB[i], w, v[9]);
           v[6] = fmaf(dD[i], w, v[6]);
-          const float dalpha = Ti * gi - acc[i] / om;
+          const float dalpha = Ti * gi - acc[i] * inv_om;
           acc[i] = fmaf(w, gi, acc[i]);
           T[i] = Ti;
           if (araw[i] < kAlphaMax) {
@@ -243,6 +245,13 @@ __global__ void k_zero_grad2d(float4 *g, const Counters *cnt, uint32_t rcap) {
 
 template <int TW, int TH, bool CODES, int NV, int PPT>
 static cudaError_t launch_bwd_shape(const BwdArgs &a, int grid, size_t smem, cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {  // the sign words of large class counts need more than 48 KB
+    cudaError_t e = cudaFuncSetAttribute(k_render_bwd<TW, TH, CODES, NV, PPT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
   k_render_bwd<TW, TH, CODES, NV, PPT><<<grid, TW * TH / PPT, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -294,7 +303,7 @@ cudaError_t launch_render_bwd(const Layout &L, const WsPtrs &P, int pbuf, const 
     a.nwc = L.nwc;
     a.loss_scale = loss_scale;
     a.npix = (double)L.npix;
-    const size_t smem = batch_smem_bytes(sc.k) + (size_t)L.tile_w * L.tile_h * (2 * L.nwc + 1) * 4;
+    const size_t smem = batch_smem_bytes(sc.k) + (size_t)L.tile_w * L.tile_h * (L.nwc | 1) * 8;
     return dispatch_bwd<true>(L, a, grid, smem, s);
   }
   const size_t smem = batch_smem_bytes(sc.k);
