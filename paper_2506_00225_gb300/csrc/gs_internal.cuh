@@ -104,7 +104,7 @@ struct WsPtrs {
   float *tfinal;
   uint32_t *nlast;
   float4 *grad2d;  // [rcap][2]: (du, dv, da, db), (dc, dopacity, dz, 0)
-  uint32_t *codes; // [npix][2 * (1 + nwc)] sign codes of the fused L1 mode
+  uint32_t *codes; // [npix][1 + nwc] (nonzero, negative) word pairs: sign codes of the fused L1 mode
   uint32_t *mask_off;  // [tiles + 1] first (tile, batch) unit of each tile
   uint32_t *masks;     // [unit][2][tile pixels] contributor bits of each staged batch
   double *lpart;   // [tiles of view 0][3] per-tile L1 sums

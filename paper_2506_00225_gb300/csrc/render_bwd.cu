@@ -94,11 +94,11 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
         const float ls = *a.loss_scale;
         const float s_rgb = (float)(ls / (3.0 * a.npix)), s_d = (float)(ls / a.npix);
         s_sem = (float)(ls / (a.npix * a.m));
-        const uint32_t *cp = a.codes + pix * code_words(a.nwc);
-        const uint32_t nz = cp[0], ng = cp[1 + a.nwc];
+        const uint2 *cp = reinterpret_cast<const uint2 *>(a.codes + pix * code_words(a.nwc));
+        const uint32_t nz = cp[0].x, ng = cp[0].y;
         dR[i] = sign_code(nz, ng, 0, s_rgb); dG[i] = sign_code(nz, ng, 1, s_rgb); dB[i] = sign_code(nz, ng, 2, s_rgb);
         dD[i] = sign_code(nz, ng, 3, s_d);
-        for (int wd = 0; wd < a.nwc; ++wd) myc[i][wd] = make_uint2(cp[1 + wd], cp[2 + a.nwc + wd]);
+        for (int wd = 0; wd < a.nwc; ++wd) myc[i][wd] = cp[1 + wd];
       } else {
         if (a.d_rgb) { dR[i] = a.d_rgb[3 * pix]; dG[i] = a.d_rgb[3 * pix + 1]; dB[i] = a.d_rgb[3 * pix + 2]; }
         if (a.d_depth) dD[i] = a.d_depth[pix];

@@ -226,7 +226,7 @@ struct FwdArgs {
   int mchunk, mstride, nchunks;
   // fused mean-L1 mode
   const float *t_rgb, *t_depth, *t_sem;
-  uint32_t *codes;   // per pixel: 2 planes (nonzero, negative) x (1 head word + nwc class words)
+  uint32_t *codes;   // per pixel: (nonzero, negative) word pairs: head (rgb, depth bits), then nwc class words
   int nwc;           // class words per plane = ceil(m / 32)
   double *lpart;     // per tile: sum|d rgb|, sum|d depth|, sum|d sem|
   Counters *counters;

@@ -129,11 +129,10 @@ __global__ void __launch_bounds__(TW *TH) k_blend(FwdArgs a) {
       const float d3 = cd - a.t_depth[pix];
       const uint32_t nz = (d0 != 0.f ? 1u : 0u) | (d1 != 0.f ? 2u : 0u) | (d2 != 0.f ? 4u : 0u) | (d3 != 0.f ? 8u : 0u);
       const uint32_t ng = (d0 < 0.f ? 1u : 0u) | (d1 < 0.f ? 2u : 0u) | (d2 < 0.f ? 4u : 0u) | (d3 < 0.f ? 8u : 0u);
-      uint32_t *cp = a.codes + pix * cw;
-      cp[0] = nz;
-      cp[1 + a.nwc] = ng;
+      uint2 *cp = reinterpret_cast<uint2 *>(a.codes + pix * cw);
+      cp[0] = make_uint2(nz, ng);
       if (!a.t_sem)
-        for (int wd = 0; wd < a.nwc; ++wd) { cp[1 + wd] = 0u; cp[2 + a.nwc + wd] = 0u; }
+        for (int wd = 0; wd < a.nwc; ++wd) cp[1 + wd] = make_uint2(0u, 0u);
       l1_rgb = fabsf(d0) + fabsf(d1) + fabsf(d2);
       l1_d = fabsf(d3);
     }
@@ -355,24 +354,30 @@ __global__ void __launch_bounds__(TW *TH, 2) k_semantic(FwdArgs a) {
       }
     }
     if (tmode) {
-      // rows hold target - rendered: per pixel (one warp), lanes over the
-      // classes of each 32-class word; ballots give the sign words
-      const int w_lo = c_lo >> 5, w_hi = (c_hi + 31) >> 5;
-      for (int p = (int)warp; p < NPIX; p += WARPS) {
-        const int qx = ox + p % TW, qy = oy + p / TW;
-        if (qx >= a.width || qy >= a.height) continue;  // uniform over the warp
-        const float *row = sP + FP::thread_of(p) * a.mstride - c_lo;
-        uint32_t *cp = a.codes + ((size_t)qy * a.width + qx) * cw;
-        for (int wd = w_lo; wd < w_hi; ++wd) {
-          const int mcl = wd * 32 + (int)lane;
-          const float v = mcl < c_hi ? row[mcl] : 0.f;
-          const uint32_t nz = __ballot_sync(0xffffffffu, v != 0.f);
-          const uint32_t ng = __ballot_sync(0xffffffffu, v > 0.f);  // rendered < target
-          l1_sem += fabsf(v);
-          if (lane == 0) {
-            cp[1 + wd] = nz;
-            cp[2 + a.nwc + wd] = ng;
+      // each thread reads its own pixel's row (target - rendered; odd stride,
+      // conflict-free) and assembles the sign words 32 classes at a time
+      if (inside) {
+        uint2 *cp = reinterpret_cast<uint2 *>(a.codes + ((size_t)py * a.width + px) * cw);
+        for (int wd = c_lo >> 5; wd < (c_hi + 31) >> 5; ++wd) {
+          const float *v = myP + (wd * 32 - c_lo);
+          uint32_t nz = 0u, ng = 0u;
+          float s = 0.f;
+          if (wd * 32 + 32 <= c_hi) {
+#pragma unroll
+            for (int b = 0; b < 32; ++b) {
+              nz |= (v[b] != 0.f ? 1u : 0u) << b;
+              ng |= (v[b] > 0.f ? 1u : 0u) << b;  // rendered < target
+              s += fabsf(v[b]);
+            }
+          } else {
+            for (int b = 0; b < c_hi - wd * 32; ++b) {
+              nz |= (v[b] != 0.f ? 1u : 0u) << b;
+              ng |= (v[b] > 0.f ? 1u : 0u) << b;
+              s += fabsf(v[b]);
+            }
           }
+          l1_sem += s;
+          cp[1 + wd] = make_uint2(nz, ng);
         }
       }
     } else if (L1 && a.t_sem) {
@@ -412,11 +417,9 @@ __global__ void __launch_bounds__(TW *TH, 2) k_semantic(FwdArgs a) {
               const uint32_t nz = __ballot_sync(0xffffffffu, d != 0.f);
               const uint32_t ng = __ballot_sync(0xffffffffu, d < 0.f);
               l1_sem += fabsf(d);
-              if (lane == 0) {
-                uint32_t *cp = a.codes + (size_t)((row[g] - a.t_sem) / a.m) * cw;
-                cp[1 + wd] = nz;
-                cp[2 + a.nwc + wd] = ng;
-              }
+              if (lane == 0)
+                reinterpret_cast<uint2 *>(a.codes + (size_t)((row[g] - a.t_sem) / a.m) * cw)[1 + wd] =
+                    make_uint2(nz, ng);
             }
           }
         }
