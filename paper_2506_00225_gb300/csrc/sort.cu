@@ -27,15 +27,20 @@ namespace gs {
 
 constexpr int kOsThreads = 256;
 constexpr int kOsWarps = kOsThreads / 32;
-constexpr int kOsItems = 16;
-constexpr int kOsTile = kOsThreads * kOsItems;
+// keys per thread of one sort tile, by element capacity: small sorts get
+// small tiles (more CTAs in flight, shorter per-tile latency), large ones
+// large tiles (fewer look-back steps, bounded look-back storage)
+inline int os_items(int64_t capacity) { return capacity <= (1 << 20) ? 4 : 16; }
 constexpr int kHistCtas = 2 * 152;
 constexpr unsigned long long kFlagA = 1ull << 62;   // tile aggregate published
 constexpr unsigned long long kFlagP = 2ull << 62;   // inclusive prefix published
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
 constexpr uint32_t kSpinLimit = 1u << 22;
 
-int sort_tiles(int64_t capacity) { return (int)((capacity + kOsTile - 1) / kOsTile); }
+int sort_tiles(int64_t capacity) {
+  const int64_t tile = (int64_t)kOsThreads * os_items(capacity);
+  return (int)((capacity + tile - 1) / tile);
+}
 
 template <typename K>
 __device__ __forceinline__ uint32_t digit_of(K key, int shift) {
@@ -45,9 +50,9 @@ __device__ __forceinline__ uint32_t digit_of(K key, int shift) {
 // Clears the tickets, the global histograms and the look-back words of the
 // tiles the current element count needs.
 __global__ void k_os_reset(const uint32_t *count_p, uint32_t cap, int passes, uint32_t *tickets, uint32_t *ghist,
-                           unsigned long long *lookback, uint32_t lb_tiles) {
+                           unsigned long long *lookback, uint32_t lb_tiles, uint32_t tile_keys) {
   const uint32_t count = min(*count_p, cap);
-  const uint32_t tiles = (count + kOsTile - 1) / kOsTile;
+  const uint32_t tiles = (count + tile_keys - 1) / tile_keys;
   const size_t words = (size_t)tiles * kRadix;
   const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
   if (tid < (size_t)passes) tickets[tid] = 0u;
@@ -85,7 +90,7 @@ __global__ void __launch_bounds__(256) k_os_hist(const K *__restrict__ keys, con
   }
 }
 
-template <typename K>
+template <typename K, int ITEMS>
 __global__ void __launch_bounds__(kOsThreads) k_os_pass(const K *__restrict__ keys_in,
                                                         const uint32_t *__restrict__ vals_in,
                                                         K *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
@@ -93,9 +98,10 @@ __global__ void __launch_bounds__(kOsThreads) k_os_pass(const K *__restrict__ ke
                                                         const uint32_t *__restrict__ ghist,
                                                         unsigned long long *lookback, uint32_t *ticket,
                                                         Counters *counters) {
+  constexpr int kTile = kOsThreads * ITEMS;
   extern __shared__ unsigned long long os_smem[];
   K *skey = reinterpret_cast<K *>(os_smem);
-  uint32_t *sval = reinterpret_cast<uint32_t *>(skey + kOsTile);
+  uint32_t *sval = reinterpret_cast<uint32_t *>(skey + kTile);
   __shared__ uint32_t wcnt[kOsWarps][kRadix];
   __shared__ uint32_t tile_pre[kRadix];
   __shared__ uint32_t out_base[kRadix];
@@ -108,24 +114,24 @@ __global__ void __launch_bounds__(kOsThreads) k_os_pass(const K *__restrict__ ke
   for (int i = threadIdx.x; i < kOsWarps * kRadix; i += kOsThreads) (&wcnt[0][0])[i] = 0u;
   __syncthreads();
   const uint32_t t = s_tile;
-  const uint32_t base = t * kOsTile;
+  const uint32_t base = t * kTile;
   if (base >= count) return;  // uniform: tiles past the data
-  const uint32_t n_tile = min((uint32_t)kOsTile, count - base);
+  const uint32_t n_tile = min((uint32_t)kTile, count - base);
 
   // stable ranking: warp-striped items, in index order within each warp
   const uint32_t lt = lanemask_lt();
-  K key[kOsItems];
-  uint32_t val[kOsItems], dig[kOsItems], loc[kOsItems];
+  K key[ITEMS];
+  uint32_t val[ITEMS], dig[ITEMS], loc[ITEMS];
 #pragma unroll
-  for (int i = 0; i < kOsItems; ++i) {
-    const uint32_t off = warp * (32 * kOsItems) + i * 32 + lane;
+  for (int i = 0; i < ITEMS; ++i) {
+    const uint32_t off = warp * (32 * ITEMS) + i * 32 + lane;
     const bool ok = off < n_tile;
     key[i] = ok ? keys_in[base + off] : (K)0;
     val[i] = ok ? vals_in[base + off] : 0u;
     dig[i] = ok ? digit_of(key[i], shift) : (uint32_t)kRadix;
   }
 #pragma unroll
-  for (int i = 0; i < kOsItems; ++i) {
+  for (int i = 0; i < ITEMS; ++i) {
     const uint32_t peers = __match_any_sync(0xffffffffu, dig[i]);
     uint32_t b = 0;
     if (dig[i] < (uint32_t)kRadix) b = wcnt[warp][dig[i]];
@@ -177,7 +183,7 @@ __global__ void __launch_bounds__(kOsThreads) k_os_pass(const K *__restrict__ ke
   __syncthreads();
   // local reorder by digit (stable), then contiguous global writes
 #pragma unroll
-  for (int i = 0; i < kOsItems; ++i) {
+  for (int i = 0; i < ITEMS; ++i) {
     if (dig[i] < (uint32_t)kRadix) {
       const uint32_t lp = tile_pre[dig[i]] + wcnt[warp][dig[i]] + loc[i];
       skey[lp] = key[i];
@@ -194,35 +200,47 @@ __global__ void __launch_bounds__(kOsThreads) k_os_pass(const K *__restrict__ ke
   }
 }
 
+template <typename K, int ITEMS>
+static cudaError_t os_passes(K *keys[2], uint32_t *vals[2], const uint32_t *count_p, uint32_t cap, int passes,
+                             uint32_t *tickets, uint32_t *ghist, unsigned long long *lookback, uint32_t lb_tiles,
+                             Counters *counters, cudaStream_t s) {
+  const size_t smem = (size_t)kOsThreads * ITEMS * (sizeof(K) + sizeof(uint32_t));
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_os_pass<K, ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  for (int p = 0; p < passes; ++p) {
+    const int src = p & 1, dst = src ^ 1;
+    k_os_pass<K, ITEMS><<<lb_tiles, kOsThreads, smem, s>>>(keys[src], vals[src], keys[dst], vals[dst], count_p, cap,
+                                                          p * kRadixBits, ghist + p * kRadix,
+                                                          lookback + (size_t)p * lb_tiles * kRadix, tickets + p,
+                                                          counters);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 template <typename K>
 static cudaError_t os_sort(K *keys[2], uint32_t *vals[2], const uint32_t *count_p, uint32_t cap, int bits,
                            uint32_t *tickets, uint32_t *ghist, unsigned long long *lookback, Counters *counters,
                            cudaStream_t s) {
   const int passes = radix_passes(bits);
   const uint32_t lb_tiles = (uint32_t)sort_tiles(cap);
+  const int items = os_items(cap);
   if (passes < 1 || passes > kMaxRadixPasses || lb_tiles == 0) return cudaErrorInvalidValue;
-  k_os_reset<<<2 * 152, 256, 0, s>>>(count_p, cap, passes, tickets, ghist, lookback, lb_tiles);
+  k_os_reset<<<2 * 152, 256, 0, s>>>(count_p, cap, passes, tickets, ghist, lookback, lb_tiles,
+                                     (uint32_t)(kOsThreads * items));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_os_hist<K><<<kHistCtas, 256, 0, s>>>(keys[0], count_p, cap, passes, ghist);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t smem = (size_t)kOsTile * (sizeof(K) + sizeof(uint32_t));
-  static bool attr_set = false;
-  if (!attr_set) {
-    e = cudaFuncSetAttribute(k_os_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  for (int p = 0; p < passes; ++p) {
-    const int src = p & 1, dst = src ^ 1;
-    k_os_pass<K><<<lb_tiles, kOsThreads, smem, s>>>(keys[src], vals[src], keys[dst], vals[dst], count_p, cap,
-                                                   p * kRadixBits, ghist + p * kRadix,
-                                                   lookback + (size_t)p * lb_tiles * kRadix, tickets + p, counters);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  if (items == 4)
+    return os_passes<K, 4>(keys, vals, count_p, cap, passes, tickets, ghist, lookback, lb_tiles, counters, s);
+  return os_passes<K, 16>(keys, vals, count_p, cap, passes, tickets, ghist, lookback, lb_tiles, counters, s);
 }
 
 cudaError_t launch_radix_sort_u64(const Layout &L, const WsPtrs &P, int bits, int *final_buf, cudaStream_t s) {

@@ -36,7 +36,7 @@ def test_stream_matches_eager_steps():
         params = [t.clone().requires_grad_(True) for t in (g.means, g.scales, g.quats, g.opacity, g.rgb, g.sem_w)]
         loss = raster.render_l1(rast_e, g, cam, tr, td, ts, *params)
         loss.backward()
-        ref.append((float(loss), [p.grad.clone() for p in params]))
+        ref.append((float(loss.detach()), [p.grad.clone() for p in params]))
     # streamed: pinned host frames, two slots, graphs
     rast = raster.Rasterizer()
     rast.forward(g, cam, check=True)
