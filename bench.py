@@ -609,7 +609,8 @@ def bench_large(args, dev, flush, wl):
         plain.append((s_, e_))
     torch.cuda.synchronize()
     ms_plain = statistics.mean(a.elapsed_time(b) for a, b in plain)
-    if rc.counters().status != 0:
+    ccnt = rc.counters()
+    if ccnt.status != 0:
         raise RuntimeError("device status after the mixed stream")
     mixed = {"metric": "mixed iterations/s (mapping step + 128 candidate views)",
              "workload": "mixed2m: the rooms2m scene + Gamma(2,0.5) uncertainty; per iteration one fused mapping "
@@ -618,7 +619,9 @@ def bench_large(args, dev, flush, wl):
              "value": 1000.0 / ms_graph, "unit": "iters/s", "ms_per_iter": ms_graph,
              "candidate_views_per_s": 1000.0 * len(cams) / ms_graph,
              "plain_per_view_launches": {"value": 1000.0 / ms_plain, "unit": "iters/s", "ms_per_iter": ms_plain},
-             "graph_batched_speedup": ms_plain / ms_graph}
+             "graph_batched_speedup": ms_plain / ms_graph,
+             "candidate_counts": {"visible_records": int(ccnt.n_records), "tile_gaussian_pairs": int(ccnt.n_pairs)},
+             "candidate_workspace_bytes": int(rc.ws.numel())}
     return large, mixed
 
 

@@ -106,10 +106,18 @@ bool make_layout(const gs_scene *scene, const gs_camera *cams, int n_views, cons
   L->off_codes = take(n_views == 1 ? 4 * (size_t)L->npix * (2 * (1 + L->nwc)) : 32);
   L->off_lpart = take(n_views == 1 ? 3 * sizeof(double) * (size_t)(tiles > 0 ? tiles : 1) : 32);
   // one unit = one staged batch of one tile: 2 words per tile pixel
-  // (none with recompute_bwd: pass 2 and the adjoint re-test the pairs)
-  L->mask_units = (n_views == 1 && !cfg.recompute_bwd) ? pcap / kBatch + (int64_t)tiles + 1 : 0;
+  // (none with recompute_bwd: pass 2 and the adjoint re-test the pairs;
+  // candidate views keep them only while they fit kCandMaskBudget, else the
+  // single-pass candidate kernel runs)
+  {
+    const int64_t units = pcap / kBatch + (int64_t)tiles + 1;
+    const int64_t bytes = 8 * units * cfg.tile_w * cfg.tile_h;
+    L->mask_units = cfg.recompute_bwd ? 0 : (n_views == 1 || bytes <= kCandMaskBudget) ? units : 0;
+  }
   L->off_mask_off = take(sizeof(uint32_t) * (size_t)(tiles + 1));
   L->off_masks = take(L->mask_units ? 8 * (size_t)L->mask_units * cfg.tile_w * cfg.tile_h : 32);
+  // last contributor of every (tile, pixel) of the candidate views
+  L->off_clast = take(n_views > 1 && L->mask_units ? 4 * (size_t)tiles * cfg.tile_w * cfg.tile_h : 32);
   L->total = off;
   return true;
 }
@@ -151,6 +159,7 @@ WsPtrs ws_ptrs(const Layout &L, void *ws) {
   P.lpart = reinterpret_cast<double *>(b + L.off_lpart);
   P.mask_off = reinterpret_cast<uint32_t *>(b + L.off_mask_off);
   P.masks = reinterpret_cast<uint32_t *>(b + L.off_masks);
+  P.clast = reinterpret_cast<uint32_t *>(b + L.off_clast);
   return P;
 }
 

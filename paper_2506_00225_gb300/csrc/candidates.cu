@@ -1,7 +1,7 @@
 // candidates.cu -- batched candidate-view rendering for next-best-view
 // scoring (Sec. 3.2).
 //
-// One launch covers every (view, tile) of all candidate views (mixed
+// One launch chain covers every (view, tile) of all candidate views (mixed
 // resolutions share one projection and one binning pass).  Per pixel it
 // composites the silhouette (Eq. 1, z_i = 1), the per-Gaussian scalar
 // uncertainty (Eq. 1, z_i = u_i) and the sparse semantic map (Eq. 3), then
@@ -11,6 +11,13 @@
 // logged one by one.  Per-view sums of U and H and the number of pixels with
 // S = 0 (Eq. 6) are reduced per CTA and added to the view's accumulators in
 // double precision.  No per-pixel map is written.
+//
+// When the workspace holds contributor bits, two passes run (as for the
+// mapping view): k_cand_blend composites U and S, records the last
+// contributor and one bit per (pixel, staged Gaussian) that contributed;
+// k_cand_sem walks only those bits to build the class distribution, class
+// chunk by class chunk, and reduces the entropy.  Otherwise the single-pass
+// k_candidates re-blends every chunk.
 #include "gs_internal.cuh"
 #include "render_common.cuh"
 
@@ -26,7 +33,39 @@ struct CandArgs {
   int n_views, k, m;
   double *out;
   int mchunk, mstride, nchunks;
+  // two-pass mode
+  const uint32_t *mask_off;
+  uint32_t *masks;
+  uint32_t mask_units;
+  uint32_t *clast;
 };
+
+// View of a global tile id: last v with tile_off[v] <= tile.
+__device__ __forceinline__ int view_of(const uint32_t *tile_off, int n_views, uint32_t tile) {
+  int lo = 0, hi = n_views;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (tile_off[mid] <= tile) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Per-view double sums of one float per thread (block reduction, then one
+// atomic per CTA).
+template <int THREADS>
+__device__ __forceinline__ void add_view_sum(float v, double *dst) {
+  __shared__ float red[THREADS / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane_id() == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < THREADS / 32; ++w) s += red[w];
+    atomicAdd(dst, s);
+  }
+}
 
 constexpr float kClipLo = 0.001f;
 
@@ -141,6 +180,190 @@ __global__ void __launch_bounds__(TW *TH) k_candidates(CandArgs a) {
   }
 }
 
+// Pass 1: U and S of Eq. 1 with the same per-pair rules as the mapping
+// blend (alpha box, 1/255 skip, 1e-4 stop); writes the last contributor and
+// the contributor bits of every staged batch; adds sum U and N_S per view.
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW *TH) k_cand_blend(CandArgs a) {
+  using FP = Footprint<TW, TH>;
+  constexpr int THREADS = FP::kThreads;
+  constexpr int NPIX = FP::kPix;
+  extern __shared__ float4 smem4[];
+  BatchSmem bs = batch_smem(smem4, 0);
+  const uint32_t tile = blockIdx.x;
+  const int v = view_of(a.tile_off, a.n_views, tile);
+  const DevCam &c = a.cams[v];
+  const uint32_t local = tile - c.tile_off;
+  const int ox = (int)(local % (uint32_t)c.tiles_x) * TW, oy = (int)(local / (uint32_t)c.tiles_x) * TH;
+  const uint2 rg = a.ranges[tile];
+  const int lx = FP::lx(), ly = FP::ly(0);
+  const int px = ox + lx, py = oy + ly, lp = ly * TW + lx;
+  const bool inside = px < c.width && py < c.height;
+  const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  const uint32_t unit0 = a.mask_off[tile];
+  const bool use_unc = a.unc != nullptr;
+
+  float T = 1.f, U = 0.f;
+  uint32_t last = 0;
+  bool done = !inside;
+  uint32_t bi = 0;
+  for (uint32_t b = rg.x; b < rg.y; b += kBatch, ++bi) {
+    const int n = (int)min((uint32_t)kBatch, rg.y - b);
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += THREADS)
+      stage_record<TW, TH>(a.rec, a.pvals[b + t], t, 0, ox, oy, bs, false, use_unc);
+    __syncthreads();
+    uint32_t bits[2] = {0u, 0u};
+    if (!__all_sync(0xffffffffu, done)) {
+      for (int base = 0; base < n; base += 32) {
+        const int jj = base + (int)lane;
+        uint32_t vis = __ballot_sync(0xffffffffu, jj < n && ((bs.wmask[jj] >> warp) & 1u));
+        while (vis) {
+          const int bit = __ffs(vis) - 1;
+          vis &= vis - 1;
+          const int j = base + bit;
+          if (done || !box_holds(bs.box[j], px, py)) continue;
+          float alpha, G, araw, dx, dy;
+          if (!gauss_alpha(bs.uv[j], bs.co[j], fpx, fpy, alpha, G, araw, dx, dy)) continue;
+          const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
+          if (Tn < kTStop) { done = true; continue; }
+          const float w = __fmul_rn(alpha, T);
+          U = fmaf(w, bs.cd[j].x, U);
+          T = Tn;
+          last = b - rg.x + j + 1;
+          bits[base >> 5] |= 1u << bit;
+        }
+      }
+    }
+    if (unit0 + bi < a.mask_units) {
+      uint32_t *mw = a.masks + (size_t)(unit0 + bi) * 2 * NPIX;
+      mw[lp] = bits[0];
+      mw[NPIX + lp] = bits[1];
+    }
+    if (__syncthreads_count(done) == THREADS) break;
+  }
+  a.clast[(size_t)tile * NPIX + lp] = last;
+  add_view_sum<THREADS>(inside && use_unc ? U : 0.f, a.out + 3 * v);
+  add_view_sum<THREADS>(inside && T == 1.f ? 1.f : 0.f, a.out + 3 * v + 2);
+}
+
+// Pass 2: the class distribution from the contributor bits (warp-uniform
+// walk over the union of the warp's bits, alpha recomputed bit-identically,
+// k adds per contributor into per-thread rows), one class chunk at a time,
+// and the clipped, renormalised entropy per pixel.
+template <int TW, int TH, int K>
+__global__ void __launch_bounds__(TW *TH, 2) k_cand_sem(CandArgs a) {
+  using FP = Footprint<TW, TH>;
+  constexpr int THREADS = FP::kThreads;
+  constexpr int NPIX = FP::kPix;
+  extern __shared__ float4 smem4[];
+  const int k = a.k;
+  char *sbase = reinterpret_cast<char *>(smem4);
+  const size_t bbytes = sem_batch_bytes(k);
+  float *sP = reinterpret_cast<float *>(sbase + 2 * bbytes);
+  __shared__ uint32_t s_maxlast;
+
+  const uint32_t tile = blockIdx.x;
+  const int v = view_of(a.tile_off, a.n_views, tile);
+  const DevCam &c = a.cams[v];
+  const uint32_t local = tile - c.tile_off;
+  const int ox = (int)(local % (uint32_t)c.tiles_x) * TW, oy = (int)(local / (uint32_t)c.tiles_x) * TH;
+  const uint2 rg = a.ranges[tile];
+  const int lx = FP::lx(), ly = FP::ly(0);
+  const int px = ox + lx, py = oy + ly, lp = ly * TW + lx;
+  const bool inside = px < c.width && py < c.height;
+  const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+  float *myP = sP + threadIdx.x * a.mstride;
+  const uint32_t unit0 = a.mask_off[tile];
+
+  const uint32_t last = a.clast[(size_t)tile * NPIX + lp];
+  if (threadIdx.x == 0) s_maxlast = 0;
+  __syncthreads();
+  if (last) atomicMax(&s_maxlast, last);
+  __syncthreads();
+  const int nbatch = (int)((s_maxlast + kBatch - 1) / kBatch);
+
+  auto buf_uv = [&](int q) { return reinterpret_cast<float2 *>(sbase + q * bbytes); };
+  auto buf_co = [&](int q) { return reinterpret_cast<float4 *>(sbase + q * bbytes + kBatch * 8); };
+  auto buf_sem = [&](int q) { return reinterpret_cast<int2 *>(sbase + q * bbytes + kBatch * 32); };
+  auto batch_n = [&](int bi) { return (int)min((uint32_t)kBatch, rg.y - (rg.x + (uint32_t)bi * kBatch)); };
+  auto issue = [&](int bi, uint32_t r) {
+    const int q = bi & 1, t = threadIdx.x;
+    cp_async8(buf_uv(q) + t, a.rec.uv + r);
+    cp_async16(buf_co(q) + t, a.rec.co + r);
+    const int2 *src = a.rec.sem + (size_t)r * k;
+    for (int l = 0; l < k; ++l) cp_async8(buf_sem(q) + t * k + l, src + l);
+  };
+
+  float Z = 0.f, Aacc = 0.f;
+  uint32_t nfloor = 0;
+  for (int ch = 0; ch < a.nchunks; ++ch) {
+    const int c_lo = ch * a.mchunk, c_hi = min(a.m, c_lo + a.mchunk), mc = c_hi - c_lo;
+    for (int q = 0; q < mc; ++q) myP[q] = 0.f;
+    float T = 1.f;
+    const int t = threadIdx.x;
+    if (nbatch > 0 && t < batch_n(0)) issue(0, a.pvals[rg.x + t]);
+    cp_async_commit();
+    uint32_t pv = (nbatch > 1 && t < batch_n(1)) ? a.pvals[rg.x + kBatch + t] : 0u;
+    cp_async_wait_all();
+    __syncthreads();
+    for (int bi = 0; bi < nbatch; ++bi) {
+      if (bi + 1 < nbatch && t < batch_n(bi + 1)) issue(bi + 1, pv);
+      cp_async_commit();
+      if (bi + 2 < nbatch && t < batch_n(bi + 2)) pv = a.pvals[rg.x + (uint32_t)(bi + 2) * kBatch + t];
+      const uint32_t b0 = (uint32_t)bi * kBatch;
+      uint32_t mine[2] = {0u, 0u};
+      if (b0 < last) {
+        const uint32_t *mw = a.masks + (size_t)(unit0 + bi) * 2 * NPIX;
+        mine[0] = mw[lp];
+        mine[1] = mw[NPIX + lp];
+      }
+      const float2 *suv = buf_uv(bi & 1);
+      const float4 *sco = buf_co(bi & 1);
+      const int2 *ssem = buf_sem(bi & 1);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t un = __reduce_or_sync(0xffffffffu, mine[h]);
+        while (un) {
+          const int jb = __ffs(un) - 1;
+          un &= un - 1;
+          const int j = h * 32 + jb;
+          float alpha = 0.f, G, araw, dx, dy;
+          gauss_alpha(suv[j], sco[j], fpx, fpy, alpha, G, araw, dx, dy);
+          const bool on = (mine[h] >> jb) & 1u;
+          const float w = on ? __fmul_rn(alpha, T) : 0.f;
+          if (on) T = __fmul_rn(T, __fsub_rn(1.f, alpha));
+          scatter_classes<K>(myP, ssem + j * k, k, c_lo, mc, w);
+        }
+      }
+      cp_async_wait_all();
+      __syncthreads();
+    }
+    if (inside) {
+      for (int q = 0; q < mc; ++q) {
+        const float p = myP[q];
+        if (p > kClipLo) {
+          const float ph = p < 1.f ? p : 1.f;
+          Z += ph;
+          Aacc = fmaf(ph, logf(ph), Aacc);
+        } else {
+          ++nfloor;
+        }
+      }
+    }
+    __syncthreads();  // the next chunk reuses the rows
+  }
+  float h = 0.f;
+  if (inside) {
+    const float zf = kClipLo * (float)nfloor;
+    Z += zf;
+    Aacc = fmaf(zf, logf(kClipLo), Aacc);
+    h = logf(Z) - Aacc / Z;
+  }
+  add_view_sum<THREADS>(h, a.out + 3 * v + 1);
+}
+
 __global__ void k_zero_doubles(double *p, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = 0.0;
@@ -159,6 +382,29 @@ static cudaError_t launch_cand_shape(const CandArgs &a, uint32_t grid, size_t sm
   return cudaGetLastError();
 }
 
+template <int TW, int TH, int K>
+static cudaError_t launch_cand_sem(const CandArgs &a, uint32_t grid, size_t smem, cudaStream_t s) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_cand_sem<TW, TH, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemBudget);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_cand_sem<TW, TH, K><<<grid, TW * TH, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int TW, int TH>
+static cudaError_t launch_cand_two_pass(const CandArgs &a, uint32_t grid, size_t smem_sem, cudaStream_t s) {
+  k_cand_blend<TW, TH><<<grid, TW * TH, batch_smem_bytes(0), s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (a.k == 3) return launch_cand_sem<TW, TH, 3>(a, grid, smem_sem, s);
+  if (a.k == 8) return launch_cand_sem<TW, TH, 8>(a, grid, smem_sem, s);
+  return launch_cand_sem<TW, TH, 0>(a, grid, smem_sem, s);
+}
+
 cudaError_t launch_candidates(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc, double *out,
                               cudaStream_t s) {
   k_zero_doubles<<<(3 * L.n_views + 255) / 256, 256, 0, s>>>(out, 3 * L.n_views);
@@ -173,10 +419,27 @@ cudaError_t launch_candidates(const Layout &L, const WsPtrs &P, int pbuf, const 
   a.n_views = L.n_views; a.k = sc.k; a.m = sc.m;
   a.out = out;
   const int threads = L.tile_w * L.tile_h;
-  chunk_classes(sc.m, threads, sc.k, true, &a.mchunk, &a.mstride, &a.nchunks);
-  const size_t smem = batch_smem_bytes(sc.k) + (size_t)threads * a.mstride * sizeof(float);
   const uint32_t grid = (uint32_t)L.total_tiles;
   if (grid == 0) return cudaSuccess;
+  if (L.mask_units > 0) {
+    // two passes: batch offsets of every tile, blend + bits, classes + entropy
+    a.mask_off = P.mask_off;
+    a.masks = P.masks;
+    a.mask_units = (uint32_t)L.mask_units;
+    a.clast = P.clast;
+    e = launch_tile_batch_offsets(P.ranges, grid, P.mask_off, P.counters, s);
+    if (e != cudaSuccess) return e;
+    const size_t fixed = 2 * sem_batch_bytes(sc.k), base = batch_smem_bytes(sc.k);
+    chunk_classes(sc.m, threads, sc.k, true, &a.mchunk, &a.mstride, &a.nchunks, fixed > base ? fixed - base : 0);
+    const size_t smem = fixed + (size_t)threads * a.mstride * sizeof(float);
+    if (L.tile_w == 16 && L.tile_h == 16) return launch_cand_two_pass<16, 16>(a, grid, smem, s);
+    if (L.tile_w == 16 && L.tile_h == 8) return launch_cand_two_pass<16, 8>(a, grid, smem, s);
+    if (L.tile_w == 8 && L.tile_h == 8) return launch_cand_two_pass<8, 8>(a, grid, smem, s);
+    if (L.tile_w == 32 && L.tile_h == 8) return launch_cand_two_pass<32, 8>(a, grid, smem, s);
+    return cudaErrorInvalidConfiguration;
+  }
+  chunk_classes(sc.m, threads, sc.k, true, &a.mchunk, &a.mstride, &a.nchunks);
+  const size_t smem = batch_smem_bytes(sc.k) + (size_t)threads * a.mstride * sizeof(float);
   if (L.tile_w == 16 && L.tile_h == 16) return launch_cand_shape<16, 16>(a, grid, smem, s);
   if (L.tile_w == 16 && L.tile_h == 8) return launch_cand_shape<16, 8>(a, grid, smem, s);
   if (L.tile_w == 8 && L.tile_h == 8) return launch_cand_shape<8, 8>(a, grid, smem, s);

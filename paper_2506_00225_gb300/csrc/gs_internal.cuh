@@ -19,6 +19,7 @@ constexpr int kProjThreads = 256;
 constexpr int kProjItems = 4;
 constexpr int kProjBlock = kProjThreads * kProjItems;  // Gaussians per projection CTA
 constexpr int kEmitCtas = 2 * 152;
+constexpr int64_t kCandMaskBudget = 48ll << 30;  // contributor-bit bytes the candidate layout may hold
 constexpr int kEmitThreads = 256;
 
 // Status bits in the workspace counters (1 << gs_status code).
@@ -70,7 +71,8 @@ struct Layout {
   size_t off_grad2d;
   int nwc;                                 // 32-class sign words per plane (fused L1 mode)
   size_t off_codes, off_lpart;
-  size_t off_mask_off, off_masks;          // contributor bitmasks of the mapping view
+  size_t off_mask_off, off_masks;          // contributor bitmasks (mapping view; candidate views when they fit)
+  size_t off_clast;                        // candidate views: last contributor per (tile, pixel)
   int64_t mask_units;                      // capacity in (tile, batch) units
   size_t total;
 };
@@ -107,6 +109,7 @@ struct WsPtrs {
   uint32_t *codes; // [npix][1 + nwc] (nonzero, negative) word pairs: sign codes of the fused L1 mode
   uint32_t *mask_off;  // [tiles + 1] first (tile, batch) unit of each tile
   uint32_t *masks;     // [unit][2][tile pixels] contributor bits of each staged batch
+  uint32_t *clast;     // [tiles][tile pixels] last contributor (candidate views)
   double *lpart;   // [tiles of view 0][3] per-tile L1 sums
 };
 
@@ -130,6 +133,9 @@ cudaError_t launch_scan_single(uint32_t *data, uint32_t n, uint32_t *total_out, 
 cudaError_t launch_radix_sort_u64(const Layout &L, const WsPtrs &P, int bits, int *final_buf, cudaStream_t s);
 cudaError_t launch_radix_sort_u32(const Layout &L, const WsPtrs &P, int bits, int *final_buf, cudaStream_t s);
 cudaError_t launch_emit_pairs(const Layout &L, const WsPtrs &P, int dbuf, cudaStream_t s);
+// first (tile, batch) unit of every tile: batches per tile, exclusive scan
+cudaError_t launch_tile_batch_offsets(const uint2 *ranges, uint32_t ntiles, uint32_t *mask_off, Counters *counters,
+                                      cudaStream_t s);
 cudaError_t launch_tile_ranges(const Layout &L, const WsPtrs &P, int pbuf, cudaStream_t s);
 cudaError_t launch_render_fwd(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc, float *rgb,
                               float *depth, float *sil, float *sem, cudaStream_t s);

@@ -215,6 +215,43 @@ inline void chunk_classes(int m, int threads, int k, bool has_sem, int *mchunk, 
   *nchunks = (m + c - 1) / c;
 }
 
+// Asynchronous global -> shared copies (sm_80+ cp.async), used to stage the
+// next batch while the current one is processed.
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Shared-memory layout of one pass-2 batch buffer: mean, conic, pixel box
+// (recomputation mode), k sem pairs.
+__host__ __device__ inline size_t sem_batch_bytes(int k) {
+  return (size_t)kBatch * (8 + 16 + 8) + (size_t)kBatch * k * 8;
+}
+
+// Adds w * weight to the accumulator slot of each of the Gaussian's k
+// (class, weight) entries that falls in the class chunk [c_lo, c_lo + mc).
+// K > 0 fixes k at compile time.
+template <int K>
+__device__ __forceinline__ void scatter_classes(float *row, const int2 *e, int k, int c_lo, int mc, float w) {
+  const int n = K > 0 ? K : k;
+#pragma unroll
+  for (int l = 0; l < n; ++l) {
+    const int2 v = e[l];
+    const int id = v.x - c_lo;
+    if ((unsigned)id < (unsigned)mc) row[id] = fmaf(w, __int_as_float(v.y), row[id]);
+  }
+}
+
 struct FwdArgs {
   const uint2 *ranges;
   const uint32_t *pvals;

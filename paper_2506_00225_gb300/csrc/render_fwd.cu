@@ -154,47 +154,10 @@ __global__ void __launch_bounds__(TW *TH) k_blend(FwdArgs a) {
   }
 }
 
-// Asynchronous global -> shared copies (sm_80+ cp.async), used to stage the
-// next batch while the current one is processed.
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
-               "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
-               "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
-               "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-// Shared-memory layout of one pass-2 batch buffer: mean, conic, pixel box
-// (recomputation mode), k sem pairs.
-__host__ __device__ inline size_t sem_batch_bytes(int k) {
-  return (size_t)kBatch * (8 + 16 + 8) + (size_t)kBatch * k * 8;
-}
-
 // Class chunking for pass 2, whose fixed part is two batch buffers.
 static void sem_chunks(int m, int npix, int k, bool acc, FwdArgs &a) {
   const size_t fixed = 2 * sem_batch_bytes(k), base = batch_smem_bytes(k);
   chunk_classes(m, npix, k, acc, &a.mchunk, &a.mstride, &a.nchunks, fixed > base ? fixed - base : 0);
-}
-
-// Adds w * weight to the accumulator slot of each of the Gaussian's k
-// (class, weight) entries that falls in the class chunk [c_lo, c_lo + mc).
-// K > 0 fixes k at compile time.
-template <int K>
-__device__ __forceinline__ void scatter_classes(float *row, const int2 *e, int k, int c_lo, int mc, float w) {
-  const int n = K > 0 ? K : k;
-#pragma unroll
-  for (int l = 0; l < n; ++l) {
-    const int2 v = e[l];
-    const int id = v.x - c_lo;
-    if ((unsigned)id < (unsigned)mc) row[id] = fmaf(w, __int_as_float(v.y), row[id]);
-  }
 }
 
 template <int TW, int TH, bool L1, int K>
@@ -516,12 +479,17 @@ static FwdArgs fwd_args(const Layout &L, const WsPtrs &P, int pbuf, const gs_sce
 }
 
 // First (tile, batch) unit of every tile: batches per tile, exclusive scan.
-static cudaError_t launch_mask_offsets(const Layout &L, const WsPtrs &P, int grid, cudaStream_t s) {
-  if (!L.mask_units) return cudaSuccess;
-  k_tile_batches<<<(grid + 255) / 256, 256, 0, s>>>(P.ranges, (uint32_t)grid, P.mask_off);
+cudaError_t launch_tile_batch_offsets(const uint2 *ranges, uint32_t ntiles, uint32_t *mask_off, Counters *counters,
+                                      cudaStream_t s) {
+  k_tile_batches<<<(ntiles + 255) / 256, 256, 0, s>>>(ranges, ntiles, mask_off);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_scan_single(P.mask_off, (uint32_t)grid, nullptr, 0xffffffffu, P.counters, s);
+  return launch_scan_single(mask_off, ntiles, nullptr, 0xffffffffu, counters, s);
+}
+
+static cudaError_t launch_mask_offsets(const Layout &L, const WsPtrs &P, int grid, cudaStream_t s) {
+  if (!L.mask_units) return cudaSuccess;
+  return launch_tile_batch_offsets(P.ranges, (uint32_t)grid, P.mask_off, P.counters, s);
 }
 
 cudaError_t launch_render_fwd(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc, float *rgb,

@@ -123,6 +123,7 @@ class Rasterizer:
         self.pair_capacity = int(pair_capacity)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.ws: torch.Tensor | None = None
+        self._shrink_ws = False  # re-allocate the workspace at its fitted size on the next call
         self.generation = 0
         # optional list collecting (name, cuda.Event) at phase boundaries
         self.phase_events: list | None = None
@@ -154,9 +155,10 @@ class Rasterizer:
         need = N.load().gs_workspace_size(ctypes.byref(sc), cams_arr, n_views, ctypes.byref(cfg))
         if need == 0:
             raise ValueError("invalid scene / camera / config for the rasterizer")
-        if self.ws is None or self.ws.numel() < need:
+        if self.ws is None or self.ws.numel() < need or (self._shrink_ws and self.ws.numel() > 2 * need):
             self.ws = None
             self.ws = torch.empty(int(need), dtype=torch.uint8, device=self.device)
+        self._shrink_ws = False
         return ctypes.c_void_p(self.ws.data_ptr())
 
     def counters(self) -> N.GsCounters:
@@ -290,6 +292,7 @@ class Rasterizer:
             cnt = N.GsCounters()
             st = lib.gs_read_counters(ws, ctypes.byref(cnt), _stream())
             if st == N.GS_OK:
+                self._fit_capacities(cnt, cfg)
                 break
             if st != N.GS_ERR_CAPACITY:
                 N.check(st, "gs_render_candidates (device status)")
@@ -299,6 +302,19 @@ class Rasterizer:
                 self.pair_capacity = int(cnt.n_pairs * 1.25) + 4096
         self._last = None
         return out
+
+    def _fit_capacities(self, cnt, cfg):
+        """After a checked candidate call: capacities far above the counts
+        are cut to 1.25x the counts, and the workspace is re-laid at the
+        next call (the default capacities are sized for the worst case; the
+        fitted layout also lets the contributor bits of the two-pass
+        candidate kernels fit).  Later calls whose counts exceed the fitted
+        capacities report the capacity status and regrow under check=True."""
+        rc = int(cnt.n_records * 1.25) + 4096
+        pc = int(cnt.n_pairs * 1.25) + 65536
+        if cfg.pair_capacity > 2 * pc or cfg.record_capacity > 2 * rc:
+            self.record_capacity, self.pair_capacity = rc, pc
+            self._shrink_ws = True
 
     # -- inspection -------------------------------------------------------------
     def workspace_views(self) -> dict:

@@ -176,14 +176,22 @@ def test_rooms2m_fused_l1_matches_plain_adjoint(rooms2m):
 
 
 def _candidates_sample(sc, cams, pick):
-    out = raster.Rasterizer().candidates(raster.Gaussians.from_scene(sc), cams).cpu().numpy()
-    assert np.isfinite(out).all()
-    for v in pick:
-        su, sh, ns, nf = oracle.candidate(sc, cams[v])
-        assert abs(out[v, 0] - su) <= 1e-5 * abs(su) + 1e-3, (v, out[v, 0], su)
-        assert abs(out[v, 1] - sh) <= 1e-5 * abs(sh), (v, out[v, 1], sh)
-        assert abs(out[v, 2] - ns) <= nf, (v, out[v, 2], ns, nf)
-    return out
+    """The first call runs with the worst-case default capacities (single-pass
+    kernel: the contributor bits do not fit); it fits the capacities, so the
+    second call runs the two-pass kernels.  Both are checked."""
+    g = raster.Gaussians.from_scene(sc)
+    rast = raster.Rasterizer()
+    outs = [rast.candidates(g, cams).cpu().numpy(), rast.candidates(g, cams).cpu().numpy()]
+    refs = {v: oracle.candidate(sc, cams[v]) for v in pick}
+    for out in outs:
+        assert np.isfinite(out).all()
+        for v in pick:
+            su, sh, ns, nf = refs[v]
+            assert abs(out[v, 0] - su) <= 1e-5 * abs(su) + 1e-3, (v, out[v, 0], su)
+            assert abs(out[v, 1] - sh) <= 1e-5 * abs(sh), (v, out[v, 1], sh)
+            assert abs(out[v, 2] - ns) <= nf, (v, out[v, 2], ns, nf)
+    np.testing.assert_allclose(outs[0], outs[1], rtol=1e-9, atol=1e-6)
+    return outs[1]
 
 
 def test_cand96_batched_sampled_views():

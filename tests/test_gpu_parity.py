@@ -319,6 +319,26 @@ def test_candidates_parity_mixed_resolutions():
         assert abs(out[v, 2] - ns) <= nf, (v, out[v, 2], ns, nf)
 
 
+def test_candidates_single_and_two_pass_agree():
+    """Without room for contributor bits (recompute_bwd) the single-pass
+    kernel runs; otherwise blend + class passes.  Same sums, and both match
+    the oracle, with M = 300 (class chunks) and k = 8."""
+    sc, _ = small_case(n=4000, m=300, k=8)
+    rng = np.random.default_rng(6)
+    sc.geo_unc = rng.gamma(2.0, 0.5, size=sc.n).astype(np.float32)
+    cams = [scenes.look_camera((0.0, 0.0, 1.5), yaw, w, h, f)
+            for yaw, (w, h, f) in zip([0, 25, -35], [(64, 40, 40.0), (96, 56, 60.0), (37, 29, 25.0)])]
+    g = raster.Gaussians.from_scene(sc)
+    a = raster.Rasterizer(recompute_bwd=True).candidates(g, cams).cpu().numpy()
+    b = raster.Rasterizer().candidates(g, cams).cpu().numpy()
+    np.testing.assert_allclose(a, b, rtol=1e-9, atol=1e-6)
+    for v, cam in enumerate(cams):
+        su, sh, ns, nf = oracle.candidate(sc, cam)
+        assert abs(b[v, 0] - su) <= 1e-5 * abs(su) + 1e-3, (v, b[v, 0], su)
+        assert abs(b[v, 1] - sh) <= 1e-5 * abs(sh), (v, b[v, 1], sh)
+        assert abs(b[v, 2] - ns) <= nf, (v, b[v, 2], ns, nf)
+
+
 def test_candidates_empty_views():
     sc, _ = small_case(n=300, m=20)
     cam = scenes.look_camera((0.0, 0.0, 1.5), 180.0, 50, 30, 40.0)
