@@ -51,8 +51,13 @@ __device__ __forceinline__ float sign_code(uint32_t nz, uint32_t ng, int bit, fl
 //   10..  dsem_w (k values)
 // which a transposed warp reduction sums over the warp's 32 pixels; each lane
 // then adds one of the totals with a single scalar atomic.
-template <int TW, int TH, bool CODES, int NV, int PPT>
+// K > 0 fixes the top-k count at compile time (exact unrolling of the
+// per-class terms); the reduction width follows: 16 values for K <= 6,
+// else 32.
+template <int TW, int TH, bool CODES, int K, int PPT>
 __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
+  constexpr int NV = (K > 0 && K <= 6) ? 16 : 32;
+  constexpr int NL = K > 0 ? K : NV - 10;  // per-class value slots walked
   using FP = Footprint<TW, TH, PPT>;
   extern __shared__ float4 smem4[];
   BatchSmem bs = batch_smem(smem4, a.k);
@@ -187,8 +192,8 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
           if (has_dsem) {
             float gs = 0.f;
 #pragma unroll
-            for (int l = 0; l < NV - 10; ++l) {
-              if (l < k) {
+            for (int l = 0; l < NL; ++l) {
+              if (K > 0 || l < k) {
                 const int2 e = sp[l];
                 float dp = 0.f;
                 if ((unsigned)e.x < (unsigned)a.m) {
@@ -243,36 +248,38 @@ __global__ void k_zero_grad2d(float4 *g, const Counters *cnt, uint32_t rcap) {
     g[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-template <int TW, int TH, bool CODES, int NV, int PPT>
+template <int TW, int TH, bool CODES, int K, int PPT>
 static cudaError_t launch_bwd_shape(const BwdArgs &a, int grid, size_t smem, cudaStream_t s) {
   static bool attr_set = false;
   if (!attr_set) {  // the sign words of large class counts need more than 48 KB
-    cudaError_t e = cudaFuncSetAttribute(k_render_bwd<TW, TH, CODES, NV, PPT>,
+    cudaError_t e = cudaFuncSetAttribute(k_render_bwd<TW, TH, CODES, K, PPT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_render_bwd<TW, TH, CODES, NV, PPT><<<grid, TW * TH / PPT, smem, s>>>(a);
+  k_render_bwd<TW, TH, CODES, K, PPT><<<grid, TW * TH / PPT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <bool CODES, int NV, int PPT>
+template <bool CODES, int K, int PPT>
 static cudaError_t dispatch_bwd_shape(int tw, int th, const BwdArgs &a, int grid, size_t smem, cudaStream_t s) {
-  if (tw == 16 && th == 16) return launch_bwd_shape<16, 16, CODES, NV, PPT>(a, grid, smem, s);
-  if (tw == 16 && th == 8) return launch_bwd_shape<16, 8, CODES, NV, PPT>(a, grid, smem, s);
-  if (tw == 8 && th == 8) return launch_bwd_shape<8, 8, CODES, NV, PPT>(a, grid, smem, s);
-  if (tw == 32 && th == 8) return launch_bwd_shape<32, 8, CODES, NV, PPT>(a, grid, smem, s);
+  if (tw == 16 && th == 16) return launch_bwd_shape<16, 16, CODES, K, PPT>(a, grid, smem, s);
+  if (tw == 16 && th == 8) return launch_bwd_shape<16, 8, CODES, K, PPT>(a, grid, smem, s);
+  if (tw == 8 && th == 8) return launch_bwd_shape<8, 8, CODES, K, PPT>(a, grid, smem, s);
+  if (tw == 32 && th == 8) return launch_bwd_shape<32, 8, CODES, K, PPT>(a, grid, smem, s);
   return cudaErrorInvalidConfiguration;
 }
 
 template <bool CODES>
 static cudaError_t dispatch_bwd(const Layout &L, const BwdArgs &a, int grid, size_t smem, cudaStream_t s) {
   if (L.ppt == 2) {
-    if (a.k <= 6) return dispatch_bwd_shape<CODES, 16, 2>(L.tile_w, L.tile_h, a, grid, smem, s);
-    return dispatch_bwd_shape<CODES, 32, 2>(L.tile_w, L.tile_h, a, grid, smem, s);
+    if (a.k == 3) return dispatch_bwd_shape<CODES, 3, 2>(L.tile_w, L.tile_h, a, grid, smem, s);
+    if (a.k == 8) return dispatch_bwd_shape<CODES, 8, 2>(L.tile_w, L.tile_h, a, grid, smem, s);
+    return dispatch_bwd_shape<CODES, 0, 2>(L.tile_w, L.tile_h, a, grid, smem, s);
   }
-  if (a.k <= 6) return dispatch_bwd_shape<CODES, 16, 1>(L.tile_w, L.tile_h, a, grid, smem, s);
-  return dispatch_bwd_shape<CODES, 32, 1>(L.tile_w, L.tile_h, a, grid, smem, s);
+  if (a.k == 3) return dispatch_bwd_shape<CODES, 3, 1>(L.tile_w, L.tile_h, a, grid, smem, s);
+  if (a.k == 8) return dispatch_bwd_shape<CODES, 8, 1>(L.tile_w, L.tile_h, a, grid, smem, s);
+  return dispatch_bwd_shape<CODES, 0, 1>(L.tile_w, L.tile_h, a, grid, smem, s);
 }
 
 cudaError_t launch_render_bwd(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc, const float *d_rgb,
