@@ -175,7 +175,6 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
           if (contrib[i]) gauss_alpha(uv, co, fpx, fpy[i], alpha[i], G[i], araw[i], dx[i], dy[i]);
           any = any || contrib[i];
         }
-        (void)any;
         float v[NV];
 #pragma unroll
         for (int q = 0; q < NV; ++q) v[q] = 0.f;
@@ -225,6 +224,29 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
             v[0] = fmaf(dpow, -(co.x * ddx + co.y * ddy), v[0]);
             v[1] = fmaf(dpow, -(co.z * ddy + co.y * ddx), v[1]);
           }
+        }
+        if (NV == 32 && __popc(__ballot_sync(0xffffffffu, any)) <= 2) {
+          // with the wide (32-value) reduction, one or two lanes touched by
+          // this Gaussian add their values directly
+          if (any) {
+            float *g2 = reinterpret_cast<float *>(a.grad2d) + 8 * (size_t)bs.rec[j];
+#pragma unroll
+            for (int q = 0; q < 7; ++q)
+              if (v[q] != 0.f) atomicAdd(g2 + q, v[q]);
+            if (a.g_rgb) {
+              float *gr = a.g_rgb + 3 * (size_t)bs.gid[j];
+#pragma unroll
+              for (int q = 0; q < 3; ++q)
+                if (v[7 + q] != 0.f) atomicAdd(gr + q, v[7 + q]);
+            }
+            if (has_dsem && a.g_sem_w) {
+              float *gw = a.g_sem_w + (size_t)bs.gid[j] * k;
+#pragma unroll
+              for (int l = 0; l < NL; ++l)
+                if ((K > 0 || l < k) && v[10 + l] != 0.f) atomicAdd(gw + l, v[10 + l]);
+            }
+          }
+          continue;
         }
         const float tot = warp_reduce_scatter<NV>(v);
         if (my_idx == (int)lane || NV == 32) {
