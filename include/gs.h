@@ -86,7 +86,8 @@ typedef struct gs_camera {
 
 /* Launch configuration.
  *   tile_w, tile_h       screen tile (compiled shapes: 16x16, 16x8, 8x8, 32x8)
- *   px_per_thread        pixels per thread in the blend kernels: 1 or 2
+ *   px_per_thread        pixels per thread in the adjoint: 1, 2 or 4 (4: 16x16
+ *                        tiles only)
  *                        (0 = default 2); results do not depend on it
  *   sem_detach_geometry  1 (default in the Python layer): the semantic
  *                        upstream gradient reaches sem_w only, never the

@@ -16,7 +16,11 @@ import torch
 from . import raster
 
 SHAPES = ((16, 16), (16, 8), (32, 8), (8, 8))
-PPTS = (2, 1)
+PPTS = (4, 2, 1)  # 4: tiles whose height is a multiple of 16 only
+
+
+def _valid(tile, ppt):
+    return ppt != 4 or tile[1] % 16 == 0
 
 _CACHE: dict = {}
 
@@ -51,6 +55,8 @@ def tune_mapping(g: raster.Gaussians, cam, t_rgb, t_depth, t_sem, reps: int = 5,
     table = []
     for tile in SHAPES:
         for ppt in PPTS:
+            if not _valid(tile, ppt):
+                continue
             ms, _ = _time_config(g, cam, (t_rgb, t_depth, t_sem), tile, ppt, reps, device)
             table.append({"tile": f"{tile[0]}x{tile[1]}", "px_per_thread": ppt, "ms": round(ms, 4)})
     best = min(table, key=lambda r: r["ms"])

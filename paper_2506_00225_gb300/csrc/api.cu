@@ -46,7 +46,8 @@ bool make_layout(const gs_scene *scene, const gs_camera *cams, int n_views, cons
   memset(L, 0, sizeof(*L));
   L->n = scene->n; L->k = scene->k; L->m = scene->m; L->n_views = n_views;
   L->tile_w = cfg.tile_w; L->tile_h = cfg.tile_h;
-  if (cfg.px_per_thread < 0 || cfg.px_per_thread > 2) return false;
+  if (cfg.px_per_thread < 0 || cfg.px_per_thread == 3 || cfg.px_per_thread > 4) return false;
+  if (cfg.px_per_thread == 4 && cfg.tile_h % 16 != 0) return false;  // warp block 8 x 16
   if (cfg.recompute_bwd != 0 && cfg.recompute_bwd != 1) return false;
   L->ppt = cfg.px_per_thread == 0 ? 2 : cfg.px_per_thread;
   uint64_t tiles = 0;

@@ -294,6 +294,12 @@ static cudaError_t dispatch_bwd_shape(int tw, int th, const BwdArgs &a, int grid
 
 template <bool CODES>
 static cudaError_t dispatch_bwd(const Layout &L, const BwdArgs &a, int grid, size_t smem, cudaStream_t s) {
+  if (L.ppt == 4) {
+    if (L.tile_w != 16 || L.tile_h != 16) return cudaErrorInvalidConfiguration;
+    if (a.k == 3) return launch_bwd_shape<16, 16, CODES, 3, 4>(a, grid, smem, s);
+    if (a.k == 8) return launch_bwd_shape<16, 16, CODES, 8, 4>(a, grid, smem, s);
+    return launch_bwd_shape<16, 16, CODES, 0, 4>(a, grid, smem, s);
+  }
   if (L.ppt == 2) {
     if (a.k == 3) return dispatch_bwd_shape<CODES, 3, 2>(L.tile_w, L.tile_h, a, grid, smem, s);
     if (a.k == 8) return dispatch_bwd_shape<CODES, 8, 2>(L.tile_w, L.tile_h, a, grid, smem, s);

@@ -122,7 +122,7 @@ def _backward_rows(wl, configs, recompute=False, seed=0):
 
 
 def test_room300k_backward_rows(room300k):
-    _backward_rows(room300k, [((16, 16), 2), ((32, 8), 1)])
+    _backward_rows(room300k, [((16, 16), 2), ((16, 16), 4), ((32, 8), 1)])
 
 
 def test_room300k_recompute_mode_rows(room300k):
