@@ -63,6 +63,11 @@ __global__ void k_os_reset(const uint32_t *count_p, uint32_t cap, int passes, ui
   }
 }
 
+// Digit histograms of every pass in one read of the keys.  Each thread
+// loads kHistItems keys before counting them (loads in flight); a warp's
+// equal digits are merged with one shared-memory add.
+constexpr int kHistItems = 4;
+
 template <typename K>
 __global__ void __launch_bounds__(256) k_os_hist(const K *__restrict__ keys, const uint32_t *count_p, uint32_t cap,
                                                  int passes, uint32_t *ghist) {
@@ -71,16 +76,25 @@ __global__ void __launch_bounds__(256) k_os_hist(const K *__restrict__ keys, con
   __syncthreads();
   const uint32_t count = min(*count_p, cap);
   const uint32_t lt = lanemask_lt();
-  const uint32_t stride = gridDim.x * blockDim.x;
-  // uniform trip count so that every lane takes part in the match
-  for (uint32_t base = blockIdx.x * blockDim.x; base < count; base += stride) {
-    const uint32_t i = base + threadIdx.x;
-    const bool ok = i < count;
-    const K k = ok ? keys[i] : (K)0;
-    for (int p = 0; p < passes; ++p) {
-      const uint32_t d = ok ? digit_of(k, p * kRadixBits) : (uint32_t)kRadix;
-      const uint32_t peers = __match_any_sync(0xffffffffu, d);
-      if (ok && (peers & lt) == 0u) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
+  const uint32_t stride = gridDim.x * blockDim.x * kHistItems;
+  // uniform trip count so that every lane takes part in the match; item it
+  // of a thread is element base + it * blockDim.x + threadIdx.x (coalesced)
+  for (uint32_t base = blockIdx.x * blockDim.x * kHistItems; base < count; base += stride) {
+    K k[kHistItems];
+    bool ok[kHistItems];
+#pragma unroll
+    for (int it = 0; it < kHistItems; ++it) {
+      const uint32_t i = base + it * blockDim.x + threadIdx.x;
+      ok[it] = i < count;
+      k[it] = ok[it] ? keys[i] : (K)0;
+    }
+#pragma unroll
+    for (int it = 0; it < kHistItems; ++it) {
+      for (int p = 0; p < passes; ++p) {
+        const uint32_t d = ok[it] ? digit_of(k[it], p * kRadixBits) : (uint32_t)kRadix;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (ok[it] && (peers & lt) == 0u) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
+      }
     }
   }
   __syncthreads();
@@ -363,14 +377,30 @@ __global__ void k_ranges_clear(uint2 *ranges, uint32_t total_tiles) {
     ranges[t] = make_uint2(0u, 0u);
 }
 
+// Each thread takes 4 consecutive sorted tile ids (one 16-byte load when
+// the group is whole) plus its neighbours, and writes the bounds of the runs
+// that start or end there.
 __global__ void k_ranges_mark(const uint32_t *__restrict__ pkeys, const Counters *cnt, uint32_t pcap,
                               uint32_t total_tiles, uint2 *ranges) {
   const uint32_t k = min(cnt->n_pairs, pcap);
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
-    const uint32_t t = pkeys[i];
-    if (t >= total_tiles) continue;
-    if (i == 0 || pkeys[i - 1] != t) ranges[t].x = i;
-    if (i + 1 == k || pkeys[i + 1] != t) ranges[t].y = i + 1;
+  for (uint32_t i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x); i0 < k; i0 += 4 * gridDim.x * blockDim.x) {
+    uint32_t t[6];
+    t[0] = i0 > 0 ? pkeys[i0 - 1] : 0xffffffffu;
+    if (i0 + 4 <= k) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(pkeys + i0);
+      t[1] = v.x; t[2] = v.y; t[3] = v.z; t[4] = v.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) t[1 + j] = i0 + j < k ? pkeys[i0 + j] : 0xffffffffu;
+    }
+    t[5] = i0 + 4 < k ? pkeys[i0 + 4] : 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t i = i0 + j, tt = t[1 + j];
+      if (i >= k || tt >= total_tiles) continue;
+      if (t[j] != tt) ranges[tt].x = i;
+      if (t[2 + j] != tt) ranges[tt].y = i + 1;
+    }
   }
 }
 
