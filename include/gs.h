@@ -103,7 +103,14 @@ typedef struct gs_camera {
  *                        adjoint; 1: no per-pixel storage besides the final
  *                        transmittance and last contributor -- both re-test
  *                        every (pixel, Gaussian) pair of the tile instead.
- *                        Results are identical. */
+ *                        Results are identical.
+ *   spin_limit           bound on the polls of one inter-CTA wait (decoupled
+ *                        look-back of the sorts); 0 = default (about 4
+ *                        million polls with a short sleep each).  A wait that
+ *                        runs out raises GS_ERR_TIMEOUT in the device status,
+ *                        later kernels of the chain skip their work, and
+ *                        gs_read_counters reports it.  Small values exist to
+ *                        exercise that path. */
 typedef struct gs_config {
   int32_t tile_w, tile_h;
   int32_t sem_detach_geometry;
@@ -111,6 +118,7 @@ typedef struct gs_config {
   int64_t record_capacity;
   int64_t pair_capacity;
   int32_t recompute_bwd;
+  int32_t spin_limit;
 } gs_config;
 
 /* Counters read back by gs_read_counters. */

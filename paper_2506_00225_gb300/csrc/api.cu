@@ -49,6 +49,8 @@ bool make_layout(const gs_scene *scene, const gs_camera *cams, int n_views, cons
   if (cfg.px_per_thread < 0 || cfg.px_per_thread == 3 || cfg.px_per_thread > 4) return false;
   if (cfg.px_per_thread == 4 && cfg.tile_h % 16 != 0) return false;  // warp block 8 x 16
   if (cfg.recompute_bwd != 0 && cfg.recompute_bwd != 1) return false;
+  if (cfg.spin_limit < 0) return false;
+  L->spin_limit = cfg.spin_limit ? (uint32_t)cfg.spin_limit : (1u << 22);
   L->ppt = cfg.px_per_thread == 0 ? 2 : cfg.px_per_thread;
   uint64_t tiles = 0;
   for (int v = 0; v < n_views; ++v) {
@@ -367,8 +369,8 @@ gs_status gs_read_counters(void *ws, gs_counters *out, gs_stream_t stream) {
   out->n_records = c.n_records;
   out->n_pairs = c.n_pairs;
   out->n_contrib = c.n_contrib;
+  if (c.status & kStatusTimeout) return GS_ERR_TIMEOUT;  // first: later counts may be meaningless
   if (c.status & kStatusCapacity) return GS_ERR_CAPACITY;
-  if (c.status & kStatusTimeout) return GS_ERR_TIMEOUT;
   return GS_OK;
 }
 

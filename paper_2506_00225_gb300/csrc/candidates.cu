@@ -34,6 +34,7 @@ struct CandArgs {
   const uint32_t *tile_off;
   int n_views, k, m;
   double *out;
+  const Counters *counters;
   int mchunk, mstride, nchunks;
   // two-pass mode
   const uint32_t *mask_off;
@@ -80,6 +81,7 @@ __global__ void __launch_bounds__(TW *TH) k_candidates(CandArgs a) {
   float *sP = bs.tail;
   __shared__ float red_u[THREADS / 32], red_h[THREADS / 32];
   __shared__ uint32_t red_n[THREADS / 32];
+  if (a.counters->status & kStatusTimeout) return;  // the binning is incomplete
 
   const uint32_t tile = blockIdx.x;
   // view of this tile: last v with tile_off[v] <= tile
@@ -192,6 +194,7 @@ __global__ void __launch_bounds__(TW *TH) k_cand_blend(CandArgs a) {
   constexpr int NPIX = FP::kPix;
   extern __shared__ float4 smem4[];
   BatchSmem bs = batch_smem(smem4, 0);
+  if (a.counters->status & kStatusTimeout) return;
   const uint32_t tile = blockIdx.x;
   const int v = view_of(a.tile_off, a.n_views, tile);
   const DevCam &c = a.cams[v];
@@ -265,6 +268,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_cand_sem(CandArgs a) {
   const size_t bbytes = sem_batch_bytes(k);
   float *sP = reinterpret_cast<float *>(sbase + 2 * bbytes);
   __shared__ uint32_t s_maxlast;
+  if (a.counters->status & kStatusTimeout) return;
 
   const uint32_t tile = blockIdx.x;
   const int v = view_of(a.tile_off, a.n_views, tile);
@@ -420,6 +424,7 @@ cudaError_t launch_candidates(const Layout &L, const WsPtrs &P, int pbuf, const 
   a.cams = P.cams; a.tile_off = P.tile_off;
   a.n_views = L.n_views; a.k = sc.k; a.m = sc.m;
   a.out = out;
+  a.counters = P.counters;
   const int threads = L.tile_w * L.tile_h;
   const uint32_t grid = (uint32_t)L.total_tiles;
   if (grid == 0) return cudaSuccess;

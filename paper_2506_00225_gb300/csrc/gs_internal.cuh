@@ -54,7 +54,8 @@ struct Counters {
 struct Layout {
   int n, k, m, n_views, tile_w, tile_h;
   int cam0_w, cam0_h;                      // first camera (the single view of mapping calls)
-  int ppt;                                 // pixels per thread in the tile kernels (1 or 2)
+  int ppt;                                 // pixels per thread in the adjoint (1, 2 or 4)
+  uint32_t spin_limit;                     // polls of one inter-CTA wait
   int64_t rcap, pcap, total_tiles, npix;  // npix: pixels of view 0 when n_views == 1
   int64_t proj_blocks;                     // projection CTAs per view
   int key_bits_depth;                      // bits of the (view, depth) record key

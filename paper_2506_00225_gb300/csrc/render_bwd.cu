@@ -30,6 +30,7 @@ struct BwdArgs {
   const uint32_t *nlast;
   const float *d_rgb, *d_depth, *d_sil, *d_sem;
   int sem_detach;
+  const Counters *counters;
   float4 *grad2d;
   float *g_rgb, *g_sem_w;
   // fused mean-L1 mode: upstream gradients decoded from sign codes
@@ -62,6 +63,7 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
   extern __shared__ float4 smem4[];
   BatchSmem bs = batch_smem(smem4, a.k);
   __shared__ uint32_t s_maxnl;
+  if (a.counters->status & kStatusTimeout) return;  // the binning is incomplete
 
   const int tile = blockIdx.x;
   const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
@@ -327,6 +329,7 @@ cudaError_t launch_render_bwd(const Layout &L, const WsPtrs &P, int pbuf, const 
   a.tfinal = P.tfinal; a.nlast = P.nlast;
   a.d_rgb = d_rgb; a.d_depth = d_depth; a.d_sil = d_sil; a.d_sem = d_sem;
   a.sem_detach = sem_detach;
+  a.counters = P.counters;
   a.grad2d = P.grad2d;
   a.g_rgb = g_rgb; a.g_sem_w = g_sem_w;
   a.mask_off = L.mask_units ? P.mask_off : nullptr;

@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(TW *TH) k_blend(FwdArgs a) {
   extern __shared__ float4 smem4[];
   BatchSmem bs = batch_smem(smem4, 0);
   __shared__ float red[2][WARPS];
+  if (a.counters->status & kStatusTimeout) return;  // the binning is incomplete
 
   const int tile = blockIdx.x;
   const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
@@ -174,6 +175,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_semantic(FwdArgs a) {
   float *sP = reinterpret_cast<float *>(sbase + 2 * bbytes);
   __shared__ float red[WARPS];
   __shared__ uint32_t s_maxlast;
+  if (a.counters->status & kStatusTimeout) return;
 
   const int tile = blockIdx.x;
   const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;

@@ -35,7 +35,6 @@ constexpr int kHistCtas = 2 * 152;
 constexpr unsigned long long kFlagA = 1ull << 62;   // tile aggregate published
 constexpr unsigned long long kFlagP = 2ull << 62;   // inclusive prefix published
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
-constexpr uint32_t kSpinLimit = 1u << 22;
 
 int sort_tiles(int64_t capacity) {
   const int64_t tile = (int64_t)kOsThreads * os_items(capacity);
@@ -111,7 +110,7 @@ __global__ void __launch_bounds__(kOsThreads) k_os_pass(const K *__restrict__ ke
                                                         const uint32_t *count_p, uint32_t cap, int shift,
                                                         const uint32_t *__restrict__ ghist,
                                                         unsigned long long *lookback, uint32_t *ticket,
-                                                        Counters *counters) {
+                                                        Counters *counters, uint32_t spin_limit) {
   constexpr int kTile = kOsThreads * ITEMS;
   extern __shared__ unsigned long long os_smem[];
   K *skey = reinterpret_cast<K *>(os_smem);
@@ -179,7 +178,7 @@ __global__ void __launch_bounds__(kOsThreads) k_os_pass(const K *__restrict__ ke
       const unsigned long long v = *reinterpret_cast<volatile unsigned long long *>(lookback + (size_t)j * kRadix + d);
       const unsigned long long flag = v & ~kValMask;
       if (flag == 0ull) {
-        if (++spins > kSpinLimit) { set_status(counters, kStatusTimeout); break; }
+        if (++spins > spin_limit) { set_status(counters, kStatusTimeout); break; }
         __nanosleep(32);
         continue;
       }
@@ -217,7 +216,7 @@ __global__ void __launch_bounds__(kOsThreads) k_os_pass(const K *__restrict__ ke
 template <typename K, int ITEMS>
 static cudaError_t os_passes(K *keys[2], uint32_t *vals[2], const uint32_t *count_p, uint32_t cap, int passes,
                              uint32_t *tickets, uint32_t *ghist, unsigned long long *lookback, uint32_t lb_tiles,
-                             Counters *counters, cudaStream_t s) {
+                             Counters *counters, uint32_t spin_limit, cudaStream_t s) {
   const size_t smem = (size_t)kOsThreads * ITEMS * (sizeof(K) + sizeof(uint32_t));
   static bool attr_set = false;
   if (!attr_set) {
@@ -230,7 +229,7 @@ static cudaError_t os_passes(K *keys[2], uint32_t *vals[2], const uint32_t *coun
     k_os_pass<K, ITEMS><<<lb_tiles, kOsThreads, smem, s>>>(keys[src], vals[src], keys[dst], vals[dst], count_p, cap,
                                                           p * kRadixBits, ghist + p * kRadix,
                                                           lookback + (size_t)p * lb_tiles * kRadix, tickets + p,
-                                                          counters);
+                                                          counters, spin_limit);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -240,7 +239,7 @@ static cudaError_t os_passes(K *keys[2], uint32_t *vals[2], const uint32_t *coun
 template <typename K>
 static cudaError_t os_sort(K *keys[2], uint32_t *vals[2], const uint32_t *count_p, uint32_t cap, int bits,
                            uint32_t *tickets, uint32_t *ghist, unsigned long long *lookback, Counters *counters,
-                           cudaStream_t s) {
+                           uint32_t spin_limit, cudaStream_t s) {
   const int passes = radix_passes(bits);
   const uint32_t lb_tiles = (uint32_t)sort_tiles(cap);
   const int items = os_items(cap);
@@ -253,8 +252,10 @@ static cudaError_t os_sort(K *keys[2], uint32_t *vals[2], const uint32_t *count_
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (items == 4)
-    return os_passes<K, 4>(keys, vals, count_p, cap, passes, tickets, ghist, lookback, lb_tiles, counters, s);
-  return os_passes<K, 16>(keys, vals, count_p, cap, passes, tickets, ghist, lookback, lb_tiles, counters, s);
+    return os_passes<K, 4>(keys, vals, count_p, cap, passes, tickets, ghist, lookback, lb_tiles, counters,
+                           spin_limit, s);
+  return os_passes<K, 16>(keys, vals, count_p, cap, passes, tickets, ghist, lookback, lb_tiles, counters,
+                          spin_limit, s);
 }
 
 cudaError_t launch_radix_sort_u64(const Layout &L, const WsPtrs &P, int bits, int *final_buf, cudaStream_t s) {
@@ -262,7 +263,7 @@ cudaError_t launch_radix_sort_u64(const Layout &L, const WsPtrs &P, int bits, in
   uint32_t *v[2] = {P.dvals[0], P.dvals[1]};
   *final_buf = radix_passes(bits) & 1;
   return os_sort<unsigned long long>(k, v, &P.counters->n_records, (uint32_t)L.rcap, bits, P.tickets, P.ghist,
-                                     P.lb_depth, P.counters, s);
+                                     P.lb_depth, P.counters, L.spin_limit, s);
 }
 
 cudaError_t launch_radix_sort_u32(const Layout &L, const WsPtrs &P, int bits, int *final_buf, cudaStream_t s) {
@@ -270,7 +271,7 @@ cudaError_t launch_radix_sort_u32(const Layout &L, const WsPtrs &P, int bits, in
   uint32_t *v[2] = {P.pvals[0], P.pvals[1]};
   *final_buf = radix_passes(bits) & 1;
   return os_sort<uint32_t>(k, v, &P.counters->n_pairs, (uint32_t)L.pcap, bits, P.tickets + kMaxRadixPasses,
-                           P.ghist + kMaxRadixPasses * kRadix, P.lb_pairs, P.counters, s);
+                           P.ghist + kMaxRadixPasses * kRadix, P.lb_pairs, P.counters, L.spin_limit, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -294,6 +295,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_count(const uint32_t *__r
                                                              uint32_t rcap, int tw, int th, uint32_t *epart,
                                                              uint32_t *rloc) {
   __shared__ uint32_t tmp[33];
+  if (cnt->status & kStatusTimeout) return;  // the depth order may hold stale entries
   const uint32_t count = min(cnt->n_records, rcap);
   uint32_t begin, end;
   emit_chunk(count, begin, end);
@@ -325,6 +327,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_write(const uint32_t *__r
                                                              uint32_t *__restrict__ pkeys,
                                                              uint32_t *__restrict__ pvals) {
   __shared__ uint32_t s_epart[kEmitCtas];
+  if (cnt->status & kStatusTimeout) return;
   for (int i = threadIdx.x; i < kEmitCtas; i += kEmitThreads) s_epart[i] = epart[i];
   __syncthreads();
   const uint32_t count = min(cnt->n_records, rcap);

@@ -114,9 +114,10 @@ class Rasterizer:
     """
 
     def __init__(self, tile=(16, 16), sem_detach_geometry=True, record_capacity=0, pair_capacity=0,
-                 device=None, px_per_thread=0, recompute_bwd=False):
+                 device=None, px_per_thread=0, recompute_bwd=False, spin_limit=0):
         self.tile = tuple(tile)
         self.recompute_bwd = bool(recompute_bwd)
+        self.spin_limit = int(spin_limit)  # 0: the library's bound on inter-CTA waits
         self.px_per_thread = int(px_per_thread)
         self.sem_detach_geometry = bool(sem_detach_geometry)
         self.record_capacity = int(record_capacity)
@@ -142,6 +143,7 @@ class Rasterizer:
         c.sem_detach_geometry = 1 if self.sem_detach_geometry else 0
         c.px_per_thread = self.px_per_thread
         c.recompute_bwd = 1 if self.recompute_bwd else 0
+        c.spin_limit = self.spin_limit
         # capacities start at a bound that never overflows for small problems
         # and grow on reported overflow (check=True)
         c.record_capacity = self.record_capacity if self.record_capacity > 0 else max(1, min(n_gauss * n_views,

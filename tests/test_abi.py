@@ -76,7 +76,7 @@ def test_workspace_size_and_layout_host_only(lib):
 
 
 @pytest.mark.parametrize("bad", ["k0", "k17", "m0", "views0", "views257", "tile0", "width0", "near0", "fx_nan",
-                                 "ppt3", "ppt4_h8", "recompute2"])
+                                 "ppt3", "ppt4_h8", "recompute2", "spin_neg"])
 def test_invalid_arguments_rejected_on_host(lib, bad):
     sc, cams, cfg = _structs()
     views = 1
@@ -102,6 +102,8 @@ def test_invalid_arguments_rejected_on_host(lib, bad):
         cfg.px_per_thread = 3
     elif bad == "ppt4_h8":
         cfg.px_per_thread, cfg.tile_h = 4, 8
+    elif bad == "spin_neg":
+        cfg.spin_limit = -1
     elif bad == "recompute2":
         cfg.recompute_bwd = 2
     assert lib.gs_workspace_size(ctypes.byref(sc), cams, views, ctypes.byref(cfg)) == 0
