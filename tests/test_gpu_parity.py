@@ -92,6 +92,39 @@ def test_binning_bitexact_multi_view_equal_depths():
     _check_lists(wv, projs, cams, (16, 16))
 
 
+def test_non_finite_gaussians_culled_like_the_oracle():
+    """NaN / Inf means and scales, zero and NaN quaternions: such Gaussians
+    get no record (as in the oracle), the rest render as usual, outputs stay
+    finite and the adjoint leaves their gradients at zero."""
+    sc, cam = small_case(n=3000, w=80, h=60)
+    rng = np.random.default_rng(3)
+    bad = rng.choice(sc.n, 120, replace=False)
+    sc.means[bad[:30], 0] = np.nan
+    sc.scales[bad[30:60], 1] = np.inf
+    sc.quats[bad[60:90], :] = 0.0
+    sc.quats[bad[90:], 2] = np.nan
+    g = raster.Gaussians.from_scene(sc)
+    rast = raster.Rasterizer()
+    rast._project_bin(g, [cam], check=True)
+    wv = rast.workspace_views()
+    p = oracle.project(sc, cam, prec="f32")
+    np.testing.assert_array_equal(wv["gid"].cpu().numpy(), np.nonzero(p["visible"])[0])
+    assert not np.isin(bad, wv["gid"].cpu().numpy()).any()
+    rgb, depth, sil, sem = _fwd(sc, cam)
+    r = oracle.render(sc, cam, prec="f32")
+    ok = r["flag"] & 1 == 0
+    for x, name in ((rgb, "rgb"), (depth, "depth"), (sil, "sil"), (sem, "sem")):
+        assert np.isfinite(x).all(), name
+        _img_close(x, r[name], ok)
+    up = torch.ones(cam.height, cam.width, 3, device="cuda")
+    rast.forward(g, cam)
+    grads = rast.backward(g, cam, up, None, None, None)
+    for name in ("means", "scales", "quats", "opacity", "rgb"):
+        v = grads[name].cpu().numpy()
+        assert np.isfinite(v).all(), name
+        assert (v[bad] == 0).all(), name
+
+
 # ---------------------------------------------------------------------------
 # forward render
 # ---------------------------------------------------------------------------
