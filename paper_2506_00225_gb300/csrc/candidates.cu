@@ -191,9 +191,11 @@ template <int TW, int TH>
 __global__ void __launch_bounds__(TW *TH) k_cand_blend(CandArgs a) {
   using FP = Footprint<TW, TH>;
   constexpr int THREADS = FP::kThreads;
+  constexpr int WARPS = FP::kWarps;
   constexpr int NPIX = FP::kPix;
   extern __shared__ float4 smem4[];
   BatchSmem bs = batch_smem(smem4, 0);
+  __shared__ uint32_t lmask[kBatch * WARPS];  // per staged Gaussian: its lanes of each warp
   if (a.counters->status & kStatusTimeout) return;
   const uint32_t tile = blockIdx.x;
   const int v = view_of(a.tile_off, a.n_views, tile);
@@ -216,19 +218,22 @@ __global__ void __launch_bounds__(TW *TH) k_cand_blend(CandArgs a) {
   for (uint32_t b = rg.x; b < rg.y; b += kBatch, ++bi) {
     const int n = (int)min((uint32_t)kBatch, rg.y - b);
     __syncthreads();
-    for (int t = threadIdx.x; t < n; t += THREADS)
-      stage_record<TW, TH>(a.rec, a.pvals[b + t], t, 0, ox, oy, bs, false, use_unc);
+    for (int t = threadIdx.x; t < n; t += THREADS) {
+      const uint32_t r = a.pvals[b + t];
+      stage_record<TW, TH>(a.rec, r, t, 0, ox, oy, bs, false, use_unc);
+      lane_masks<TW, TH>(__ldg(a.rec.box + r), ox, oy, lmask + t * WARPS);
+    }
     __syncthreads();
     uint32_t bits[2] = {0u, 0u};
     if (!__all_sync(0xffffffffu, done)) {
       for (int base = 0; base < n; base += 32) {
         const int jj = base + (int)lane;
-        uint32_t vis = __ballot_sync(0xffffffffu, jj < n && ((bs.wmask[jj] >> warp) & 1u));
+        uint32_t vis = __ballot_sync(0xffffffffu, jj < n && lmask[jj * WARPS + warp] != 0u);
         while (vis) {
           const int bit = __ffs(vis) - 1;
           vis &= vis - 1;
           const int j = base + bit;
-          if (done || !box_holds(bs.box[j], px, py)) continue;
+          if (done || !((lmask[j * WARPS + warp] >> lane) & 1u)) continue;
           float alpha, G, araw, dx, dy;
           if (!gauss_alpha(bs.uv[j], bs.co[j], fpx, fpy, alpha, G, araw, dx, dy)) continue;
           const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));

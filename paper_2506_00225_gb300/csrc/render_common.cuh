@@ -115,6 +115,28 @@ __device__ __forceinline__ void stage_record(const RecPtrs &rec, uint32_t r, int
   }
 }
 
+// Lane masks of a staged record for every warp of a PPT = 1 tile: bit l of
+// masks[w] is set when lane l's pixel of warp w lies in the record's alpha
+// box (image pixels b; tile origin ox, oy).  A warp's lanes hold an 8 x 4
+// block, lane l at column l % 8 and row l / 8.
+template <int TW, int TH>
+__device__ __forceinline__ void lane_masks(short4 b, int ox, int oy, uint32_t *masks) {
+  using FP = Footprint<TW, TH, 1>;
+#pragma unroll
+  for (int w = 0; w < FP::kWarps; ++w) {
+    const int x0 = ox + (w % FP::kWX) * 8, y0 = oy + (w / FP::kWX) * 4;
+    const int cl = max((int)b.x - x0, 0), ch = min((int)b.y - x0, 7);
+    const int rl = max((int)b.z - y0, 0), rh = min((int)b.w - y0, 3);
+    uint32_t m = 0u;
+    if (cl <= ch && rl <= rh) {
+      const uint32_t cols = (0xffu >> (7 - ch)) & (0xffu << cl);
+      const uint32_t rows = (0xffffffffu >> (8 * (3 - rh))) & (0xffffffffu << (8 * rl));
+      m = (cols * 0x01010101u) & rows;
+    }
+    masks[w] = m;
+  }
+}
+
 // Pixel inside the packed box (x0 | x1 << 16, y0 | y1 << 16).
 __device__ __forceinline__ bool box_holds(int2 bb, int px, int py) {
   const int x0 = bb.x & 0xffff, x1 = (int)((unsigned)bb.x >> 16);
