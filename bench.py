@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--workload", default="room300k")
     ap.add_argument("--no-candidates", action="store_true")
     ap.add_argument("--cand-steps", type=int, default=5)
+    ap.add_argument("--cand-workload", default="cand96", choices=["cand96", "mixed2m"],
+                    help="candidate set of the candidates measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 2M-Gaussian mapping and mixed-stream runs")
     ap.add_argument("--only", choices=["candidates", "large"], default=None,
@@ -638,8 +640,8 @@ def bench_large(args, dev, flush, wl):
 def bench_candidates(args, dev, flush):
     import torch
     from paper_2506_00225_gb300 import raster, scenes
-    wl = scenes.workload("cand96")
-    sc, cams = wl["scene"], wl["cams"]
+    wl = scenes.workload(args.cand_workload)
+    sc, cams = wl["scene"], wl.get("cand_cams", wl["cams"])
     g = raster.Gaussians.from_scene(sc, dev)
     rast = raster.Rasterizer(device=dev)
     out = rast.candidates(g, cams, check=True)
@@ -657,25 +659,30 @@ def bench_candidates(args, dev, flush):
         ts.append((s, e))
     torch.cuda.synchronize()
     ms = statistics.mean(a.elapsed_time(b) for a, b in ts)
-    # the same views, one plain launch chain per view
-    singles = [raster.Rasterizer(device=dev) for _ in range(3)]
-    outs = []
-    for v, c in enumerate(cams[:3]):
-        outs.append(singles[v % 3].candidates(g, [c], check=True))
+    # the same views, one plain launch chain per view (one rasterizer per
+    # resolution, sized by a checked call first)
+    singles = {}
+    for c in cams:
+        key = (c.width, c.height)
+        if key not in singles:
+            singles[key] = raster.Rasterizer(device=dev)
+            singles[key].candidates(g, [c], check=True)
     torch.cuda.synchronize()
     flush.zero_()
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     s.record()
-    for v, c in enumerate(cams):
-        singles[v % 3].candidates(g, [c], check=False)
+    for c in cams:
+        singles[(c.width, c.height)].candidates(g, [c], check=False)
     e.record()
     torch.cuda.synchronize()
     per_view_ms = s.elapsed_time(e)
     npix = sum(c.width * c.height for c in cams)
     return {"metric": "candidate views/s", "value": 1000.0 * len(cams) / ms, "unit": "views/s",
             "ms_per_batch": ms, "mpix_per_s": npix / (ms * 1e-3) / 1e6,
-            "workload": "cand96: the 300k room + Gamma(2,0.5) uncertainty, 96 poses (4x4 grid at 0.5 m x 6 yaws), "
-                        "resolutions cycling 170x300 / 340x600 / 680x1200",
+            "workload": ("cand96: the 300k room + Gamma(2,0.5) uncertainty, 96 poses (4x4 grid at 0.5 m x 6 yaws), "
+                         "resolutions cycling 170x300 / 340x600 / 680x1200") if args.cand_workload == "cand96" else
+                        ("mixed2m candidates: the 2M-Gaussian rooms (M=256, top-8) + Gamma(2,0.5) uncertainty, "
+                         "128 views (64 @170x300, 48 @340x600, 16 @680x1200)"),
             "n_records": int(cnt.n_records), "n_pairs": int(cnt.n_pairs),
             "per_view_launches": {"value": 1000.0 * len(cams) / per_view_ms, "unit": "views/s",
                                   "ms": per_view_ms},

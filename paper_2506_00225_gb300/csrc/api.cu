@@ -119,8 +119,9 @@ bool make_layout(const gs_scene *scene, const gs_camera *cams, int n_views, cons
   }
   L->off_mask_off = take(sizeof(uint32_t) * (size_t)(tiles + 1));
   L->off_masks = take(L->mask_units ? 8 * (size_t)L->mask_units * cfg.tile_w * cfg.tile_h : 32);
-  // last contributor of every (tile, pixel) of the candidate views
-  L->off_clast = take(n_views > 1 && L->mask_units ? 4 * (size_t)tiles * cfg.tile_w * cfg.tile_h : 32);
+  // last contributor of every (tile, pixel), written by the two-pass
+  // candidate kernels (any number of views) whenever the bits exist
+  L->off_clast = take(L->mask_units ? 4 * (size_t)tiles * cfg.tile_w * cfg.tile_h : 32);
   L->total = off;
   return true;
 }

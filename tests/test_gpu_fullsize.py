@@ -206,6 +206,22 @@ def test_cand96_batched_sampled_views():
     _candidates_sample(wl["scene"], cams, pick)
 
 
+def test_single_view_candidate_calls():
+    """One view per call (the plain per-view path the benchmark compares
+    against): the two-pass kernels with n_views = 1, one view of each
+    resolution, against the oracle."""
+    wl = scenes.workload("cand96")
+    sc = wl["scene"]
+    g = raster.Gaussians.from_scene(sc)
+    for cam in wl["cams"][:3]:
+        rast = raster.Rasterizer()
+        out = rast.candidates(g, [cam]).cpu().numpy()
+        su, sh, ns, nf = oracle.candidate(sc, cam)
+        assert abs(out[0, 0] - su) <= 1e-5 * abs(su) + 1e-3, (out[0, 0], su)
+        assert abs(out[0, 1] - sh) <= 1e-5 * abs(sh), (out[0, 1], sh)
+        assert abs(out[0, 2] - ns) <= nf, (out[0, 2], ns, nf)
+
+
 def test_mixed2m_candidates_sampled_views():
     """The 128 candidate views of the 2M-Gaussian scene (M=256, k=8) in one
     batched launch; the oracle checks six 170x300 views and one 340x600."""
