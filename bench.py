@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--cand-steps", type=int, default=5)
     ap.add_argument("--cand-workload", default="cand96", choices=["cand96", "mixed2m"],
                     help="candidate set of the candidates measurement")
+    ap.add_argument("--cand-tile", default="16x16", help="WxH tile of the candidate kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 2M-Gaussian mapping and mixed-stream runs")
     ap.add_argument("--only", choices=["candidates", "large"], default=None,
@@ -643,7 +644,8 @@ def bench_candidates(args, dev, flush):
     wl = scenes.workload(args.cand_workload)
     sc, cams = wl["scene"], wl.get("cand_cams", wl["cams"])
     g = raster.Gaussians.from_scene(sc, dev)
-    rast = raster.Rasterizer(device=dev)
+    ctile = tuple(int(x) for x in args.cand_tile.lower().split("x"))
+    rast = raster.Rasterizer(tile=ctile, device=dev)
     out = rast.candidates(g, cams, check=True)
     cnt = rast.counters()
     for _ in range(2):
@@ -665,7 +667,7 @@ def bench_candidates(args, dev, flush):
     for c in cams:
         key = (c.width, c.height)
         if key not in singles:
-            singles[key] = raster.Rasterizer(device=dev)
+            singles[key] = raster.Rasterizer(tile=ctile, device=dev)
             singles[key].candidates(g, [c], check=True)
     torch.cuda.synchronize()
     flush.zero_()

@@ -152,76 +152,90 @@ __device__ __forceinline__ GIn load_gaussian(const gs_scene &sc, int g) {
   return r;
 }
 
-// Pass 1: count visible Gaussians per projection block.
-__global__ void __launch_bounds__(kProjThreads) k_project_count(gs_scene sc, const DevCam *cams, int nb,
+// The Gaussians of one projection block are read once and projected for a
+// group of up to kViewsPerCta views (grid.y runs over the view groups).
+constexpr int kViewsPerCta = 16;
+
+// Pass 1: count visible Gaussians per (view, projection block).
+__global__ void __launch_bounds__(kProjThreads) k_project_count(gs_scene sc, const DevCam *cams, int nb, int n_views,
                                                                 uint32_t *blockcnt) {
   __shared__ uint32_t tmp[33];
-  const int v = blockIdx.x / nb, b = blockIdx.x % nb;
-  const DevCam c = cams[v];
+  const int b = blockIdx.x;
+  const int v0 = blockIdx.y * kViewsPerCta, v1 = min(n_views, v0 + kViewsPerCta);
   const int g0 = b * kProjBlock + threadIdx.x * kProjItems;
-  uint32_t cnt = 0;
+  GIn in[kProjItems];
 #pragma unroll
-  for (int i = 0; i < kProjItems; ++i) {
-    const int g = g0 + i;
-    if (g < sc.n) {
-      GIn in = load_gaussian(sc, g);
-      Proj p;
-      cnt += project_gaussian(in.mx, in.my, in.mz, in.sx, in.sy, in.sz, in.q, c, p) ? 1u : 0u;
+  for (int i = 0; i < kProjItems; ++i)
+    if (g0 + i < sc.n) in[i] = load_gaussian(sc, g0 + i);
+  for (int v = v0; v < v1; ++v) {
+    const DevCam c = cams[v];
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int i = 0; i < kProjItems; ++i) {
+      if (g0 + i < sc.n) {
+        Proj p;
+        cnt += project_gaussian(in[i].mx, in[i].my, in[i].mz, in[i].sx, in[i].sy, in[i].sz, in[i].q, c, p) ? 1u
+                                                                                                          : 0u;
+      }
     }
+    uint32_t total;
+    block_exclusive_scan(cnt, tmp, &total);
+    if (threadIdx.x == 0) blockcnt[v * nb + b] = total;
   }
-  uint32_t total;
-  block_exclusive_scan(cnt, tmp, &total);
-  if (threadIdx.x == 0) blockcnt[blockIdx.x] = total;
 }
 
 // Pass 2: recompute (bit-identical) and write compacted records in
 // (view, Gaussian index) order, plus the (view, depth) sort keys.
-__global__ void __launch_bounds__(kProjThreads) k_project_emit(gs_scene sc, const DevCam *cams, int nb,
+__global__ void __launch_bounds__(kProjThreads) k_project_emit(gs_scene sc, const DevCam *cams, int nb, int n_views,
                                                                const uint32_t *blockoff, uint32_t rcap,
                                                                WsPtrs P) {
   __shared__ uint32_t tmp[33];
-  const int v = blockIdx.x / nb, b = blockIdx.x % nb;
-  const DevCam c = cams[v];
+  const int b = blockIdx.x;
+  const int v0 = blockIdx.y * kViewsPerCta, v1 = min(n_views, v0 + kViewsPerCta);
   const int g0 = b * kProjBlock + threadIdx.x * kProjItems;
-  Proj p[kProjItems];
-  bool vis[kProjItems];
-  uint32_t cnt = 0;
+  GIn in[kProjItems];
 #pragma unroll
-  for (int i = 0; i < kProjItems; ++i) {
-    const int g = g0 + i;
-    vis[i] = false;
-    if (g < sc.n) {
-      GIn in = load_gaussian(sc, g);
-      vis[i] = project_gaussian(in.mx, in.my, in.mz, in.sx, in.sy, in.sz, in.q, c, p[i]);
+  for (int i = 0; i < kProjItems; ++i)
+    if (g0 + i < sc.n) in[i] = load_gaussian(sc, g0 + i);
+  for (int v = v0; v < v1; ++v) {
+    const DevCam c = cams[v];
+    Proj p[kProjItems];
+    bool vis[kProjItems];
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int i = 0; i < kProjItems; ++i) {
+      vis[i] = false;
+      if (g0 + i < sc.n)
+        vis[i] = project_gaussian(in[i].mx, in[i].my, in[i].mz, in[i].sx, in[i].sy, in[i].sz, in[i].q, c, p[i]);
+      cnt += vis[i] ? 1u : 0u;
     }
-    cnt += vis[i] ? 1u : 0u;
-  }
-  uint32_t total;
-  uint32_t rank = blockoff[blockIdx.x] + block_exclusive_scan(cnt, tmp, &total);
+    uint32_t total;
+    uint32_t rank = blockoff[v * nb + b] + block_exclusive_scan(cnt, tmp, &total);
 #pragma unroll
-  for (int i = 0; i < kProjItems; ++i) {
-    if (!vis[i]) continue;
-    const uint32_t r = rank++;
-    if (r >= rcap) continue;
-    P.rec_uv[r] = make_float2(p[i].u, p[i].v);
-    P.rec_conic[r] = make_float4(p[i].ca, p[i].cb, p[i].cc, __ldg(sc.opacity + g0 + i));
-    P.rec_depth[r] = p[i].depth;
-    P.rec_rect[r] = make_short4((short)p[i].x0, (short)p[i].x1, (short)p[i].y0, (short)p[i].y1);
-    P.rec_gid[r] = g0 + i;
-    P.rec_view[r] = v;
-    // blend record: alpha box, colour + depth, uncertainty, sparse semantics
-    const int g = g0 + i;
-    const float op = __ldg(sc.opacity + g);
-    P.rec_box[r] = alpha_box(p[i], op);
-    P.rec_cd[r] = make_float4(sc.rgb ? __ldg(sc.rgb + 3 * g) : 0.f, sc.rgb ? __ldg(sc.rgb + 3 * g + 1) : 0.f,
-                              sc.rgb ? __ldg(sc.rgb + 3 * g + 2) : 0.f, p[i].depth);
-    P.rec_unc[r] = sc.geo_unc ? __ldg(sc.geo_unc + g) : 0.f;
-    if (sc.sem_ids)
-      for (int l = 0; l < sc.k; ++l)
-        P.rec_sem[(size_t)r * sc.k + l] = make_int2(__ldg(sc.sem_ids + (size_t)g * sc.k + l),
-                                                    __float_as_int(__ldg(sc.sem_w + (size_t)g * sc.k + l)));
-    P.dkeys[0][r] = ((unsigned long long)v << 31) | (unsigned long long)__float_as_uint(p[i].depth);
-    P.dvals[0][r] = r;
+    for (int i = 0; i < kProjItems; ++i) {
+      if (!vis[i]) continue;
+      const uint32_t r = rank++;
+      if (r >= rcap) continue;
+      const int g = g0 + i;
+      const float op = __ldg(sc.opacity + g);
+      P.rec_uv[r] = make_float2(p[i].u, p[i].v);
+      P.rec_conic[r] = make_float4(p[i].ca, p[i].cb, p[i].cc, op);
+      P.rec_depth[r] = p[i].depth;
+      P.rec_rect[r] = make_short4((short)p[i].x0, (short)p[i].x1, (short)p[i].y0, (short)p[i].y1);
+      P.rec_gid[r] = g;
+      P.rec_view[r] = v;
+      // blend record: alpha box, colour + depth, uncertainty, sparse semantics
+      P.rec_box[r] = alpha_box(p[i], op);
+      P.rec_cd[r] = make_float4(sc.rgb ? __ldg(sc.rgb + 3 * g) : 0.f, sc.rgb ? __ldg(sc.rgb + 3 * g + 1) : 0.f,
+                                sc.rgb ? __ldg(sc.rgb + 3 * g + 2) : 0.f, p[i].depth);
+      P.rec_unc[r] = sc.geo_unc ? __ldg(sc.geo_unc + g) : 0.f;
+      if (sc.sem_ids)
+        for (int l = 0; l < sc.k; ++l)
+          P.rec_sem[(size_t)r * sc.k + l] = make_int2(__ldg(sc.sem_ids + (size_t)g * sc.k + l),
+                                                      __float_as_int(__ldg(sc.sem_w + (size_t)g * sc.k + l)));
+      P.dkeys[0][r] = ((unsigned long long)v << 31) | (unsigned long long)__float_as_uint(p[i].depth);
+      P.dvals[0][r] = r;
+    }
   }
 }
 
@@ -265,12 +279,13 @@ cudaError_t launch_project(const Layout &L, const WsPtrs &P, const gs_scene &sc,
   const int nb = (int)L.proj_blocks;
   const int grid = nb * L.n_views;
   if (grid == 0) return cudaSuccess;
-  k_project_count<<<grid, kProjThreads, 0, s>>>(sc, P.cams, nb, P.blockcnt);
+  const dim3 g2(nb, (L.n_views + kViewsPerCta - 1) / kViewsPerCta);
+  k_project_count<<<g2, kProjThreads, 0, s>>>(sc, P.cams, nb, L.n_views, P.blockcnt);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = launch_scan_single(P.blockcnt, (uint32_t)grid, &P.counters->n_records, (uint32_t)L.rcap, P.counters, s);
   if (e != cudaSuccess) return e;
-  k_project_emit<<<grid, kProjThreads, 0, s>>>(sc, P.cams, nb, P.blockcnt, (uint32_t)L.rcap, P);
+  k_project_emit<<<g2, kProjThreads, 0, s>>>(sc, P.cams, nb, L.n_views, P.blockcnt, (uint32_t)L.rcap, P);
   return cudaGetLastError();
 }
 
