@@ -241,11 +241,12 @@ __global__ void __launch_bounds__(TW *TH) k_cand_blend(CandArgs a) {
           const float w = __fmul_rn(alpha, T);
           U = fmaf(w, bs.cd[j].x, U);
           T = Tn;
-          last = b - rg.x + j + 1;
           bits[base >> 5] |= 1u << bit;
         }
       }
     }
+    if (bits[1]) last = b - rg.x + 32 + (32 - __clz(bits[1]));
+    else if (bits[0]) last = b - rg.x + (32 - __clz(bits[0]));
     if (unit0 + bi < a.mask_units) {
       uint32_t *mw = a.masks + (size_t)(unit0 + bi) * 2 * NPIX;
       mw[lp] = bits[0];

@@ -101,12 +101,14 @@ __global__ void __launch_bounds__(TW *TH) k_blend(FwdArgs a) {
           const float4 cdp = bs.cd[j];
           cr = fmaf(w, cdp.x, cr); cg = fmaf(w, cdp.y, cg); cb = fmaf(w, cdp.z, cb); cd = fmaf(w, cdp.w, cd);
           T = Tn;
-          last = b - rg.x + j + 1;
-          ++ncontrib;
           bits[base >> 5] |= 1u << bit;
         }
       }
     }
+    // last contributor and contribution count from the batch's bits
+    if (bits[1]) last = b - rg.x + 32 + (32 - __clz(bits[1]));
+    else if (bits[0]) last = b - rg.x + (32 - __clz(bits[0]));
+    ncontrib += __popc(bits[0]) + __popc(bits[1]);
     if (a.masks && unit0 + bi < a.mask_units) {
       uint32_t *mw = a.masks + (size_t)(unit0 + bi) * 2 * NPIX;
       mw[lp] = bits[0];
