@@ -387,7 +387,7 @@ def main():
     t_bwd = ph_ms.get("render_bwd", 0.0) * 1e-3
     t_fwd = ph_ms.get("render_fwd", 0.0) * 1e-3
     alu = flops_bwd / t_bwd / 1e12
-    bwd_kernel = "k_render_bwd<%d, %d, 1, %d, %d>" % (best["tile"][0], best["tile"][1], 16 if k <= 6 else 32,
+    bwd_kernel = "k_render_bwd<%d, %d, 1, %d, %d>" % (best["tile"][0], best["tile"][1], k if k in (3, 8) else 0,
                                                       best["px_per_thread"])
     roofline = {"bound": "alu", "kernel": bwd_kernel, "achieved": alu, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": alu / fp32_peak,
