@@ -386,6 +386,16 @@ def main():
     # launches the 2D-gradient clear and the projection adjoint, ~2 % of it)
     t_bwd = ph_ms.get("render_bwd", 0.0) * 1e-3
     t_fwd = ph_ms.get("render_fwd", 0.0) * 1e-3
+    t_front = ph_ms.get("project", 0.0) * 1e-3
+    # projection: 44 B read per Gaussian in each of its two passes, 112 B
+    # written per record (+ 8 B per semantic entry); depth sort: 32 B per
+    # record and pass (8-bit digits); pair emission: 12 B per pair; tile
+    # sort: 20 B per pair and pass; ranges: 8 B per pair
+    dpass = (31 + 7) // 8
+    tpass = (max(1, (((W + best["tile"][0] - 1) // best["tile"][0]) * ((H + best["tile"][1] - 1) // best["tile"][1]) - 1)
+                 .bit_length()) + 7) // 8
+    bytes_front = (sc.n * 44 * 2 + n_records * (112 + 8 * k) + n_records * 32 * dpass + n_pairs * 12
+                   + n_pairs * 20 * tpass + n_pairs * 8)
     alu = flops_bwd / t_bwd / 1e12
     bwd_kernel = "k_render_bwd<%d, %d, 1, %d, %d>" % (best["tile"][0], best["tile"][1], k if k in (3, 8) else 0,
                                                       best["px_per_thread"])
@@ -400,7 +410,12 @@ def main():
                 "hbm_frac_of_" + peak_src: (bytes_bwd / t_bwd / 1e9) / hbm_peak,
                 "forward": {"kernels": "k_blend + k_semantic (+ batch offsets, loss reduction)",
                             "ms": t_fwd * 1e3, "algorithmic_bytes": bytes_fwd,
-                            "hbm_frac_of_" + peak_src: (bytes_fwd / t_fwd / 1e9) / hbm_peak}}
+                            "hbm_frac_of_" + peak_src: (bytes_fwd / t_fwd / 1e9) / hbm_peak},
+                "project_bin_sort": {"kernels": "projection (count, emit), record depth sort, pair emission, tile "
+                                                "sort, ranges",
+                                     "ms": t_front * 1e3, "algorithmic_bytes": bytes_front,
+                                     "achieved_gbs": bytes_front / t_front / 1e9,
+                                     "hbm_frac_of_" + peak_src: (bytes_front / t_front / 1e9) / hbm_peak}}
     roofline["phases_ms"] = {k_: round(v, 4) for k_, v in ph_ms.items()}
 
     # ---- e2e through the public API with host buffers ------------------------
