@@ -446,3 +446,79 @@ def test_golden_closed_forms():
     for m, v in zip(d["entropy_empty_pixel"]["m"], d["entropy_empty_pixel"]["value"]):
         sc = mk_scene([[0.0, 0.0, -1.0]], [[1.0, 1.0, 1.0]], [[1, 0, 0, 0]], [0.5], m=m)
         assert abs(oracle.candidate(sc, cam, prec="f64")[1] - v) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# mapping objective (Sec. 3.1): geometric L1 under the silhouette mask,
+# entropy-masked Hellinger + cosine semantic term
+# ---------------------------------------------------------------------------
+
+def test_mapping_loss_semantic_closed_forms():
+    from oracle import mapping_loss as ml
+    k = 3
+    # identical sharp distributions: Hellinger 0, cosine 1 -> term 0 and a
+    # zero gradient
+    q = np.array([0.9, 0.05, 0.05, 0.0])
+    t, g = ml.semantic_terms(q[None], q[None], k)
+    assert abs(t[0]) < 1e-12 and np.abs(g).max() < 1e-12
+    # disjoint one-hots: Hellinger sqrt(0.5 * 2) = 1, cosine 0 -> 0.8 + 0.2
+    t, _ = ml.semantic_terms(np.array([[1.0, 0, 0]]), np.array([[0, 1.0, 0]]), k)
+    assert abs(t[0] - 1.0) < 1e-5
+    # scaled prediction: cosine unchanged (1), Hellinger of (Q, c Q) = sqrt(0.5) |1 - sqrt(c)|
+    c = 0.49
+    t, _ = ml.semantic_terms(q[None], c * q[None], k)
+    assert abs(t[0] - 0.8 * math.sqrt(0.5) * (1 - math.sqrt(c)) * math.sqrt((q).sum())) < 1e-5
+    # entropy mask: uniform over k + 1 classes has H = ln(k + 1) > ln k -> masked
+    # out (exactly uniform over k sits on the threshold: a rounding tie)
+    qu = np.array([[0.25, 0.25, 0.25, 0.25]])
+    t, g = ml.semantic_terms(qu, np.array([[0.0, 0.0, 0.0, 1.0]]), k)
+    assert t[0] == 0.0 and not g.any()
+    # just below ln k -> kept
+    qs = np.array([[0.36, 0.33, 0.31, 0.0]])
+    assert -(qs[qs > 0] * np.log(qs[qs > 0])).sum() < math.log(k)
+    t, _ = ml.semantic_terms(qs, np.array([[0.0, 0.0, 0.0, 1.0]]), k)
+    assert t[0] > 0.5
+
+
+def test_mapping_loss_geometric_closed_form_and_mask():
+    from oracle import mapping_loss as ml
+    rgb = np.array([[[0.6, 0.3, 0.55]], [[0.2, 0.2, 0.2]]])
+    t_rgb = np.array([[[0.5, 0.5, 0.5]], [[0.9, 0.9, 0.9]]])
+    depth = np.array([[2.3], [1.0]])
+    t_depth = np.array([[2.0], [5.0]])
+    sil = np.array([[1.0], [0.99]])  # the second pixel sits on the threshold: excluded
+    sem = np.zeros((2, 1, 2))
+    t_sem = np.full((2, 1, 2), 0.5)  # uniform over k = 2: masked semantic term
+    loss, d_rgb, d_depth, d_sem = ml.mapping_loss(rgb, depth, sil, sem, t_rgb, t_depth, t_sem, k=2)
+    assert abs(loss - (0.3 + 0.5 * (0.1 + 0.2 + 0.05))) < 1e-12
+    np.testing.assert_array_equal(d_depth, [[1.0], [0.0]])
+    np.testing.assert_array_equal(d_rgb[0, 0], [0.5, -0.5, 0.5])
+    assert not d_rgb[1].any() and not d_sem.any()
+
+
+def test_mapping_loss_gradient_matches_central_differences():
+    from oracle import mapping_loss as ml
+    rng = np.random.default_rng(11)
+    H, W, M, k = 3, 4, 7, 2
+    t_sem = rng.dirichlet(np.full(M, 0.15), size=(H, W))   # mostly sharp: H < ln 2 for many pixels
+    sem = rng.dirichlet(np.full(M, 1.0), size=(H, W)) * 0.9 + 0.01
+    rgb, t_rgb = rng.uniform(size=(H, W, 3)), rng.uniform(size=(H, W, 3))
+    depth, t_depth = rng.uniform(1, 3, size=(H, W)), rng.uniform(1, 3, size=(H, W))
+    sil = rng.uniform(0.95, 1.0, size=(H, W))
+    keep = np.abs(rgb - t_rgb).min() > 1e-3 and np.abs(depth - t_depth).min() > 1e-3
+    assert keep
+    f = lambda **kw: ml.mapping_loss(**{**dict(rgb=rgb, depth=depth, sil=sil, sem=sem, t_rgb=t_rgb,
+                                                t_depth=t_depth, t_sem=t_sem, k=k), **kw})[0]
+    _, d_rgb, d_depth, d_sem = ml.mapping_loss(rgb, depth, sil, sem, t_rgb, t_depth, t_sem, k)
+    masked = sum(1 for y in range(H) for x in range(W)
+                 if -(t_sem[y, x] * np.log(t_sem[y, x])).sum() < math.log(k))
+    assert 0 < masked < H * W
+    h = 1e-6
+    for name, arr, grad in (("sem", sem, d_sem), ("depth", depth, d_depth), ("rgb", rgb, d_rgb)):
+        num = np.zeros_like(arr)
+        for idx in np.ndindex(arr.shape):
+            a, b = arr.copy(), arr.copy()
+            a[idx] += h
+            b[idx] -= h
+            num[idx] = (f(**{name: a}) - f(**{name: b})) / (2 * h)
+        np.testing.assert_allclose(grad, num, rtol=1e-5, atol=1e-8, err_msg=name)
