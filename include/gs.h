@@ -253,6 +253,25 @@ gs_status gs_l1_loss(int64_t npix, int m, const float *rgb, const float *t_rgb, 
                      const float *t_depth, const float *sem, const float *t_sem, float *d_rgb, float *d_depth,
                      float *d_sem, float *loss, double *partial, gs_stream_t stream);
 
+/* Number of doubles of the `partial` scratch gs_mapping_loss needs. */
+#define GS_MAPPING_LOSS_PARTIALS 2048
+
+/* The mapping objective of Sec. 3.1 on rendered maps (npix pixels, m
+ * classes, top-k count k of the map):
+ *   sum_p [S(p) > 0.99] (|D(p) - D*(p)| + 0.5 sum_c |C_c(p) - C*_c(p)|)
+ *   + mean_p M_H(p) (0.8 D_HD(Q(p) || P(p)) + 0.2 (1 - cos(Q(p), P(p))))
+ * with the target distribution Q = t_sem, the rendered P = sem, the entropy
+ * mask M_H = [H(Q) < ln k] (Sec. 3.1 "Semantic Loss", Eq. 4), the Hellinger
+ * distance D_HD = sqrt(0.5 sum_m (sqrt(Q_m + e) - sqrt(max(P_m, 0) + e))^2),
+ * e = 1e-12, and the cosine similarity (0 for a zero norm).  The semantic
+ * term is skipped when sem is NULL.  Writes the gradients with respect to
+ * rgb [npix][3], depth [npix] and sem [npix][m] (any output may be NULL; the
+ * silhouette only masks, so it gets none) and *loss (device float).
+ * partial: caller scratch of GS_MAPPING_LOSS_PARTIALS doubles. */
+gs_status gs_mapping_loss(int64_t npix, int m, int k, const float *rgb, const float *t_rgb, const float *depth,
+                          const float *t_depth, const float *sil, const float *sem, const float *t_sem, float *d_rgb,
+                          float *d_depth, float *d_sem, float *loss, double *partial, gs_stream_t stream);
+
 /* Bytes of the fixed device scratch array used by gs_render_fwd_noalloc. */
 #define GS_NOALLOC_SCRATCH_BYTES (32u << 20)
 

@@ -13,9 +13,10 @@ c_int32, c_int64, c_uint32, c_void_p, c_size_t, c_double = (ctypes.c_int32, ctyp
 
 GS_OK, GS_ERR_ARG, GS_ERR_CAPACITY, GS_ERR_CUDA, GS_ERR_TIMEOUT, GS_ERR_UNSUPPORTED, GS_ERR_TOO_LARGE = range(7)
 GS_NOALLOC_SCRATCH_BYTES = 32 << 20
+GS_MAPPING_LOSS_PARTIALS = 2048
 
 EXPORTS = ["gs_workspace_size", "gs_workspace_layout", "gs_project", "gs_bin_sort", "gs_render_fwd",
-           "gs_render_bwd", "gs_render_fwd_l1", "gs_render_bwd_l1", "gs_render_candidates", "gs_l1_loss",
+           "gs_render_bwd", "gs_render_fwd_l1", "gs_render_bwd_l1", "gs_render_candidates", "gs_l1_loss", "gs_mapping_loss",
            "gs_render_fwd_noalloc", "gs_read_counters", "gs_status_string"]
 
 
@@ -67,6 +68,8 @@ _SIGS = {
                                             c_void_p]),
     "gs_l1_loss": (ctypes.c_int, [c_int64, ctypes.c_int] + [c_void_p] * 6 + [c_void_p] * 3 + [c_void_p, c_void_p,
                                                                                              c_void_p]),
+    "gs_mapping_loss": (ctypes.c_int, [c_int64, ctypes.c_int, ctypes.c_int] + [c_void_p] * 7 + [c_void_p] * 3 +
+                        [c_void_p, c_void_p, c_void_p]),
     "gs_render_fwd_noalloc": (ctypes.c_int, [P(GsScene), P(GsCamera), P(GsConfig)] + [c_void_p] * 4 +
                               [c_void_p, c_void_p]),
     "gs_read_counters": (ctypes.c_int, [c_void_p, P(GsCounters), c_void_p]),

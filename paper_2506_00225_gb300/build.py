@@ -29,6 +29,7 @@ SOURCES = {
     "render_bwd.cu": [],
     "candidates.cu": [],
     "loss.cu": [],
+    "mapping_loss.cu": [],
     "api.cu": [],
     "noalloc.cu": [],
 }

@@ -361,6 +361,16 @@ gs_status gs_l1_loss(int64_t npix, int m, const float *rgb, const float *t_rgb, 
   return GS_OK;
 }
 
+gs_status gs_mapping_loss(int64_t npix, int m, int k, const float *rgb, const float *t_rgb, const float *depth,
+                          const float *t_depth, const float *sil, const float *sem, const float *t_sem, float *d_rgb,
+                          float *d_depth, float *d_sem, float *loss, double *partial, gs_stream_t stream) {
+  if (npix < 1 || !loss || !partial || !rgb || !t_rgb || !depth || !t_depth || !sil) return GS_ERR_ARG;
+  if (sem && (!t_sem || m < 1 || k < 1 || k > kMaxK)) return GS_ERR_ARG;
+  GS_CHECK_CUDA(launch_mapping_loss(npix, m, k, rgb, t_rgb, depth, t_depth, sil, sem, t_sem, d_rgb, d_depth, d_sem,
+                                    loss, partial, (cudaStream_t)stream));
+  return GS_OK;
+}
+
 gs_status gs_read_counters(void *ws, gs_counters *out, gs_stream_t stream) {
   if (!ws || !out) return GS_ERR_ARG;
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return GS_ERR_CUDA;

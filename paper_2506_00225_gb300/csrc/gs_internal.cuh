@@ -154,6 +154,10 @@ cudaError_t launch_candidates(const Layout &L, const WsPtrs &P, int pbuf, const 
 cudaError_t launch_l1_loss(int64_t npix, int m, const float *rgb, const float *t_rgb, const float *depth,
                            const float *t_depth, const float *sem, const float *t_sem, float *d_rgb, float *d_depth,
                            float *d_sem, float *loss, double *partial, cudaStream_t s);
+cudaError_t launch_mapping_loss(int64_t npix, int m, int k, const float *rgb, const float *t_rgb, const float *depth,
+                                const float *t_depth, const float *sil, const float *sem, const float *t_sem,
+                                float *d_rgb, float *d_depth, float *d_sem, float *loss, double *partial,
+                                cudaStream_t s);
 
 // Which of the two ping-pong buffers holds the sorted data after the passes.
 inline int depth_sort_buffer(const Layout &L) { return radix_passes(L.key_bits_depth) & 1; }

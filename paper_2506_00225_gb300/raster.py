@@ -451,3 +451,50 @@ def l1_loss_and_grads(rgb, depth, sem, t_rgb, t_depth, t_sem):
                                 _ptr(t_sem), _ptr(d_rgb), _ptr(d_depth), _ptr(d_sem), _ptr(loss), _ptr(part),
                                 _stream()), "gs_l1_loss")
     return loss, d_rgb, d_depth, d_sem
+
+
+_PARTIAL_ML = {}
+
+
+def mapping_loss_and_grads(rgb, depth, sil, sem, t_rgb, t_depth, t_sem, k: int):
+    """The mapping objective of Sec. 3.1 on rendered maps (silhouette-masked
+    depth / colour L1, summed; entropy-masked Hellinger + cosine semantic
+    term, averaged) and its gradients with respect to rgb, depth and sem, in
+    one native pass.  Returns (loss[()], d_rgb, d_depth, d_sem)."""
+    dev = rgb.device
+    npix = int(depth.numel())
+    m = int(sem.shape[-1]) if sem is not None else 0
+    part = _PARTIAL_ML.get(dev)
+    if part is None:
+        part = _PARTIAL_ML[dev] = torch.empty(N.GS_MAPPING_LOSS_PARTIALS, dtype=torch.float64, device=dev)
+    loss = torch.empty((), dtype=torch.float32, device=dev)
+    d_rgb = torch.empty_like(rgb)
+    d_depth = torch.empty_like(depth)
+    d_sem = torch.empty_like(sem) if sem is not None else None
+    c = lambda t: None if t is None else t.contiguous()
+    N.check(N.load().gs_mapping_loss(npix, m, int(k), _ptr(c(rgb)), _ptr(c(t_rgb)), _ptr(c(depth)), _ptr(c(t_depth)),
+                                     _ptr(c(sil)), _ptr(c(sem)), _ptr(c(t_sem)), _ptr(d_rgb), _ptr(d_depth),
+                                     _ptr(d_sem), _ptr(loss), _ptr(part), _stream()), "gs_mapping_loss")
+    return loss, d_rgb, d_depth, d_sem
+
+
+class _MappingLossFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, k, t_rgb, t_depth, t_sem, rgb, depth, sil, sem):
+        loss, d_rgb, d_depth, d_sem = mapping_loss_and_grads(rgb.detach(), depth.detach(), sil.detach(),
+                                                             None if sem is None else sem.detach(), t_rgb, t_depth,
+                                                             t_sem, k)
+        ctx.save_for_backward(d_rgb, d_depth, d_sem if d_sem is not None else torch.zeros(0, device=rgb.device))
+        ctx.has_sem = d_sem is not None
+        return loss
+
+    @staticmethod
+    def backward(ctx, gl):
+        d_rgb, d_depth, d_sem = ctx.saved_tensors
+        return (None, None, None, None, d_rgb * gl, d_depth * gl, None, d_sem * gl if ctx.has_sem else None)
+
+
+def mapping_loss(rgb, depth, sil, sem, t_rgb, t_depth, t_sem, k: int):
+    """Differentiable mapping objective of Sec. 3.1 on rendered maps (e.g. the
+    outputs of ``rasterize``): its backward feeds the rasterizer's adjoint."""
+    return _MappingLossFn.apply(int(k), t_rgb, t_depth, t_sem, rgb, depth, sil, sem)
