@@ -272,6 +272,37 @@ gs_status gs_mapping_loss(int64_t npix, int m, int k, const float *rgb, const fl
                           const float *t_depth, const float *sil, const float *sem, const float *t_sem, float *d_rgb,
                           float *d_depth, float *d_sem, float *loss, double *partial, gs_stream_t stream);
 
+/* Forward render of one view fused with the Sec. 3.1 mapping objective of
+ * gs_mapping_loss (the silhouette-masked depth / colour L1 sum plus the mean
+ * entropy-masked Hellinger + cosine semantic term, Eq. 4, Eq. 5), evaluated
+ * inside the tile kernels: the semantic map and its gradient are never
+ * written.  Targets in the output layouts of gs_render_fwd; t_sem may be NULL
+ * to drop the semantic term.  Outputs rgb, depth, sil are optional (NULL to
+ * skip); *loss is a device float.  The workspace keeps, per pixel, the signs
+ * of the masked depth / colour errors, and per (Gaussian, entry) the
+ * semantic term's gradient with respect to sem_w, for gs_render_bwd_objective.
+ * Same preconditions as gs_render_fwd, and in addition:
+ *   - cfg->sem_detach_geometry = 1 (the semantic term reaches the semantic
+ *     weights only, Sec. 3.1), and the contributor bits are kept
+ *     (recompute_bwd = 0);
+ *   - the per-pixel class accumulator of a tile fits shared memory in one
+ *     chunk (m up to 104 classes at 16x16 tiles with k = 3) and k <= 16.
+ * Otherwise returns GS_ERR_UNSUPPORTED before any GPU work: render with
+ * gs_render_fwd and evaluate gs_mapping_loss on the maps instead. */
+gs_status gs_render_fwd_objective(const gs_scene *scene, const gs_camera *cam, const gs_config *cfg, void *ws,
+                                  const float *t_rgb, const float *t_depth, const float *t_sem, float *rgb,
+                                  float *depth, float *sil, float *loss, gs_stream_t stream);
+
+/* Adjoint of gs_render_fwd_objective: accumulates (+=) the gradients of
+ * (*loss_scale) * loss into g_* (layouts of gs_render_bwd), equal to
+ * gs_render_bwd with the upstream gradients gs_mapping_loss writes.
+ * loss_scale is a DEVICE float read on the stream.  Must follow the
+ * gs_render_fwd_objective it differentiates, with the same workspace and
+ * configuration. */
+gs_status gs_render_bwd_objective(const gs_scene *scene, const gs_camera *cam, const gs_config *cfg, void *ws,
+                                  const float *loss_scale, float *g_means, float *g_scales, float *g_quats,
+                                  float *g_opacity, float *g_rgb, float *g_sem_w, gs_stream_t stream);
+
 /* Bytes of the fixed device scratch array used by gs_render_fwd_noalloc. */
 #define GS_NOALLOC_SCRATCH_BYTES (32u << 20)
 

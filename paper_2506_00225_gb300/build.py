@@ -30,6 +30,7 @@ SOURCES = {
     "candidates.cu": [],
     "loss.cu": [],
     "mapping_loss.cu": [],
+    "render_objective.cu": [],
     "api.cu": [],
     "noalloc.cu": [],
 }

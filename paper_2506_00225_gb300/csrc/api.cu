@@ -108,6 +108,7 @@ bool make_layout(const gs_scene *scene, const gs_camera *cams, int n_views, cons
   L->nwc = (scene->m + 31) / 32;
   L->off_codes = take(n_views == 1 ? 4 * (size_t)L->npix * (2 * (1 + L->nwc)) : 32);
   L->off_lpart = take(n_views == 1 ? 3 * sizeof(double) * (size_t)(tiles > 0 ? tiles : 1) : 32);
+  L->off_semg = take(n_views == 1 ? 4 * (size_t)scene->n * scene->k : 32);
   // one unit = one staged batch of one tile: 2 words per tile pixel
   // (none with recompute_bwd: pass 2 and the adjoint re-test the pairs;
   // candidate views keep them only while they fit kCandMaskBudget, else the
@@ -161,6 +162,7 @@ WsPtrs ws_ptrs(const Layout &L, void *ws) {
   P.grad2d = reinterpret_cast<float4 *>(b + L.off_grad2d);
   P.codes = reinterpret_cast<uint32_t *>(b + L.off_codes);
   P.lpart = reinterpret_cast<double *>(b + L.off_lpart);
+  P.semg = reinterpret_cast<float *>(b + L.off_semg);
   P.mask_off = reinterpret_cast<uint32_t *>(b + L.off_mask_off);
   P.masks = reinterpret_cast<uint32_t *>(b + L.off_masks);
   P.clast = reinterpret_cast<uint32_t *>(b + L.off_clast);
@@ -330,6 +332,49 @@ gs_status gs_render_bwd_l1(const gs_scene *scene, const gs_camera *cam, const gs
   cudaStream_t s = (cudaStream_t)stream;
   GS_CHECK_CUDA(launch_render_bwd(L, P, pair_sort_buffer(L), *scene, nullptr, nullptr, nullptr, nullptr,
                                   c.sem_detach_geometry ? 1 : 0, g_rgb, g_sem_w, s, loss_scale));
+  GS_CHECK_CUDA(launch_project_bwd(L, P, *scene, g_means, g_scales, g_quats, g_opacity, s));
+  return GS_OK;
+}
+
+// Preconditions of the fused Sec. 3.1 objective beyond gs_render_fwd's.
+static gs_status objective_supported(const Layout &L, const gs_scene *scene, const gs_config &c) {
+  if (!c.sem_detach_geometry || !objective_fits(L, scene->k, scene->m)) return GS_ERR_UNSUPPORTED;
+  return GS_OK;
+}
+
+gs_status gs_render_fwd_objective(const gs_scene *scene, const gs_camera *cam, const gs_config *cfg, void *ws,
+                                  const float *t_rgb, const float *t_depth, const float *t_sem, float *rgb,
+                                  float *depth, float *sil, float *loss, gs_stream_t stream) {
+  Layout L;
+  if (!ws || !aligned(ws, 256) || !make_layout(scene, cam, 1, cfg, &L)) return GS_ERR_ARG;
+  if (!scene_ptrs_ok(scene, true) || (scene->n > 0 && !scene->rgb)) return GS_ERR_ARG;
+  if (!t_rgb || !t_depth || !loss) return GS_ERR_ARG;
+  if (!shape_compiled(L.tile_w, L.tile_h)) return GS_ERR_UNSUPPORTED;
+  const gs_config c = cfg ? *cfg : default_config();
+  const gs_status st = objective_supported(L, scene, c);
+  if (st != GS_OK) return st;
+  WsPtrs P = ws_ptrs(L, ws);
+  GS_CHECK_CUDA(launch_render_fwd_objective(L, P, pair_sort_buffer(L), *scene, t_rgb, t_depth, t_sem, rgb, depth,
+                                            sil, loss, (cudaStream_t)stream));
+  return GS_OK;
+}
+
+gs_status gs_render_bwd_objective(const gs_scene *scene, const gs_camera *cam, const gs_config *cfg, void *ws,
+                                  const float *loss_scale, float *g_means, float *g_scales, float *g_quats,
+                                  float *g_opacity, float *g_rgb, float *g_sem_w, gs_stream_t stream) {
+  Layout L;
+  if (!ws || !aligned(ws, 256) || !make_layout(scene, cam, 1, cfg, &L)) return GS_ERR_ARG;
+  if (!scene_ptrs_ok(scene, true) || (scene->n > 0 && !scene->rgb) || !loss_scale) return GS_ERR_ARG;
+  if (scene->n > 0 && (!g_means || !g_scales || !g_quats || !g_opacity || !g_rgb || !g_sem_w)) return GS_ERR_ARG;
+  if (!shape_compiled(L.tile_w, L.tile_h)) return GS_ERR_UNSUPPORTED;
+  const gs_config c = cfg ? *cfg : default_config();
+  const gs_status st = objective_supported(L, scene, c);
+  if (st != GS_OK) return st;
+  WsPtrs P = ws_ptrs(L, ws);
+  cudaStream_t s = (cudaStream_t)stream;
+  GS_CHECK_CUDA(launch_render_bwd(L, P, pair_sort_buffer(L), *scene, nullptr, nullptr, nullptr, nullptr, 1, g_rgb,
+                                  g_sem_w, s, loss_scale, 1));
+  GS_CHECK_CUDA(launch_add_semg(P, *scene, loss_scale, g_sem_w, s));
   GS_CHECK_CUDA(launch_project_bwd(L, P, *scene, g_means, g_scales, g_quats, g_opacity, s));
   return GS_OK;
 }

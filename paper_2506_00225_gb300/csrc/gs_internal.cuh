@@ -72,6 +72,7 @@ struct Layout {
   size_t off_grad2d;
   int nwc;                                 // 32-class sign words per plane (fused L1 mode)
   size_t off_codes, off_lpart;
+  size_t off_semg;                         // mapping view: [n][k] objective gradient of sem_w (unscaled)
   size_t off_mask_off, off_masks;          // contributor bitmasks (mapping view; candidate views when they fit)
   size_t off_clast;                        // candidate views: last contributor per (tile, pixel)
   int64_t mask_units;                      // capacity in (tile, batch) units
@@ -112,6 +113,7 @@ struct WsPtrs {
   uint32_t *masks;     // [unit][2][tile pixels] contributor bits of each staged batch
   uint32_t *clast;     // [tiles][tile pixels] last contributor (candidate views)
   double *lpart;   // [tiles of view 0][3] per-tile L1 sums
+  float *semg;     // [n][k] d(semantic term)/d(sem_w) of the fused Sec. 3.1 objective, before dL/dloss
 };
 
 // Host side (api.cu).
@@ -143,10 +145,22 @@ cudaError_t launch_render_fwd(const Layout &L, const WsPtrs &P, int pbuf, const 
 cudaError_t launch_render_fwd_l1(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc,
                                  const float *t_rgb, const float *t_depth, const float *t_sem, float *rgb,
                                  float *depth, float *sil, float *sem, float *loss, cudaStream_t s);
-// loss_scale != nullptr selects the fused-L1 adjoint (upstream from sign codes)
+// loss_scale != nullptr selects the fused-loss adjoint (upstream from sign
+// codes); objective = 1 takes the Sec. 3.1 objective's scales and no class codes
 cudaError_t launch_render_bwd(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc, const float *d_rgb,
                               const float *d_depth, const float *d_sil, const float *d_sem, int sem_detach,
-                              float *g_rgb, float *g_sem_w, cudaStream_t s, const float *loss_scale = nullptr);
+                              float *g_rgb, float *g_sem_w, cudaStream_t s, const float *loss_scale = nullptr,
+                              int objective = 0);
+// Fused Sec. 3.1 objective (render_paper.cu): whether the mapping view's
+// class accumulator fits one shared-memory chunk; the forward (blend with the
+// silhouette-masked geometry, semantic term and its sem_w gradient); the
+// adjoint's g_sem_w += dL/dloss * semg.
+bool objective_fits(const Layout &L, int k, int m);
+cudaError_t launch_render_fwd_objective(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc,
+                                        const float *t_rgb, const float *t_depth, const float *t_sem, float *rgb,
+                                        float *depth, float *sil, float *loss, cudaStream_t s);
+cudaError_t launch_add_semg(const WsPtrs &P, const gs_scene &sc, const float *loss_scale, float *g_sem_w,
+                            cudaStream_t s);
 cudaError_t launch_project_bwd(const Layout &L, const WsPtrs &P, const gs_scene &sc, float *g_means,
                                float *g_scales, float *g_quats, float *g_opacity, cudaStream_t s);
 cudaError_t launch_candidates(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc, double *out,

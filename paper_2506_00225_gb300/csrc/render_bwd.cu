@@ -37,6 +37,7 @@ struct BwdArgs {
   const uint32_t *codes;
   int nwc;
   const float *loss_scale;  // device dL/dloss
+  int objective;            // Sec. 3.1 objective: 0.5 / 1 weights of colour / depth sums, no class codes
   double npix;
   const uint32_t *mask_off;  // contributor bitmasks of the forward pass
   const uint32_t *masks;
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
   const int k = a.k;
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   // warp-uniform: every lane takes the same branches around the shuffles
-  const bool has_dsem = CODES || a.d_sem != nullptr;
+  const bool has_dsem = (CODES && !a.objective) || a.d_sem != nullptr;
   float s_sem = 0.f;
 
   int py[PPT];
@@ -99,7 +100,8 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
       nl[i] = a.nlast[pix];
       if (CODES) {
         const float ls = *a.loss_scale;
-        const float s_rgb = (float)(ls / (3.0 * a.npix)), s_d = (float)(ls / a.npix);
+        const float s_rgb = a.objective ? 0.5f * ls : (float)(ls / (3.0 * a.npix));
+        const float s_d = a.objective ? ls : (float)(ls / a.npix);
         s_sem = (float)(ls / (a.npix * a.m));
         const uint2 *cp = reinterpret_cast<const uint2 *>(a.codes + pix * code_words(a.nwc));
         const uint32_t nz = cp[0].x, ng = cp[0].y;
@@ -314,7 +316,8 @@ static cudaError_t dispatch_bwd(const Layout &L, const BwdArgs &a, int grid, siz
 
 cudaError_t launch_render_bwd(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc, const float *d_rgb,
                               const float *d_depth, const float *d_sil, const float *d_sem, int sem_detach,
-                              float *g_rgb, float *g_sem_w, cudaStream_t s, const float *loss_scale) {
+                              float *g_rgb, float *g_sem_w, cudaStream_t s, const float *loss_scale,
+                              int objective) {
   k_zero_grad2d<<<2 * 152, 256, 0, s>>>(P.grad2d, P.counters, (uint32_t)L.rcap);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -338,10 +341,11 @@ cudaError_t launch_render_bwd(const Layout &L, const WsPtrs &P, int pbuf, const 
   if (grid == 0) return cudaSuccess;
   if (loss_scale) {
     a.codes = P.codes;
-    a.nwc = L.nwc;
+    a.nwc = objective ? 0 : L.nwc;
     a.loss_scale = loss_scale;
     a.npix = (double)L.npix;
-    const size_t smem = batch_smem_bytes(sc.k) + (size_t)L.tile_w * L.tile_h * (L.nwc | 1) * 8;
+    a.objective = objective;
+    const size_t smem = batch_smem_bytes(sc.k) + (size_t)L.tile_w * L.tile_h * (a.nwc | 1) * 8;
     return dispatch_bwd<true>(L, a, grid, smem, s);
   }
   const size_t smem = batch_smem_bytes(sc.k);

@@ -12,6 +12,7 @@ constexpr int kBatch = 64;                       // Gaussians staged per batch
 constexpr float kTStop = 0.0001f;                // transmittance stop
 constexpr float kAlphaMin = 1.0f / 255.0f;       // skip threshold
 constexpr float kAlphaMax = 0.99f;               // opacity cap
+constexpr float kSilMinLoss = 0.99f;             // silhouette threshold of the Sec. 3.1 objective
 constexpr size_t kSmemBudget = 112 * 1024;       // per CTA: two 256-thread CTAs per SM
 
 // Each warp owns an 8 x (4 PPT) pixel block of the tile; lane l sits at
@@ -283,6 +284,8 @@ struct FwdArgs {
   float *tfinal;
   uint32_t *nlast;
   int mchunk, mstride, nchunks;
+  int objective;     // 1: Sec. 3.1 objective (silhouette-masked geometry; semantic term by k_sem_objective)
+  float *semg;       // objective mode: d(objective)/d(sem_w) [n][k], accumulated by the semantic pass
   // fused mean-L1 mode
   const float *t_rgb, *t_depth, *t_sem;
   uint32_t *codes;   // per pixel: (nonzero, negative) word pairs: head (rgb, depth bits), then nwc class words
@@ -297,5 +300,12 @@ struct FwdArgs {
 
 // Per-pixel sign-code layout of the fused L1 mode.
 __host__ __device__ inline int code_words(int nwc) { return 2 * (1 + nwc); }
+
+// Host side (render_fwd.cu): the blend arguments of the mapping view, the
+// blend pass alone in its fused-loss form, and the per-tile loss reduction.
+FwdArgs fwd_args(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc);
+cudaError_t launch_blend_objective(const Layout &L, const FwdArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_loss_final(const double *lpart, int ntiles, double npix, double m, int has_sem, int objective,
+                              float *loss, cudaStream_t s);
 
 }  // namespace gs

@@ -134,14 +134,19 @@ __global__ void __launch_bounds__(TW *TH) k_blend(FwdArgs a) {
       const int cw = code_words(a.nwc);
       const float d0 = cr - a.t_rgb[3 * pix], d1 = cg - a.t_rgb[3 * pix + 1], d2 = cb - a.t_rgb[3 * pix + 2];
       const float d3 = cd - a.t_depth[pix];
-      const uint32_t nz = (d0 != 0.f ? 1u : 0u) | (d1 != 0.f ? 2u : 0u) | (d2 != 0.f ? 4u : 0u) | (d3 != 0.f ? 8u : 0u);
+      // Sec. 3.1 objective mode: only pixels with S > 0.99 count
+      const bool keep = !a.objective || 1.f - T > kSilMinLoss;
+      const uint32_t nz = keep ? ((d0 != 0.f ? 1u : 0u) | (d1 != 0.f ? 2u : 0u) | (d2 != 0.f ? 4u : 0u) |
+                                  (d3 != 0.f ? 8u : 0u)) : 0u;
       const uint32_t ng = (d0 < 0.f ? 1u : 0u) | (d1 < 0.f ? 2u : 0u) | (d2 < 0.f ? 4u : 0u) | (d3 < 0.f ? 8u : 0u);
       uint2 *cp = reinterpret_cast<uint2 *>(a.codes + pix * cw);
       cp[0] = make_uint2(nz, ng);
       if (!a.t_sem)
         for (int wd = 0; wd < a.nwc; ++wd) cp[1 + wd] = make_uint2(0u, 0u);
-      l1_rgb = fabsf(d0) + fabsf(d1) + fabsf(d2);
-      l1_d = fabsf(d3);
+      if (keep) {
+        l1_rgb = fabsf(d0) + fabsf(d1) + fabsf(d2);
+        l1_d = fabsf(d3);
+      }
     }
   }
   if (L1) {
@@ -412,7 +417,11 @@ __global__ void __launch_bounds__(TW *TH, 2) k_semantic(FwdArgs a) {
 }
 
 // loss = sum|d rgb| / (3 npix) + sum|d depth| / npix + sum|d sem| / (npix m)
-__global__ void k_l1_tiles_final(const double *lpart, int ntiles, double npix, double m, int has_sem, float *loss) {
+// Mean-L1 mode: rgb / (3 npix) + depth / npix + sem / (npix m).  Sec. 3.1
+// objective mode (objective != 0): 0.5 rgb + depth (sums over the silhouette
+// mask) + sem / npix (mean of the per-pixel semantic terms).
+__global__ void k_l1_tiles_final(const double *lpart, int ntiles, double npix, double m, int has_sem, int objective,
+                                 float *loss) {
   __shared__ double red[3][32];
   double s[3] = {0.0, 0.0, 0.0};
   for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
@@ -427,8 +436,14 @@ __global__ void k_l1_tiles_final(const double *lpart, int ntiles, double npix, d
     double t[3] = {0.0, 0.0, 0.0};
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
       for (int i = 0; i < 3; ++i) t[i] += red[i][w];
-    double l = t[0] / (3.0 * npix) + t[1] / npix;
-    if (has_sem) l += t[2] / (npix * m);
+    double l;
+    if (objective) {
+      l = 0.5 * t[0] + t[1];
+      if (has_sem) l += t[2] / npix;
+    } else {
+      l = t[0] / (3.0 * npix) + t[1] / npix;
+      if (has_sem) l += t[2] / (npix * m);
+    }
     *loss = (float)l;
   }
 }
@@ -467,7 +482,7 @@ static cudaError_t dispatch_fwd(const Layout &L, const FwdArgs &a, int grid, siz
   return cudaErrorInvalidConfiguration;
 }
 
-static FwdArgs fwd_args(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc) {
+FwdArgs fwd_args(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc) {
   FwdArgs a{};
   a.ranges = P.ranges;
   a.pvals = P.pvals[pbuf];
@@ -532,7 +547,16 @@ cudaError_t launch_render_fwd_l1(const Layout &L, const WsPtrs &P, int pbuf, con
   if (e != cudaSuccess) return e;
   e = dispatch_fwd<true>(L, a, grid, smem, acc, s);
   if (e != cudaSuccess) return e;
-  k_l1_tiles_final<<<1, 1024, 0, s>>>(P.lpart, grid, (double)L.npix, (double)sc.m, t_sem ? 1 : 0, loss);
+  return launch_loss_final(P.lpart, grid, (double)L.npix, (double)sc.m, t_sem ? 1 : 0, 0, loss, s);
+}
+
+cudaError_t launch_blend_objective(const Layout &L, const FwdArgs &a, int grid, cudaStream_t s) {
+  return dispatch_fwd<true>(L, a, grid, 0, false, s);
+}
+
+cudaError_t launch_loss_final(const double *lpart, int ntiles, double npix, double m, int has_sem, int objective,
+                              float *loss, cudaStream_t s) {
+  k_l1_tiles_final<<<1, 1024, 0, s>>>(lpart, ntiles, npix, m, has_sem, objective, loss);
   return cudaGetLastError();
 }
 

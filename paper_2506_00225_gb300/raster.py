@@ -275,6 +275,54 @@ class Rasterizer:
         self._mark("bwd_end")
         return grads
 
+    def forward_objective(self, g: Gaussians, cam, t_rgb, t_depth, t_sem=None, check=True, outputs=False):
+        """Project, bin, render and evaluate the Sec. 3.1 mapping objective
+        (silhouette-masked depth / colour L1 sum + mean entropy-masked
+        Hellinger + cosine semantic term) inside the render passes.  Returns
+        the loss (0-dim device tensor) and, when ``outputs``, (rgb, depth,
+        sil) as well.  Raises GsError(GS_ERR_UNSUPPORTED) when the
+        configuration has no fused form (semantics not detached from the
+        geometry, the recompute mode, or too many classes for one tile
+        accumulator)."""
+        self._mark("project")
+        sc, cams_arr, cfg, ws = self._project_bin(g, [cam], check)
+        self._mark("render_fwd")
+        H, W = cam.height, cam.width
+        dev = self.device
+        loss = torch.empty((), dtype=torch.float32, device=dev)
+        outs = (None, None, None)
+        if outputs:
+            outs = (torch.empty((H, W, 3), dtype=torch.float32, device=dev),
+                    torch.empty((H, W), dtype=torch.float32, device=dev),
+                    torch.empty((H, W), dtype=torch.float32, device=dev))
+        N.check(N.load().gs_render_fwd_objective(ctypes.byref(sc), cams_arr, ctypes.byref(cfg), ws,
+                                                 _ptr(_f32(t_rgb)), _ptr(_f32(t_depth)), _ptr(_f32(t_sem)),
+                                                 *[_ptr(o) for o in outs], _ptr(loss), _stream()),
+                "gs_render_fwd_objective")
+        self._mark("fwd_end")
+        self.generation += 1
+        return (loss, outs) if outputs else loss
+
+    def backward_objective(self, g: Gaussians, cam, loss_scale: torch.Tensor, grads=None):
+        """Adjoint of the last forward_objective, scaled by the device scalar
+        ``loss_scale`` (dL/dloss)."""
+        if self._last is None:
+            raise RuntimeError("backward before forward")
+        sc, cams_arr, V, cfg = self._last
+        if grads is None:
+            grads = dict(means=torch.zeros_like(g.means), scales=torch.zeros_like(g.scales),
+                         quats=torch.zeros_like(g.quats), opacity=torch.zeros_like(g.opacity),
+                         rgb=torch.zeros_like(g.rgb), sem_w=torch.zeros_like(g.sem_w))
+        ws = ctypes.c_void_p(self.ws.data_ptr())
+        ls = loss_scale.to(torch.float32).contiguous()
+        self._mark("render_bwd")
+        N.check(N.load().gs_render_bwd_objective(ctypes.byref(sc), cams_arr, ctypes.byref(cfg), ws, _ptr(ls),
+                                                 _ptr(grads["means"]), _ptr(grads["scales"]), _ptr(grads["quats"]),
+                                                 _ptr(grads["opacity"]), _ptr(grads["rgb"]), _ptr(grads["sem_w"]),
+                                                 _stream()), "gs_render_bwd_objective")
+        self._mark("bwd_end")
+        return grads
+
     # -- candidates -----------------------------------------------------------
     def candidates(self, g: Gaussians, cams, check=True, out=None) -> torch.Tensor:
         """Per-view (sum U, sum H, N_S) for candidate poses: float64 [V,3]."""
@@ -425,6 +473,51 @@ def render_l1(rast: Rasterizer, g: Gaussians, cam, t_rgb, t_depth, t_sem=None, m
     sem_w = g.sem_w if sem_w is None else sem_w
     return _RenderL1Fn.apply(rast, cam, g.sem_ids, g.m, check, t_rgb, t_depth, t_sem, means, scales, quats, opacity,
                              rgb, sem_w)
+
+
+class _RenderObjectiveFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, rast, cam, sem_ids, m, check, t_rgb, t_depth, t_sem, means, scales, quats, opacity, rgb,
+                sem_w):
+        g = Gaussians(means.detach(), scales.detach(), quats.detach(), opacity.detach(), rgb.detach(), sem_ids,
+                      sem_w.detach(), m)
+        loss = rast.forward_objective(g, cam, t_rgb, t_depth, t_sem, check=check)
+        ctx.rast, ctx.cam, ctx.gen, ctx.g = rast, cam, rast.generation, g
+        return loss
+
+    @staticmethod
+    def backward(ctx, gl):
+        rast = ctx.rast
+        if rast.generation != ctx.gen:
+            raise RuntimeError("the rasterizer's workspace was reused by another forward before this backward")
+        grads = rast.backward_objective(ctx.g, ctx.cam, gl)
+        return (None, None, None, None, None, None, None, None, grads["means"], grads["scales"], grads["quats"],
+                grads["opacity"], grads["rgb"], grads["sem_w"])
+
+
+def render_objective(rast: Rasterizer, g: Gaussians, cam, t_rgb, t_depth, t_sem=None, means=None, scales=None,
+                     quats=None, opacity=None, rgb=None, sem_w=None, check=True, fused=None):
+    """Differentiable render + Sec. 3.1 mapping objective against targets
+    (colour [H,W,3], depth [H,W], class distribution [H,W,m] or None).
+    Returns the scalar loss.  ``fused=None`` takes the fused kernels where the
+    configuration allows and otherwise renders the maps and evaluates
+    ``mapping_loss`` on them (both on the GPU); True / False force one."""
+    means = g.means if means is None else means
+    scales = g.scales if scales is None else scales
+    quats = g.quats if quats is None else quats
+    opacity = g.opacity if opacity is None else opacity
+    rgb = g.rgb if rgb is None else rgb
+    sem_w = g.sem_w if sem_w is None else sem_w
+    if fused is not False:
+        try:
+            return _RenderObjectiveFn.apply(rast, cam, g.sem_ids, g.m, check, t_rgb, t_depth, t_sem, means, scales,
+                                            quats, opacity, rgb, sem_w)
+        except N.GsError as e:
+            if fused or e.code != N.GS_ERR_UNSUPPORTED:
+                raise
+    out = rasterize(rast, g, cam, means, scales, quats, opacity, rgb, sem_w, want_sem=t_sem is not None,
+                    check=check)
+    return mapping_loss(out[0], out[1], out[2], out[3], t_rgb, t_depth, t_sem, g.k)
 
 
 # ---------------------------------------------------------------------------

@@ -150,3 +150,32 @@ def test_product_has_no_oracle_dependency():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "gs_oracle" not in txt, f
+
+
+@pytest.mark.parametrize("case", ["attached", "recompute", "m256k8", "ok_n0"])
+def test_objective_preconditions_on_host(lib, case):
+    """gs_render_fwd_objective / gs_render_bwd_objective refuse, before any GPU
+    work, the configurations without a fused form: semantics reaching the
+    geometry, the recompute mode (no contributor bits), a class accumulator
+    that does not fit one shared-memory chunk (256 classes, top-8, 16x16)."""
+    sc, cams, cfg = _structs(n=0)
+    if case == "attached":
+        cfg.sem_detach_geometry = 0
+    elif case == "recompute":
+        cfg.recompute_bwd = 1
+    elif case == "m256k8":
+        sc.m, sc.k = 256, 8
+    fake = ctypes.c_void_p(1 << 40)  # never dereferenced: every call below returns before GPU work
+    t = ctypes.c_void_p(1 << 41)
+    if case == "ok_n0":
+        # accepted configuration: a missing target is the only error left
+        assert lib.gs_render_fwd_objective(ctypes.byref(sc), cams, ctypes.byref(cfg), fake, None, t, t, None, None,
+                                           None, t, None) == N.GS_ERR_ARG
+        assert lib.gs_render_bwd_objective(ctypes.byref(sc), cams, ctypes.byref(cfg), fake, None, None, None, None,
+                                           None, None, None, None) == N.GS_ERR_ARG
+        return
+    fwd = lib.gs_render_fwd_objective(ctypes.byref(sc), cams, ctypes.byref(cfg), fake, t, t, t, None, None, None,
+                                      t, None)
+    bwd = lib.gs_render_bwd_objective(ctypes.byref(sc), cams, ctypes.byref(cfg), fake, t, None, None, None, None,
+                                      None, None, None)
+    assert fwd == N.GS_ERR_UNSUPPORTED and bwd == N.GS_ERR_UNSUPPORTED
