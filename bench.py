@@ -11,6 +11,11 @@ GPUs (replicas).  The same step with the semantic map materialised, a
 separate L1 kernel and the map-sized gradient (``raster.rasterize``) is timed
 too and reported under ``unfused_step``.
 
+Key ``objective_step``: the same frame with the Sec. 3.1 objective
+(silhouette-masked depth / colour L1, entropy-masked Hellinger + cosine
+semantic term; sharpened target distributions), fused into the render
+passes and through the rendered maps.
+
 Also measured in the same run (key ``candidates``): batched candidate-view
 rendering of 96 poses of mixed resolution (views/s), and the same views
 issued as one plain launch chain per view.  Key ``large_scene``: the mapping
@@ -55,7 +60,7 @@ def parse():
     ap.add_argument("--cand-tile", default="16x16", help="WxH tile of the candidate kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 2M-Gaussian mapping and mixed-stream runs")
-    ap.add_argument("--only", choices=["candidates", "large"], default=None,
+    ap.add_argument("--only", choices=["candidates", "large", "objective"], default=None,
                     help="run only that part and print its dict (for profiling; not the benchmark line)")
     ap.add_argument("--tile", default=None, help="WxH: fixed tile shape instead of the autotuner's")
     ap.add_argument("--ppt", type=int, default=2, help="pixels per thread of the adjoint with --tile")
@@ -259,6 +264,20 @@ def main():
     build.build()
     if args.only is not None:
         flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+        if args.only == "objective":
+            wl = scenes.workload(args.workload)
+            sc, cam = wl["scene"], wl["cams"][0]
+            g = raster.Gaussians.from_scene(sc, dev)
+            with torch.no_grad():
+                t_rgb, t_depth, _, t_sem = raster.Rasterizer(device=dev).forward(
+                    raster.Gaussians.from_scene(wl["target"], dev), cam, check=True)
+            tw_, th_ = (int(x) for x in (args.tile or "16x16").lower().split("x"))
+            rast = raster.Rasterizer(tile=(tw_, th_), px_per_thread=args.ppt, device=dev)
+            rast.forward(g, cam, check=True)
+            params = [t.clone().requires_grad_(True) for t in (g.means, g.scales, g.quats, g.opacity, g.rgb, g.sem_w)]
+            print(json.dumps(bench_objective(args, rast, g, cam, params, t_rgb, t_depth, t_sem, flush, world, dev,
+                                             args.steps)))
+            return 0
         if args.only == "candidates":
             print(json.dumps(bench_candidates(args, dev, flush)))
         else:
@@ -308,21 +327,7 @@ def main():
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
 
     def phase_times(step, steps):
-        """Eager steps; a device-side sleep before each step lets the host
-        enqueue the whole step first, so the phase events bracket GPU work
-        only.  Returns mean per-phase device times (ms)."""
-        ph = {}
-        for _ in range(steps):
-            flush.zero_()
-            torch.cuda._sleep(4_000_000)
-            rast.phase_events = []
-            step(t_rgb, t_depth, t_sem)
-            evs = rast.phase_events
-            rast.phase_events = None
-            torch.cuda.synchronize()
-            for (n0, e0), (_, e1) in zip(evs[:-1], evs[1:]):
-                ph.setdefault(n0, []).append(e0.elapsed_time(e1))
-        return {k_: statistics.mean(v) for k_, v in ph.items()}
+        return phase_times_of(rast, lambda: step(t_rgb, t_depth, t_sem), steps, flush)
 
     def capture(step):
         return capture_graph(lambda: step(t_rgb, t_depth, t_sem))
@@ -361,6 +366,9 @@ def main():
     # the map-sized gradient read back by the adjoint
     un_ms = timed_graph(g_unfused, min(50, max(3, args.steps // 2)))
     un_total = max_over_ranks(sum(un_ms), world, dev) / len(un_ms)
+
+    objective = bench_objective(args, rast, g, cam, params, t_rgb, t_depth, t_sem, flush, world, dev,
+                                min(50, max(3, args.steps // 2)))
 
     # ---- roofline ---------------------------------------------------------------
     peaks = {}
@@ -491,6 +499,7 @@ def main():
                                  "phases_ms": {k_: round(v, 4) for k_, v in un_ph.items()},
                                  "what": "rasterize (writes the HxWxM map) + separate L1 kernel + adjoint reading "
                                          "the HxWxM gradient"},
+                "objective_step": objective,
                 "candidates": cand,
                 "large_scene": large,
                 "mixed_stream": mixed}
@@ -499,6 +508,73 @@ def main():
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def phase_times_of(rast, step, steps, flush):
+    """Eager steps; a device-side sleep before each step lets the host
+    enqueue the whole step first, so the phase events bracket GPU work
+    only.  Returns mean per-phase device times (ms)."""
+    import torch
+    ph = {}
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda._sleep(4_000_000)
+        rast.phase_events = []
+        step()
+        evs = rast.phase_events
+        rast.phase_events = None
+        torch.cuda.synchronize()
+        for (n0, e0), (_, e1) in zip(evs[:-1], evs[1:]):
+            ph.setdefault(n0, []).append(e0.elapsed_time(e1))
+    return {k_: statistics.mean(v) for k_, v in ph.items()}
+
+
+def sharpened(t_sem, gamma=4.0):
+    """Target class distributions sharpened as Q^gamma / sum Q^gamma (pixels
+    without mass stay zero): confident per-pixel labels, most of them under
+    the entropy mask's ln k threshold."""
+    q = t_sem.clamp_min(0.0) ** gamma
+    s_ = q.sum(-1, keepdim=True)
+    return (q / s_.clamp_min(1e-30)).contiguous()
+
+
+def bench_objective(args, rast, g, cam, params, t_rgb, t_depth, t_sem, flush, world, dev, steps):
+    """The Sec. 3.1 objective step (silhouette-masked depth / colour L1 +
+    mean entropy-masked Hellinger / cosine term) on the mapping frame with the
+    sharpened target distribution: fused into the render passes, and through
+    the maps (rasterize writes the HxWxM map, gs_mapping_loss, adjoint
+    reading the HxWxM gradient).  Each step graph-replayed."""
+    import math
+    import torch
+    from paper_2506_00225_gb300 import raster
+    q = sharpened(t_sem)
+    h = -(q * torch.log(q.clamp_min(1e-30))).sum(-1)
+    kept = float((h < math.log(g.k)).double().mean())
+
+    def objective_step(fused):
+        def step():
+            for p in params:
+                p.grad = None
+            loss = raster.render_objective(rast, g, cam, t_rgb, t_depth, q, *params, check=False, fused=fused)
+            loss.backward()
+            return loss
+        return step
+
+    out = {"what": "Sec. 3.1 mapping objective, one graph-replayed fwd+bwd step on the mapping frame; target "
+                   "distributions sharpened (Q^4, renormalised)",
+           "pixels_kept_by_entropy_mask": kept}
+    for name, fused in (("fused", True), ("through_maps", False)):
+        ostep = objective_step(fused)
+        for _ in range(args.warmup):
+            ostep()
+        o_ph = phase_times_of(rast, ostep, min(20, max(3, steps // 3)), flush)
+        o_graph, _ = capture_graph(ostep)
+        o_ms = time_graph(o_graph, steps, flush)
+        o_t = max_over_ranks(sum(o_ms), world, dev) / len(o_ms)
+        out[name] = {"value": world * 1000.0 / o_t, "unit": "iters/s", "ms_per_step": o_t,
+                     "phases_ms": {k_: round(v, 4) for k_, v in o_ph.items()}}
+        del o_graph
+    return out
 
 
 def capture_graph(step):

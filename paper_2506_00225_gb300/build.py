@@ -34,7 +34,7 @@ SOURCES = {
     "api.cu": [],
     "noalloc.cu": [],
 }
-HEADERS = ["gs_internal.cuh", "render_common.cuh"]
+HEADERS = ["gs_internal.cuh", "render_common.cuh", "objective_math.cuh"]
 
 
 def nvcc() -> str:

@@ -12,26 +12,21 @@
 // differentiable at 0; a zero distance or norm gives a zero gradient for its
 // term.
 //
-// One warp per pixel: lanes stride over the classes, warp sums give the
-// pixel's entropy, distance, norms and dot product, then the lanes write the
-// class gradients (coalesced).  Per-CTA partial sums in double, reduced by one
-// CTA: deterministic.
+// A warp takes 4 consecutive pixels at a time: lanes 0-3 their geometry,
+// all lanes their classes (c = lane + 32 i, held in registers up to 128
+// classes, so that the four pixels' loads and warp sums overlap), then the
+// lanes write the class gradients (coalesced).  Per-CTA partial sums in
+// double, reduced by one CTA: deterministic.
 #include "gs_internal.cuh"
+#include "objective_math.cuh"
 
 namespace gs {
 
 constexpr int kMlThreads = 256;
 constexpr int kMlCtas = 4 * 152;
+constexpr int kMlG = 4;  // pixels per warp round
 constexpr float kSilMin = 0.99f;
 constexpr float kWColour = 0.5f;
-constexpr float kLamHd = 0.8f, kLamCos = 0.2f;
-constexpr float kEpsSqrt = 1e-12f, kEpsDiv = 1e-12f;
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 __global__ void __launch_bounds__(kMlThreads) k_mapping_loss(int64_t npix, int m, float log_k, const float *rgb,
                                                              const float *t_rgb, const float *depth,
@@ -43,9 +38,10 @@ __global__ void __launch_bounds__(kMlThreads) k_mapping_loss(int64_t npix, int m
   const int64_t nwarps = ((int64_t)gridDim.x * kMlThreads) >> 5;
   const float inv_n = 1.f / (float)npix;
   double geo = 0.0, semt = 0.0;
-  for (int64_t p = warp0; p < npix; p += nwarps) {
-    // geometry and colour (lane 0)
-    if (lane == 0) {
+  for (int64_t p0 = warp0 * kMlG; p0 < npix; p0 += nwarps * kMlG) {
+    // geometry and colour: lane g < 4 takes pixel p0 + g
+    if (lane < kMlG && p0 + lane < npix) {
+      const int64_t p = p0 + lane;
       const float mg = sil[p] > kSilMin ? 1.f : 0.f;
       const float ed = depth[p] - t_depth[p];
       float l = fabsf(ed);
@@ -58,44 +54,70 @@ __global__ void __launch_bounds__(kMlThreads) k_mapping_loss(int64_t npix, int m
       geo += (double)(mg * l);
     }
     if (!sem) continue;
-    // semantics: warp sums over the classes
-    const float *q = t_sem + p * m, *pr = sem + p * m;
-    float hq = 0.f, s2 = 0.f, qq = 0.f, pp = 0.f, qp = 0.f;
-    for (int c = (int)lane; c < m; c += 32) {
-      const float qv = q[c], pv = pr[c];
-      if (qv > 0.f) hq -= qv * logf(qv);
-      const float d = sqrtf(fmaxf(qv, 0.f) + kEpsSqrt) - sqrtf(fmaxf(pv, 0.f) + kEpsSqrt);
-      s2 = fmaf(d, d, s2);
-      qq = fmaf(qv, qv, qq);
-      pp = fmaf(pv, pv, pp);
-      qp = fmaf(qv, pv, qp);
-    }
-    hq = warp_sum(hq); s2 = warp_sum(s2); qq = warp_sum(qq); pp = warp_sum(pp); qp = warp_sum(qp);
-    const bool keep = hq < log_k;
-    const float dist = sqrtf(0.5f * s2);
-    const float den = sqrtf(qq) * sqrtf(pp);
-    const float cosv = den > kEpsDiv ? qp / den : 0.f;
-    if (lane == 0 && keep) semt += (double)(kLamHd * dist + kLamCos * (1.f - cosv));
-    if (d_sem) {
-      float *g = d_sem + p * m;
-      for (int c = (int)lane; c < m; c += 32) {
-        float gv = 0.f;
-        if (keep) {
-          const float qv = q[c], pv = pr[c];
-          float dhd = 0.f;
-          if (dist > kEpsDiv && pv >= 0.f) {
-            const float sp = sqrtf(pv + kEpsSqrt), sq = sqrtf(fmaxf(qv, 0.f) + kEpsSqrt);
-            dhd = (sp - sq) / (4.f * dist * sp);
-          }
-          float dcos = 0.f;
-          if (den > kEpsDiv) dcos = qv / den - cosv * pv / fmaxf(pp, kEpsDiv);
-          gv = (kLamHd * dhd - kLamCos * dcos) * inv_n;
+    if (m <= 32 * kObjMI) {
+      float qv[kMlG][kObjMI], pv[kMlG][kObjMI], st[kMlG][5];
+      ClassRoots rt[kMlG][kObjMI];
+      bool ok[kMlG];
+#pragma unroll
+      for (int g = 0; g < kMlG; ++g) {
+        ok[g] = p0 + g < npix;
+        const int64_t base = ok[g] ? (p0 + g) * m : 0;
+#pragma unroll
+        for (int i = 0; i < kObjMI; ++i) {
+          const int c = (int)lane + 32 * i;
+          const bool in = ok[g] && c < m;
+          qv[g][i] = in ? t_sem[base + c] : 0.f;
+          pv[g][i] = in ? sem[base + c] : 0.f;
         }
-        g[c] = gv;
+      }
+#pragma unroll
+      for (int g = 0; g < kMlG; ++g) {
+#pragma unroll
+        for (int j = 0; j < 5; ++j) st[g][j] = 0.f;
+#pragma unroll
+        for (int i = 0; i < kObjMI; ++i) rt[g][i] = class_sums(qv[g][i], pv[g][i], st[g]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int g = 0; g < kMlG; ++g)
+#pragma unroll
+          for (int j = 0; j < 5; ++j) st[g][j] += __shfl_xor_sync(0xffffffffu, st[g][j], o);
+#pragma unroll
+      for (int g = 0; g < kMlG; ++g) {
+        const PixelTerm t = pixel_term(st[g], ok[g], log_k);
+        if (lane == 0 && t.keep) semt += (double)t.value;
+        if (d_sem && ok[g]) {
+          float *gr = d_sem + (p0 + g) * m;
+#pragma unroll
+          for (int i = 0; i < kObjMI; ++i) {
+            const int c = (int)lane + 32 * i;
+            if (c < m) gr[c] = t.keep ? class_grad(qv[g][i], pv[g][i], rt[g][i], t, inv_n) : 0.f;
+          }
+        }
+      }
+    } else {
+      for (int g = 0; g < kMlG && p0 + g < npix; ++g) {
+        const int64_t p = p0 + g;
+        const float *q = t_sem + p * m, *pr = sem + p * m;
+        float st[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int c = (int)lane; c < m; c += 32) class_sums(q[c], pr[c], st);
+        warp_sum5(st);
+        const PixelTerm t = pixel_term(st, true, log_k);
+        if (lane == 0 && t.keep) semt += (double)t.value;
+        if (d_sem) {
+          float *gr = d_sem + p * m;
+          for (int c = (int)lane; c < m; c += 32) {
+            gr[c] = t.keep ? class_grad(q[c], pr[c], class_roots(q[c], pr[c]), t, inv_n) : 0.f;
+          }
+        }
       }
     }
   }
   __shared__ double red[2][kMlThreads / 32];
+  // lanes 0-3 hold geometry sums, lane 0 the semantic sum
+#pragma unroll
+  for (int o = 2; o > 0; o >>= 1) geo += __shfl_xor_sync(0xffffffffu, geo, o);
   if (lane == 0) { red[0][threadIdx.x >> 5] = geo; red[1][threadIdx.x >> 5] = semt; }
   __syncthreads();
   if (threadIdx.x == 0) {

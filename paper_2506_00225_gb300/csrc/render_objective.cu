@@ -26,11 +26,9 @@
 // whose accumulator fits one shared-memory chunk.
 #include "gs_internal.cuh"
 #include "render_common.cuh"
+#include "objective_math.cuh"
 
 namespace gs {
-
-constexpr float kObjLamHd = 0.8f, kObjLamCos = 0.2f;
-constexpr float kObjEpsSqrt = 1e-12f, kObjEpsDiv = 1e-12f;
 
 template <int TW, int TH, int K>
 __global__ void __launch_bounds__(TW *TH, 2) k_sem_objective(FwdArgs a, float log_k, float inv_n) {
@@ -44,6 +42,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_sem_objective(FwdArgs a, float lo
   float *sP = reinterpret_cast<float *>(sbase + 2 * bbytes);
   __shared__ double red[WARPS];
   __shared__ uint32_t s_maxlast;
+  __shared__ uint8_t s_keep[NPIX];  // raster pixel of the tile: its semantic term is kept
   if (a.counters->status & kStatusTimeout) return;  // the binning is incomplete
 
   const int tile = blockIdx.x;
@@ -82,10 +81,12 @@ __global__ void __launch_bounds__(TW *TH, 2) k_sem_objective(FwdArgs a, float lo
     for (int l = 0; l < k; ++l) cp_async8(buf_sem(q) + t * k + l, src + l);
   };
   // One front-to-back walk over the tile's batches (copies of batch bi + 1
-  // in flight while bi is processed).  For every Gaussian j in the union of
-  // the warp's contributor bits: f(gid, w, entries) with w = alpha T on the
-  // lanes it contributes to and 0 on the others (warp-uniform call).
-  auto walk = [&](auto &&f) {
+  // in flight while bi is processed); a thread that is not live takes no
+  // contributor bits.  For every Gaussian j in the union of
+  // the warp's contributor bits: f(gid, on, w, entries) with on = the lane's
+  // pixel takes the Gaussian, w = alpha T there and 0 elsewhere (a
+  // warp-uniform call).
+  auto walk = [&](bool live, auto &&f) {
     float T = 1.f;
     const int t = threadIdx.x;
     if (nbatch > 0 && t < batch_n(0)) issue(0, a.pvals[rg.x + t]);
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_sem_objective(FwdArgs a, float lo
       if (bi + 2 < nbatch && t < batch_n(bi + 2)) pv = a.pvals[rg.x + (uint32_t)(bi + 2) * kBatch + t];
       const uint32_t b0 = (uint32_t)bi * kBatch;
       uint32_t mine[2] = {0u, 0u};
-      if (b0 < last) {
+      if (live && b0 < last) {
         const uint32_t *mw = a.masks + (size_t)(unit0 + bi) * 2 * NPIX;
         mine[0] = mw[lp];
         mine[1] = mw[NPIX + lp];
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_sem_objective(FwdArgs a, float lo
           const bool on = (mine[h] >> jb) & 1u;
           const float w = on ? __fmul_rn(alpha, T) : 0.f;
           if (on) T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-          f(sgid[j], w, ssem + j * k);
+          f(sgid[j], on, w, ssem + j * k);
         }
       }
       cp_async_wait_all();
@@ -130,56 +131,81 @@ __global__ void __launch_bounds__(TW *TH, 2) k_sem_objective(FwdArgs a, float lo
 
   // (1) the rendered class distribution P of this thread's pixel
   for (int c = 0; c < m; ++c) myP[c] = 0.f;
-  walk([&](int, float w, const int2 *e) { scatter_classes<K>(myP, e, k, 0, m, w); });
+  walk(true, [&](int, bool, float w, const int2 *e) { scatter_classes<K>(myP, e, k, 0, m, w); });
 
   // (2) per pixel: the semantic term, and d term / d P (over the pixel
-  // count) in place of P
+  // count) in place of P.  Up to 128 classes a warp takes kG pixels at a
+  // time with their classes in registers, so that their loads and shuffle
+  // chains overlap; beyond, one pixel at a time with a second read.
   double term_sum = 0.0;
-  for (int p = (int)warp; p < NPIX; p += WARPS) {
-    float *row = sP + FP::thread_of(p) * a.mstride;
-    const int qx = ox + p % TW, qy = oy + p / TW;
-    if (qx >= a.width || qy >= a.height) {  // warp-uniform
-      for (int c = (int)lane; c < m; c += 32) row[c] = 0.f;
-      continue;
-    }
-    const float *q = a.t_sem + ((size_t)qy * a.width + qx) * m;
-    float hq = 0.f, s2 = 0.f, qq = 0.f, pp = 0.f, qp = 0.f;
-    for (int c = (int)lane; c < m; c += 32) {
-      const float qv = __ldg(q + c), pv = row[c];
-      if (qv > 0.f) hq -= qv * logf(qv);
-      const float d = sqrtf(fmaxf(qv, 0.f) + kObjEpsSqrt) - sqrtf(fmaxf(pv, 0.f) + kObjEpsSqrt);
-      s2 = fmaf(d, d, s2);
-      qq = fmaf(qv, qv, qq);
-      pp = fmaf(pv, pv, pp);
-      qp = fmaf(qv, pv, qp);
-    }
+  if (m <= 32 * kObjMI) {
+    constexpr int kG = 4;
+    for (int p0 = (int)warp * kG; p0 < NPIX; p0 += WARPS * kG) {
+      float qv[kG][kObjMI], pv[kG][kObjMI], st[kG][5];
+      ClassRoots rt[kG][kObjMI];
+      float *row[kG];
+      bool ok[kG];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      hq += __shfl_xor_sync(0xffffffffu, hq, o);
-      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-      qq += __shfl_xor_sync(0xffffffffu, qq, o);
-      pp += __shfl_xor_sync(0xffffffffu, pp, o);
-      qp += __shfl_xor_sync(0xffffffffu, qp, o);
-    }
-    const bool keep = hq < log_k;
-    const float dist = sqrtf(0.5f * s2);
-    const float den = sqrtf(qq) * sqrtf(pp);
-    const float cosv = den > kObjEpsDiv ? qp / den : 0.f;
-    if (lane == 0 && keep) term_sum += (double)(kObjLamHd * dist + kObjLamCos * (1.f - cosv));
-    for (int c = (int)lane; c < m; c += 32) {
-      float gv = 0.f;
-      if (keep) {
-        const float qv = __ldg(q + c), pv = row[c];
-        float dhd = 0.f;
-        if (dist > kObjEpsDiv && pv >= 0.f) {
-          const float sp = sqrtf(pv + kObjEpsSqrt), sq = sqrtf(fmaxf(qv, 0.f) + kObjEpsSqrt);
-          dhd = (sp - sq) / (4.f * dist * sp);
+      for (int g = 0; g < kG; ++g) {
+        const int p = p0 + g;
+        const int qx = ox + p % TW, qy = oy + p / TW;
+        ok[g] = qx < a.width && qy < a.height;
+        row[g] = sP + FP::thread_of(p) * a.mstride;
+        const float *q = a.t_sem + (ok[g] ? ((size_t)qy * a.width + qx) * m : 0);
+#pragma unroll
+        for (int i = 0; i < kObjMI; ++i) {
+          const int c = (int)lane + 32 * i;
+          const bool in = ok[g] && c < m;
+          qv[g][i] = in ? __ldg(q + c) : 0.f;
+          pv[g][i] = in ? row[g][c] : 0.f;
         }
-        float dcos = 0.f;
-        if (den > kObjEpsDiv) dcos = qv / den - cosv * pv / fmaxf(pp, kObjEpsDiv);
-        gv = (kObjLamHd * dhd - kObjLamCos * dcos) * inv_n;
       }
-      row[c] = gv;
+#pragma unroll
+      for (int g = 0; g < kG; ++g) {
+#pragma unroll
+        for (int j = 0; j < 5; ++j) st[g][j] = 0.f;
+#pragma unroll
+        for (int i = 0; i < kObjMI; ++i) rt[g][i] = class_sums(qv[g][i], pv[g][i], st[g]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int g = 0; g < kG; ++g)
+#pragma unroll
+          for (int j = 0; j < 5; ++j) st[g][j] += __shfl_xor_sync(0xffffffffu, st[g][j], o);
+#pragma unroll
+      for (int g = 0; g < kG; ++g) {
+        const PixelTerm t = pixel_term(st[g], ok[g], log_k);
+        if (lane == 0) {
+          if (t.keep) term_sum += (double)t.value;
+          s_keep[p0 + g] = t.keep;
+        }
+#pragma unroll
+        for (int i = 0; i < kObjMI; ++i) {
+          const int c = (int)lane + 32 * i;
+          if (c < m) row[g][c] = t.keep ? class_grad(qv[g][i], pv[g][i], rt[g][i], t, inv_n) : 0.f;
+        }
+      }
+    }
+  } else {
+    for (int p = (int)warp; p < NPIX; p += WARPS) {
+      float *row = sP + FP::thread_of(p) * a.mstride;
+      const int qx = ox + p % TW, qy = oy + p / TW;
+      const bool ok = qx < a.width && qy < a.height;  // warp-uniform
+      const float *q = a.t_sem + (ok ? ((size_t)qy * a.width + qx) * m : 0);
+      float st[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      if (ok)
+        for (int c = (int)lane; c < m; c += 32) class_sums(__ldg(q + c), row[c], st);
+      warp_sum5(st);
+      const PixelTerm t = pixel_term(st, ok, log_k);
+      if (lane == 0) {
+        if (t.keep) term_sum += (double)t.value;
+        s_keep[p] = t.keep;
+      }
+      for (int c = (int)lane; c < m; c += 32) {
+        const float qv = ok ? __ldg(q + c) : 0.f, pv = row[c];
+        row[c] = t.keep ? class_grad(qv, pv, class_roots(qv, pv), t, inv_n) : 0.f;
+      }
     }
   }
   if (lane == 0) red[warp] = term_sum;
@@ -192,9 +218,23 @@ __global__ void __launch_bounds__(TW *TH, 2) k_sem_objective(FwdArgs a, float lo
 
   // (3) d(objective)/d(weight l of Gaussian g) = sum_p w_gp dP_p[id_gl]:
   // lanes hold their pixel's products, a transposed warp sum leaves the
-  // total of entry l on lane l
+  // total of entry l on lane l (one or two contributing lanes add directly).
+  // Pixels outside the entropy mask have a zero gradient row: they skip.
   const int nl = K > 0 ? K : k;
-  walk([&](int gid, float w, const int2 *e) {
+  walk(s_keep[lp] != 0, [&](int gid, bool on, float w, const int2 *e) {
+    if (__popc(__ballot_sync(0xffffffffu, on)) <= 2) {
+      // one or two lanes: their products go straight to the atomics
+      if (on) {
+#pragma unroll
+        for (int l = 0; l < (K > 0 ? K : 16); ++l) {
+          if (K == 0 && l >= nl) break;
+          const int2 en = e[l];
+          const float v = (unsigned)en.x < (unsigned)m ? w * myP[en.x] : 0.f;
+          if (v != 0.f) atomicAdd(a.semg + (size_t)gid * k + l, v);
+        }
+      }
+      return;
+    }
     float v[16];
 #pragma unroll
     for (int l = 0; l < 16; ++l) v[l] = 0.f;
