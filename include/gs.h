@@ -272,6 +272,20 @@ gs_status gs_mapping_loss(int64_t npix, int m, int k, const float *rgb, const fl
                           const float *t_depth, const float *sil, const float *sem, const float *t_sem, float *d_rgb,
                           float *d_depth, float *d_sem, float *loss, double *partial, gs_stream_t stream);
 
+/* Dense-semantic comparator (supplement "Sparse Rendering" and "Runtime
+ * Analysis"): gs_render_fwd with every Gaussian carrying a full distribution
+ * over all m classes instead of its top-k entries.  sem_dense is a
+ * caller-owned device array [n][m] (row-major float; the scene's sparse
+ * sem_ids / sem_w are not read for the class map); Eq. 3 blends all m
+ * classes of every contributor.  Outputs as gs_render_fwd (sem [H,W,m] or
+ * NULL; sem_dense may be NULL only when sem is).  A dense array holding a
+ * Gaussian's top-k weights at their ids and zeros elsewhere renders exactly
+ * the sparse map.  Same preconditions as gs_render_fwd; the contributor bits
+ * must be kept (recompute_bwd = 0), else GS_ERR_UNSUPPORTED. */
+gs_status gs_render_fwd_dense(const gs_scene *scene, const gs_camera *cam, const gs_config *cfg, void *ws,
+                              const float *sem_dense, float *rgb, float *depth, float *sil, float *sem,
+                              gs_stream_t stream);
+
 /* Forward render of one view fused with the Sec. 3.1 mapping objective of
  * gs_mapping_loss (the silhouette-masked depth / colour L1 sum plus the mean
  * entropy-masked Hellinger + cosine semantic term, Eq. 4, Eq. 5), evaluated

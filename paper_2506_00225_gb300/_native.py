@@ -16,7 +16,7 @@ GS_NOALLOC_SCRATCH_BYTES = 32 << 20
 GS_MAPPING_LOSS_PARTIALS = 2048
 
 EXPORTS = ["gs_workspace_size", "gs_workspace_layout", "gs_project", "gs_bin_sort", "gs_render_fwd",
-           "gs_render_bwd", "gs_render_fwd_l1", "gs_render_bwd_l1", "gs_render_fwd_objective",
+           "gs_render_bwd", "gs_render_fwd_l1", "gs_render_bwd_l1", "gs_render_fwd_dense", "gs_render_fwd_objective",
            "gs_render_bwd_objective", "gs_render_candidates", "gs_l1_loss", "gs_mapping_loss", "gs_render_fwd_noalloc",
            "gs_read_counters", "gs_status_string"]
 
@@ -65,6 +65,8 @@ _SIGS = {
                          [c_void_p] * 5 + [c_void_p]),
     "gs_render_bwd_l1": (ctypes.c_int, [P(GsScene), P(GsCamera), P(GsConfig), c_void_p, c_void_p] +
                          [c_void_p] * 6 + [c_void_p]),
+    "gs_render_fwd_dense": (ctypes.c_int, [P(GsScene), P(GsCamera), P(GsConfig), c_void_p, c_void_p] +
+                            [c_void_p] * 4 + [c_void_p]),
     "gs_render_fwd_objective": (ctypes.c_int, [P(GsScene), P(GsCamera), P(GsConfig), c_void_p] + [c_void_p] * 3 +
                                 [c_void_p] * 4 + [c_void_p]),
     "gs_render_bwd_objective": (ctypes.c_int, [P(GsScene), P(GsCamera), P(GsConfig), c_void_p, c_void_p] +

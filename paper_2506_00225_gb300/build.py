@@ -31,6 +31,7 @@ SOURCES = {
     "loss.cu": [],
     "mapping_loss.cu": [],
     "render_objective.cu": [],
+    "render_dense.cu": [],
     "api.cu": [],
     "noalloc.cu": [],
 }

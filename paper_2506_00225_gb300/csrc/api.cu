@@ -336,6 +336,20 @@ gs_status gs_render_bwd_l1(const gs_scene *scene, const gs_camera *cam, const gs
   return GS_OK;
 }
 
+gs_status gs_render_fwd_dense(const gs_scene *scene, const gs_camera *cam, const gs_config *cfg, void *ws,
+                              const float *sem_dense, float *rgb, float *depth, float *sil, float *sem,
+                              gs_stream_t stream) {
+  Layout L;
+  if (!ws || !aligned(ws, 256) || !make_layout(scene, cam, 1, cfg, &L)) return GS_ERR_ARG;
+  if (!scene_ptrs_ok(scene, true) || (scene->n > 0 && !scene->rgb)) return GS_ERR_ARG;
+  if (sem && scene->n > 0 && !sem_dense) return GS_ERR_ARG;
+  if (!shape_compiled(L.tile_w, L.tile_h) || !dense_supported(L)) return GS_ERR_UNSUPPORTED;
+  WsPtrs P = ws_ptrs(L, ws);
+  GS_CHECK_CUDA(launch_render_fwd_dense(L, P, pair_sort_buffer(L), *scene, sem_dense, rgb, depth, sil, sem,
+                                        (cudaStream_t)stream));
+  return GS_OK;
+}
+
 // Preconditions of the fused Sec. 3.1 objective beyond gs_render_fwd's.
 static gs_status objective_supported(const Layout &L, const gs_scene *scene, const gs_config &c) {
   if (!c.sem_detach_geometry || !objective_fits(L, scene->k, scene->m)) return GS_ERR_UNSUPPORTED;

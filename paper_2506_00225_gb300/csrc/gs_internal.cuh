@@ -159,6 +159,12 @@ bool objective_fits(const Layout &L, int k, int m);
 cudaError_t launch_render_fwd_objective(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc,
                                         const float *t_rgb, const float *t_depth, const float *t_sem, float *rgb,
                                         float *depth, float *sil, float *loss, cudaStream_t s);
+// Dense-semantic comparator (render_dense.cu): every Gaussian carries all
+// m class probabilities (dense [n][m]); needs the contributor bits.
+bool dense_supported(const Layout &L);
+cudaError_t launch_render_fwd_dense(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc,
+                                    const float *dense, float *rgb, float *depth, float *sil, float *sem,
+                                    cudaStream_t s);
 cudaError_t launch_add_semg(const WsPtrs &P, const gs_scene &sc, const float *loss_scale, float *g_sem_w,
                             cudaStream_t s);
 cudaError_t launch_project_bwd(const Layout &L, const WsPtrs &P, const gs_scene &sc, float *g_means,

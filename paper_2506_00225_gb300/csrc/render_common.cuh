@@ -302,9 +302,11 @@ struct FwdArgs {
 __host__ __device__ inline int code_words(int nwc) { return 2 * (1 + nwc); }
 
 // Host side (render_fwd.cu): the blend arguments of the mapping view, the
-// blend pass alone in its fused-loss form, and the per-tile loss reduction.
+// blend pass alone (fused-loss or plain form), and the per-tile loss
+// reduction.
 FwdArgs fwd_args(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc);
 cudaError_t launch_blend_objective(const Layout &L, const FwdArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_blend_plain(const Layout &L, const FwdArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_loss_final(const double *lpart, int ntiles, double npix, double m, int has_sem, int objective,
                               float *loss, cudaStream_t s);
 

@@ -554,6 +554,10 @@ cudaError_t launch_blend_objective(const Layout &L, const FwdArgs &a, int grid, 
   return dispatch_fwd<true>(L, a, grid, 0, false, s);
 }
 
+cudaError_t launch_blend_plain(const Layout &L, const FwdArgs &a, int grid, cudaStream_t s) {
+  return dispatch_fwd<false>(L, a, grid, 0, false, s);
+}
+
 cudaError_t launch_loss_final(const double *lpart, int ntiles, double npix, double m, int has_sem, int objective,
                               float *loss, cudaStream_t s) {
   k_l1_tiles_final<<<1, 1024, 0, s>>>(lpart, ntiles, npix, m, has_sem, objective, loss);

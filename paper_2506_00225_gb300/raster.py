@@ -212,6 +212,29 @@ class Rasterizer:
         self.generation += 1
         return rgb, depth, sil, sem
 
+    def forward_dense(self, g: Gaussians, cam, sem_dense: torch.Tensor, check=True):
+        """Dense-semantic comparator: project, bin and render one view with
+        every Gaussian carrying all m class probabilities (``sem_dense``
+        [n, m] float32 on the device).  Returns rgb, depth, sil, sem."""
+        self._mark("project")
+        sc, cams_arr, cfg, ws = self._project_bin(g, [cam], check)
+        self._mark("render_fwd")
+        H, W = cam.height, cam.width
+        dev = self.device
+        rgb = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+        depth = torch.empty((H, W), dtype=torch.float32, device=dev)
+        sil = torch.empty((H, W), dtype=torch.float32, device=dev)
+        sem = torch.empty((H, W, g.m), dtype=torch.float32, device=dev)
+        dense = _f32(sem_dense)
+        if tuple(dense.shape) != (g.n, g.m):
+            raise ValueError(f"sem_dense must be [{g.n}, {g.m}], got {tuple(dense.shape)}")
+        N.check(N.load().gs_render_fwd_dense(ctypes.byref(sc), cams_arr, ctypes.byref(cfg), ws, _ptr(dense),
+                                             _ptr(rgb), _ptr(depth), _ptr(sil), _ptr(sem), _stream()),
+                "gs_render_fwd_dense")
+        self._mark("fwd_end")
+        self.generation += 1
+        return rgb, depth, sil, sem
+
     def backward(self, g: Gaussians, cam, d_rgb=None, d_depth=None, d_sil=None, d_sem=None, grads=None):
         """Adjoint of the last forward.  Returns (or accumulates into) a dict of
         gradients for means, scales, quats, opacity, rgb, sem_w."""

@@ -304,6 +304,39 @@ def candidate_cameras_grid(xs, ys, z=1.5, yaws=(0, 60, 120, 180, 240, 300), res_
     return cams
 
 
+def dense_distributions(scene: Scene, seed: int, floor: float = 0.1) -> np.ndarray:
+    """Full per-Gaussian class distributions [N, M] for the dense comparator:
+    (1 - floor) times the Gaussian's top-k weights renormalised to sum 1,
+    placed at their class ids, plus floor times a Dirichlet(1) draw over all
+    M classes (every class gets some mass)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n, m = scene.n, scene.m
+    dense = np.zeros((n, m), np.float64)
+    w = scene.sem_w.astype(np.float64)
+    w = w / np.maximum(w.sum(1, keepdims=True), 1e-12)
+    np.add.at(dense, (np.repeat(np.arange(n), scene.k), scene.sem_ids.reshape(-1)), w.reshape(-1))
+    dense = (1.0 - floor) * dense + floor * rng.dirichlet(np.ones(m), size=n)
+    return _f32(dense)
+
+
+def sparse_to_dense(scene: Scene) -> np.ndarray:
+    """The scene's top-k (id, weight) entries scattered into [N, M] (zeros
+    elsewhere)."""
+    dense = np.zeros((scene.n, scene.m), np.float32)
+    np.add.at(dense, (np.repeat(np.arange(scene.n), scene.k), scene.sem_ids.reshape(-1)),
+              scene.sem_w.reshape(-1))
+    return dense
+
+
+def dense_as_sparse(scene: Scene, dense: np.ndarray) -> Scene:
+    """The same Gaussians with k = M entries (id c, weight dense[:, c]): the
+    dense representation written in the sparse one's form."""
+    n, m = dense.shape
+    ids = np.ascontiguousarray(np.broadcast_to(np.arange(m, dtype=np.int32), (n, m)))
+    return Scene(scene.means, scene.scales, scene.quats, scene.opacity, scene.rgb, ids,
+                 _f32(dense), m, scene.geo_unc)
+
+
 def workload(name: str):
     """Named workloads.  Returns a dict with the scene(s) and camera(s).
 
@@ -316,6 +349,10 @@ def workload(name: str):
     rooms2m    : 2M Gaussians in 2x2 rooms, 256 classes top-8, 680x1200 view.
     mixed2m    : rooms2m + 128 candidate views (64 @170x300, 48 @340x600,
                  16 @680x1200) on a 0.5 m grid across the rooms, seeded shuffle.
+    dense204k  : 290k-Gaussian room, 102 classes top-3, one 340x600 view (f=300)
+                 from a corner, (0.4,0.4,1.5) yaw 45, in which about 204k
+                 Gaussians are visible, plus full 102-class distributions per
+                 Gaussian (the dense comparator's input).
     """
     if name == "plain10k":
         sc = scene_plain(0)
@@ -348,4 +385,8 @@ def workload(name: str):
         cams = [look_camera((poses[i][0], poses[i][1], 1.5), poses[i][2], res[j][1], res[j][0], res[j][2])
                 for j, i in enumerate(order)]
         return {"scene": sc, "cams": [base["cams"][0]], "target": base["target"], "cand_cams": cams}
+    if name == "dense204k":
+        sc = scene_room(6, 290_000, 102, 3)
+        cam = look_camera((0.4, 0.4, 1.5), 45.0, 600, 340, 300.0)
+        return {"scene": sc, "cams": [cam], "sem_dense": dense_distributions(sc, 7)}
     raise KeyError(name)

@@ -179,3 +179,20 @@ def test_objective_preconditions_on_host(lib, case):
     bwd = lib.gs_render_bwd_objective(ctypes.byref(sc), cams, ctypes.byref(cfg), fake, t, None, None, None, None,
                                       None, None, None)
     assert fwd == N.GS_ERR_UNSUPPORTED and bwd == N.GS_ERR_UNSUPPORTED
+
+
+def test_dense_preconditions_on_host(lib):
+    """gs_render_fwd_dense: a semantic output without the dense array is an
+    argument error; the recompute mode has no contributor bits."""
+    sc, cams, cfg = _structs(n=0)
+    fake = ctypes.c_void_p(1 << 40)  # never dereferenced: both calls return before GPU work
+    t = ctypes.c_void_p(1 << 41)
+    sc.n = 5
+    sc.means = sc.scales = sc.opacity = sc.rgb = sc.sem_ids = sc.sem_w = t
+    sc.quats = t
+    assert lib.gs_render_fwd_dense(ctypes.byref(sc), cams, ctypes.byref(cfg), fake, None, None, None, None, t,
+                                   None) == N.GS_ERR_ARG
+    sc.n = 0
+    cfg.recompute_bwd = 1
+    assert lib.gs_render_fwd_dense(ctypes.byref(sc), cams, ctypes.byref(cfg), fake, None, None, None, None, None,
+                                   None) == N.GS_ERR_UNSUPPORTED
