@@ -822,6 +822,21 @@ def bench_candidates(args, dev, flush):
     torch.cuda.synchronize()
     per_view_ms = s.elapsed_time(e)
     npix = sum(c.width * c.height for c in cams)
+    # the Eq. 6-8 scoring tail on the device after the batched render
+    from paper_2506_00225_gb300 import explore
+    npix_t = torch.tensor([c.width * c.height for c in cams], dtype=torch.int32, device=dev)
+    pos_t = torch.tensor(np.stack([c.position() for c in cams]), dtype=torch.float32, device=dev)
+    cur_t = torch.tensor(cams[0].position(), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        explore.score_candidates(out, npix_t, pos_t, cur_t)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(100):
+        explore.score_candidates(out, npix_t, pos_t, cur_t)
+    e.record()
+    torch.cuda.synchronize()
+    score_us = s.elapsed_time(e) * 10.0
     return {"metric": "candidate views/s", "value": 1000.0 * len(cams) / ms, "unit": "views/s",
             "ms_per_batch": ms, "mpix_per_s": npix / (ms * 1e-3) / 1e6,
             "workload": ("cand96: the 300k room + Gamma(2,0.5) uncertainty, 96 poses (4x4 grid at 0.5 m x 6 yaws), "
@@ -831,7 +846,9 @@ def bench_candidates(args, dev, flush):
             "n_records": int(cnt.n_records), "n_pairs": int(cnt.n_pairs),
             "per_view_launches": {"value": 1000.0 * len(cams) / per_view_ms, "unit": "views/s",
                                   "ms": per_view_ms},
-            "batched_speedup": per_view_ms / ms}
+            "batched_speedup": per_view_ms / ms,
+            "scoring_us": {"value": score_us, "what": "gs_score_candidates over all the views (Eq. 6-8 softmaxes, "
+                                                      "motion cost, pruning, best index), mean of 100 calls"}}
 
 
 if __name__ == "__main__":

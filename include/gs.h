@@ -317,6 +317,46 @@ gs_status gs_render_bwd_objective(const gs_scene *scene, const gs_camera *cam, c
                                   const float *loss_scale, float *g_means, float *g_scales, float *g_quats,
                                   float *g_opacity, float *g_rgb, float *g_sem_w, gs_stream_t stream);
 
+/* Scoring tail of the candidate renders (Sec. 3.2, Eq. 6-8), on the device
+ * and stream-ordered (graph-capturable after gs_render_candidates).  Over the
+ * n_views candidates given:
+ *   I_geo = softmax(log N_S) = N_S / sum N_S (all 0 when no view has N_S > 0)
+ *   I_sem = softmax(sum_p H)
+ *   I     = (1 - softmax(l)) I_geo I_sem,  l = |position - current|
+ * softmaxes in double with the maximum subtracted.  Device inputs: sums
+ * [n_views][3] as written by gs_render_candidates (sum U, sum H, N_S), npix
+ * [n_views] pixels per view, positions [n_views][3] candidate positions,
+ * current [3] the camera's position.  Device outputs: scores [n_views][4] =
+ * (I, I_geo, I_sem, 1 - softmax(l)); keep [n_views] = 1 unless
+ * N_S < prune_frac * npix (the pool's pruning rule, prune_frac = 0.005 in
+ * the paper); *best = index of the largest I among kept views (lowest index
+ * on ties), -1 when none is kept.  0 <= prune_frac <= 1. */
+gs_status gs_score_candidates(int n_views, const double *sums, const int32_t *npix, const float *positions,
+                              const float *current, double prune_frac, double *scores, int32_t *keep,
+                              int32_t *best, gs_stream_t stream);
+
+/* Host: candidate cameras at n_positions positions (host [n_positions][3])
+ * times n_dirs viewing directions, the points of an n_dirs-point Fibonacci
+ * lattice on the unit sphere (Sec. 3.2 "Exploration Strategy": v2 = 5 in the
+ * coarse stage, 15 in the fine one): direction i has height
+ * z = 1 - (2 i + 1) / n_dirs and azimuth i times the golden angle
+ * pi (3 - sqrt 5).  Camera rows are right = d x (0, 0, 1) normalised,
+ * down = d x right, forward = d (OpenCV axes, world z up); principal point
+ * at the image centre.  Writes out[p * n_dirs + i] (host array). */
+gs_status gs_candidate_poses(int n_positions, const float *positions, int n_dirs, int width, int height, float fx,
+                             float fy, float near_plane, gs_camera *out);
+
+/* Host: candidate positions on a lattice of spacing `step` (v1: 1 m coarse,
+ * 0.5 m fine) over newly freed space.  For every voxel centre (host
+ * [n_voxels][3]) within `band` of one of the n_heights heights h, the
+ * lattice point (round(x / step) step, round(y / step) step, h) is a
+ * candidate; duplicates are merged and the points written in ascending
+ * (i, j, height index) order to out (host [capacity][3]).  Returns the number
+ * of distinct points (writing at most capacity of them), or -1 on invalid
+ * arguments. */
+int64_t gs_candidate_positions(int64_t n_voxels, const float *centres, float step, int n_heights,
+                               const float *heights, float band, float *out, int64_t capacity);
+
 /* Bytes of the fixed device scratch array used by gs_render_fwd_noalloc. */
 #define GS_NOALLOC_SCRATCH_BYTES (32u << 20)
 

@@ -18,7 +18,8 @@ GS_MAPPING_LOSS_PARTIALS = 2048
 EXPORTS = ["gs_workspace_size", "gs_workspace_layout", "gs_project", "gs_bin_sort", "gs_render_fwd",
            "gs_render_bwd", "gs_render_fwd_l1", "gs_render_bwd_l1", "gs_render_fwd_dense", "gs_render_fwd_objective",
            "gs_render_bwd_objective", "gs_render_candidates", "gs_l1_loss", "gs_mapping_loss", "gs_render_fwd_noalloc",
-           "gs_read_counters", "gs_status_string"]
+           "gs_score_candidates", "gs_candidate_poses", "gs_candidate_positions", "gs_read_counters",
+           "gs_status_string"]
 
 
 class GsScene(ctypes.Structure):
@@ -79,6 +80,12 @@ _SIGS = {
                         [c_void_p, c_void_p, c_void_p]),
     "gs_render_fwd_noalloc": (ctypes.c_int, [P(GsScene), P(GsCamera), P(GsConfig)] + [c_void_p] * 4 +
                               [c_void_p, c_void_p]),
+    "gs_score_candidates": (ctypes.c_int, [ctypes.c_int] + [c_void_p] * 4 + [c_double] + [c_void_p] * 3 +
+                            [c_void_p]),
+    "gs_candidate_poses": (ctypes.c_int, [ctypes.c_int, c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_float, ctypes.c_float, ctypes.c_float, P(GsCamera)]),
+    "gs_candidate_positions": (c_int64, [c_int64, c_void_p, ctypes.c_float, ctypes.c_int, c_void_p, ctypes.c_float,
+                                         c_void_p, c_int64]),
     "gs_read_counters": (ctypes.c_int, [c_void_p, P(GsCounters), c_void_p]),
     "gs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }

@@ -32,6 +32,7 @@ SOURCES = {
     "mapping_loss.cu": [],
     "render_objective.cu": [],
     "render_dense.cu": [],
+    "explore.cu": [],
     "api.cu": [],
     "noalloc.cu": [],
 }

@@ -1,0 +1,87 @@
+"""Candidate management around the candidate renders (Sec. 3.2): candidate
+positions on a lattice over newly freed space, Fibonacci-lattice viewing
+directions, and the Eq. 6-8 scoring tail on the device (argument
+marshalling only; the work runs in ``libgs``)."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native as N
+from .scenes import Camera
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def candidate_positions(voxel_centres: np.ndarray, step: float, heights, band: float) -> np.ndarray:
+    """Lattice points (spacing ``step``) over the given voxel centres at the
+    given heights (a voxel counts for a height within ``band`` of it).
+    Returns [C, 3] float32, ascending (i, j, height index)."""
+    c = np.ascontiguousarray(voxel_centres, dtype=np.float32).reshape(-1, 3)
+    h = np.ascontiguousarray(heights, dtype=np.float32).reshape(-1)
+    lib = N.load()
+    n = lib.gs_candidate_positions(c.shape[0], c.ctypes.data_as(ctypes.c_void_p), float(step), h.size,
+                                   h.ctypes.data_as(ctypes.c_void_p), float(band), None, 0)
+    if n < 0:
+        raise ValueError("invalid candidate position arguments")
+    out = np.empty((max(n, 1), 3), np.float32)
+    n2 = lib.gs_candidate_positions(c.shape[0], c.ctypes.data_as(ctypes.c_void_p), float(step), h.size,
+                                    h.ctypes.data_as(ctypes.c_void_p), float(band),
+                                    out.ctypes.data_as(ctypes.c_void_p), n)
+    assert n2 == n
+    return out[:n]
+
+
+def candidate_poses(positions: np.ndarray, n_dirs: int, width: int, height: int, f: float,
+                    near: float = 0.2) -> list[Camera]:
+    """Cameras at every position looking along the n_dirs directions of a
+    Fibonacci lattice on the sphere (position-major order)."""
+    p = np.ascontiguousarray(positions, dtype=np.float32).reshape(-1, 3)
+    arr = (N.GsCamera * max(1, p.shape[0] * n_dirs))()
+    N.check(N.load().gs_candidate_poses(p.shape[0], p.ctypes.data_as(ctypes.c_void_p), int(n_dirs), int(width),
+                                        int(height), float(f), float(f), float(near), arr), "gs_candidate_poses")
+    cams = []
+    for i in range(p.shape[0] * n_dirs):
+        c = arr[i]
+        cams.append(Camera(c.width, c.height, c.fx, c.fy, c.cx, c.cy, c.near_plane,
+                           np.array(c.w2c[:], dtype=np.float32).reshape(3, 4)))
+    return cams
+
+
+def score_candidates(sums: torch.Tensor, npix: torch.Tensor, positions: torch.Tensor, current: torch.Tensor,
+                     prune_frac: float = 0.005):
+    """Eq. 6-8 on the device from the per-view sums of ``Rasterizer.candidates``
+    (float64 [V, 3]): returns scores float64 [V, 4] = (I, I_geo, I_sem,
+    1 - softmax(l)), keep int32 [V] (0: N_S below prune_frac of the view's
+    pixels) and best int32 [1] (largest I among kept views, -1 if none).
+    Stream-ordered: no host synchronisation."""
+    dev = sums.device
+    V = int(sums.shape[0])
+    sums = sums.to(torch.float64).contiguous()
+    npix = npix.to(device=dev, dtype=torch.int32).contiguous()
+    positions = positions.to(device=dev, dtype=torch.float32).contiguous()
+    current = current.to(device=dev, dtype=torch.float32).contiguous()
+    scores = torch.empty((V, 4), dtype=torch.float64, device=dev)
+    keep = torch.empty(V, dtype=torch.int32, device=dev)
+    best = torch.empty(1, dtype=torch.int32, device=dev)
+    N.check(N.load().gs_score_candidates(V, _ptr(sums), _ptr(npix), _ptr(positions), _ptr(current),
+                                         float(prune_frac), _ptr(scores), _ptr(keep), _ptr(best),
+                                         ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)),
+            "gs_score_candidates")
+    return scores, keep, best
+
+
+def next_best_view(rast, g, cams: list[Camera], current_position, prune_frac: float = 0.005):
+    """Renders the candidate views (one batched call) and scores them:
+    returns (sums [V, 3], scores [V, 4], keep [V], best [1]) on the device."""
+    sums = rast.candidates(g, cams)
+    dev = sums.device
+    npix = torch.tensor([c.width * c.height for c in cams], dtype=torch.int32, device=dev)
+    pos = torch.tensor(np.stack([c.position() for c in cams]), dtype=torch.float32, device=dev)
+    cur = torch.tensor(np.asarray(current_position, np.float32), device=dev)
+    scores, keep, best = score_candidates(sums, npix, pos, cur, prune_frac)
+    return sums, scores, keep, best

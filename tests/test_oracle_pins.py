@@ -522,3 +522,94 @@ def test_mapping_loss_gradient_matches_central_differences():
             b[idx] -= h
             num[idx] = (f(**{name: a}) - f(**{name: b})) / (2 * h)
         np.testing.assert_allclose(grad, num, rtol=1e-5, atol=1e-8, err_msg=name)
+
+
+# ---------------------------------------------------------------------------
+# candidate scoring and generation (Sec. 3.2, Eq. 6-8, "Exploration Strategy")
+# ---------------------------------------------------------------------------
+
+def test_scoring_closed_forms():
+    from oracle import explore as ex
+    # Eq. 6: the softmax of log N is the normalisation N / sum N (0 for N = 0)
+    ns = np.array([0.0, 5.0, 15.0, 30.0])
+    sums = np.stack([np.zeros(4), np.full(4, 7.0), ns], axis=1)
+    pos = np.array([[1.0, 0, 0], [0, 1.0, 0], [0, 0, 1.0], [-1.0, 0, 0]])  # all at distance 1
+    sc, keep, best = ex.score(sums, np.full(4, 1000), pos, np.zeros(3))
+    np.testing.assert_allclose(sc[:, 1], ns / ns.sum(), rtol=1e-15)
+    # equal entropy sums and equal distances: uniform 1/V factors
+    np.testing.assert_allclose(sc[:, 2], 0.25, rtol=1e-15)
+    np.testing.assert_allclose(sc[:, 3], 0.75, rtol=1e-15)
+    np.testing.assert_allclose(sc[:, 0], 0.75 * 0.25 * ns / ns.sum(), rtol=1e-14)
+    # pruning: N_S < 0.5 % of 1000 pixels = 5 -> only the first is dropped
+    assert keep.tolist() == [False, True, True, True] and best == 3
+    # a hand-evaluated three-candidate case: N_S = (10, 30, 60), sum H =
+    # (2, 3, 2), distances (0, 1, 2) from the current position
+    sums = np.array([[0, 2.0, 10], [0, 3.0, 30], [0, 2.0, 60]])
+    pos = np.array([[0.0, 0, 0], [0, 1.0, 0], [0, 0, 2.0]])
+    sc, keep, best = ex.score(sums, np.full(3, 100), pos, np.zeros(3))
+    e = math.e
+    igeo = np.array([0.1, 0.3, 0.6])
+    isem = np.array([1.0, e, 1.0]) / (2.0 + e)
+    mov = 1.0 - np.array([1.0, e, e * e]) / (1.0 + e + e * e)
+    np.testing.assert_allclose(sc[:, 0], mov * igeo * isem, rtol=1e-14)
+    assert keep.all() and best == int(np.argmax(mov * igeo * isem)) == 1
+    # no candidate reveals anything: the geometric factor is 0 for all
+    sc, keep, best = ex.score(np.zeros((2, 3)), np.full(2, 10), np.zeros((2, 3)), np.zeros(3))
+    assert not sc[:, 1].any() and not sc[:, 0].any() and best == -1
+
+
+def test_fibonacci_lattice_properties():
+    from oracle import explore as ex
+    for n in (5, 15, 200):
+        d = ex.fibonacci_directions(n)
+        np.testing.assert_allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-15)
+        # heights equally spaced in (-1, 1), symmetric about 0
+        np.testing.assert_allclose(np.diff(d[:, 2]), -2.0 / n, atol=1e-15)
+        assert abs(d[:, 2].sum()) < 1e-12
+        # azimuth steps of the golden angle (mod 2 pi)
+        az = np.arctan2(d[:, 1], d[:, 0])
+        step = np.mod(np.diff(az), 2 * math.pi)
+        np.testing.assert_allclose(step, math.pi * (3 - math.sqrt(5)), atol=1e-12)
+    # near-uniform coverage (area per point 4 pi / n): every direction of a
+    # dense random sample lies within 2.9 / sqrt(n) rad of a lattice point
+    # (the lattice reaches 2.61; an azimuth step of 2 rad instead of the
+    # golden angle leaves holes of 3.36), and no two points are closer than
+    # 2.8 / sqrt(n) (the lattice: 3.10)
+    n = 200
+    d = ex.fibonacci_directions(n)
+    rng = np.random.default_rng(0)
+    u = rng.normal(size=(20000, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    cover = np.arccos(np.clip((u @ d.T).max(1), -1, 1)).max()
+    assert cover < 2.9 / math.sqrt(n)
+    g = np.clip(d @ d.T, -1, 1) - 2 * np.eye(n)
+    assert np.arccos(g.max()) > 2.8 / math.sqrt(n)
+
+
+def test_look_along_pose():
+    from oracle import explore as ex
+    rng = np.random.default_rng(1)
+    for d in ex.fibonacci_directions(15):
+        p = rng.uniform(-3, 3, size=3)
+        w = ex.look_along(p, d)
+        r, t = w[:, :3], w[:, 3]
+        np.testing.assert_allclose(r @ r.T, np.eye(3), atol=1e-14)
+        assert abs(np.linalg.det(r) - 1.0) < 1e-12
+        np.testing.assert_allclose(r @ p + t, 0.0, atol=1e-12)            # the centre maps to the origin
+        np.testing.assert_allclose(r @ (p + d) + t, [0, 0, 1], atol=1e-12)  # one metre ahead on the axis
+        assert (r[1] @ np.array([0, 0, 1.0])) <= 1e-12                      # image "down" never points up
+    # a horizontal direction reproduces the scenes' horizontal look-at camera
+    from paper_2506_00225_gb300 import scenes
+    cam = scenes.look_camera((1.0, 2.0, 1.5), 30.0, 64, 48, 50.0)
+    d = np.array([math.cos(math.radians(30)), math.sin(math.radians(30)), 0.0])
+    np.testing.assert_allclose(ex.look_along((1.0, 2.0, 1.5), d), cam.w2c, atol=1e-6)
+
+
+def test_candidate_positions_closed_form():
+    from oracle import explore as ex
+    centres = np.array([[0.1, 0.2, 1.50], [0.4, -0.3, 1.45], [0.6, 0.0, 1.5], [2.9, 1.1, 0.8], [3.1, 0.9, 1.52]])
+    p = ex.candidate_positions(centres, 1.0, [1.5], 0.1)
+    # rounding to the 1 m lattice: (0, 0), (0, 0), (1, 0), -, (3, 1)
+    np.testing.assert_allclose(p, [[0, 0, 1.5], [1, 0, 1.5], [3, 1, 1.5]], atol=1e-7)
+    p2 = ex.candidate_positions(centres, 0.5, [0.8, 1.5], 0.1)
+    assert len(p2) == 5 and set(np.round(p2[:, 2], 5)) == {0.8, 1.5}
