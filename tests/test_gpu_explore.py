@@ -67,7 +67,7 @@ def test_scores_of_oracle_candidate_sums_over_generated_poses():
     """Candidates generated the paper's way (lattice positions over free
     space, 5 Fibonacci directions), their sums from the oracle's candidate
     reductions, scored on the device and by the oracle."""
-    sc = scenes.scene_plain(3, n=4000, m=16, k=3)
+    sc = scenes.scene_plain(3, n=800, m=16, k=3)  # sparse enough to leave holes: some views kept, some pruned
     rng = np.random.default_rng(2)
     free = rng.uniform([-1.5, -1.5, 1.3], [1.5, 1.5, 1.7], size=(400, 3))
     pos = explore.candidate_positions(free, 1.0, [1.5], 0.25)
@@ -76,7 +76,7 @@ def test_scores_of_oracle_candidate_sums_over_generated_poses():
     npix = np.array([c.width * c.height for c in cams])
     cur = np.array([0.2, -0.1, 1.5])
     s, k, b = _check(sums, npix, np.stack([c.position() for c in cams]), cur)
-    assert len(cams) == 5 * len(pos) and k.any()
+    assert len(cams) == 5 * len(pos) and k.any() and not k.all()
 
 
 def test_next_best_view_pipeline_runs_on_device():
