@@ -20,6 +20,10 @@ Key ``dense_comparator``: the supplement's runtime comparison -- one forward
 render of a 340x600x102 class map from 204k Gaussians with the sparse top-3
 representation and with full 102-class distributions per Gaussian.
 
+Key ``exploration``: the 5 cm Exploration Map update from one depth frame,
+the extraction of the voxels it freed, and the top-k initialisation of new
+Gaussians.
+
 Also measured in the same run (key ``candidates``): batched candidate-view
 rendering of 96 poses of mixed resolution (views/s), and the same views
 issued as one plain launch chain per view.  Key ``large_scene``: the mapping
@@ -64,7 +68,7 @@ def parse():
     ap.add_argument("--cand-tile", default="16x16", help="WxH tile of the candidate kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 2M-Gaussian mapping and mixed-stream runs")
-    ap.add_argument("--only", choices=["candidates", "large", "objective", "dense"], default=None,
+    ap.add_argument("--only", choices=["candidates", "large", "objective", "dense", "explore"], default=None,
                     help="run only that part and print its dict (for profiling; not the benchmark line)")
     ap.add_argument("--tile", default=None, help="WxH: fixed tile shape instead of the autotuner's")
     ap.add_argument("--ppt", type=int, default=2, help="pixels per thread of the adjoint with --tile")
@@ -268,6 +272,9 @@ def main():
     build.build()
     if args.only is not None:
         flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+        if args.only == "explore":
+            print(json.dumps(bench_explore(args, dev, flush)))
+            return 0
         if args.only == "dense":
             print(json.dumps(bench_dense(args, dev, flush, args.steps)))
             return 0
@@ -466,6 +473,7 @@ def main():
         raise RuntimeError(f"device status {st.status} after the timed region")
 
     dense_cmp = bench_dense(args, dev, flush, 20)
+    explore_steps = bench_explore(args, dev, flush)
 
     cand = None
     if not args.no_candidates:
@@ -510,6 +518,7 @@ def main():
                                          "the HxWxM gradient"},
                 "objective_step": objective,
                 "dense_comparator": dense_cmp,
+                "exploration": explore_steps,
                 "candidates": cand,
                 "large_scene": large,
                 "mixed_stream": mixed}
@@ -619,6 +628,49 @@ def bench_dense(args, dev, flush, steps):
         del graph
     out["dense_over_sparse"] = out["dense"]["ms"] / out["sparse"]["ms"]
     out["dense_over_sparse_render_pass"] = out["dense"]["render_fwd_ms"] / max(out["sparse"]["render_fwd_ms"], 1e-9)
+    return out
+
+
+def bench_explore(args, dev, flush):
+    """The steps around the path: a 5 cm Exploration Map update from one
+    680x1200 rendered depth frame of the 300k room (every pixel, and every
+    4th row and column) and the extraction of the voxels it freed; the top-k
+    initialisation of 100k new Gaussians from a 680x1200x102 observed
+    distribution map."""
+    import torch
+    from paper_2506_00225_gb300 import explore, raster, scenes
+    wl = scenes.workload("room300k")
+    sc, cam = wl["scene"], wl["cams"][0]
+    g = raster.Gaussians.from_scene(sc, dev)
+    rast = raster.Rasterizer(device=dev)
+    with torch.no_grad():
+        _, depth, sil, sem = rast.forward(g, cam, check=True)
+    depth = torch.where(sil > 0.5, depth / sil.clamp_min(1e-6), torch.zeros_like(depth)).contiguous()
+    vm = explore.VoxelMap((0.0, 0.0, 0.0), 0.05, (120, 120, 60), device=dev)
+
+    def timed(fn, reps=20):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s_.record()
+            fn()
+            e_.record()
+            ts.append((s_, e_))
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(b) for a, b in ts)
+
+    out = {"workload": "Exploration Map of the 6x6x3 m room at 5 cm (120x120x60 voxels) from one 680x1200 depth "
+                       "frame; top-k (k=3) of 100k new Gaussians from a 680x1200x102 distribution map"}
+    for stride in (1, 4):
+        vm.state.zero_()
+        out[f"voxel_update_stride{stride}_ms"] = timed(lambda: vm.integrate(depth, cam, stride, 10.0))
+    vm.prev.zero_()
+    out["new_free_ms"] = timed(lambda: vm.new_free(1 << 20))
+    out["new_free_voxels"] = int(vm.count.item())
+    rows = torch.randint(0, cam.width * cam.height, (100_000,), device=dev)
+    probs = torch.softmax(torch.randn(cam.height, cam.width, sc.m, device=dev), -1)
+    out["topk_init_100k_ms"] = timed(lambda: explore.topk_init(probs, 3, rows))
     return out
 
 

@@ -357,6 +357,60 @@ gs_status gs_candidate_poses(int n_positions, const float *positions, int n_dirs
 int64_t gs_candidate_positions(int64_t n_voxels, const float *centres, float step, int n_heights,
                                const float *heights, float band, float *out, int64_t capacity);
 
+/* Sparse semantic representation, initialisation (Sec. 3.1 "Sparse Semantic
+ * Representation"): for each of n new Gaussians, the k classes of highest
+ * probability in its observed distribution, row rows[i] of probs
+ * ([*][m] device array; rows NULL: row i), written as ids [n][k] (int32,
+ * descending probability, the lower class id first on ties, NaN ranked
+ * below every number) and w [n][k] (the probabilities as observed, not
+ * renormalised).  1 <= k <= min(m, 16).  Row indices are the caller's to
+ * keep in range. */
+gs_status gs_topk_init(int64_t n, int m, int k, const float *probs, const int64_t *rows, int32_t *ids, float *w,
+                       gs_stream_t stream);
+
+/* Update of the sparse representation from a new observation with the ids
+ * fixed: w[i][l] = probs[rows[i]][ids[i][l]] (entries whose id is outside
+ * [0, m) are left unchanged). */
+gs_status gs_topk_gather(int64_t n, int m, int k, const float *probs, const int64_t *rows, const int32_t *ids,
+                         float *w, gs_stream_t stream);
+
+/* Exploration Map (Sec. 3.2, 5 cm voxels in the paper): a voxel grid with
+ * origin (world metres, the corner of voxel (0, 0, 0)), voxel edge length
+ * and size; voxel (x, y, z) has linear index (z ny + y) nx + x. */
+typedef struct {
+  float origin[3];
+  float voxel;
+  int32_t nx, ny, nz;
+} gs_voxel_grid;
+
+/* uint32 words of a grid's state array (2 bits per voxel, 16 per word: bit
+ * 2j seen free, bit 2j + 1 seen occupied); -1 for an invalid grid.  A new
+ * map is all zero (unknown). */
+int64_t gs_voxel_words(const gs_voxel_grid *grid);
+
+/* uint32 words of the scratch gs_voxel_new_free needs; -1 if invalid. */
+int64_t gs_voxel_scratch_words(const gs_voxel_grid *grid);
+
+/* Updates the state (device, gs_voxel_words words) from one depth frame
+ * (device [height][width] float, camera-space z as rendered by
+ * gs_render_fwd) seen by cam: for every stride-th column and row, the
+ * segment from the camera centre to the back-projected point marks every
+ * voxel it passes free and the voxel holding the point occupied (only bits
+ * are set: the result does not depend on the order of the rays).  Depths
+ * above max_depth are cut at max_depth and mark nothing occupied; depths
+ * that are not positive and finite are skipped.  Parts of a segment outside
+ * the grid are ignored. */
+gs_status gs_voxel_update(const gs_voxel_grid *grid, uint32_t *state, const float *depth, const gs_camera *cam,
+                          int stride, float max_depth, gs_stream_t stream);
+
+/* The voxels newly freed between two states (free and not occupied in cur,
+ * unknown in prev): their centres written in ascending voxel index to
+ * centres (device [capacity][3]), their number (which may exceed capacity)
+ * to *count (device uint32).  scratch: device, gs_voxel_scratch_words
+ * words. */
+gs_status gs_voxel_new_free(const gs_voxel_grid *grid, const uint32_t *prev, const uint32_t *cur, uint32_t *scratch,
+                            float *centres, int64_t capacity, uint32_t *count, gs_stream_t stream);
+
 /* Bytes of the fixed device scratch array used by gs_render_fwd_noalloc. */
 #define GS_NOALLOC_SCRATCH_BYTES (32u << 20)
 

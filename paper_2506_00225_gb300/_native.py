@@ -18,7 +18,8 @@ GS_MAPPING_LOSS_PARTIALS = 2048
 EXPORTS = ["gs_workspace_size", "gs_workspace_layout", "gs_project", "gs_bin_sort", "gs_render_fwd",
            "gs_render_bwd", "gs_render_fwd_l1", "gs_render_bwd_l1", "gs_render_fwd_dense", "gs_render_fwd_objective",
            "gs_render_bwd_objective", "gs_render_candidates", "gs_l1_loss", "gs_mapping_loss", "gs_render_fwd_noalloc",
-           "gs_score_candidates", "gs_candidate_poses", "gs_candidate_positions", "gs_read_counters",
+           "gs_score_candidates", "gs_candidate_poses", "gs_candidate_positions", "gs_topk_init", "gs_topk_gather",
+           "gs_voxel_words", "gs_voxel_scratch_words", "gs_voxel_update", "gs_voxel_new_free", "gs_read_counters",
            "gs_status_string"]
 
 
@@ -38,6 +39,11 @@ class GsConfig(ctypes.Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("sem_detach_geometry", c_int32), ("px_per_thread", c_int32),
                 ("record_capacity", c_int64), ("pair_capacity", c_int64), ("recompute_bwd", c_int32),
                 ("spin_limit", c_int32)]
+
+
+class GsVoxelGrid(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_float * 3), ("voxel", ctypes.c_float), ("nx", c_int32), ("ny", c_int32),
+                ("nz", c_int32)]
 
 
 class GsCounters(ctypes.Structure):
@@ -86,6 +92,14 @@ _SIGS = {
                                           ctypes.c_float, ctypes.c_float, ctypes.c_float, P(GsCamera)]),
     "gs_candidate_positions": (c_int64, [c_int64, c_void_p, ctypes.c_float, ctypes.c_int, c_void_p, ctypes.c_float,
                                          c_void_p, c_int64]),
+    "gs_topk_init": (ctypes.c_int, [c_int64, ctypes.c_int, ctypes.c_int] + [c_void_p] * 4 + [c_void_p]),
+    "gs_topk_gather": (ctypes.c_int, [c_int64, ctypes.c_int, ctypes.c_int] + [c_void_p] * 4 + [c_void_p]),
+    "gs_voxel_words": (c_int64, [P(GsVoxelGrid)]),
+    "gs_voxel_scratch_words": (c_int64, [P(GsVoxelGrid)]),
+    "gs_voxel_update": (ctypes.c_int, [P(GsVoxelGrid), c_void_p, c_void_p, P(GsCamera), ctypes.c_int, ctypes.c_float,
+                                       c_void_p]),
+    "gs_voxel_new_free": (ctypes.c_int, [P(GsVoxelGrid), c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p,
+                                         c_void_p]),
     "gs_read_counters": (ctypes.c_int, [c_void_p, P(GsCounters), c_void_p]),
     "gs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }

@@ -33,6 +33,8 @@ SOURCES = {
     "render_objective.cu": [],
     "render_dense.cu": [],
     "explore.cu": [],
+    "topk.cu": [],
+    "voxel.cu": ["-fmad=false"],
     "api.cu": [],
     "noalloc.cu": [],
 }

@@ -85,3 +85,101 @@ def next_best_view(rast, g, cams: list[Camera], current_position, prune_frac: fl
     cur = torch.tensor(np.asarray(current_position, np.float32), device=dev)
     scores, keep, best = score_candidates(sums, npix, pos, cur, prune_frac)
     return sums, scores, keep, best
+
+
+# ---------------------------------------------------------------------------
+# sparse semantic representation (Sec. 3.1): top-k initialisation, updates
+# ---------------------------------------------------------------------------
+
+def topk_init(probs: torch.Tensor, k: int, rows: torch.Tensor | None = None):
+    """Top-k (ids int32 [n, k], weights float32 [n, k]) of the observed class
+    distributions: rows ``rows`` of ``probs`` [*, m] (all rows if None)."""
+    m = int(probs.shape[-1])
+    p = probs.reshape(-1, m).to(torch.float32).contiguous()
+    r = None if rows is None else rows.to(device=p.device, dtype=torch.int64).contiguous()
+    n = p.shape[0] if r is None else r.numel()
+    ids = torch.empty((n, k), dtype=torch.int32, device=p.device)
+    w = torch.empty((n, k), dtype=torch.float32, device=p.device)
+    N.check(N.load().gs_topk_init(n, m, int(k), _ptr(p), _ptr(r), _ptr(ids), _ptr(w),
+                                  ctypes.c_void_p(torch.cuda.current_stream(p.device).cuda_stream)), "gs_topk_init")
+    return ids, w
+
+
+def topk_gather(probs: torch.Tensor, ids: torch.Tensor, w: torch.Tensor, rows: torch.Tensor | None = None):
+    """Updates w [n, k] in place with the observed probabilities at the fixed
+    ids [n, k]."""
+    m = int(probs.shape[-1])
+    p = probs.reshape(-1, m).to(torch.float32).contiguous()
+    r = None if rows is None else rows.to(device=p.device, dtype=torch.int64).contiguous()
+    if not (w.is_contiguous() and w.dtype == torch.float32):
+        raise ValueError("w must be a contiguous float32 tensor")
+    N.check(N.load().gs_topk_gather(int(ids.shape[0]), m, int(ids.shape[1]), _ptr(p), _ptr(r),
+                                    _ptr(ids.to(torch.int32).contiguous()), _ptr(w),
+                                    ctypes.c_void_p(torch.cuda.current_stream(p.device).cuda_stream)),
+            "gs_topk_gather")
+    return w
+
+
+# ---------------------------------------------------------------------------
+# Exploration Map (Sec. 3.2): voxel occupancy from depth, newly freed voxels
+# ---------------------------------------------------------------------------
+
+class VoxelMap:
+    """Voxel occupancy grid on the device (2 bits per voxel).  ``update``
+    integrates one depth frame and returns the centres of the voxels it newly
+    freed (device float32 [c, 3]) and their count."""
+
+    def __init__(self, origin, voxel: float, dims, device=None):
+        self.grid = N.GsVoxelGrid()
+        for i in range(3):
+            self.grid.origin[i] = float(origin[i])
+        self.grid.voxel = float(voxel)
+        self.grid.nx, self.grid.ny, self.grid.nz = (int(d) for d in dims)
+        lib = N.load()
+        words = lib.gs_voxel_words(ctypes.byref(self.grid))
+        if words < 0:
+            raise ValueError("invalid voxel grid")
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.state = torch.zeros(words, dtype=torch.int32, device=self.device)
+        self.prev = torch.zeros_like(self.state)
+        self.scratch = torch.empty(lib.gs_voxel_scratch_words(ctypes.byref(self.grid)), dtype=torch.int32,
+                                   device=self.device)
+        self.count = torch.zeros(1, dtype=torch.int32, device=self.device)
+
+    def integrate(self, depth: torch.Tensor, cam: Camera, stride: int = 1, max_depth: float = 10.0):
+        """Sets the free / occupied bits seen in one depth frame."""
+        from .raster import cameras_array
+        d = depth.to(torch.float32).contiguous()
+        N.check(N.load().gs_voxel_update(ctypes.byref(self.grid), _ptr(self.state), _ptr(d), cameras_array([cam]),
+                                         int(stride), float(max_depth),
+                                         ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)),
+                "gs_voxel_update")
+
+    def new_free(self, capacity: int):
+        """Centres of the voxels free now and unknown at the last snapshot
+        (at most ``capacity`` written), and their total count (device)."""
+        out = torch.empty((max(1, capacity), 3), dtype=torch.float32, device=self.device)
+        N.check(N.load().gs_voxel_new_free(ctypes.byref(self.grid), _ptr(self.prev), _ptr(self.state),
+                                           _ptr(self.scratch), _ptr(out), int(capacity), _ptr(self.count),
+                                           ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)),
+                "gs_voxel_new_free")
+        return out, self.count
+
+    def snapshot(self):
+        self.prev.copy_(self.state)
+
+    def update(self, depth: torch.Tensor, cam: Camera, stride: int = 1, max_depth: float = 10.0,
+               capacity: int = 1 << 16):
+        """snapshot, integrate, and the newly freed voxels."""
+        self.snapshot()
+        self.integrate(depth, cam, stride, max_depth)
+        return self.new_free(capacity)
+
+    def states(self) -> np.ndarray:
+        """Per-voxel state [nz, ny, nx] uint8 on the host: 0 unknown, 1 free,
+        2 occupied."""
+        w = self.state.cpu().numpy().view(np.uint32)
+        bits = (w[:, None] >> (2 * np.arange(16, dtype=np.uint32))[None, :]) & 3
+        st = bits.reshape(-1)[: self.grid.nx * self.grid.ny * self.grid.nz]
+        out = np.where(st & 2, 2, np.where(st & 1, 1, 0)).astype(np.uint8)
+        return out.reshape(self.grid.nz, self.grid.ny, self.grid.nx)

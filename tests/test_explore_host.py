@@ -72,3 +72,26 @@ def test_score_argument_checks_on_host(lib):
     assert lib.gs_score_candidates(3, None, fake, fake, fake, 0.005, fake, fake, fake, None) == N.GS_ERR_ARG
     assert lib.gs_score_candidates(3, fake, fake, fake, fake, 1.5, fake, fake, fake, None) == N.GS_ERR_ARG
     assert lib.gs_score_candidates(3, fake, fake, fake, fake, float("nan"), fake, fake, fake, None) == N.GS_ERR_ARG
+
+
+def test_topk_and_voxel_argument_checks_on_host(lib):
+    fake = ctypes.c_void_p(1 << 40)  # never dereferenced: every call returns before GPU work
+    assert lib.gs_topk_init(10, 5, 6, fake, None, fake, fake, None) == N.GS_ERR_ARG   # k > m
+    assert lib.gs_topk_init(10, 40, 17, fake, None, fake, fake, None) == N.GS_ERR_ARG  # k > 16
+    assert lib.gs_topk_init(10, 40, 3, None, None, fake, fake, None) == N.GS_ERR_ARG
+    assert lib.gs_topk_init(0, 40, 3, None, None, None, None, None) == N.GS_OK          # nothing to do
+    assert lib.gs_topk_gather(10, 40, 0, fake, None, fake, fake, None) == N.GS_ERR_ARG
+    g = N.GsVoxelGrid()
+    g.voxel, g.nx, g.ny, g.nz = 0.05, 100, 80, 40
+    assert lib.gs_voxel_words(ctypes.byref(g)) == (100 * 80 * 40 + 15) // 16
+    assert lib.gs_voxel_scratch_words(ctypes.byref(g)) == ((100 * 80 * 40 + 15) // 16 + 2047) // 2048 + 1
+    cam = (N.GsCamera * 1)()
+    cam[0].width, cam[0].height, cam[0].fx, cam[0].fy = 8, 6, 5.0, 5.0
+    assert lib.gs_voxel_update(ctypes.byref(g), fake, fake, cam, 0, 5.0, None) == N.GS_ERR_ARG
+    assert lib.gs_voxel_update(ctypes.byref(g), fake, fake, cam, 1, 0.0, None) == N.GS_ERR_ARG
+    assert lib.gs_voxel_new_free(ctypes.byref(g), fake, fake, fake, None, 5, fake, None) == N.GS_ERR_ARG
+    bad = N.GsVoxelGrid()
+    bad.voxel, bad.nx, bad.ny, bad.nz = 0.0, 10, 10, 10
+    assert lib.gs_voxel_words(ctypes.byref(bad)) == -1
+    bad.voxel, bad.nx = 0.05, 0
+    assert lib.gs_voxel_words(ctypes.byref(bad)) == -1

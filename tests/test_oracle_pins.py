@@ -613,3 +613,89 @@ def test_candidate_positions_closed_form():
     np.testing.assert_allclose(p, [[0, 0, 1.5], [1, 0, 1.5], [3, 1, 1.5]], atol=1e-7)
     p2 = ex.candidate_positions(centres, 0.5, [0.8, 1.5], 0.1)
     assert len(p2) == 5 and set(np.round(p2[:, 2], 5)) == {0.8, 1.5}
+
+
+# ---------------------------------------------------------------------------
+# sparse top-k initialisation / update (Sec. 3.1) and the Exploration Map
+# (Sec. 3.2)
+# ---------------------------------------------------------------------------
+
+def test_topk_hand_examples():
+    from oracle import sparse as sp
+    probs = np.array([[0.1, 0.5, 0.2, 0.2, 0.0],      # tie 0.2 / 0.2: lower id first
+                      [np.nan, 0.3, 0.3, 0.3, 0.1],   # NaN last; three-way tie by id
+                      [0.0, 0.0, 0.0, 0.0, 1.0]], np.float32)
+    ids, w = sp.topk_init(probs, 3)
+    assert ids.tolist() == [[1, 2, 3], [1, 2, 3], [4, 0, 1]]
+    np.testing.assert_array_equal(w, np.float32([[0.5, 0.2, 0.2], [0.3, 0.3, 0.3], [1.0, 0.0, 0.0]]))
+    # rows select observations; k = m returns a full descending order
+    ids, w = sp.topk_init(probs, 5, rows=[2, 0])
+    assert ids.tolist() == [[4, 0, 1, 2, 3], [1, 2, 3, 0, 4]]
+    # gather with fixed ids; an invalid id keeps its value
+    g = sp.topk_gather(probs, np.array([[4, 0, -1]], np.int32), np.array([[9.0, 9.0, 9.0]], np.float32), rows=[0])
+    np.testing.assert_array_equal(g, np.float32([[0.0, 0.1, 9.0]]))
+
+
+def test_topk_matches_python_selection():
+    from oracle import sparse as sp
+    rng = np.random.default_rng(0)
+    probs = rng.integers(0, 6, size=(50, 13)).astype(np.float32) / 5.0  # many ties
+    ids, w = sp.topk_init(probs, 4)
+    for i in range(50):
+        ref = sorted(range(13), key=lambda c: (-float(probs[i, c]), c))[:4]
+        assert ids[i].tolist() == ref
+        assert w[i].tolist() == [float(probs[i, c]) for c in ref]
+
+
+def _axis_cam(pos, yaw, w, h, f):
+    from paper_2506_00225_gb300 import scenes
+    return scenes.look_camera(pos, yaw, w, h, f)
+
+
+def test_voxel_axis_aligned_ray_closed_form():
+    """A 1x1 camera at the centre of voxel (0, 2, 2) looking along +x with
+    depth 5 voxels: voxels x = 0..4 free, x = 5 occupied (its centre holds the
+    point); cut at max_depth 3.2 voxels: x = 0..3 free, nothing occupied."""
+    from oracle import voxel as vx
+    vs = 0.25
+    cam = _axis_cam(((0.5) * vs, 2.5 * vs, 2.5 * vs), 0.0, 1, 1, 10.0)
+    depth = np.array([[5.0 * vs]], np.float32)
+    sure, maybe = vx.integrate((0, 0, 0), vs, (8, 5, 5), depth, cam)
+    st = vx.state_of(sure)
+    assert [int(st[2, 2, x]) for x in range(8)] == [1, 1, 1, 1, 1, 2, 0, 0]
+    assert st.sum() == 5 * 1 + 2 and (maybe == sure).all()
+    sure, _ = vx.integrate((0, 0, 0), vs, (8, 5, 5), depth, cam, max_depth=3.2 * vs)
+    assert [int(vx.state_of(sure)[2, 2, x]) for x in range(8)] == [1, 1, 1, 1, 0, 0, 0, 0]
+    # invalid depths mark nothing
+    for bad in (0.0, -1.0, np.nan, np.inf):
+        s_, m_ = vx.integrate((0, 0, 0), vs, (8, 5, 5), np.array([[bad]], np.float32), cam)
+        assert not s_.any() and not m_.any()
+
+
+def test_voxel_ray_entering_from_outside_and_sampling():
+    """A camera outside the grid: only the voxels inside count.  The decided
+    voxels agree with a dense sampling of the segment (a voxel sampled by the
+    segment is met; a voxel met by the segment beyond a margin is sampled)."""
+    from oracle import voxel as vx
+    vs = 0.2
+    cam = _axis_cam((-1.0, 0.53, 0.61), 17.0, 9, 7, 6.0)
+    rng = np.random.default_rng(3)
+    depth = rng.uniform(1.0, 4.0, size=(7, 9)).astype(np.float32)
+    sure, maybe = vx.integrate((0, 0, 0), vs, (12, 9, 6), depth, cam)
+    assert (sure & ~maybe).sum() == 0
+    # dense sampling of every segment (points strictly inside, away from p)
+    sampled = np.zeros_like(sure)
+    n = np.array([12, 9, 6])
+    for o, p, hit in vx.ray_points(depth, cam, 1, 10.0):
+        a, b = o / vs, p / vs
+        t = np.linspace(0.0, 1.0, 20001)[:-1]
+        pts = a[None] + t[:, None] * (b - a)[None]
+        c = np.floor(pts).astype(np.int64)
+        ok = np.all((c >= 0) & (c < n), axis=1)
+        end = np.floor(b).astype(np.int64)
+        c = c[ok & ~np.all(c == end, axis=1)]
+        sampled[c[:, 2], c[:, 1], c[:, 0]] |= 1
+    free_sure = (sure & 1).astype(bool)
+    assert free_sure.any()
+    assert (sampled.astype(bool) <= (maybe & 1).astype(bool)).all()  # every sampled voxel may be free
+    assert ((sure & 1).astype(bool) <= sampled.astype(bool) | (maybe & 2).astype(bool)).all()
