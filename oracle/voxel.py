@@ -101,7 +101,9 @@ def integrate(origin, voxel, dims, depth, cam, stride=1, max_depth=10.0):
         in_sure = _meets(a, b, lo + EPS, lo + 1.0 - EPS)
         in_maybe = _meets(a, b, lo - EPS, lo + 1.0 + EPS)
         is_end = np.all(cells == end, axis=1) if end_in else np.zeros(len(cells), bool)
-        fs = in_sure & ~is_end & (not end_tie)
+        # a point within EPS of a face leaves the cells around it undecided
+        near_end = np.all(np.abs(cells - end) <= 1, axis=1) if end_tie else np.zeros(len(cells), bool)
+        fs = in_sure & ~is_end & ~near_end
         fm = in_maybe & ~is_end
         np.bitwise_or.at(sure, (cells[fs, 2], cells[fs, 1], cells[fs, 0]), 1)
         np.bitwise_or.at(maybe, (cells[fm, 2], cells[fm, 1], cells[fm, 0]), 1)

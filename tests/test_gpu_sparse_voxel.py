@@ -5,8 +5,9 @@ gs_voxel_new_free) on the GPU against the oracle.
 Bars: top-k ids and weights bit-exact (a selection: integers and copied
 floats).  Voxel states: every bit the oracle decides is set exactly as
 decided, and bits the oracle leaves as near ties (segments grazing a voxel
-edge within 1e-3 voxel, points on a face) may go either way; at most 0.5 %
-of the touched voxels are such ties.  Newly freed voxels: bit-exact
+edge within 1e-3 voxel; the cells around a point within 1e-3 voxel of a
+face) may go either way; at most 1.5 % of the touched voxels are such ties
+(about 0.5 % in these cases).  Newly freed voxels: bit-exact
 against the oracle on seeded random grids."""
 import numpy as np
 import pytest
@@ -60,8 +61,10 @@ def test_topk_init_all_rows_and_gather():
 def _check_bits(gpu_bits, sure, maybe):
     assert ((sure & ~gpu_bits) == 0).all(), "a decided bit is missing"
     assert ((gpu_bits & ~maybe) == 0).all(), "a bit the oracle rules out is set"
+    # undecided: the 3x3x3 cells around the ~0.6 % of end points that lie
+    # within 1e-3 voxel of a face, and grazed edges
     ties = (sure != maybe)
-    assert ties.sum() <= max(3, int(0.005 * (maybe != 0).sum())), ties.sum()
+    assert ties.sum() <= max(3, int(0.015 * (maybe != 0).sum())), ties.sum()
 
 
 def _bits_of(vm):
