@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--cand-tile", default="16x16", help="WxH tile of the candidate kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 2M-Gaussian mapping and mixed-stream runs")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the objective, dense-comparator and exploration measurements")
     ap.add_argument("--only", choices=["candidates", "large", "objective", "dense", "explore"], default=None,
                     help="run only that part and print its dict (for profiling; not the benchmark line)")
     ap.add_argument("--tile", default=None, help="WxH: fixed tile shape instead of the autotuner's")
@@ -381,8 +383,8 @@ def main():
     un_ms = timed_graph(g_unfused, min(50, max(3, args.steps // 2)))
     un_total = max_over_ranks(sum(un_ms), world, dev) / len(un_ms)
 
-    objective = bench_objective(args, rast, g, cam, params, t_rgb, t_depth, t_sem, flush, world, dev,
-                                min(50, max(3, args.steps // 2)))
+    objective = None if args.no_extras else bench_objective(args, rast, g, cam, params, t_rgb, t_depth, t_sem,
+                                                            flush, world, dev, min(50, max(3, args.steps // 2)))
 
     # ---- roofline ---------------------------------------------------------------
     peaks = {}
@@ -472,8 +474,8 @@ def main():
     if st.status != 0:
         raise RuntimeError(f"device status {st.status} after the timed region")
 
-    dense_cmp = bench_dense(args, dev, flush, 20)
-    explore_steps = bench_explore(args, dev, flush)
+    dense_cmp = None if args.no_extras else bench_dense(args, dev, flush, 20)
+    explore_steps = None if args.no_extras else bench_explore(args, dev, flush)
 
     cand = None
     if not args.no_candidates:
