@@ -85,18 +85,19 @@ def integrate(origin, voxel, dims, depth, cam, stride=1, max_depth=10.0):
     for o, p, hit in ray_points(depth, cam, stride, max_depth):
         a = (o - org) / vs
         b = (p - org) / vs
-        lo_i = np.maximum(np.floor(np.minimum(a, b)).astype(np.int64) - 1, 0)
-        hi_i = np.minimum(np.floor(np.maximum(a, b)).astype(np.int64) + 1, n - 1)
         end_in = hit and bool(np.all(b >= 0) and np.all(b < n))
         end = np.floor(b).astype(np.int64)
         end_tie = hit and bool(np.any(np.abs(b - np.round(b)) < EPS)) and bool(np.all(b > -EPS)) and \
             bool(np.all(b < n + EPS))
-        if np.any(lo_i > hi_i):
-            cells = np.zeros((0, 3), np.int64)
-        else:
-            gx, gy, gz = np.meshgrid(np.arange(lo_i[0], hi_i[0] + 1), np.arange(lo_i[1], hi_i[1] + 1),
-                                     np.arange(lo_i[2], hi_i[2] + 1), indexing="ij")
-            cells = np.stack([gx.ravel(), gy.ravel(), gz.ravel()], axis=1)
+        # cells to test: the 3x3x3 neighbourhoods of points sampled along the
+        # segment every 1/4 voxel (a cube the segment meets holds a segment
+        # point within 1/8 voxel of a sample, so it lies in that sample's
+        # neighbourhood); each is then decided by the slab test below
+        ns = max(2, int(math.ceil(np.abs(b - a).max() * 4.0)) + 1)
+        smp = np.floor(a[None] + np.linspace(0.0, 1.0, ns)[:, None] * (b - a)[None]).astype(np.int64)
+        off = np.stack(np.meshgrid([-1, 0, 1], [-1, 0, 1], [-1, 0, 1], indexing="ij"), -1).reshape(-1, 3)
+        cells = np.unique((smp[:, None, :] + off[None]).reshape(-1, 3), axis=0)
+        cells = cells[np.all((cells >= 0) & (cells < n), axis=1)]
         lo = cells.astype(np.float64)
         in_sure = _meets(a, b, lo + EPS, lo + 1.0 - EPS)
         in_maybe = _meets(a, b, lo - EPS, lo + 1.0 + EPS)

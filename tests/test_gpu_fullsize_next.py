@@ -1,0 +1,160 @@
+"""Parity at the benchmark sizes for the rows past the core path:
+
+* the Sec. 3.1 objective on the 680x1200 frame of the 300k room: the GPU's
+  per-pixel gradients of gs_mapping_loss (on its own render) against the
+  oracle's (on the oracle's render of the same rows), every 20th row;
+  pixels whose decisions are near ties in either side's render (errors
+  within 1e-4 of 0, silhouette within 1e-4 of 0.99, entropy within 1e-4 of
+  ln k) or flagged by the oracle's render are excluded and counted;
+* the fused objective against the route through the maps on the full frame
+  (a property at any size: loss 1e-6 relative, gradients 1e-4);
+* the dense comparator on the 204k-visible 340x600x102 workload against the
+  oracle rendering the same Gaussians with k = M, every 20th row (1e-5);
+* the 5 cm Exploration Map of the 6x6x3 m room from a 680x1200 depth frame
+  of the room's walls (every 60th row and column of rays) against the
+  oracle's decided bits.
+
+Targets are seeded synthetic maps (colour U[0,1], depth U[0.5,4] m, class
+distributions peaked on two classes); the depth frame is the analytic
+distance to the room's walls."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import mapping_loss as ml
+from oracle import voxel as ovx
+from paper_2506_00225_gb300 import explore, raster, scenes
+
+pytestmark = pytest.mark.gpu
+
+ROWS = (7, None, 20)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_00225_gb300 import build
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def room300k():
+    return scenes.workload("room300k")
+
+
+def _targets(seed, H, W, m):
+    rng = np.random.default_rng(seed)
+    t_rgb = rng.uniform(size=(H, W, 3)).astype(np.float32)
+    t_depth = rng.uniform(0.5, 4.0, size=(H, W)).astype(np.float32)
+    q = np.zeros((H, W, m), np.float32)
+    cls = np.argsort(rng.uniform(size=(H, W, m)), axis=-1)[..., :2]
+    np.put_along_axis(q, cls, rng.dirichlet([1.0, 1.0], size=(H, W)).astype(np.float32), axis=-1)
+    return t_rgb, t_depth, q
+
+
+def _grad_close(a, b, rtol, name):
+    scale = np.abs(b).max() + 1e-30
+    err = np.abs(a - b) / (np.abs(b) + 0.01 * scale)
+    assert err.max() <= rtol, (name, err.max())
+
+
+def test_mapping_loss_gradients_fullsize_rows(room300k):
+    sc, cam = room300k["scene"], room300k["cams"][0]
+    H, W = cam.height, cam.width
+    t_rgb, t_depth, t_sem = _targets(5, H, W, sc.m)
+    g = raster.Gaussians.from_scene(sc)
+    rgb, depth, sil, sem = raster.Rasterizer().forward(g, cam)
+    tt = [torch.from_numpy(x).cuda() for x in (t_rgb, t_depth, t_sem)]
+    _, d_rgb, d_depth, d_sem = raster.mapping_loss_and_grads(rgb, depth, sil, sem, *tt, sc.k)
+    ys = np.arange(ROWS[0], H, ROWS[2])
+    ref = oracle.render(sc, cam, prec="f32", rows=(ROWS[0], H, ROWS[2]))
+    r_rgb, r_depth, r_sil, r_sem = (ref[n][ys] for n in ("rgb", "depth", "sil", "sem"))
+    _, o_rgb, o_depth, o_sem = ml.mapping_loss(r_rgb, r_depth, r_sil, r_sem, t_rgb[ys], t_depth[ys], t_sem[ys], sc.k)
+    # pixels whose mask or sign decisions are near ties, or flagged by the oracle
+    q = t_sem[ys].astype(np.float64)
+    h = -np.where(q > 0, q * np.log(np.where(q > 0, q, 1.0)), 0.0).sum(-1)
+    tie = ((ref["flag"][ys] != 0) | (np.abs(r_sil - 0.99) < 1e-4) | (np.abs(h - math.log(sc.k)) < 1e-4)
+           | (np.abs(r_depth - t_depth[ys]) < 1e-4) | (np.abs(r_rgb - t_rgb[ys]).min(-1) < 1e-4))
+    ok = ~tie
+    assert tie.sum() <= max(5, tie.size // 200), tie.sum()
+    np.testing.assert_array_equal(d_rgb.cpu().numpy()[ys][ok], o_rgb[ok].astype(np.float32))
+    np.testing.assert_array_equal(d_depth.cpu().numpy()[ys][ok], o_depth[ok].astype(np.float32))
+    # class gradients: where the rendered class has mass (the Hellinger
+    # derivative grows without bound as P_m -> 0), within 1e-3 of the largest
+    ds = d_sem.cpu().numpy()[ys].astype(np.float64)
+    live = ok[..., None] & (r_sem > 1e-5)
+    assert np.isfinite(ds).all()
+    scale = np.abs(o_sem[live]).max()
+    assert np.abs(ds - o_sem)[live].max() <= 1e-3 * scale
+
+
+def test_fused_objective_fullsize_matches_maps(room300k):
+    sc, cam = room300k["scene"], room300k["cams"][0]
+    t = [torch.from_numpy(x).cuda() for x in _targets(6, cam.height, cam.width, sc.m)]
+    g = raster.Gaussians.from_scene(sc)
+    rast = raster.Rasterizer(sem_detach_geometry=True)
+    res = []
+    for fused in (True, False):
+        params = [x.clone().requires_grad_(True) for x in (g.means, g.scales, g.quats, g.opacity, g.rgb, g.sem_w)]
+        loss = raster.render_objective(rast, g, cam, *t, *params, fused=fused)
+        loss.backward()
+        torch.cuda.synchronize()
+        res.append((float(loss.detach()), [p.grad.cpu().numpy() for p in params]))
+    (lf, gf), (lu, gu) = res
+    assert abs(lf - lu) <= 1e-6 * abs(lu)
+    for name, a, b in zip(["means", "scales", "quats", "opacity", "rgb", "sem_w"], gf, gu):
+        _grad_close(a, b, 1e-4, name)
+    assert np.abs(gf[5]).max() > 0
+
+
+def test_dense_comparator_fullsize_rows():
+    w = scenes.workload("dense204k")
+    sc, cam, dense = w["scene"], w["cams"][0], w["sem_dense"]
+    g = raster.Gaussians.from_scene(sc)
+    out = raster.Rasterizer().forward_dense(g, cam, torch.from_numpy(dense).cuda())
+    ys = np.arange(ROWS[0], cam.height, ROWS[2])
+    ref = oracle.render(scenes.dense_as_sparse(sc, dense), cam, prec="f32", rows=(ROWS[0], cam.height, ROWS[2]))
+    ok = ref["flag"][ys] == 0
+    assert (~ok).sum() <= max(3, ok.size // 1000)
+    for name, x in zip(["rgb", "depth", "sil", "sem"], out):
+        err = np.abs(x.cpu().numpy()[ys] - ref[name][ys])
+        if err.ndim == 3:
+            err = err.max(-1)
+        assert err[ok].max() <= 1e-5, (name, err[ok].max())
+
+
+def _wall_depth(cam, lo, hi):
+    """Camera-space z of the first wall of the box [lo, hi] hit by each
+    pixel's ray (the camera inside the box)."""
+    w2c = np.asarray(cam.w2c, np.float64)
+    r, c0 = w2c[:, :3], -w2c[:, :3].T @ w2c[:, 3]
+    u, v = np.meshgrid(np.arange(cam.width) + 0.5, np.arange(cam.height) + 0.5)
+    dc = np.stack([(u - cam.cx) / cam.fx, (v - cam.cy) / cam.fy, np.ones_like(u)], -1)  # z = 1 in the camera
+    dw = dc @ r  # world direction per unit camera z
+    t = np.full(u.shape, np.inf)
+    for k in range(3):
+        with np.errstate(divide="ignore", invalid="ignore"):
+            for plane in (lo[k], hi[k]):
+                tk = (plane - c0[k]) / dw[..., k]
+                t = np.where((tk > 0) & (tk < t), tk, t)
+    return t.astype(np.float32)
+
+
+def test_exploration_map_fullsize_ray_subset(room300k):
+    cam = room300k["cams"][0]
+    depth = _wall_depth(cam, (0.0, 0.0, 0.0), (6.0, 6.0, 3.0))
+    origin, vs, dims = (0.0, 0.0, 0.0), 0.05, (120, 120, 60)
+    vm = explore.VoxelMap(origin, vs, dims)
+    vm.integrate(torch.from_numpy(depth).cuda(), cam, stride=60, max_depth=10.0)
+    torch.cuda.synchronize()
+    w = vm.state.cpu().numpy().view(np.uint32)
+    bits = ((w[:, None] >> (2 * np.arange(16, dtype=np.uint32))[None, :]) & 3).reshape(-1)
+    bits = bits[: 120 * 120 * 60].astype(np.uint8).reshape(60, 120, 120)
+    sure, maybe = ovx.integrate(origin, vs, dims, depth, cam, stride=60, max_depth=10.0)
+    assert ((sure & ~bits) == 0).all() and ((bits & ~maybe) == 0).all()
+    assert (sure != maybe).sum() <= max(3, int(0.015 * (maybe != 0).sum()))
+    assert (bits & 2).sum() > 100 and (bits & 1).sum() > 1000
