@@ -10,9 +10,9 @@
   (a property at any size: loss 1e-6 relative, gradients 1e-4);
 * the dense comparator on the 204k-visible 340x600x102 workload against the
   oracle rendering the same Gaussians with k = M, every 20th row (1e-5);
-* the 5 cm Exploration Map of the 6x6x3 m room from a 680x1200 depth frame
-  of the room's walls (every 60th row and column of rays) against the
-  oracle's decided bits.
+* the 5 cm Exploration Map around the 6x6x3 m room (grid shifted by a
+  fraction of a voxel) from a 680x1200 depth frame of the room's walls
+  (every 60th row and column of rays) against the oracle's decided bits.
 
 Targets are seeded synthetic maps (colour U[0,1], depth U[0.5,4] m, class
 distributions peaked on two classes); the depth frame is the analytic
@@ -74,6 +74,7 @@ def test_mapping_loss_gradients_fullsize_rows(room300k):
     ref = oracle.render(sc, cam, prec="f32", rows=(ROWS[0], H, ROWS[2]))
     r_rgb, r_depth, r_sil, r_sem = (ref[n][ys] for n in ("rgb", "depth", "sil", "sem"))
     _, o_rgb, o_depth, o_sem = ml.mapping_loss(r_rgb, r_depth, r_sil, r_sem, t_rgb[ys], t_depth[ys], t_sem[ys], sc.k)
+    o_sem = o_sem * (ys.size / H)  # the oracle averaged the semantic term over the sampled rows only
     # pixels whose mask or sign decisions are near ties, or flagged by the oracle
     q = t_sem[ys].astype(np.float64)
     h = -np.where(q > 0, q * np.log(np.where(q > 0, q, 1.0)), 0.0).sum(-1)
@@ -86,7 +87,7 @@ def test_mapping_loss_gradients_fullsize_rows(room300k):
     # class gradients: where the rendered class has mass (the Hellinger
     # derivative grows without bound as P_m -> 0), within 1e-3 of the largest
     ds = d_sem.cpu().numpy()[ys].astype(np.float64)
-    live = ok[..., None] & (r_sem > 1e-5)
+    live = ok[..., None] & (r_sem > 1e-3)
     assert np.isfinite(ds).all()
     scale = np.abs(o_sem[live]).max()
     assert np.abs(ds - o_sem)[live].max() <= 1e-3 * scale
@@ -147,13 +148,15 @@ def _wall_depth(cam, lo, hi):
 def test_exploration_map_fullsize_ray_subset(room300k):
     cam = room300k["cams"][0]
     depth = _wall_depth(cam, (0.0, 0.0, 0.0), (6.0, 6.0, 3.0))
-    origin, vs, dims = (0.0, 0.0, 0.0), 0.05, (120, 120, 60)
+    # a grid around the room, shifted by a fraction of a voxel so that the
+    # walls do not lie on voxel faces (a point on a face is a near tie)
+    origin, vs, dims = (-0.3123, -0.2877, -0.2211), 0.05, (132, 132, 72)
     vm = explore.VoxelMap(origin, vs, dims)
     vm.integrate(torch.from_numpy(depth).cuda(), cam, stride=60, max_depth=10.0)
     torch.cuda.synchronize()
     w = vm.state.cpu().numpy().view(np.uint32)
     bits = ((w[:, None] >> (2 * np.arange(16, dtype=np.uint32))[None, :]) & 3).reshape(-1)
-    bits = bits[: 120 * 120 * 60].astype(np.uint8).reshape(60, 120, 120)
+    bits = bits[: 132 * 132 * 72].astype(np.uint8).reshape(72, 132, 132)
     sure, maybe = ovx.integrate(origin, vs, dims, depth, cam, stride=60, max_depth=10.0)
     assert ((sure & ~bits) == 0).all() and ((bits & ~maybe) == 0).all()
     assert (sure != maybe).sum() <= max(3, int(0.015 * (maybe != 0).sum()))
