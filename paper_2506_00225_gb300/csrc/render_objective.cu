@@ -134,80 +134,57 @@ __global__ void __launch_bounds__(TW *TH, 2) k_sem_objective(FwdArgs a, float lo
   walk(true, [&](int, bool, float w, const int2 *e) { scatter_classes<K>(myP, e, k, 0, m, w); });
 
   // (2) per pixel: the semantic term, and d term / d P (over the pixel
-  // count) in place of P.  Up to 128 classes a warp takes kG pixels at a
-  // time with their classes in registers, so that their loads and shuffle
-  // chains overlap; beyond, one pixel at a time with a second read.
+  // count) in place of P.  Thread per pixel: its own row (shared memory,
+  // odd stride: conflict-free) and its target row (global, two classes per
+  // 8-byte load when the row allows; consecutive classes share a 32-byte
+  // sector, so most reads hit L1).  A class where both distributions are 0
+  // adds exactly nothing to the sums and has a zero gradient (its row entry
+  // is already 0), so only the others do the arithmetic.  Pixels outside
+  // the entropy mask keep their row (pass 3 skips them).
   double term_sum = 0.0;
-  if (m <= 32 * kObjMI) {
-    constexpr int kG = 4;
-    for (int p0 = (int)warp * kG; p0 < NPIX; p0 += WARPS * kG) {
-      float qv[kG][kObjMI], pv[kG][kObjMI], st[kG][5];
-      ClassRoots rt[kG][kObjMI];
-      float *row[kG];
-      bool ok[kG];
+  {
+    const float *q = a.t_sem + (inside ? ((size_t)py * a.width + px) * m : 0);
+    const bool pairs = (reinterpret_cast<uintptr_t>(q) & 7) == 0;
+    const int m2 = pairs ? (m & ~3) : 0;  // classes read as 8-byte pairs, four per step
+    float st[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (inside) {
+      for (int c = 0; c < m2; c += 4) {
+        const float2 q0 = __ldg(reinterpret_cast<const float2 *>(q + c));
+        const float2 q1 = __ldg(reinterpret_cast<const float2 *>(q + c + 2));
+        const float qv[4] = {q0.x, q0.y, q1.x, q1.y};
 #pragma unroll
-      for (int g = 0; g < kG; ++g) {
-        const int p = p0 + g;
-        const int qx = ox + p % TW, qy = oy + p / TW;
-        ok[g] = qx < a.width && qy < a.height;
-        row[g] = sP + FP::thread_of(p) * a.mstride;
-        const float *q = a.t_sem + (ok[g] ? ((size_t)qy * a.width + qx) * m : 0);
-#pragma unroll
-        for (int i = 0; i < kObjMI; ++i) {
-          const int c = (int)lane + 32 * i;
-          const bool in = ok[g] && c < m;
-          qv[g][i] = in ? __ldg(q + c) : 0.f;
-          pv[g][i] = in ? row[g][c] : 0.f;
+        for (int u = 0; u < 4; ++u) {
+          const float pv = myP[c + u];
+          if (qv[u] != 0.f || pv != 0.f) class_sums(qv[u], pv, st);
         }
       }
-#pragma unroll
-      for (int g = 0; g < kG; ++g) {
-#pragma unroll
-        for (int j = 0; j < 5; ++j) st[g][j] = 0.f;
-#pragma unroll
-        for (int i = 0; i < kObjMI; ++i) rt[g][i] = class_sums(qv[g][i], pv[g][i], st[g]);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int g = 0; g < kG; ++g)
-#pragma unroll
-          for (int j = 0; j < 5; ++j) st[g][j] += __shfl_xor_sync(0xffffffffu, st[g][j], o);
-#pragma unroll
-      for (int g = 0; g < kG; ++g) {
-        const PixelTerm t = pixel_term(st[g], ok[g], log_k);
-        if (lane == 0) {
-          if (t.keep) term_sum += (double)t.value;
-          s_keep[p0 + g] = t.keep;
-        }
-#pragma unroll
-        for (int i = 0; i < kObjMI; ++i) {
-          const int c = (int)lane + 32 * i;
-          if (c < m) row[g][c] = t.keep ? class_grad(qv[g][i], pv[g][i], rt[g][i], t, inv_n) : 0.f;
-        }
+      for (int c = m2; c < m; ++c) {
+        const float qv = __ldg(q + c), pv = myP[c];
+        if (qv != 0.f || pv != 0.f) class_sums(qv, pv, st);
       }
     }
-  } else {
-    for (int p = (int)warp; p < NPIX; p += WARPS) {
-      float *row = sP + FP::thread_of(p) * a.mstride;
-      const int qx = ox + p % TW, qy = oy + p / TW;
-      const bool ok = qx < a.width && qy < a.height;  // warp-uniform
-      const float *q = a.t_sem + (ok ? ((size_t)qy * a.width + qx) * m : 0);
-      float st[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-      if (ok)
-        for (int c = (int)lane; c < m; c += 32) class_sums(__ldg(q + c), row[c], st);
-      warp_sum5(st);
-      const PixelTerm t = pixel_term(st, ok, log_k);
-      if (lane == 0) {
-        if (t.keep) term_sum += (double)t.value;
-        s_keep[p] = t.keep;
+    const PixelTerm t = pixel_term(st, inside, log_k);
+    s_keep[lp] = t.keep;
+    if (t.keep) {
+      term_sum = (double)t.value;
+      for (int c = 0; c < m2; c += 4) {
+        const float2 q0 = __ldg(reinterpret_cast<const float2 *>(q + c));
+        const float2 q1 = __ldg(reinterpret_cast<const float2 *>(q + c + 2));
+        const float qv[4] = {q0.x, q0.y, q1.x, q1.y};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float pv = myP[c + u];
+          if (qv[u] != 0.f || pv != 0.f) myP[c + u] = class_grad(qv[u], pv, class_roots(qv[u], pv), t, inv_n);
+        }
       }
-      for (int c = (int)lane; c < m; c += 32) {
-        const float qv = ok ? __ldg(q + c) : 0.f, pv = row[c];
-        row[c] = t.keep ? class_grad(qv, pv, class_roots(qv, pv), t, inv_n) : 0.f;
+      for (int c = m2; c < m; ++c) {
+        const float qv = __ldg(q + c), pv = myP[c];
+        if (qv != 0.f || pv != 0.f) myP[c] = class_grad(qv, pv, class_roots(qv, pv), t, inv_n);
       }
     }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) term_sum += __shfl_xor_sync(0xffffffffu, term_sum, o);
   if (lane == 0) red[warp] = term_sum;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -235,17 +212,37 @@ __global__ void __launch_bounds__(TW *TH, 2) k_sem_objective(FwdArgs a, float lo
       }
       return;
     }
-    float v[16];
+    if constexpr (K > 0 && K <= 4) {
+      // few entries: K independent butterfly sums (5K shuffles) beat the
+      // 16-slot transposed reduction
+      float v[K];
 #pragma unroll
-    for (int l = 0; l < 16; ++l) v[l] = 0.f;
+      for (int l = 0; l < K; ++l) {
+        const int2 en = e[l];
+        v[l] = (unsigned)en.x < (unsigned)m ? w * myP[en.x] : 0.f;
+      }
 #pragma unroll
-    for (int l = 0; l < (K > 0 ? K : 16); ++l) {
-      if (K == 0 && l >= nl) break;
-      const int2 en = e[l];
-      if ((unsigned)en.x < (unsigned)m) v[l] = w * myP[en.x];
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int l = 0; l < K; ++l) v[l] += __shfl_xor_sync(0xffffffffu, v[l], o);
+      float tot = v[0];
+#pragma unroll
+      for (int l = 1; l < K; ++l)
+        if ((int)lane == l) tot = v[l];
+      if ((int)lane < K && tot != 0.f) atomicAdd(a.semg + (size_t)gid * k + lane, tot);
+    } else {
+      float v[16];
+#pragma unroll
+      for (int l = 0; l < 16; ++l) v[l] = 0.f;
+#pragma unroll
+      for (int l = 0; l < (K > 0 ? K : 16); ++l) {
+        if (K == 0 && l >= nl) break;
+        const int2 en = e[l];
+        if ((unsigned)en.x < (unsigned)m) v[l] = w * myP[en.x];
+      }
+      const float tot = warp_reduce_scatter<16>(v);
+      if ((int)lane < nl && tot != 0.f) atomicAdd(a.semg + (size_t)gid * k + lane, tot);
     }
-    const float tot = warp_reduce_scatter<16>(v);
-    if ((int)lane < nl && tot != 0.f) atomicAdd(a.semg + (size_t)gid * k + lane, tot);
   });
 }
 
