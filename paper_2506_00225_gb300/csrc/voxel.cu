@@ -4,7 +4,8 @@
 //
 // State: 2 bits per voxel packed 16 to a 32-bit word (bit 2j: seen free,
 // bit 2j+1: seen occupied; occupied wins).  An update only sets bits, with
-// atomicOr, so its result does not depend on the thread schedule.  Voxel
+// warp-aggregated atomicOr, so its result does not depend on the thread
+// schedule.  Voxel
 // (x, y, z) has linear index (z ny + y) nx + x.
 //
 // Update: one thread per sampled pixel (every stride-th column and row).
@@ -39,16 +40,16 @@ struct VoxArgs {
   float max_depth;
 };
 
-__device__ __forceinline__ uint32_t load_relaxed(const uint32_t *p) {
-  uint32_t v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
+// Sets one state bit of voxel vox.  The lanes of the warp that set bits of
+// the same word at this point are grouped (they usually are: neighbouring
+// pixels' rays pass the same voxels), their bits OR-ed, and one of them
+// issues a single atomicOr whose result is not used (no wait).
 __device__ __forceinline__ void set_bit(uint32_t *state, int64_t vox, uint32_t which) {
   const uint32_t bit = 1u << (2 * (uint32_t)(vox & 15) + which);
-  uint32_t *w = state + (vox >> 4);
-  if (!(load_relaxed(w) & bit)) atomicOr(w, bit);
+  const unsigned long long word = (unsigned long long)(vox >> 4);
+  const uint32_t grp = __match_any_sync(__activemask(), word);
+  const uint32_t bits = __reduce_or_sync(grp, bit);
+  if (lane_id() == (uint32_t)(__ffs(grp) - 1)) atomicOr(state + word, bits);
 }
 
 __global__ void __launch_bounds__(kVoxThreads) k_voxel_update(VoxArgs a, uint32_t *state, const float *depth) {
