@@ -48,6 +48,7 @@ struct Counters {
   uint32_t n_records;
   uint32_t n_pairs;
   uint32_t n_contrib;  // (pixel, Gaussian) contributions of the last forward render
+  uint32_t tiles_done; // tickets of the tile pass that finishes the loss (0 between launches)
 };
 
 // Host-computed workspace layout (offsets in bytes from the base pointer).

@@ -136,6 +136,7 @@ __global__ void k_setup_views(CamTable tab, int n_views, DevCam *cams, uint32_t 
     counters->n_records = 0u;
     counters->n_pairs = 0u;
     counters->n_contrib = 0u;
+    counters->tiles_done = 0u;
   }
 }
 

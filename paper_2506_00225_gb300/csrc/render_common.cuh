@@ -291,12 +291,52 @@ struct FwdArgs {
   uint32_t *codes;   // per pixel: (nonzero, negative) word pairs: head (rgb, depth bits), then nwc class words
   int nwc;           // class words per plane = ceil(m / 32)
   double *lpart;     // per tile: sum|d rgb|, sum|d depth|, sum|d sem|
+  float *loss;       // written by the last tile of the semantic pass (fused-loss modes)
+  double npix_d;     // pixels of the view
   Counters *counters;
   // contributor bitmasks (pass 1 writes, pass 2 and the adjoint read)
   const uint32_t *mask_off;
   uint32_t *masks;
   uint32_t mask_units;
 };
+
+// The fused-loss semantic passes end with this: every CTA has written its
+// tile's three sums; the CTA that takes the last ticket adds all tiles'
+// sums (a fixed order: deterministic) and writes the loss, then leaves the
+// ticket counter at 0 for the next launch.  Mean-L1 mode: rgb / (3 npix) +
+// depth / npix + sem / (npix m); Sec. 3.1 objective mode: 0.5 rgb + depth
+// (sums over the silhouette mask) + sem / npix.  No CTA waits on another.
+template <int THREADS>
+__device__ __forceinline__ void finish_loss(const FwdArgs &a, int objective) {
+  constexpr int WARPS = THREADS / 32;
+  __shared__ int s_last;
+  __shared__ double s_red[3][WARPS];
+  if (threadIdx.x == 0) {
+    __threadfence();  // this tile's sums before the ticket
+    s_last = atomicAdd(&a.counters->tiles_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double s[3] = {0.0, 0.0, 0.0};
+  for (uint32_t t = threadIdx.x; t < gridDim.x; t += THREADS)
+    for (int i = 0; i < 3; ++i) s[i] += __ldcg(a.lpart + 3 * (size_t)t + i);
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s[i] += __shfl_xor_sync(0xffffffffu, s[i], o);
+    if ((threadIdx.x & 31) == 0) s_red[i][threadIdx.x >> 5] = s[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t[3] = {0.0, 0.0, 0.0};
+    for (int w = 0; w < WARPS; ++w)
+      for (int i = 0; i < 3; ++i) t[i] += s_red[i][w];
+    const double l = objective ? 0.5 * t[0] + t[1] + t[2] / a.npix_d
+                               : t[0] / (3.0 * a.npix_d) + t[1] / a.npix_d + t[2] / (a.npix_d * a.m);
+    *a.loss = (float)l;
+    a.counters->tiles_done = 0u;
+  }
+}
 
 // Per-pixel sign-code layout of the fused L1 mode.
 __host__ __device__ inline int code_words(int nwc) { return 2 * (1 + nwc); }

@@ -413,6 +413,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_semantic(FwdArgs a) {
       for (int w = 0; w < WARPS; ++w) s += red[w];
       a.lpart[3 * (size_t)tile + 2] = s;
     }
+    finish_loss<THREADS>(a, 0);
   }
 }
 
@@ -545,9 +546,12 @@ cudaError_t launch_render_fwd_l1(const Layout &L, const WsPtrs &P, int pbuf, con
   if (grid == 0) return cudaSuccess;
   cudaError_t e = launch_mask_offsets(L, P, grid, s);
   if (e != cudaSuccess) return e;
+  a.loss = loss;
+  a.npix_d = (double)L.npix;
   e = dispatch_fwd<true>(L, a, grid, smem, acc, s);
   if (e != cudaSuccess) return e;
-  return launch_loss_final(P.lpart, grid, (double)L.npix, (double)sc.m, t_sem ? 1 : 0, 0, loss, s);
+  if (t_sem) return cudaSuccess;  // the semantic pass's last tile wrote the loss
+  return launch_loss_final(P.lpart, grid, (double)L.npix, (double)sc.m, 0, 0, loss, s);
 }
 
 cudaError_t launch_blend_objective(const Layout &L, const FwdArgs &a, int grid, cudaStream_t s) {

@@ -192,6 +192,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_sem_objective(FwdArgs a, float lo
     for (int w = 0; w < WARPS; ++w) s += red[w];
     a.lpart[3 * (size_t)tile + 2] = s;
   }
+  finish_loss<TW * TH>(a, 1);
 
   // (3) d(objective)/d(weight l of Gaussian g) = sum_p w_gp dP_p[id_gl]:
   // lanes hold their pixel's products, a transposed warp sum leaves the
@@ -325,6 +326,8 @@ cudaError_t launch_render_fwd_objective(const Layout &L, const WsPtrs &P, int pb
   if (e != cudaSuccess) return e;
   e = launch_blend_objective(L, a, grid, s);
   if (e != cudaSuccess) return e;
+  a.loss = loss;
+  a.npix_d = (double)L.npix;
   if (t_sem) {
     const float log_k = logf((float)sc.k), inv_n = 1.f / (float)L.npix;
     if (L.tile_w == 16 && L.tile_h == 16) e = dispatch_sem_objective<16, 16>(a, grid, smem, log_k, inv_n, s);
@@ -332,9 +335,9 @@ cudaError_t launch_render_fwd_objective(const Layout &L, const WsPtrs &P, int pb
     else if (L.tile_w == 8 && L.tile_h == 8) e = dispatch_sem_objective<8, 8>(a, grid, smem, log_k, inv_n, s);
     else if (L.tile_w == 32 && L.tile_h == 8) e = dispatch_sem_objective<32, 8>(a, grid, smem, log_k, inv_n, s);
     else e = cudaErrorInvalidConfiguration;
-    if (e != cudaSuccess) return e;
+    return e;  // the semantic pass's last tile wrote the loss
   }
-  return launch_loss_final(P.lpart, grid, (double)L.npix, (double)sc.m, t_sem ? 1 : 0, 1, loss, s);
+  return launch_loss_final(P.lpart, grid, (double)L.npix, (double)sc.m, 0, 1, loss, s);
 }
 
 cudaError_t launch_add_semg(const WsPtrs &P, const gs_scene &sc, const float *loss_scale, float *g_sem_w,

@@ -92,6 +92,21 @@ def cameras_array(cams):
     return arr
 
 
+def zero_grads(g: "Gaussians") -> dict:
+    """Zeroed gradient buffers for every parameter of ``g``, as views of one
+    allocation (one fill instead of six; quaternions first, so every view
+    starts 16-byte aligned for its row size)."""
+    shapes = dict(quats=tuple(g.quats.shape), means=tuple(g.means.shape), scales=tuple(g.scales.shape),
+                  rgb=tuple(g.rgb.shape), sem_w=tuple(g.sem_w.shape), opacity=tuple(g.opacity.shape))
+    sizes = {k: int(np.prod(v)) for k, v in shapes.items()}
+    flat = torch.zeros(sum(sizes.values()), dtype=torch.float32, device=g.means.device)
+    out, off = {}, 0
+    for k, shp in shapes.items():
+        out[k] = flat[off:off + sizes[k]].view(shp)
+        off += sizes[k]
+    return {k: out[k] for k in ("means", "scales", "quats", "opacity", "rgb", "sem_w")}
+
+
 def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
@@ -242,9 +257,7 @@ class Rasterizer:
             raise RuntimeError("backward before forward")
         sc, cams_arr, V, cfg = self._last
         if grads is None:
-            grads = dict(means=torch.zeros_like(g.means), scales=torch.zeros_like(g.scales),
-                         quats=torch.zeros_like(g.quats), opacity=torch.zeros_like(g.opacity),
-                         rgb=torch.zeros_like(g.rgb), sem_w=torch.zeros_like(g.sem_w))
+            grads = zero_grads(g)
         ws = ctypes.c_void_p(self.ws.data_ptr())
         self._mark("render_bwd")
         N.check(N.load().gs_render_bwd(ctypes.byref(sc), cams_arr, ctypes.byref(cfg), ws, _ptr(_f32(d_rgb)),
@@ -285,9 +298,7 @@ class Rasterizer:
             raise RuntimeError("backward before forward")
         sc, cams_arr, V, cfg = self._last
         if grads is None:
-            grads = dict(means=torch.zeros_like(g.means), scales=torch.zeros_like(g.scales),
-                         quats=torch.zeros_like(g.quats), opacity=torch.zeros_like(g.opacity),
-                         rgb=torch.zeros_like(g.rgb), sem_w=torch.zeros_like(g.sem_w))
+            grads = zero_grads(g)
         ws = ctypes.c_void_p(self.ws.data_ptr())
         ls = loss_scale.to(torch.float32).contiguous()
         self._mark("render_bwd")
@@ -333,9 +344,7 @@ class Rasterizer:
             raise RuntimeError("backward before forward")
         sc, cams_arr, V, cfg = self._last
         if grads is None:
-            grads = dict(means=torch.zeros_like(g.means), scales=torch.zeros_like(g.scales),
-                         quats=torch.zeros_like(g.quats), opacity=torch.zeros_like(g.opacity),
-                         rgb=torch.zeros_like(g.rgb), sem_w=torch.zeros_like(g.sem_w))
+            grads = zero_grads(g)
         ws = ctypes.c_void_p(self.ws.data_ptr())
         ls = loss_scale.to(torch.float32).contiguous()
         self._mark("render_bwd")
