@@ -116,25 +116,29 @@ __device__ __forceinline__ void stage_record(const RecPtrs &rec, uint32_t r, int
   }
 }
 
-// Lane masks of a staged record for every warp of a PPT = 1 tile: bit l of
-// masks[w] is set when lane l's pixel of warp w lies in the record's alpha
-// box (image pixels b; tile origin ox, oy).  A warp's lanes hold an 8 x 4
-// block, lane l at column l % 8 and row l / 8.
-template <int TW, int TH>
+// Lane masks of a staged record for every warp of a tile: bit l of
+// masks[w PPT + i] is set when lane l's i-th pixel of warp w lies in the
+// record's alpha box (image pixels b; tile origin ox, oy).  A warp's lanes
+// hold an 8 x 4 PPT block, lane l at column l % 8 and rows l / 8 + 4 i.
+template <int TW, int TH, int PPT = 1>
 __device__ __forceinline__ void lane_masks(short4 b, int ox, int oy, uint32_t *masks) {
-  using FP = Footprint<TW, TH, 1>;
+  using FP = Footprint<TW, TH, PPT>;
 #pragma unroll
   for (int w = 0; w < FP::kWarps; ++w) {
-    const int x0 = ox + (w % FP::kWX) * 8, y0 = oy + (w / FP::kWX) * 4;
-    const int cl = max((int)b.x - x0, 0), ch = min((int)b.y - x0, 7);
-    const int rl = max((int)b.z - y0, 0), rh = min((int)b.w - y0, 3);
-    uint32_t m = 0u;
-    if (cl <= ch && rl <= rh) {
-      const uint32_t cols = (0xffu >> (7 - ch)) & (0xffu << cl);
-      const uint32_t rows = (0xffffffffu >> (8 * (3 - rh))) & (0xffffffffu << (8 * rl));
-      m = (cols * 0x01010101u) & rows;
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+      // rows 4 i .. 4 i + 3 of warp w's block
+      const int x0 = ox + (w % FP::kWX) * 8, y0 = oy + (w / FP::kWX) * FP::kBH + 4 * i;
+      const int cl = max((int)b.x - x0, 0), ch = min((int)b.y - x0, 7);
+      const int rl = max((int)b.z - y0, 0), rh = min((int)b.w - y0, 3);
+      uint32_t m = 0u;
+      if (cl <= ch && rl <= rh) {
+        const uint32_t cols = (0xffu >> (7 - ch)) & (0xffu << cl);
+        const uint32_t rows = (0xffffffffu >> (8 * (3 - rh))) & (0xffffffffu << (8 * rl));
+        m = (cols * 0x01010101u) & rows;
+      }
+      masks[w * PPT + i] = m;
     }
-    masks[w] = m;
   }
 }
 
@@ -292,6 +296,7 @@ struct FwdArgs {
   int nwc;           // class words per plane = ceil(m / 32)
   double *lpart;     // per tile: sum|d rgb|, sum|d depth|, sum|d sem|
   float *loss;       // written by the last tile of the semantic pass (fused-loss modes)
+  int blend_ppt;     // pixels per thread of the blend pass (1 or 2)
   double npix_d;     // pixels of the view
   Counters *counters;
   // contributor bitmasks (pass 1 writes, pass 2 and the adjoint read)

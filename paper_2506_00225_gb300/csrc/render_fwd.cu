@@ -46,75 +46,110 @@ __global__ void k_tile_batches(const uint2 *__restrict__ ranges, uint32_t ntiles
   if (t < ntiles) units[t] = (ranges[t].y - ranges[t].x + kBatch - 1) / kBatch;
 }
 
-template <int TW, int TH, bool L1>
-__global__ void __launch_bounds__(TW *TH) k_blend(FwdArgs a) {
-  using FP = Footprint<TW, TH, 1>;
+template <int TW, int TH, bool L1, int PPT>
+__global__ void __launch_bounds__(TW *TH / PPT) k_blend(FwdArgs a) {
+  using FP = Footprint<TW, TH, PPT>;
   constexpr int THREADS = FP::kThreads;
   constexpr int WARPS = FP::kWarps;
   constexpr int NPIX = FP::kPix;
   extern __shared__ float4 smem4[];
   BatchSmem bs = batch_smem(smem4, 0);
   __shared__ float red[2][WARPS];
-  __shared__ uint32_t lmask[kBatch * WARPS];  // per staged Gaussian: its lanes of each warp
+  // per staged Gaussian, warp and pixel row group i: its lanes
+  __shared__ uint32_t lmask[kBatch * WARPS * PPT];
   if (a.counters->status & kStatusTimeout) return;  // the binning is incomplete
 
   const int tile = blockIdx.x;
   const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
   const int ox = tx * TW, oy = ty * TH;
   const uint2 rg = a.ranges[tile];
-  const int lx = FP::lx(), ly = FP::ly(0);
-  const int px = ox + lx, py = oy + ly;
-  const int lp = ly * TW + lx;
-  const bool inside = px < a.width && py < a.height;
-  const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+  const int lx = FP::lx();
+  const int px = ox + lx;
+  const float fpx = (float)px + 0.5f;
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t unit0 = a.masks ? a.mask_off[tile] : 0u;
 
-  float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, cd = 0.f;
-  uint32_t last = 0, ncontrib = 0;
-  bool done = !inside;
+  // PPT pixels per thread, one column, rows 4 apart: they share every
+  // staged load and the x offset of every Gaussian
+  int py[PPT], lp[PPT];
+  float fpy[PPT], T[PPT], cr[PPT], cg[PPT], cb[PPT], cd[PPT];
+  uint32_t last[PPT];
+  bool inside[PPT], done[PPT];
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    const int ly = FP::ly(i);
+    py[i] = oy + ly;
+    lp[i] = ly * TW + lx;
+    fpy[i] = (float)py[i] + 0.5f;
+    inside[i] = px < a.width && py[i] < a.height;
+    done[i] = !inside[i];
+    T[i] = 1.f; cr[i] = cg[i] = cb[i] = cd[i] = 0.f;
+    last[i] = 0;
+  }
+  uint32_t ncontrib = 0;
+  auto all_done = [&]() {
+    bool d = true;
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) d = d && done[i];
+    return d;
+  };
   uint32_t bi = 0;
   for (uint32_t b = rg.x; b < rg.y; b += kBatch, ++bi) {
     const int n = (int)min((uint32_t)kBatch, rg.y - b);
     __syncthreads();
     for (int t = threadIdx.x; t < n; t += THREADS) {
       const uint32_t r = a.pvals[b + t];
-      stage_record<TW, TH, 1>(a.rec, r, t, 0, ox, oy, bs, false, false);
-      lane_masks<TW, TH>(__ldg(a.rec.box + r), ox, oy, lmask + t * WARPS);
+      stage_record<TW, TH, PPT>(a.rec, r, t, 0, ox, oy, bs, false, false);
+      lane_masks<TW, TH, PPT>(__ldg(a.rec.box + r), ox, oy, lmask + t * WARPS * PPT);
     }
     __syncthreads();
-    uint32_t bits[2] = {0u, 0u};
-    if (!__all_sync(0xffffffffu, done)) {
+    uint32_t bits[PPT][2];
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) bits[i][0] = bits[i][1] = 0u;
+    if (!__all_sync(0xffffffffu, all_done())) {
       for (int base = 0; base < n; base += 32) {
         const int jj = base + (int)lane;
-        uint32_t vis = __ballot_sync(0xffffffffu, jj < n && lmask[jj * WARPS + warp] != 0u);
+        bool any = false;
+        if (jj < n)
+#pragma unroll
+          for (int i = 0; i < PPT; ++i) any = any || lmask[(jj * WARPS + warp) * PPT + i] != 0u;
+        uint32_t vis = __ballot_sync(0xffffffffu, any);
         while (vis) {
           const int bit = __ffs(vis) - 1;
           vis &= vis - 1;
           const int j = base + bit;
-          if (done || !((lmask[j * WARPS + warp] >> lane) & 1u)) continue;
-          float alpha, G, araw, dx, dy;
-          if (!gauss_alpha(bs.uv[j], bs.co[j], fpx, fpy, alpha, G, araw, dx, dy)) continue;
-          const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
-          if (Tn < kTStop) { done = true; continue; }
-          const float w = __fmul_rn(alpha, T);
-          const float4 cdp = bs.cd[j];
-          cr = fmaf(w, cdp.x, cr); cg = fmaf(w, cdp.y, cg); cb = fmaf(w, cdp.z, cb); cd = fmaf(w, cdp.w, cd);
-          T = Tn;
-          bits[base >> 5] |= 1u << bit;
+          const float2 uv = bs.uv[j];
+          const float4 co = bs.co[j];
+#pragma unroll
+          for (int i = 0; i < PPT; ++i) {
+            if (done[i] || !((lmask[(j * WARPS + warp) * PPT + i] >> lane) & 1u)) continue;
+            float alpha, G, araw, dx, dy;
+            if (!gauss_alpha(uv, co, fpx, fpy[i], alpha, G, araw, dx, dy)) continue;
+            const float Tn = __fmul_rn(T[i], __fsub_rn(1.f, alpha));
+            if (Tn < kTStop) { done[i] = true; continue; }
+            const float w = __fmul_rn(alpha, T[i]);
+            const float4 cdp = bs.cd[j];
+            cr[i] = fmaf(w, cdp.x, cr[i]); cg[i] = fmaf(w, cdp.y, cg[i]); cb[i] = fmaf(w, cdp.z, cb[i]);
+            cd[i] = fmaf(w, cdp.w, cd[i]);
+            T[i] = Tn;
+            bits[i][base >> 5] |= 1u << bit;
+          }
         }
       }
     }
     // last contributor and contribution count from the batch's bits
-    if (bits[1]) last = b - rg.x + 32 + (32 - __clz(bits[1]));
-    else if (bits[0]) last = b - rg.x + (32 - __clz(bits[0]));
-    ncontrib += __popc(bits[0]) + __popc(bits[1]);
-    if (a.masks && unit0 + bi < a.mask_units) {
-      uint32_t *mw = a.masks + (size_t)(unit0 + bi) * 2 * NPIX;
-      mw[lp] = bits[0];
-      mw[NPIX + lp] = bits[1];
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+      if (bits[i][1]) last[i] = b - rg.x + 32 + (32 - __clz(bits[i][1]));
+      else if (bits[i][0]) last[i] = b - rg.x + (32 - __clz(bits[i][0]));
+      ncontrib += __popc(bits[i][0]) + __popc(bits[i][1]);
+      if (a.masks && unit0 + bi < a.mask_units) {
+        uint32_t *mw = a.masks + (size_t)(unit0 + bi) * 2 * NPIX;
+        mw[lp[i]] = bits[i][0];
+        mw[NPIX + lp[i]] = bits[i][1];
+      }
     }
-    if (__syncthreads_count(done) == THREADS) break;
+    if (__syncthreads_count(all_done()) == THREADS) break;
   }
   {
     uint32_t nc = ncontrib;
@@ -123,19 +158,21 @@ __global__ void __launch_bounds__(TW *TH) k_blend(FwdArgs a) {
     if (lane == 0 && nc) atomicAdd(&a.counters->n_contrib, nc);
   }
   float l1_rgb = 0.f, l1_d = 0.f;
-  if (inside) {
-    const size_t pix = (size_t)py * a.width + px;
-    if (a.rgb_out) { a.rgb_out[3 * pix] = cr; a.rgb_out[3 * pix + 1] = cg; a.rgb_out[3 * pix + 2] = cb; }
-    if (a.depth_out) a.depth_out[pix] = cd;
-    if (a.sil_out) a.sil_out[pix] = 1.f - T;
-    a.tfinal[pix] = T;
-    a.nlast[pix] = last;
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    if (!inside[i]) continue;
+    const size_t pix = (size_t)py[i] * a.width + px;
+    if (a.rgb_out) { a.rgb_out[3 * pix] = cr[i]; a.rgb_out[3 * pix + 1] = cg[i]; a.rgb_out[3 * pix + 2] = cb[i]; }
+    if (a.depth_out) a.depth_out[pix] = cd[i];
+    if (a.sil_out) a.sil_out[pix] = 1.f - T[i];
+    a.tfinal[pix] = T[i];
+    a.nlast[pix] = last[i];
     if (L1) {
       const int cw = code_words(a.nwc);
-      const float d0 = cr - a.t_rgb[3 * pix], d1 = cg - a.t_rgb[3 * pix + 1], d2 = cb - a.t_rgb[3 * pix + 2];
-      const float d3 = cd - a.t_depth[pix];
+      const float d0 = cr[i] - a.t_rgb[3 * pix], d1 = cg[i] - a.t_rgb[3 * pix + 1];
+      const float d2 = cb[i] - a.t_rgb[3 * pix + 2], d3 = cd[i] - a.t_depth[pix];
       // Sec. 3.1 objective mode: only pixels with S > 0.99 count
-      const bool keep = !a.objective || 1.f - T > kSilMinLoss;
+      const bool keep = !a.objective || 1.f - T[i] > kSilMinLoss;
       const uint32_t nz = keep ? ((d0 != 0.f ? 1u : 0u) | (d1 != 0.f ? 2u : 0u) | (d2 != 0.f ? 4u : 0u) |
                                   (d3 != 0.f ? 8u : 0u)) : 0u;
       const uint32_t ng = (d0 < 0.f ? 1u : 0u) | (d1 < 0.f ? 2u : 0u) | (d2 < 0.f ? 4u : 0u) | (d3 < 0.f ? 8u : 0u);
@@ -144,8 +181,8 @@ __global__ void __launch_bounds__(TW *TH) k_blend(FwdArgs a) {
       if (!a.t_sem)
         for (int wd = 0; wd < a.nwc; ++wd) cp[1 + wd] = make_uint2(0u, 0u);
       if (keep) {
-        l1_rgb = fabsf(d0) + fabsf(d1) + fabsf(d2);
-        l1_d = fabsf(d3);
+        l1_rgb += fabsf(d0) + fabsf(d1) + fabsf(d2);
+        l1_d += fabsf(d3);
       }
     }
   }
@@ -464,7 +501,8 @@ static cudaError_t launch_semantic(const FwdArgs &a, int grid, size_t smem, cuda
 
 template <int TW, int TH, bool L1>
 static cudaError_t launch_shape(const FwdArgs &a, int grid, size_t smem_sem, bool run_sem, cudaStream_t s) {
-  k_blend<TW, TH, L1><<<grid, TW * TH, batch_smem_bytes(0), s>>>(a);
+  if (a.blend_ppt == 2) k_blend<TW, TH, L1, 2><<<grid, TW * TH / 2, batch_smem_bytes(0), s>>>(a);
+  else k_blend<TW, TH, L1, 1><<<grid, TW * TH, batch_smem_bytes(0), s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !run_sem) return e;
   // the common top-k sizes get an unrolled scatter
@@ -499,6 +537,7 @@ FwdArgs fwd_args(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc)
   a.codes = P.codes;
   a.nwc = L.nwc;
   a.lpart = P.lpart;
+  a.blend_ppt = L.ppt >= 2 ? 2 : 1;  // every compiled tile height is a multiple of 8
   return a;
 }
 
