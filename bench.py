@@ -485,14 +485,15 @@ def main():
         large, mixed = bench_large(args, dev, flush, scenes.workload("mixed2m"))
 
     # launches of our kernels per fused step: project 4 (setup, count, scan,
-    # emit); depth sort: reset, histogram, one per pass; pair emission 3;
-    # tile sort: reset, histogram, one per pass; ranges 2; fused forward 4
+    # emit); depth sort: reset, histogram, one per pass; pair emission 4
+    # (count, scan, tile-sort reset, write + tile-digit histogram); tile
+    # sort: one per pass; ranges 2; fused forward 4
     # (batches per tile, their scan, blend pass, semantic pass whose last CTA
     # reduces the loss); backward 3 (zero, blend adjoint, projection adjoint)
     passes = lambda bits: (bits + 7) // 8
     tw_, th_ = best["tile"]
     tiles = ((W + tw_ - 1) // tw_) * ((H + th_ - 1) // th_)
-    per_step = 4 + (2 + passes(31)) + 3 + (2 + passes(max(1, (tiles - 1).bit_length()))) + 2 + 4 + 3
+    per_step = 4 + (2 + passes(31)) + 4 + passes(max(1, (tiles - 1).bit_length())) + 2 + 4 + 3
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -11,8 +11,9 @@
 //      bits only.
 // Stability carries the depth order (and the gid tie-break) into each tile.
 //
-// Radix sort: 8-bit digits, one histogram kernel for all digit passes, then
-// one kernel per pass.  Each CTA takes a tile ticket from an atomic counter,
+// Radix sort: 8-bit digits, one histogram kernel for all digit passes (for
+// the tile sort the pair emission counts the digits itself), then one
+// kernel per pass.  Each CTA takes a tile ticket from an atomic counter,
 // ranks its keys stably (warp match + per-warp counters), publishes its
 // per-digit counts and looks back over earlier tiles for their prefixes
 // (decoupled look-back).  A CTA only waits on tiles whose tickets were taken
@@ -236,21 +237,34 @@ static cudaError_t os_passes(K *keys[2], uint32_t *vals[2], const uint32_t *coun
   return cudaSuccess;
 }
 
+// Clears the tickets, histograms and look-back words of a sort of at most
+// `cap` elements (the element count is read on the device).
+static cudaError_t os_reset(const uint32_t *count_p, uint32_t cap, int passes, uint32_t *tickets, uint32_t *ghist,
+                            unsigned long long *lookback, cudaStream_t s) {
+  const uint32_t lb_tiles = (uint32_t)sort_tiles(cap);
+  if (passes < 1 || passes > kMaxRadixPasses || lb_tiles == 0) return cudaErrorInvalidValue;
+  k_os_reset<<<2 * 152, 256, 0, s>>>(count_p, cap, passes, tickets, ghist, lookback, lb_tiles,
+                                     (uint32_t)(kOsThreads * os_items(cap)));
+  return cudaGetLastError();
+}
+
+// hist_ready: the reset and the digit histograms were done by the producer
+// of the keys (the pair emission), so only the passes run here.
 template <typename K>
 static cudaError_t os_sort(K *keys[2], uint32_t *vals[2], const uint32_t *count_p, uint32_t cap, int bits,
                            uint32_t *tickets, uint32_t *ghist, unsigned long long *lookback, Counters *counters,
-                           uint32_t spin_limit, cudaStream_t s) {
+                           uint32_t spin_limit, cudaStream_t s, bool hist_ready = false) {
   const int passes = radix_passes(bits);
   const uint32_t lb_tiles = (uint32_t)sort_tiles(cap);
   const int items = os_items(cap);
   if (passes < 1 || passes > kMaxRadixPasses || lb_tiles == 0) return cudaErrorInvalidValue;
-  k_os_reset<<<2 * 152, 256, 0, s>>>(count_p, cap, passes, tickets, ghist, lookback, lb_tiles,
-                                     (uint32_t)(kOsThreads * items));
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_os_hist<K><<<kHistCtas, 256, 0, s>>>(keys[0], count_p, cap, passes, ghist);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (!hist_ready) {
+    cudaError_t e = os_reset(count_p, cap, passes, tickets, ghist, lookback, s);
+    if (e != cudaSuccess) return e;
+    k_os_hist<K><<<kHistCtas, 256, 0, s>>>(keys[0], count_p, cap, passes, ghist);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   if (items == 4)
     return os_passes<K, 4>(keys, vals, count_p, cap, passes, tickets, ghist, lookback, lb_tiles, counters,
                            spin_limit, s);
@@ -270,8 +284,9 @@ cudaError_t launch_radix_sort_u32(const Layout &L, const WsPtrs &P, int bits, in
   uint32_t *k[2] = {P.pkeys[0], P.pkeys[1]};
   uint32_t *v[2] = {P.pvals[0], P.pvals[1]};
   *final_buf = radix_passes(bits) & 1;
+  // the pair emission has reset this sort and counted its digits
   return os_sort<uint32_t>(k, v, &P.counters->n_pairs, (uint32_t)L.pcap, bits, P.tickets + kMaxRadixPasses,
-                           P.ghist + kMaxRadixPasses * kRadix, P.lb_pairs, P.counters, L.spin_limit, s);
+                           P.ghist + kMaxRadixPasses * kRadix, P.lb_pairs, P.counters, L.spin_limit, s, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -311,12 +326,43 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_count(const uint32_t *__r
   if (threadIdx.x == 0) epart[blockIdx.x] = run;
 }
 
+// Pair p of the depth-ordered emission: returns its global tile id and sets
+// r to its record.
+__device__ __forceinline__ uint32_t emit_one(uint32_t p, uint32_t count, uint32_t per, const uint32_t *s_epart,
+                                             const uint32_t *__restrict__ sorted_rec, const short4 *__restrict__ rect,
+                                             const int32_t *__restrict__ rview, const DevCam *__restrict__ cams,
+                                             const uint32_t *__restrict__ rloc, int tw, int th, uint32_t &r) {
+  int lo = 0, hi = kEmitCtas - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (s_epart[mid] <= p) lo = mid; else hi = mid - 1;
+  }
+  const uint32_t local = p - s_epart[lo];
+  uint32_t qlo = (uint32_t)lo * per, qhi = min(count, qlo + per) - 1;
+  while (qlo < qhi) {
+    const uint32_t mid = (qlo + qhi + 1) >> 1;
+    if (__ldg(rloc + mid) <= local) qlo = mid; else qhi = mid - 1;
+  }
+  const uint32_t j = local - __ldg(rloc + qlo);
+  r = __ldg(sorted_rec + qlo);
+  const short4 rc = __ldg(rect + r);
+  const DevCam &c = cams[__ldg(rview + r)];
+  const int tx0 = rc.x / tw, gw = rc.y / tw - tx0 + 1, ty0 = rc.z / th;
+  const int ty = ty0 + (int)(j / (uint32_t)gw), tx = tx0 + (int)(j % (uint32_t)gw);
+  return c.tile_off + (uint32_t)(ty * c.tiles_x + tx);
+}
+
 // Pass 2, balanced over pairs: each thread takes pair indices, finds the
 // chunk (largest c with epart[c] <= p) and then the record (largest q of the
 // chunk with rloc[q] <= p - epart[c]) by binary search -- records with no
 // tile are never selected -- and writes the pair's tile id and record.
 // Consecutive threads write consecutive pairs, and the output equals the
-// depth-ordered, row-major-within-record emission.
+// depth-ordered, row-major-within-record emission.  The same kernel counts
+// the 8-bit digits of the tile ids for the tile sort that follows: a warp's
+// 32 consecutive pairs mostly come in runs of equal digits (the tiles of one
+// record), so each run adds its length with one shared-memory atomic, and
+// each CTA adds its counts to the global histograms at the end.
+constexpr int kEmitHistPasses = 4;  // 32-bit tile ids
 __global__ void __launch_bounds__(kEmitThreads) k_emit_write(const uint32_t *__restrict__ sorted_rec,
                                                              const short4 *__restrict__ rect,
                                                              const int32_t *__restrict__ rview,
@@ -325,34 +371,45 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_write(const uint32_t *__r
                                                              const uint32_t *__restrict__ epart,
                                                              const uint32_t *__restrict__ rloc,
                                                              uint32_t *__restrict__ pkeys,
-                                                             uint32_t *__restrict__ pvals) {
+                                                             uint32_t *__restrict__ pvals, int hist_passes,
+                                                             uint32_t *__restrict__ ghist) {
   __shared__ uint32_t s_epart[kEmitCtas];
+  __shared__ uint32_t s_hist[kEmitHistPasses * kRadix];
   if (cnt->status & kStatusTimeout) return;
   for (int i = threadIdx.x; i < kEmitCtas; i += kEmitThreads) s_epart[i] = epart[i];
+  for (int i = threadIdx.x; i < kEmitHistPasses * kRadix; i += kEmitThreads) s_hist[i] = 0u;
   __syncthreads();
   const uint32_t count = min(cnt->n_records, rcap);
   const uint32_t npairs = min(cnt->n_pairs, pcap);
   const uint32_t per = (count + kEmitCtas - 1) / kEmitCtas;
-  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < npairs; p += gridDim.x * blockDim.x) {
-    int lo = 0, hi = kEmitCtas - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (s_epart[mid] <= p) lo = mid; else hi = mid - 1;
+  const uint32_t lane = lane_id();
+  // warp-uniform trip count: every lane takes part in the run counting
+  for (uint32_t p0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); p0 < npairs; p0 += gridDim.x * blockDim.x) {
+    const uint32_t p = p0 + lane;
+    uint32_t key = 0xffffffffu;
+    if (p < npairs) {
+      uint32_t r;
+      key = emit_one(p, count, per, s_epart, sorted_rec, rect, rview, cams, rloc, tw, th, r);
+      pkeys[p] = key;
+      pvals[p] = r;
     }
-    const uint32_t local = p - s_epart[lo];
-    uint32_t qlo = (uint32_t)lo * per, qhi = min(count, qlo + per) - 1;
-    while (qlo < qhi) {
-      const uint32_t mid = (qlo + qhi + 1) >> 1;
-      if (__ldg(rloc + mid) <= local) qlo = mid; else qhi = mid - 1;
+    for (int q = 0; q < hist_passes; ++q) {
+      // lanes past the end carry digit kRadix, which starts a run and is not counted
+      const uint32_t d = p < npairs ? (key >> (q * kRadixBits)) & (kRadix - 1) : (uint32_t)kRadix;
+      const uint32_t prev = __shfl_up_sync(0xffffffffu, d, 1);
+      const bool start = lane == 0 || prev != d;
+      const uint32_t starts = __ballot_sync(0xffffffffu, start);
+      if (start && d < (uint32_t)kRadix) {
+        const uint32_t after = lane == 31 ? 0u : starts & (0xffffffffu << (lane + 1));
+        const uint32_t end = after ? (uint32_t)(__ffs(after) - 1) : 32u;
+        atomicAdd(&s_hist[q * kRadix + d], end - lane);
+      }
     }
-    const uint32_t j = local - __ldg(rloc + qlo);
-    const uint32_t r = __ldg(sorted_rec + qlo);
-    const short4 rc = __ldg(rect + r);
-    const DevCam &c = cams[__ldg(rview + r)];
-    const int tx0 = rc.x / tw, gw = rc.y / tw - tx0 + 1, ty0 = rc.z / th;
-    const int ty = ty0 + (int)(j / (uint32_t)gw), tx = tx0 + (int)(j % (uint32_t)gw);
-    pkeys[p] = c.tile_off + (uint32_t)(ty * c.tiles_x + tx);
-    pvals[p] = r;
+  }
+  if (hist_passes > 0) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < hist_passes * kRadix; i += kEmitThreads)
+      if (s_hist[i]) atomicAdd(ghist + i, s_hist[i]);
   }
 }
 
@@ -363,9 +420,15 @@ cudaError_t launch_emit_pairs(const Layout &L, const WsPtrs &P, int dbuf, cudaSt
   if (e != cudaSuccess) return e;
   e = launch_scan_single(P.epart, (uint32_t)kEmitCtas, &P.counters->n_pairs, (uint32_t)L.pcap, P.counters, s);
   if (e != cudaSuccess) return e;
+  // the tile sort's reset, then the emission counts its digits
+  const int passes = radix_passes(L.key_bits_tile);
+  if (passes > kEmitHistPasses) return cudaErrorInvalidValue;
+  uint32_t *ghist = P.ghist + kMaxRadixPasses * kRadix;
+  e = os_reset(&P.counters->n_pairs, (uint32_t)L.pcap, passes, P.tickets + kMaxRadixPasses, ghist, P.lb_pairs, s);
+  if (e != cudaSuccess) return e;
   k_emit_write<<<8 * 152, kEmitThreads, 0, s>>>(P.dvals[dbuf], P.rec_rect, P.rec_view, P.cams, P.counters,
                                                 (uint32_t)L.rcap, (uint32_t)L.pcap, L.tile_w, L.tile_h, P.epart,
-                                                P.rloc, P.pkeys[0], P.pvals[0]);
+                                                P.rloc, P.pkeys[0], P.pvals[0], passes, ghist);
   return cudaGetLastError();
 }
 
