@@ -31,7 +31,7 @@ constexpr int kOsWarps = kOsThreads / 32;
 // keys per thread of one sort tile, by element capacity: small sorts get
 // small tiles (more CTAs in flight, shorter per-tile latency), large ones
 // large tiles (fewer look-back steps, bounded look-back storage)
-inline int os_items(int64_t capacity) { return capacity <= (1 << 20) ? 4 : 16; }
+inline int os_items(int64_t capacity) { return capacity <= (1 << 20) ? 8 : 16; }
 constexpr int kHistCtas = 2 * 152;
 constexpr unsigned long long kFlagA = 1ull << 62;   // tile aggregate published
 constexpr unsigned long long kFlagP = 2ull << 62;   // inclusive prefix published
@@ -265,8 +265,8 @@ static cudaError_t os_sort(K *keys[2], uint32_t *vals[2], const uint32_t *count_
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  if (items == 4)
-    return os_passes<K, 4>(keys, vals, count_p, cap, passes, tickets, ghist, lookback, lb_tiles, counters,
+  if (items == 8)
+    return os_passes<K, 8>(keys, vals, count_p, cap, passes, tickets, ghist, lookback, lb_tiles, counters,
                            spin_limit, s);
   return os_passes<K, 16>(keys, vals, count_p, cap, passes, tickets, ghist, lookback, lb_tiles, counters,
                           spin_limit, s);
@@ -326,12 +326,11 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_count(const uint32_t *__r
   if (threadIdx.x == 0) epart[blockIdx.x] = run;
 }
 
-// Pair p of the depth-ordered emission: returns its global tile id and sets
-// r to its record.
-__device__ __forceinline__ uint32_t emit_one(uint32_t p, uint32_t count, uint32_t per, const uint32_t *s_epart,
-                                             const uint32_t *__restrict__ sorted_rec, const short4 *__restrict__ rect,
-                                             const int32_t *__restrict__ rview, const DevCam *__restrict__ cams,
-                                             const uint32_t *__restrict__ rloc, int tw, int th, uint32_t &r) {
+// Record (position in the depth order) of pair p of the emission: the chunk
+// c (largest with epart[c] <= p), then the largest q of the chunk with
+// rloc[q] <= p - epart[c].  Records with no tile are never selected.
+__device__ __forceinline__ uint32_t find_record(uint32_t p, uint32_t count, uint32_t per, const uint32_t *s_epart,
+                                                const uint32_t *__restrict__ rloc) {
   int lo = 0, hi = kEmitCtas - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -343,8 +342,19 @@ __device__ __forceinline__ uint32_t emit_one(uint32_t p, uint32_t count, uint32_
     const uint32_t mid = (qlo + qhi + 1) >> 1;
     if (__ldg(rloc + mid) <= local) qlo = mid; else qhi = mid - 1;
   }
-  const uint32_t j = local - __ldg(rloc + qlo);
-  r = __ldg(sorted_rec + qlo);
+  return qlo;
+}
+
+// First pair of depth-order record q in the whole emission (chunk q / per).
+__device__ __forceinline__ uint32_t pair_start(uint32_t q, uint32_t per, const uint32_t *s_epart,
+                                               const uint32_t *__restrict__ rloc) {
+  return s_epart[q / per] + __ldg(rloc + q);
+}
+
+// Global tile id of the j-th tile (row-major) of record r's tile rectangle.
+__device__ __forceinline__ uint32_t pair_tile(uint32_t r, uint32_t j, const short4 *__restrict__ rect,
+                                              const int32_t *__restrict__ rview, const DevCam *__restrict__ cams,
+                                              int tw, int th) {
   const short4 rc = __ldg(rect + r);
   const DevCam &c = cams[__ldg(rview + r)];
   const int tx0 = rc.x / tw, gw = rc.y / tw - tx0 + 1, ty0 = rc.z / th;
@@ -352,17 +362,21 @@ __device__ __forceinline__ uint32_t emit_one(uint32_t p, uint32_t count, uint32_
   return c.tile_off + (uint32_t)(ty * c.tiles_x + tx);
 }
 
-// Pass 2, balanced over pairs: each thread takes pair indices, finds the
-// chunk (largest c with epart[c] <= p) and then the record (largest q of the
-// chunk with rloc[q] <= p - epart[c]) by binary search -- records with no
-// tile are never selected -- and writes the pair's tile id and record.
-// Consecutive threads write consecutive pairs, and the output equals the
-// depth-ordered, row-major-within-record emission.  The same kernel counts
-// the 8-bit digits of the tile ids for the tile sort that follows: a warp's
-// 32 consecutive pairs mostly come in runs of equal digits (the tiles of one
-// record), so each run adds its length with one shared-memory atomic, and
-// each CTA adds its counts to the global histograms at the end.
-constexpr int kEmitHistPasses = 4;  // 32-bit tile ids
+// Pass 2, balanced over pairs.  A CTA takes blocks of kEmitBlock consecutive
+// pairs; two threads find the records of the block's first and last pair
+// (search over the chunk totals, then over the chunk's rloc), the block's
+// records' first pairs are staged in shared memory, and every pair finds its
+// record by a binary search there -- one chain of dependent global loads
+// per block instead of one per pair.  Consecutive threads write consecutive
+// pairs, and the output equals the depth-ordered, row-major-within-record
+// emission.  The same kernel counts the 8-bit digits of the tile ids for the
+// tile sort that follows: a warp's 32 consecutive pairs mostly come in runs
+// of equal digits (the tiles of one record), so each run adds its length
+// with one shared-memory atomic, and each CTA adds its counts to the global
+// histograms at the end.
+constexpr int kEmitHistPasses = 4;                          // 32-bit tile ids
+constexpr int kEmitItems = 8;                               // pairs per thread and block
+constexpr int kEmitBlock = kEmitThreads * kEmitItems;       // pairs per CTA block
 __global__ void __launch_bounds__(kEmitThreads) k_emit_write(const uint32_t *__restrict__ sorted_rec,
                                                              const short4 *__restrict__ rect,
                                                              const int32_t *__restrict__ rview,
@@ -375,6 +389,8 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_write(const uint32_t *__r
                                                              uint32_t *__restrict__ ghist) {
   __shared__ uint32_t s_epart[kEmitCtas];
   __shared__ uint32_t s_hist[kEmitHistPasses * kRadix];
+  __shared__ uint32_t s_start[kEmitBlock];  // first pair of records qa, qa + 1, ...
+  __shared__ uint32_t s_q[2];
   if (cnt->status & kStatusTimeout) return;
   for (int i = threadIdx.x; i < kEmitCtas; i += kEmitThreads) s_epart[i] = epart[i];
   for (int i = threadIdx.x; i < kEmitHistPasses * kRadix; i += kEmitThreads) s_hist[i] = 0u;
@@ -383,28 +399,67 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_write(const uint32_t *__r
   const uint32_t npairs = min(cnt->n_pairs, pcap);
   const uint32_t per = (count + kEmitCtas - 1) / kEmitCtas;
   const uint32_t lane = lane_id();
-  // warp-uniform trip count: every lane takes part in the run counting
-  for (uint32_t p0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); p0 < npairs; p0 += gridDim.x * blockDim.x) {
-    const uint32_t p = p0 + lane;
-    uint32_t key = 0xffffffffu;
-    if (p < npairs) {
-      uint32_t r;
-      key = emit_one(p, count, per, s_epart, sorted_rec, rect, rview, cams, rloc, tw, th, r);
-      pkeys[p] = key;
-      pvals[p] = r;
-    }
-    for (int q = 0; q < hist_passes; ++q) {
-      // lanes past the end carry digit kRadix, which starts a run and is not counted
-      const uint32_t d = p < npairs ? (key >> (q * kRadixBits)) & (kRadix - 1) : (uint32_t)kRadix;
-      const uint32_t prev = __shfl_up_sync(0xffffffffu, d, 1);
-      const bool start = lane == 0 || prev != d;
-      const uint32_t starts = __ballot_sync(0xffffffffu, start);
-      if (start && d < (uint32_t)kRadix) {
-        const uint32_t after = lane == 31 ? 0u : starts & (0xffffffffu << (lane + 1));
-        const uint32_t end = after ? (uint32_t)(__ffs(after) - 1) : 32u;
-        atomicAdd(&s_hist[q * kRadix + d], end - lane);
+  for (uint32_t P0 = blockIdx.x * (uint32_t)kEmitBlock; P0 < npairs; P0 += gridDim.x * (uint32_t)kEmitBlock) {
+    const uint32_t P1 = min(npairs, P0 + (uint32_t)kEmitBlock);
+    if (threadIdx.x < 2) s_q[threadIdx.x] = find_record(threadIdx.x ? P1 - 1 : P0, count, per, s_epart, rloc);
+    __syncthreads();
+    const uint32_t qa = s_q[0], nrec = s_q[1] - qa + 1;
+    // more records than staging slots only with records of no tile
+    const bool staged = nrec <= (uint32_t)kEmitBlock;
+    if (staged)
+      for (uint32_t i = threadIdx.x; i < nrec; i += kEmitThreads) s_start[i] = pair_start(qa + i, per, s_epart, rloc);
+    __syncthreads();
+    uint32_t rec[kEmitItems], jj[kEmitItems], key[kEmitItems];
+#pragma unroll
+    for (int it = 0; it < kEmitItems; ++it) {
+      const uint32_t p = P0 + it * kEmitThreads + threadIdx.x;
+      rec[it] = 0u; jj[it] = 0u;
+      if (p < P1) {
+        if (staged) {
+          int lo = 0, hi = (int)nrec - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_start[mid] <= p) lo = mid; else hi = mid - 1;
+          }
+          rec[it] = qa + (uint32_t)lo;
+          jj[it] = p - s_start[lo];
+        } else {
+          rec[it] = find_record(p, count, per, s_epart, rloc);
+          jj[it] = p - pair_start(rec[it], per, s_epart, rloc);
+        }
       }
     }
+#pragma unroll
+    for (int it = 0; it < kEmitItems; ++it)
+      if (P0 + it * kEmitThreads + threadIdx.x < P1) rec[it] = __ldg(sorted_rec + rec[it]);
+#pragma unroll
+    for (int it = 0; it < kEmitItems; ++it) {
+      const uint32_t p = P0 + it * kEmitThreads + threadIdx.x;
+      key[it] = 0xffffffffu;
+      if (p < P1) {
+        key[it] = pair_tile(rec[it], jj[it], rect, rview, cams, tw, th);
+        pkeys[p] = key[it];
+        pvals[p] = rec[it];
+      }
+    }
+    // lanes of a warp hold consecutive pairs of each item
+#pragma unroll
+    for (int it = 0; it < kEmitItems; ++it) {
+      const bool ok = P0 + it * kEmitThreads + threadIdx.x < P1;
+      for (int q = 0; q < hist_passes; ++q) {
+        // lanes past the end carry digit kRadix, which starts a run and is not counted
+        const uint32_t d = ok ? (key[it] >> (q * kRadixBits)) & (kRadix - 1) : (uint32_t)kRadix;
+        const uint32_t prev = __shfl_up_sync(0xffffffffu, d, 1);
+        const bool start = lane == 0 || prev != d;
+        const uint32_t starts = __ballot_sync(0xffffffffu, start);
+        if (start && d < (uint32_t)kRadix) {
+          const uint32_t after = lane == 31 ? 0u : starts & (0xffffffffu << (lane + 1));
+          const uint32_t end = after ? (uint32_t)(__ffs(after) - 1) : 32u;
+          atomicAdd(&s_hist[q * kRadix + d], end - lane);
+        }
+      }
+    }
+    __syncthreads();  // s_q and s_start are rewritten by the next block
   }
   if (hist_passes > 0) {
     __syncthreads();
