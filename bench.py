@@ -411,14 +411,14 @@ def main():
     t_bwd = ph_ms.get("render_bwd", 0.0) * 1e-3
     t_fwd = ph_ms.get("render_fwd", 0.0) * 1e-3
     t_front = ph_ms.get("project", 0.0) * 1e-3
-    # projection: 44 B read per Gaussian in each of its two passes, 112 B
+    # projection: 44 B read per Gaussian (one pass for a single view), 112 B
     # written per record (+ 8 B per semantic entry); depth sort: 32 B per
     # record and pass (8-bit digits); pair emission: 12 B per pair; tile
     # sort: 20 B per pair and pass; ranges: 8 B per pair
     dpass = (31 + 7) // 8
     tpass = (max(1, (((W + best["tile"][0] - 1) // best["tile"][0]) * ((H + best["tile"][1] - 1) // best["tile"][1]) - 1)
                  .bit_length()) + 7) // 8
-    bytes_front = (sc.n * 44 * 2 + n_records * (112 + 8 * k) + n_records * 32 * dpass + n_pairs * 12
+    bytes_front = (sc.n * 44 + n_records * (112 + 8 * k) + n_records * 32 * dpass + n_pairs * 12
                    + n_pairs * 20 * tpass + n_pairs * 8)
     alu = flops_bwd / t_bwd / 1e12
     bwd_kernel = "k_render_bwd<%d, %d, 1, %d, %d>" % (best["tile"][0], best["tile"][1], k if k in (3, 8) else 0,
@@ -435,7 +435,7 @@ def main():
                 "forward": {"kernels": "k_blend + k_semantic (+ batch offsets, loss reduction)",
                             "ms": t_fwd * 1e3, "algorithmic_bytes": bytes_fwd,
                             "hbm_frac_of_" + peak_src: (bytes_fwd / t_fwd / 1e9) / hbm_peak},
-                "project_bin_sort": {"kernels": "projection (count, emit), record depth sort, pair emission, tile "
+                "project_bin_sort": {"kernels": "projection (one pass), record depth sort, pair emission, tile "
                                                 "sort, ranges",
                                      "ms": t_front * 1e3, "algorithmic_bytes": bytes_front,
                                      "achieved_gbs": bytes_front / t_front / 1e9,
@@ -484,8 +484,9 @@ def main():
     if not args.no_large:
         large, mixed = bench_large(args, dev, flush, scenes.workload("mixed2m"))
 
-    # launches of our kernels per fused step: project 4 (setup, count, scan,
-    # emit); depth sort: reset, histogram, one per pass; pair emission 4
+    # launches of our kernels per fused step: project 2 (setup, one-pass
+    # single-view projection; its look-back words are cleared by a memset,
+    # not counted); depth sort: reset, histogram, one per pass; pair emission 4
     # (count, scan, tile-sort reset, write + tile-digit histogram); tile
     # sort: one per pass; ranges 2; fused forward 4
     # (batches per tile, their scan, blend pass, semantic pass whose last CTA
@@ -493,7 +494,7 @@ def main():
     passes = lambda bits: (bits + 7) // 8
     tw_, th_ = best["tile"]
     tiles = ((W + tw_ - 1) // tw_) * ((H + th_ - 1) // th_)
-    per_step = 4 + (2 + passes(31)) + 4 + passes(max(1, (tiles - 1).bit_length())) + 2 + 4 + 3
+    per_step = 2 + (2 + passes(31)) + 4 + passes(max(1, (tiles - 1).bit_length())) + 2 + 4 + 3
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

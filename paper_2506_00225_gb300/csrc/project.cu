@@ -1,5 +1,6 @@
 // project.cu -- per-(view, Gaussian) EWA projection, visibility compaction
-// and the single-CTA exclusive scan used for compaction offsets.
+// (count / scan / emit passes for several views, one look-back pass for a
+// single view) and the single-CTA exclusive scan used for compaction offsets.
 //
 // Sec. 3.1 "Gaussian Mapping" (transform to camera space, project to the
 // image plane); the EWA projection with 0.3 px^2 dilation, 3-sigma radius and
@@ -185,6 +186,30 @@ __global__ void __launch_bounds__(kProjThreads) k_project_count(gs_scene sc, con
   }
 }
 
+// Writes visible record r (Gaussian g projected into view v) and its
+// (view, depth) sort key.
+__device__ __forceinline__ void write_record(const gs_scene &sc, const WsPtrs &P, uint32_t r, int g, int v,
+                                             const Proj &p) {
+  const float op = __ldg(sc.opacity + g);
+  P.rec_uv[r] = make_float2(p.u, p.v);
+  P.rec_conic[r] = make_float4(p.ca, p.cb, p.cc, op);
+  P.rec_depth[r] = p.depth;
+  P.rec_rect[r] = make_short4((short)p.x0, (short)p.x1, (short)p.y0, (short)p.y1);
+  P.rec_gid[r] = g;
+  P.rec_view[r] = v;
+  // blend record: alpha box, colour + depth, uncertainty, sparse semantics
+  P.rec_box[r] = alpha_box(p, op);
+  P.rec_cd[r] = make_float4(sc.rgb ? __ldg(sc.rgb + 3 * g) : 0.f, sc.rgb ? __ldg(sc.rgb + 3 * g + 1) : 0.f,
+                            sc.rgb ? __ldg(sc.rgb + 3 * g + 2) : 0.f, p.depth);
+  P.rec_unc[r] = sc.geo_unc ? __ldg(sc.geo_unc + g) : 0.f;
+  if (sc.sem_ids)
+    for (int l = 0; l < sc.k; ++l)
+      P.rec_sem[(size_t)r * sc.k + l] = make_int2(__ldg(sc.sem_ids + (size_t)g * sc.k + l),
+                                                  __float_as_int(__ldg(sc.sem_w + (size_t)g * sc.k + l)));
+  P.dkeys[0][r] = ((unsigned long long)v << 31) | (unsigned long long)__float_as_uint(p.depth);
+  P.dvals[0][r] = r;
+}
+
 // Pass 2: recompute (bit-identical) and write compacted records in
 // (view, Gaussian index) order, plus the (view, depth) sort keys.
 __global__ void __launch_bounds__(kProjThreads) k_project_emit(gs_scene sc, const DevCam *cams, int nb, int n_views,
@@ -216,27 +241,88 @@ __global__ void __launch_bounds__(kProjThreads) k_project_emit(gs_scene sc, cons
     for (int i = 0; i < kProjItems; ++i) {
       if (!vis[i]) continue;
       const uint32_t r = rank++;
-      if (r >= rcap) continue;
-      const int g = g0 + i;
-      const float op = __ldg(sc.opacity + g);
-      P.rec_uv[r] = make_float2(p[i].u, p[i].v);
-      P.rec_conic[r] = make_float4(p[i].ca, p[i].cb, p[i].cc, op);
-      P.rec_depth[r] = p[i].depth;
-      P.rec_rect[r] = make_short4((short)p[i].x0, (short)p[i].x1, (short)p[i].y0, (short)p[i].y1);
-      P.rec_gid[r] = g;
-      P.rec_view[r] = v;
-      // blend record: alpha box, colour + depth, uncertainty, sparse semantics
-      P.rec_box[r] = alpha_box(p[i], op);
-      P.rec_cd[r] = make_float4(sc.rgb ? __ldg(sc.rgb + 3 * g) : 0.f, sc.rgb ? __ldg(sc.rgb + 3 * g + 1) : 0.f,
-                                sc.rgb ? __ldg(sc.rgb + 3 * g + 2) : 0.f, p[i].depth);
-      P.rec_unc[r] = sc.geo_unc ? __ldg(sc.geo_unc + g) : 0.f;
-      if (sc.sem_ids)
-        for (int l = 0; l < sc.k; ++l)
-          P.rec_sem[(size_t)r * sc.k + l] = make_int2(__ldg(sc.sem_ids + (size_t)g * sc.k + l),
-                                                      __float_as_int(__ldg(sc.sem_w + (size_t)g * sc.k + l)));
-      P.dkeys[0][r] = ((unsigned long long)v << 31) | (unsigned long long)__float_as_uint(p[i].depth);
-      P.dvals[0][r] = r;
+      if (r < rcap) write_record(sc, P, r, g0 + i, v, p[i]);
     }
+  }
+}
+
+// Single-view projection in one pass (the mapping view): each CTA takes a
+// block ticket, projects its Gaussians, publishes its visible count and
+// looks back over the blocks ticketed before it (decoupled look-back) for
+// its offset, then writes its records -- the same records, in the same
+// (Gaussian index) order, as the count / scan / emit passes, without the
+// count pass and the scan.  A look-back word holds a flag in its top two
+// bits (aggregate or inclusive prefix published) and a count below, so the
+// path is taken for n < 2^30.  A CTA only waits on blocks whose tickets were
+// taken earlier (their CTAs are running); every wait is bounded and, if the
+// bound is hit, raises the timeout status instead of hanging (later kernels
+// then skip their work).  The block ticketed last writes the record count.
+constexpr uint32_t kPjFlagA = 1u << 30;  // block count published
+constexpr uint32_t kPjFlagP = 2u << 30;  // inclusive prefix published
+constexpr uint32_t kPjVal = kPjFlagA - 1u;
+
+__global__ void __launch_bounds__(kProjThreads) k_project_single(gs_scene sc, const DevCam *cams, int nb,
+                                                                 uint32_t rcap, uint32_t *lookback,
+                                                                 uint32_t *ticket, uint32_t spin_limit,
+                                                                 WsPtrs P) {
+  __shared__ uint32_t tmp[33];
+  __shared__ uint32_t s_b, s_off;
+  if (threadIdx.x == 0) s_b = atomicAdd(ticket, 1u);
+  __syncthreads();
+  const int b = (int)s_b;
+  const int g0 = b * kProjBlock + threadIdx.x * kProjItems;
+  GIn in[kProjItems];
+#pragma unroll
+  for (int i = 0; i < kProjItems; ++i)
+    if (g0 + i < sc.n) in[i] = load_gaussian(sc, g0 + i);
+  const DevCam c = cams[0];
+  Proj p[kProjItems];
+  bool vis[kProjItems];
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int i = 0; i < kProjItems; ++i) {
+    vis[i] = false;
+    if (g0 + i < sc.n)
+      vis[i] = project_gaussian(in[i].mx, in[i].my, in[i].mz, in[i].sx, in[i].sy, in[i].sz, in[i].q, c, p[i]);
+    cnt += vis[i] ? 1u : 0u;
+  }
+  uint32_t total;
+  const uint32_t ex = block_exclusive_scan(cnt, tmp, &total);
+  if (threadIdx.x == 0) {
+    uint32_t excl = 0u;
+    if (b == 0) {
+      atomicExch(lookback, kPjFlagP | total);
+    } else {
+      atomicExch(lookback + b, kPjFlagA | total);
+      int j = b - 1;
+      uint32_t spins = 0;
+      while (j >= 0) {
+        const uint32_t w = *reinterpret_cast<volatile uint32_t *>(lookback + j);
+        const uint32_t flag = w & ~kPjVal;
+        if (flag == 0u) {
+          if (++spins > spin_limit) { set_status(P.counters, kStatusTimeout); break; }
+          __nanosleep(32);
+          continue;
+        }
+        excl += w & kPjVal;
+        if (flag == kPjFlagP) break;
+        --j;
+      }
+      atomicExch(lookback + b, kPjFlagP | ((excl + total) & kPjVal));
+    }
+    s_off = excl;
+    if (b == nb - 1) {
+      P.counters->n_records = excl + total;
+      if (excl + total > rcap) set_status(P.counters, kStatusCapacity);
+    }
+  }
+  __syncthreads();
+  uint32_t rank = s_off + ex;
+#pragma unroll
+  for (int i = 0; i < kProjItems; ++i) {
+    if (!vis[i]) continue;
+    const uint32_t r = rank++;
+    if (r < rcap) write_record(sc, P, r, g0 + i, 0, p[i]);
   }
 }
 
@@ -280,6 +366,14 @@ cudaError_t launch_project(const Layout &L, const WsPtrs &P, const gs_scene &sc,
   const int nb = (int)L.proj_blocks;
   const int grid = nb * L.n_views;
   if (grid == 0) return cudaSuccess;
+  if (L.n_views == 1 && (int64_t)sc.n < (int64_t)kPjVal) {
+    // blockcnt holds nb + 1 words: the look-back words, then the ticket
+    cudaError_t e = cudaMemsetAsync(P.blockcnt, 0, sizeof(uint32_t) * ((size_t)nb + 1), s);
+    if (e != cudaSuccess) return e;
+    k_project_single<<<nb, kProjThreads, 0, s>>>(sc, P.cams, nb, (uint32_t)L.rcap, P.blockcnt, P.blockcnt + nb,
+                                                 L.spin_limit, P);
+    return cudaGetLastError();
+  }
   const dim3 g2(nb, (L.n_views + kViewsPerCta - 1) / kViewsPerCta);
   k_project_count<<<g2, kProjThreads, 0, s>>>(sc, P.cams, nb, L.n_views, P.blockcnt);
   cudaError_t e = cudaGetLastError();
