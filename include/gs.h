@@ -105,7 +105,8 @@ typedef struct gs_camera {
  *                        every (pixel, Gaussian) pair of the tile instead.
  *                        Results are identical.
  *   spin_limit           bound on the polls of one inter-CTA wait (decoupled
- *                        look-back of the sorts); 0 = default (about 4
+ *                        look-back of the sorts and of the single-view
+ *                        projection); 0 = default (about 4
  *                        million polls with a short sleep each).  A wait that
  *                        runs out raises GS_ERR_TIMEOUT in the device status,
  *                        later kernels of the chain skip their work, and
