@@ -352,12 +352,17 @@ __device__ __forceinline__ uint32_t pair_start(uint32_t q, uint32_t per, const u
 }
 
 // Global tile id of the j-th tile (row-major) of record r's tile rectangle.
+// TW, TH > 0 fix the tile shape at compile time (the divisions become
+// shifts); 0 takes tw, th.  Rectangle coordinates are non-negative.
+template <int TW, int TH>
 __device__ __forceinline__ uint32_t pair_tile(uint32_t r, uint32_t j, const short4 *__restrict__ rect,
                                               const int32_t *__restrict__ rview, const DevCam *__restrict__ cams,
                                               int tw, int th) {
+  const uint32_t w = TW > 0 ? (uint32_t)TW : (uint32_t)tw, h = TH > 0 ? (uint32_t)TH : (uint32_t)th;
   const short4 rc = __ldg(rect + r);
   const DevCam &c = cams[__ldg(rview + r)];
-  const int tx0 = rc.x / tw, gw = rc.y / tw - tx0 + 1, ty0 = rc.z / th;
+  const int tx0 = (int)((uint32_t)rc.x / w), gw = (int)((uint32_t)rc.y / w) - tx0 + 1;
+  const int ty0 = (int)((uint32_t)rc.z / h);
   const int ty = ty0 + (int)(j / (uint32_t)gw), tx = tx0 + (int)(j % (uint32_t)gw);
   return c.tile_off + (uint32_t)(ty * c.tiles_x + tx);
 }
@@ -377,6 +382,7 @@ __device__ __forceinline__ uint32_t pair_tile(uint32_t r, uint32_t j, const shor
 constexpr int kEmitHistPasses = 4;                          // 32-bit tile ids
 constexpr int kEmitItems = 8;                               // pairs per thread and block
 constexpr int kEmitBlock = kEmitThreads * kEmitItems;       // pairs per CTA block
+template <int TW, int TH>
 __global__ void __launch_bounds__(kEmitThreads) k_emit_write(const uint32_t *__restrict__ sorted_rec,
                                                              const short4 *__restrict__ rect,
                                                              const int32_t *__restrict__ rview,
@@ -437,7 +443,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_write(const uint32_t *__r
       const uint32_t p = P0 + it * kEmitThreads + threadIdx.x;
       key[it] = 0xffffffffu;
       if (p < P1) {
-        key[it] = pair_tile(rec[it], jj[it], rect, rview, cams, tw, th);
+        key[it] = pair_tile<TW, TH>(rec[it], jj[it], rect, rview, cams, tw, th);
         pkeys[p] = key[it];
         pvals[p] = rec[it];
       }
@@ -481,9 +487,15 @@ cudaError_t launch_emit_pairs(const Layout &L, const WsPtrs &P, int dbuf, cudaSt
   uint32_t *ghist = P.ghist + kMaxRadixPasses * kRadix;
   e = os_reset(&P.counters->n_pairs, (uint32_t)L.pcap, passes, P.tickets + kMaxRadixPasses, ghist, P.lb_pairs, s);
   if (e != cudaSuccess) return e;
-  k_emit_write<<<8 * 152, kEmitThreads, 0, s>>>(P.dvals[dbuf], P.rec_rect, P.rec_view, P.cams, P.counters,
-                                                (uint32_t)L.rcap, (uint32_t)L.pcap, L.tile_w, L.tile_h, P.epart,
-                                                P.rloc, P.pkeys[0], P.pvals[0], passes, ghist);
+  const int tw = L.tile_w, th = L.tile_h;
+  auto kern = tw == 16 && th == 16 ? k_emit_write<16, 16>
+            : tw == 16 && th == 8  ? k_emit_write<16, 8>
+            : tw == 8 && th == 8   ? k_emit_write<8, 8>
+            : tw == 32 && th == 8  ? k_emit_write<32, 8>
+                                   : k_emit_write<0, 0>;
+  kern<<<8 * 152, kEmitThreads, 0, s>>>(P.dvals[dbuf], P.rec_rect, P.rec_view, P.cams, P.counters, (uint32_t)L.rcap,
+                                        (uint32_t)L.pcap, tw, th, P.epart, P.rloc, P.pkeys[0], P.pvals[0], passes,
+                                        ghist);
   return cudaGetLastError();
 }
 
