@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--cand-tile", default="16x16", help="WxH tile of the candidate kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 2M-Gaussian mapping and mixed-stream runs")
+    ap.add_argument("--clocks-dir", default="/tmp",
+                    help="directory for the nvidia-smi clock samples taken during the timed region")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the objective, dense-comparator and exploration measurements")
     ap.add_argument("--only", choices=["candidates", "large", "objective", "dense", "explore"], default=None,
@@ -366,8 +368,7 @@ def main():
     torch.cuda.synchronize()
 
     # ---- timed region (headline: fused step, whole step replayed as one CUDA graph)
-    clocks = ClockSampler(local, os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv")) \
-        if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ClockSampler(local, f"/tmp/clocks_rank{rank}.csv")
+    clocks = ClockSampler(local, os.path.join(args.clocks_dir, f"clocks_rank{rank}.csv"))
     clocks.wait_first()
     barrier(world)
     torch.cuda.synchronize()

@@ -16,7 +16,7 @@ Written from the paper's definitions, in float64, one candidate at a time:
 * positions: the lattice points of spacing v1 over newly freed voxels, at
   the sampled heights.
 
-Readings where the paper is silent (listed in the design doc): the softmaxes run
+Readings where the paper is silent: the softmaxes run
 over the candidates scored together; when no candidate has N_S > 0 the
 geometric factor is 0 for all (the softmax of all -inf is undefined); the
 best candidate is the largest I among the kept ones, the lowest index on

@@ -15,7 +15,7 @@ Written from the paper's definitions, in float64, per pixel, no fusion:
   sqrt P_m)^2) and the cosine similarity cos = Q.P / (|Q| |P|); the pixel
   term M_H (0.8 D_HD + 0.2 (1 - cos)) is averaged over the pixels.
 
-Readings where the paper is silent (listed in the design doc): the colour L1 sums
+Readings where the paper is silent: the colour L1 sums
 its channels; the semantic term is a mean over pixels while the geometric
 one is a sum, as printed; the two are added; P_m < 0 counts as 0 under the
 square root (weights are not constrained in the optimisation); the square

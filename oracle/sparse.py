@@ -6,7 +6,7 @@ A Gaussian keeps the k classes of highest probability of its first observed
 distribution; later observations update the k probabilities with the ids
 fixed.  Written as a per-row sort of (probability, class id) pairs.
 
-Readings where the paper is silent (listed in the design doc): equal
+Readings where the paper is silent: equal
 probabilities are ranked by the lower class id; NaN ranks below every
 number; the kept probabilities are stored as observed (no renormalisation,
 the renderer blends them as given).

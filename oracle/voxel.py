@@ -11,7 +11,7 @@ with the cube grown and shrunk by EPS voxel edges; where the two disagree
 the voxel is a near tie (the segment grazes an edge or corner, or p lies on
 a face) and is reported as such rather than decided.
 
-Readings where the paper is silent (listed in the design doc): depth is the
+Readings where the paper is silent: depth is the
 camera-space z of the rendered depth map; a voxel seen both free and
 occupied is occupied; the newly freed voxels of an update are those free
 now and unknown before.
