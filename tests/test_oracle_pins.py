@@ -371,6 +371,64 @@ def test_adjoint_matches_central_differences(seed):
     assert skipped <= total // 20
 
 
+def _deep_stack_scene(seed):
+    """Tens of large, half-transparent Gaussians stacked along the optical
+    axis: every pixel composites many layers, so the adjoint's transmittance
+    recovery runs through long products and the 1e-4 stop rule cuts some
+    pixels' lists."""
+    rng = np.random.default_rng(seed)
+    n, m, k = 40, 6, 3
+    cam = look_camera((0.0, 0.0, 0.0), 0.0, 24, 20, 24.0)
+    c2w = cam.w2c[:, :3].astype(np.float64).T
+    z = rng.uniform(1.5, 4.0, n)
+    tc = np.stack([rng.uniform(-0.15, 0.15, n) * z, rng.uniform(-0.15, 0.15, n) * z, z], 1)
+    means = tc @ c2w.T + cam.position()
+    scales = np.exp(rng.normal(-0.6, 0.2, (n, 3))) * z[:, None] / 3.0
+    ids = np.stack([rng.choice(m, k, replace=False) for _ in range(n)]).astype(np.int32)
+    sc = mk_scene(means, scales, rand_quat(rng, n), rng.uniform(0.2, 0.6, n), rgb=rng.uniform(0, 1, (n, 3)),
+                  ids=ids, w=rng.uniform(0.1, 0.9, (n, k)), m=m)
+    W, H = cam.width, cam.height
+    up = dict(d_rgb=rng.normal(size=(H, W, 3)), d_depth=rng.normal(size=(H, W)), d_sil=rng.normal(size=(H, W)),
+              d_sem=rng.normal(size=(H, W, m)))
+    return sc, cam, up
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_adjoint_directional_derivatives_deep_stacks(seed):
+    """v . grad L equals the central difference of L along v (double
+    precision), for random directions v through all parameters at once, on
+    scenes where each pixel composites many layers."""
+    sc, cam, up = _deep_stack_scene(seed)
+    r0 = oracle.render(sc, cam, prec="f64")
+    assert np.median(r0["n_contrib"]) >= 20  # deep per-pixel lists
+    assert (r0["T"] < 0.01).mean() > 0.3  # most light absorbed on many pixels
+    assert r0["T"].min() < 2e-4  # the 1e-4 stop rule is reached
+    g = oracle.render_bwd(sc, cam, **up, sem_detach=False, prec="f64")
+    fields = ["means", "scales", "quats", "opacity", "rgb", "sem_w"]
+    rng = np.random.default_rng(100 + seed)
+    h = 1e-6
+    checked = 0
+    for _ in range(6):
+        v = {f: rng.normal(size=getattr(sc, f).shape) for f in fields}
+        v["scales"] *= sc.scales  # relative steps for the scales
+        dirn = sum(float((g[f] * v[f]).sum()) for f in fields)
+        mag = sum(float(np.abs(g[f] * v[f]).sum()) for f in fields)
+        vals, sigs = [], []
+        for sgn in (1, -1):
+            arrs = {f: np.array(getattr(sc, f), np.float64) + sgn * h * v[f] for f in fields}
+            sc2 = Scene(arrs["means"], arrs["scales"], arrs["quats"], arrs["opacity"], arrs["rgb"], sc.sem_ids,
+                        arrs["sem_w"], sc.m)
+            L, nc, fl = _loss(sc2, cam, up)
+            vals.append(L)
+            sigs.append(nc)
+        if not np.array_equal(sigs[0], sigs[1]):
+            continue  # a skip or stop decision flipped between the two sides
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - dirn) <= 1e-6 * abs(dirn) + 1e-8 * mag, (fd, dirn, mag)
+        checked += 1
+    assert checked >= 4
+
+
 def test_semantic_gradient_block():
     """With the block on, geometric gradients do not depend on the semantic
     upstream gradient, and semantic-weight gradients do not change."""
