@@ -51,7 +51,7 @@ import numpy as np  # noqa: E402
 
 L2_BYTES = 129 * 1024 * 1024
 ORACLE_ROW_STEP = 6       # CPU baseline: every 6th pixel row of the view (~10 s)
-ORACLE_ROW_STEP_REF = 40  # reference arm: every 40th row per step (~1.5 s)
+ORACLE_ROW_STEP_REF = 40  # reference arm: every 40th row per step (~0.3-0.8 s)
 
 
 def parse():
@@ -207,9 +207,9 @@ def bench_config(world: int) -> dict:
             "parallelism": f"replicas x{world}"}
 
 
-def cpu_baseline(wl, row_step=ORACLE_ROW_STEP) -> dict:
-    """Times the CPU oracle's forward + backward of the mapping step on every
-    row_step-th pixel row and scales to a full step."""
+def _oracle_sample(wl, row_step):
+    """Seconds of the CPU oracle's forward + backward of the mapping step on
+    every row_step-th pixel row, and the number of rows."""
     import oracle
     sc, cam = wl["scene"], wl["cams"][0]
     H, W, m = cam.height, cam.width, sc.m
@@ -218,37 +218,64 @@ def cpu_baseline(wl, row_step=ORACLE_ROW_STEP) -> dict:
               d_depth=np.sign(rng.normal(size=(H, W))).astype(np.float32) / (H * W),
               d_sem=np.sign(rng.normal(size=(H, W, m))).astype(np.float32) / (H * W * m))
     rows = (0, H, row_step)
-    nrows = len(range(*rows))
     t0 = time.perf_counter()
     oracle.render(sc, cam, prec="f32", rows=rows)
     oracle.render_bwd(sc, cam, **up, prec="f32", rows=rows)
-    dt = time.perf_counter() - t0
+    return time.perf_counter() - t0, len(range(*rows))
+
+
+def _sample_text(nrows, H, row_step, dt, extra=""):
+    return (f"forward (OpenMP over rows, {os.cpu_count()} threads) + backward (1 thread) of the CPU oracle on "
+            f"{nrows} of {H} pixel rows (every {row_step}th) of the 680x1200 view, {dt:.2f} s measured, "
+            f"scaled by {H / nrows:.2f} to one step{extra}")
+
+
+def cpu_baseline(wl, row_step=ORACLE_ROW_STEP) -> dict:
+    """Times the CPU oracle's forward + backward of the mapping step on every
+    row_step-th pixel row and scales to a full step (every 6th row: within
+    2 % of a full-image run of the oracle)."""
+    H = wl["cams"][0].height
+    dt, nrows = _oracle_sample(wl, row_step)
     per_step = dt * H / nrows
     return {"value": 1.0 / per_step, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"forward (OpenMP over rows, {os.cpu_count()} threads) + backward (1 thread) of the CPU "
-                      f"oracle on {nrows} of {H} pixel rows (every {row_step}th) of the 680x1200 view, "
-                      f"{dt:.2f} s measured, scaled by {H / nrows:.2f} to one step"}
+            "sample": _sample_text(nrows, H, row_step, dt)}
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, K timed steps after W
+    warm-up steps.  A step is the oracle on every 40th pixel row (so that
+    the run stays within minutes), scaled to a full step by the ratio of the
+    every-6th-row estimate to the every-40th-row estimate, both measured
+    once before the steps: the oracle's per-call fixed cost (projection of
+    all Gaussians) would otherwise be multiplied by the row scale."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
     from paper_2506_00225_gb300 import scenes
     wl = scenes.workload(args.workload)
+    H = wl["cams"][0].height
+    _oracle_sample(wl, ORACLE_ROW_STEP_REF)  # first call: library load, first touch of the scene
+    t6, n6 = _oracle_sample(wl, ORACLE_ROW_STEP)
+    t40, n40 = _oracle_sample(wl, ORACLE_ROW_STEP_REF)
+    corr = (t6 * H / n6) / (t40 * H / n40)
     times = []
+    dt = t40
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(wl, ORACLE_ROW_STEP_REF)
+        dt, nrows = _oracle_sample(wl, ORACLE_ROW_STEP_REF)
         if i >= args.warmup:
-            times.append(1.0 / cb["value"])
+            times.append(dt * H / nrows * corr)
     ms = 1000.0 * statistics.mean(times)
     value = 1000.0 / ms
+    cb = {"value": value, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
+          "sample": _sample_text(n40, H, ORACLE_ROW_STEP_REF, dt,
+                                 f" and by {corr:.3f} (every-6th-row estimate {t6 * H / n6:.2f} s over "
+                                 f"every-40th-row estimate {t40 * H / n40:.2f} s, measured before the steps)")}
     line = {"metric": "mapping fwd+bwd iters/s @680x1200", "value": value, "unit": "iters/s",
             "n_gpus": max(1, world), "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "impl": "reference",
             "config": bench_config(max(1, world)),
-            "cpu_baseline": dict(cb, value=value),
+            "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
