@@ -230,15 +230,36 @@ def _sample_text(nrows, H, row_step, dt, extra=""):
             f"scaled by {H / nrows:.2f} to one step{extra}")
 
 
-def cpu_baseline(wl, row_step=ORACLE_ROW_STEP) -> dict:
+def _single_thread_sample(workload: str, row_step: int):
+    """The same sample in a fresh process with one OpenMP thread (the
+    oracle's thread count is fixed when its library loads)."""
+    code = ("import json, bench; from paper_2506_00225_gb300 import scenes; "
+            f"print(json.dumps(bench._oracle_sample(scenes.workload({workload!r}), {row_step})))")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=dict(os.environ, OMP_NUM_THREADS="1"),
+                       capture_output=True, text=True, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-500:])
+    dt, nrows = json.loads(r.stdout.strip().splitlines()[-1])
+    return dt, nrows
+
+
+def cpu_baseline(wl, row_step=ORACLE_ROW_STEP, workload="room300k") -> dict:
     """Times the CPU oracle's forward + backward of the mapping step on every
     row_step-th pixel row and scales to a full step (every 6th row: within
-    2 % of a full-image run of the oracle)."""
+    2 % of a full-image run of the oracle); the same sample with one thread
+    is reported beside it."""
     H = wl["cams"][0].height
     dt, nrows = _oracle_sample(wl, row_step)
     per_step = dt * H / nrows
-    return {"value": 1.0 / per_step, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": _sample_text(nrows, H, row_step, dt)}
+    out = {"value": 1.0 / per_step, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": _sample_text(nrows, H, row_step, dt)}
+    try:
+        dt1, n1 = _single_thread_sample(workload, row_step)
+        out["single_thread"] = {"value": 1.0 / (dt1 * H / n1), "unit": "iters/s", "cores": 1,
+                                "sample": f"the same {n1} rows with OMP_NUM_THREADS=1, {dt1:.2f} s measured"}
+    except Exception as e:  # the single-thread figure is context; its failure must not lose the line
+        out["single_thread"] = {"value": None, "error": str(e)[-200:]}
+    return out
 
 
 def run_reference(args):
@@ -526,7 +547,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wl)
+        cpu = cpu_baseline(wl, workload=args.workload)
 
     if rank == 0:
         line = {"metric": "mapping fwd+bwd iters/s @680x1200", "value": value, "unit": "iters/s",
