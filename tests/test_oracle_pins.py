@@ -504,6 +504,21 @@ def test_golden_closed_forms():
     for m, v in zip(d["entropy_empty_pixel"]["m"], d["entropy_empty_pixel"]["value"]):
         sc = mk_scene([[0.0, 0.0, -1.0]], [[1.0, 1.0, 1.0]], [[1, 0, 0, 0]], [0.5], m=m)
         assert abs(oracle.candidate(sc, cam, prec="f64")[1] - v) < 1e-12
+    # one capped Gaussian (alpha = 0.99) at the pixel centre: P = 0.99 w
+    e = d["entropy_clip_then_normalise"]
+    p = np.asarray(e["p"])
+    nz = np.nonzero(p)[0]
+    sc = mk_scene([[0.0, 0.0, 1.0]], [[1.0, 1.0, 1.0]], [[1, 0, 0, 0]], [0.99], ids=nz[None, :].astype(np.int32),
+                  w=(p[nz] / 0.99)[None, :], m=p.size)
+    assert abs(oracle.candidate(sc, cam, prec="f64")[1] - e["value"]) < 1e-6
+    # the stop rule: stacked alpha = 0.95 Gaussians at the centre pixel
+    st = d["stop_rule_alpha_0p95"]
+    cam3 = ident_cam(3, 3, 10.0)
+    sc = mk_scene([[0.0, 0.0, 1.0 + 0.1 * i] for i in range(5)], [[1.0, 1.0, 1.0]] * 5, [[1, 0, 0, 0]] * 5,
+                  [0.95] * 5)
+    r = oracle.render(sc, cam3, prec="f64")
+    assert r["n_contrib"][1, 1] == st["n_contrib"]
+    assert abs(r["sil"][1, 1] - st["silhouette_exact_alpha"]) < 1e-9  # 0.95 stored as float32
 
 
 # ---------------------------------------------------------------------------
