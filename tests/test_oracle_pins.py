@@ -136,6 +136,82 @@ def test_projection_matches_numeric_jacobian():
     assert checked > 150
 
 
+def test_frustum_clamp_of_the_jacobian():
+    """A Gaussian beyond 1.3 tan(half field of view) of the optical axis is
+    linearised at the clamped point (x/z clamped to +-1.3 (W/2)/f): its
+    conic equals the EWA form with a numerically differentiated pinhole map
+    at that point, and differs from the one at its own mean."""
+    W = H = 41
+    f, z, s = 40.0, 2.0, 0.5
+    cam = ident_cam(W, H, f)
+    lim = 1.3 * (W / 2.0) / f
+    for sign in (1.0, -1.0):
+        mean = np.array([sign * 0.8 * z, 0.1, z])
+        sc = mk_scene([mean], [[s, s, s]], [[1, 0, 0, 0]], [0.9])
+        p = oracle.project(sc, cam, prec="f64")
+        assert p["visible"][0]
+        m32 = np.asarray(sc.means[0], np.float64)
+        s32 = float(sc.scales[0, 0])
+
+        def pix(X):
+            return np.array([f * X[0] / X[2] + W / 2.0, f * X[1] / X[2] + H / 2.0])
+
+        def ewa_conic(X):
+            J = np.zeros((2, 3))
+            for i in range(3):
+                e = np.zeros(3); e[i] = 1e-6
+                J[:, i] = (pix(X + e) - pix(X - e)) / 2e-6
+            S2 = J @ (s32 ** 2 * np.eye(3)) @ J.T + 0.3 * np.eye(2)
+            inv = np.linalg.inv(S2)
+            return np.array([inv[0, 0], inv[0, 1], inv[1, 1]])
+
+        clamped = np.array([np.clip(m32[0] / m32[2], -lim, lim) * m32[2], m32[1], m32[2]])
+        np.testing.assert_allclose(p["conic"][0], ewa_conic(clamped), rtol=1e-6)
+        assert np.abs(p["conic"][0] - ewa_conic(m32)).max() > 1e-3 * np.abs(p["conic"][0]).max()
+
+
+def test_near_plane_culls_at_and_before_it():
+    """t_z <= near (0.2 m) is culled, just beyond it is kept."""
+    cam = ident_cam(9, 9, 8.0, near=0.2)
+    zs = [0.19, 0.2, 0.21, 0.25]
+    sc = mk_scene([[0.0, 0.0, z] for z in zs], [[0.01, 0.01, 0.01]] * 4, [[1, 0, 0, 0]] * 4, [0.5] * 4)
+    p = oracle.project(sc, cam, prec="f64")
+    assert list(p["visible"]) == [False, False, True, True]
+
+
+def test_opacity_cap_and_equal_depth_order():
+    """alpha is capped at 0.99 (a Gaussian of opacity 0.999 leaves S = 0.99
+    at its centre); Gaussians at exactly equal depth composite in ascending
+    index order."""
+    cam = ident_cam(1, 1, 10.0)
+    sc = mk_scene([[0.0, 0.0, 1.0]], [[1.0, 1.0, 1.0]], [[1, 0, 0, 0]], [0.999])
+    r = oracle.render(sc, cam, prec="f64")
+    assert abs(r["sil"][0, 0] - 0.99) < 1e-15
+    sc = mk_scene([[0.0, 0.0, 1.0]] * 2, [[1.0, 1.0, 1.0]] * 2, [[1, 0, 0, 0]] * 2, [0.5, 0.5],
+                  rgb=[[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    r = oracle.render(sc, cam, prec="f64")
+    np.testing.assert_allclose(r["rgb"][0, 0], [0.5, 0.25, 0.0], atol=1e-15)
+
+
+def test_uncertainty_composited_like_colour_and_hole_count():
+    """Per-Gaussian uncertainty is composited by Eq. 1 (U = u1 a1 + u2 a2 (1 - a1)
+    for two stacked Gaussians at the pixel centre); N_S counts only pixels
+    with S exactly 0, not faint ones (S = 0.005)."""
+    cam = ident_cam(1, 1, 10.0)
+    sc = mk_scene([[0.0, 0.0, 1.0], [0.0, 0.0, 1.5]], [[1.0, 1.0, 1.0]] * 2, [[1, 0, 0, 0]] * 2, [0.5, 0.6],
+                  unc=[2.0, 3.0])
+    r = oracle.render(sc, cam, prec="f64", unc=True)
+    a1, a2 = 0.5, float(np.float32(0.6))
+    assert abs(r["unc"][0, 0] - (2.0 * a1 + 3.0 * a2 * (1 - a1))) < 1e-12
+    su, sh, ns, nf = oracle.candidate(sc, cam, prec="f64")
+    assert abs(su - (2.0 * a1 + 3.0 * a2 * (1 - a1))) < 1e-12 and ns == 0
+    faint = mk_scene([[0.0, 0.0, 1.0]], [[1.0, 1.0, 1.0]], [[1, 0, 0, 0]], [0.005], unc=[1.0])
+    assert abs(oracle.render(faint, cam, prec="f64")["sil"][0, 0] - float(np.float32(0.005))) < 1e-12
+    assert oracle.candidate(faint, cam, prec="f64")[2] == 0
+    behind = mk_scene([[0.0, 0.0, -1.0]], [[1.0, 1.0, 1.0]], [[1, 0, 0, 0]], [0.5], unc=[1.0])
+    assert oracle.candidate(behind, cam, prec="f64")[2] == 1
+
+
 def test_rect_rule_bruteforce_and_tiles():
     """Pixel rectangle = bounding set of pixels whose centre lies within the
     radius of the 2D mean (per axis); tile rectangle = tiles it touches."""
