@@ -447,6 +447,67 @@ def test_adjoint_matches_central_differences(seed):
     assert skipped <= total // 20
 
 
+def _fd_compare(sc, cam, up, fields, rel=1e-5, abs_frac=1e-6):
+    """Central differences of the double-precision render against the
+    oracle's adjoint, coordinate by coordinate; coordinates whose two
+    perturbed renders differ in their contributor counts are skipped."""
+    g = oracle.render_bwd(sc, cam, **up, sem_detach=False, prec="f64")
+    skipped = total = 0
+    for fld in fields:
+        flat = getattr(sc, fld).reshape(-1)
+        ga = g[fld].reshape(-1)
+        scale = np.abs(ga).max() + 1e-12
+        for j in range(flat.size):
+            x0 = float(flat[j])
+            h = 1e-6 * max(1.0, abs(x0))
+            vals, sigs = [], []
+            for sgn in (1, -1):
+                sc2 = Scene(*[np.array(getattr(sc, a), dtype=np.float64) for a in ["means", "scales", "quats",
+                                                                                      "opacity", "rgb"]],
+                            sc.sem_ids, np.array(sc.sem_w, np.float64), sc.m)
+                getattr(sc2, fld).reshape(-1)[j] = x0 + sgn * h
+                L, nc, _ = _loss(sc2, cam, up)
+                vals.append(L)
+                sigs.append(nc)
+            total += 1
+            if not np.array_equal(sigs[0], sigs[1]):
+                skipped += 1
+                continue
+            fd = (vals[0] - vals[1]) / (2 * h)
+            assert abs(fd - ga[j]) <= rel * abs(ga[j]) + abs_frac * scale, (fld, j, fd, ga[j])
+    return skipped, total
+
+
+def test_adjoint_beyond_frustum_clamp_and_at_opacity_cap():
+    """Gaussians whose means lie beyond the 1.3 tan(half-FOV) clamp on each
+    side (their Jacobian is taken at the clamped point, so the chain to the
+    mean differs) and one whose alpha is capped at 0.99 on its centre pixel
+    (no gradient through alpha there): the adjoint still matches central
+    differences."""
+    rng = np.random.default_rng(11)
+    cam = ident_cam(20, 18, 24.0)
+    limx, limy = 1.3 * 10.0 / 24.0, 1.3 * 9.0 / 24.0
+    z = np.array([2.0, 2.2, 2.4, 2.6, 1.9])  # distinct depths: no order flips under perturbation
+    rx = np.array([1.2 * limx, -1.25 * limx, 0.1, -0.05, 0.0])
+    ry = np.array([0.05, -0.1, 1.2 * limy, -1.25 * limy, 0.0])
+    means = np.stack([rx * z, ry * z, z], 1)
+    # the last Gaussian sits on the centre of pixel (10, 9): alpha capped there
+    means[4, :2] = [(10.5 - 10.0) / 24.0 * 1.9, (9.5 - 9.0) / 24.0 * 1.9]
+    scales = np.array([[0.3, 0.25, 0.2], [0.28, 0.3, 0.22], [0.26, 0.3, 0.2], [0.3, 0.24, 0.25], [0.15, 0.15, 0.15]])
+    sc = mk_scene(means, scales, rand_quat(rng, 5), [0.8, 0.7, 0.75, 0.85, 0.9995], rgb=rng.uniform(0, 1, (5, 3)),
+                  ids=np.stack([rng.choice(4, 2, replace=False) for _ in range(5)]).astype(np.int32),
+                  w=rng.uniform(0.1, 0.9, (5, 2)), m=4)
+    p = oracle.project(sc, cam, prec="f64")
+    assert p["visible"].all()
+    H, W = cam.height, cam.width
+    up = dict(d_rgb=rng.normal(size=(H, W, 3)), d_depth=rng.normal(size=(H, W)), d_sil=rng.normal(size=(H, W)),
+              d_sem=rng.normal(size=(H, W, 4)))
+    r = oracle.render(sc, cam, prec="f64")
+    assert r["sil"][9, 10] >= 0.99  # the capped pixel
+    skipped, total = _fd_compare(sc, cam, up, ["means", "scales", "quats", "opacity"])
+    assert skipped <= total // 20
+
+
 def _deep_stack_scene(seed):
     """Tens of large, half-transparent Gaussians stacked along the optical
     axis: every pixel composites many layers, so the adjoint's transmittance
