@@ -909,3 +909,40 @@ def test_voxel_ray_entering_from_outside_and_sampling():
     assert free_sure.any()
     assert (sampled.astype(bool) <= (maybe & 1).astype(bool)).all()  # every sampled voxel may be free
     assert ((sure & 1).astype(bool) <= sampled.astype(bool) | (maybe & 2).astype(bool)).all()
+
+
+def test_scoring_tie_and_band_boundary():
+    """Equal scores among kept candidates pick the lowest index; a voxel
+    centre exactly one band away from a height yields a candidate position,
+    one just beyond does not."""
+    from oracle import explore as ex
+    sums = np.array([[0, 1.0, 50], [0, 1.0, 50], [0, 1.0, 10]])
+    pos = np.array([[1.0, 0, 0], [0, 1.0, 0], [0, 0, 1.0]])
+    sc, keep, best = ex.score(sums, np.full(3, 100), pos, np.zeros(3))
+    assert sc[0, 0] == sc[1, 0] > sc[2, 0] and keep.all() and best == 0
+    centres = np.array([[0.0, 0.0, 1.75], [2.0, 0.0, 1.7501]])
+    p = ex.candidate_positions(centres, 1.0, [1.5], 0.25)
+    np.testing.assert_allclose(p, [[0.0, 0.0, 1.5]])
+
+
+def test_voxel_off_centre_pixel_depth_limit_and_states():
+    """Pixel centres (u + 0.5, v + 0.5) set the ray: in a 2x1 image (f = 2)
+    the left pixel's ray leans 0.25 m per metre to its side, so a depth of
+    1 m ends in voxel (4, 3, 2); a depth equal to max_depth still marks its
+    voxel occupied; occupied wins over free; newly freed voxels are free now
+    and unknown before (not occupied before)."""
+    from oracle import voxel as vx
+    vs = 0.25
+    cam = _axis_cam((0.5 * vs, 2.5 * vs, 2.5 * vs), 0.0, 2, 1, 2.0)
+    depth = np.array([[1.0, 0.0]], np.float32)  # the right pixel is invalid
+    sure, maybe = vx.integrate((0, 0, 0), vs, (8, 6, 5), depth, cam)
+    st = vx.state_of(sure)
+    assert st[2, 3, 4] == 2 and (st == 2).sum() == 1 and (maybe == sure).all()
+    ax = _axis_cam((0.5 * vs, 2.5 * vs, 2.5 * vs), 0.0, 1, 1, 10.0)
+    d5 = np.array([[5.0 * vs]], np.float32)
+    sure, _ = vx.integrate((0, 0, 0), vs, (8, 5, 5), d5, ax, max_depth=5.0 * vs)
+    assert vx.state_of(sure)[2, 2, 5] == 2
+    assert vx.state_of(np.array([0, 1, 2, 3], np.uint8)).tolist() == [0, 1, 2, 2]
+    prev = np.array([[[2, 0, 1, 3]]], np.uint8)
+    cur = np.array([[[1, 1, 1, 1]]], np.uint8)
+    np.testing.assert_allclose(vx.new_free(prev, cur, (0.0, 0.0, 0.0), vs), [[1.5 * vs, 0.5 * vs, 0.5 * vs]])
