@@ -957,7 +957,28 @@ def bench_candidates(args, dev, flush):
                                   "ms": per_view_ms},
             "batched_speedup": per_view_ms / ms,
             "scoring_us": {"value": score_us, "what": "gs_score_candidates over all the views (Eq. 6-8 softmaxes, "
-                                                      "motion cost, pruning, best index), mean of 100 calls"}}
+                                                      "motion cost, pruning, best index), mean of 100 calls"},
+            "cpu_baseline": (cpu_candidates_baseline(sc, cams)
+                             if args.cand_workload == "cand96" and not args.no_cpu_baseline else None)}
+
+
+def cpu_candidates_baseline(sc, cams) -> dict:
+    """The CPU oracle's candidate reductions (Eq. 6, Eq. 7 with Eq. 4) timed
+    on one full view of each resolution of the 96-view set (views 0, 1, 2:
+    170x300, 340x600, 680x1200) and scaled to the set (32 of each)."""
+    try:
+        import oracle
+        ts = []
+        for v in (0, 1, 2):
+            t0 = time.perf_counter()
+            oracle.candidate(sc, cams[v])
+            ts.append(time.perf_counter() - t0)
+        per_batch = (len(cams) / 3.0) * sum(ts)
+        return {"value": len(cams) / per_batch, "unit": "views/s", "cores": 1, "kind": "oracle",
+                "sample": "one full view of each resolution (170x300, 340x600, 680x1200: "
+                          + ", ".join(f"{t:.2f}" for t in ts) + " s, one thread), scaled to 32 views of each"}
+    except Exception as e:  # context only: its failure must not lose the line
+        return {"value": None, "error": str(e)[-200:]}
 
 
 if __name__ == "__main__":
