@@ -236,7 +236,7 @@ def _single_thread_sample(workload: str, row_step: int):
     code = ("import json, bench; from paper_2506_00225_gb300 import scenes; "
             f"print(json.dumps(bench._oracle_sample(scenes.workload({workload!r}), {row_step})))")
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=dict(os.environ, OMP_NUM_THREADS="1"),
-                       capture_output=True, text=True, timeout=900)
+                       capture_output=True, text=True, timeout=180)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-500:])
     dt, nrows = json.loads(r.stdout.strip().splitlines()[-1])
