@@ -196,3 +196,31 @@ def test_dense_preconditions_on_host(lib):
     cfg.recompute_bwd = 1
     assert lib.gs_render_fwd_dense(ctypes.byref(sc), cams, ctypes.byref(cfg), fake, None, None, None, None, None,
                                    None) == N.GS_ERR_UNSUPPORTED
+
+
+def test_noalloc_size_and_argument_checks_on_host(lib):
+    """The allocation-free entry point refuses, before any GPU work, sizes
+    whose workspace would exceed its fixed scratch array and invalid
+    arguments (no device is touched: the pointers are never dereferenced)."""
+    fake = ctypes.c_void_p(1 << 40)
+
+    def call(sc, cams, cfg):
+        return lib.gs_render_fwd_noalloc(ctypes.byref(sc), cams, ctypes.byref(cfg), fake, fake, fake, None, None,
+                                         None)
+
+    def with_pointers(sc):
+        sc.means = sc.scales = sc.quats = sc.opacity = sc.rgb = sc.sem_ids = sc.sem_w = fake
+        return sc
+
+    sc, cams, cfg = _structs(n=4_000_000, w=1200, h=680)
+    size = lib.gs_workspace_size(ctypes.byref(sc), cams, 1, ctypes.byref(cfg))
+    assert size > N.GS_NOALLOC_SCRATCH_BYTES
+    assert call(with_pointers(sc), cams, cfg) == N.GS_ERR_TOO_LARGE
+    # NULL scene arrays with n > 0, misaligned quaternions, a tile shape without kernels
+    sc, cams, cfg = _structs(n=100)
+    assert call(sc, cams, cfg) == N.GS_ERR_ARG
+    sc = with_pointers(sc)
+    sc.quats = ctypes.c_void_p((1 << 40) + 4)
+    assert call(sc, cams, cfg) == N.GS_ERR_ARG
+    sc, cams, cfg = _structs(n=100, tile=(12, 12))
+    assert call(with_pointers(sc), cams, cfg) == N.GS_ERR_UNSUPPORTED
