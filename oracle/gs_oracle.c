@@ -33,6 +33,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #ifdef ORC_DOUBLE
 typedef double real;
@@ -492,62 +495,101 @@ void SFX(orc_render_bwd)(int n, int k, int m, const real *means, const real *sca
   SCENE_FROM_ARGS
   view_t vw;
   view_build(&sc, cam, W, H, &vw);
-  /* per-Gaussian 2D gradients */
-  real *g2 = (real *)calloc((size_t)(n > 0 ? n : 1) * 6, sizeof(real)); /* du dv dca dcb dcc dz */
-  int cap = vw.nv > 0 ? vw.nv : 1;
-  contrib_t *list = (contrib_t *)malloc(sizeof(contrib_t) * (size_t)cap);
+  /* Rows are shared round-robin among the threads; each thread accumulates
+   * its pixels' terms per visible Gaussian in a private array: du dv dca dcb
+   * dcc dz (2D gradients), r g b, opacity, then k semantic weights.  The
+   * arrays are added in thread order at the end, so a given thread count
+   * gives the same sums on every run. */
+  const int nv = vw.nv, stride = 10 + k;
+  int *vis_of = (int *)malloc(sizeof(int) * (size_t)(n > 0 ? n : 1));
+  for (int g = 0; g < n; ++g) vis_of[g] = -1;
+  for (int i = 0; i < nv; ++i) vis_of[vw.order[i]] = i;
+  int nthr = 1;
+#ifdef _OPENMP
+  nthr = omp_get_max_threads();
+#endif
+  real *acc_all = (real *)calloc((size_t)nthr * (size_t)(nv > 0 ? nv : 1) * (size_t)stride, sizeof(real));
+  const int cap = nv > 0 ? nv : 1;
   if (y_step < 1) y_step = 1;
   if (y_end > H || y_end < 0) y_end = H;
-  for (int y = y_begin; y < y_end; y += y_step)
-    for (int x = 0; x < W; ++x) {
-      size_t pid = (size_t)y * W + x;
-      pix_t o;
-      composite_pixel(&sc, &vw, x, y, NULL, &o, list, cap);
-      real dc[3] = {0, 0, 0}, dd = 0, ds = 0;
-      if (d_rgb) { dc[0] = d_rgb[3 * pid]; dc[1] = d_rgb[3 * pid + 1]; dc[2] = d_rgb[3 * pid + 2]; }
-      if (d_depth) dd = d_depth[pid];
-      if (d_sil) ds = d_sil[pid];
-      const real *dp = d_sem ? d_sem + pid * m : NULL;
-      real acc = 0; /* sum over later contributors of w_j * g_j */
-      for (int i = o.n_contrib - 1; i >= 0; --i) {
-        const contrib_t *c = &list[i];
-        int g = c->gid;
-        const proj_t *p = &vw.proj[g];
-        real w = c->alpha * c->T;
-        real gi = dc[0] * sc.rgb[3 * g] + dc[1] * sc.rgb[3 * g + 1] + dc[2] * sc.rgb[3 * g + 2] +
-                  dd * p->tz + ds;
-        real gsem = 0;
-        for (int j = 0; j < k; ++j) {
-          real dpj = dp ? dp[sc.sem_ids[g * k + j]] : 0;
-          g_sem_w[g * k + j] += dpj * w;
-          gsem += dpj * sc.sem_w[g * k + j];
-        }
-        if (!sem_detach) gi += gsem;
-        for (int ch = 0; ch < 3; ++ch) g_rgb[3 * g + ch] += dc[ch] * w;
-        g2[6 * g + 5] += dd * w;
-        real dalpha = c->T * gi - acc / ((real)1 - c->alpha);
-        acc += w * gi;
-        if (c->a < ALPHA_MAX) {
-          g_opacity[g] += dalpha * c->G;
-          real dpow = dalpha * c->a;
-          real dx = c->dx, dy = c->dy;
-          g2[6 * g + 2] += dpow * (-(real)0.5 * dx * dx);
-          g2[6 * g + 3] += dpow * (-dx * dy);
-          g2[6 * g + 4] += dpow * (-(real)0.5 * dy * dy);
-          g2[6 * g + 0] += dpow * (-(p->ca * dx + p->cb * dy));
-          g2[6 * g + 1] += dpow * (-(p->cc * dy + p->cb * dx));
+  const int nrows = y_end > y_begin ? (y_end - y_begin + y_step - 1) / y_step : 0;
+#pragma omp parallel num_threads(nthr)
+  {
+    int t = 0;
+#ifdef _OPENMP
+    t = omp_get_thread_num();
+#endif
+    real *A = acc_all + (size_t)t * (size_t)(nv > 0 ? nv : 1) * (size_t)stride;
+    contrib_t *list = (contrib_t *)malloc(sizeof(contrib_t) * (size_t)cap);
+#pragma omp for schedule(static, 1)
+    for (int r = 0; r < nrows; ++r) {
+      const int y = y_begin + r * y_step;
+      for (int x = 0; x < W; ++x) {
+        size_t pid = (size_t)y * W + x;
+        pix_t o;
+        composite_pixel(&sc, &vw, x, y, NULL, &o, list, cap);
+        real dc[3] = {0, 0, 0}, dd = 0, ds = 0;
+        if (d_rgb) { dc[0] = d_rgb[3 * pid]; dc[1] = d_rgb[3 * pid + 1]; dc[2] = d_rgb[3 * pid + 2]; }
+        if (d_depth) dd = d_depth[pid];
+        if (d_sil) ds = d_sil[pid];
+        const real *dp = d_sem ? d_sem + pid * m : NULL;
+        real acc = 0; /* sum over later contributors of w_j * g_j */
+        for (int i = o.n_contrib - 1; i >= 0; --i) {
+          const contrib_t *c = &list[i];
+          int g = c->gid;
+          const proj_t *p = &vw.proj[g];
+          real *e = A + (size_t)vis_of[g] * stride;
+          real w = c->alpha * c->T;
+          real gi = dc[0] * sc.rgb[3 * g] + dc[1] * sc.rgb[3 * g + 1] + dc[2] * sc.rgb[3 * g + 2] +
+                    dd * p->tz + ds;
+          real gsem = 0;
+          for (int j = 0; j < k; ++j) {
+            real dpj = dp ? dp[sc.sem_ids[g * k + j]] : 0;
+            e[10 + j] += dpj * w;
+            gsem += dpj * sc.sem_w[g * k + j];
+          }
+          if (!sem_detach) gi += gsem;
+          for (int ch = 0; ch < 3; ++ch) e[6 + ch] += dc[ch] * w;
+          e[5] += dd * w;
+          real dalpha = c->T * gi - acc / ((real)1 - c->alpha);
+          acc += w * gi;
+          if (c->a < ALPHA_MAX) {
+            e[9] += dalpha * c->G;
+            real dpow = dalpha * c->a;
+            real dx = c->dx, dy = c->dy;
+            e[2] += dpow * (-(real)0.5 * dx * dx);
+            e[3] += dpow * (-dx * dy);
+            e[4] += dpow * (-(real)0.5 * dy * dy);
+            e[0] += dpow * (-(p->ca * dx + p->cb * dy));
+            e[1] += dpow * (-(p->cc * dy + p->cb * dx));
+          }
         }
       }
     }
-  for (int g = 0; g < n; ++g) {
-    const proj_t *p = &vw.proj[g];
-    if (!p->visible) continue;
-    const real *e = g2 + 6 * g;
-    project_adjoint(p, scales + 3 * g, cam, e[0], e[1], e[2], e[3], e[4], e[5], g_means + 3 * g,
-                    g_scales + 3 * g, g_quats + 4 * g);
+    free(list);
   }
-  free(list);
-  free(g2);
+#pragma omp parallel
+  {
+    real *e = (real *)malloc(sizeof(real) * (size_t)stride);
+#pragma omp for schedule(static)
+    for (int i = 0; i < nv; ++i) {
+      const int g = vw.order[i];
+      const proj_t *p = &vw.proj[g];
+      for (int q = 0; q < stride; ++q) e[q] = 0;
+      for (int t = 0; t < nthr; ++t) {
+        const real *src = acc_all + ((size_t)t * (size_t)nv + (size_t)i) * (size_t)stride;
+        for (int q = 0; q < stride; ++q) e[q] += src[q];
+      }
+      for (int ch = 0; ch < 3; ++ch) g_rgb[3 * g + ch] += e[6 + ch];
+      g_opacity[g] += e[9];
+      for (int j = 0; j < k; ++j) g_sem_w[g * k + j] += e[10 + j];
+      project_adjoint(p, scales + 3 * g, cam, e[0], e[1], e[2], e[3], e[4], e[5], g_means + 3 * g,
+                      g_scales + 3 * g, g_quats + 4 * g);
+    }
+    free(e);
+  }
+  free(acc_all);
+  free(vis_of);
   view_free(&vw);
 }
 

@@ -97,17 +97,17 @@ MUTANTS = [
      'gq[0] += (dw - w * dot) / p->qn;',
      'gq[0] += dw / p->qn;'),
     ('oracle/gs_oracle.c', 'opacity grad G->a',
-     'g_opacity[g] += dalpha * c->G;',
-     'g_opacity[g] += dalpha * c->a;'),
+     'e[9] += dalpha * c->G;',
+     'e[9] += dalpha * c->a;'),
     ('oracle/gs_oracle.c', 'depth grad w->alpha',
-     'g2[6 * g + 5] += dd * w;',
-     'g2[6 * g + 5] += dd * c->alpha;'),
+     'e[5] += dd * w;',
+     'e[5] += dd * c->alpha;'),
     ('oracle/gs_oracle.c', 'cap branch always',
      'if (c->a < ALPHA_MAX) {',
      'if (1) {'),
     ('oracle/gs_oracle.c', 'sem grad w->T',
-     'g_sem_w[g * k + j] += dpj * w;',
-     'g_sem_w[g * k + j] += dpj * c->T;'),
+     'e[10 + j] += dpj * w;',
+     'e[10 + j] += dpj * c->T;'),
     ('oracle/gs_oracle.c', 'sem detach ignored',
      'if (!sem_detach) gi += gsem;',
      'gi += gsem;'),
