@@ -418,9 +418,10 @@ gs_status gs_voxel_new_free(const gs_voxel_grid *grid, const uint32_t *prev, con
 /* No-allocation variant of one forward render (the paper has no counterpart:
  * this is an interface for callers of this library).
  *
- * Some callers cannot allocate device memory: code running while a CUDA graph
- * is being captured, real-time loops that must never block inside an
- * allocator, and plug-in hosts that own all device memory.  This entry point
+ * Some callers cannot allocate device memory: plug-in hosts that own all
+ * device memory and give their plug-ins none, and real-time loops that must
+ * never block inside an allocator (cudaMalloc and cudaFree may synchronise
+ * the device).  This entry point
  * runs the same kernels as gs_project + gs_bin_sort + gs_render_fwd for one
  * view, but its workspace is a fixed device array of
  * GS_NOALLOC_SCRATCH_BYTES inside the library, so it calls no cudaMalloc,
@@ -433,7 +434,9 @@ gs_status gs_voxel_new_free(const gs_voxel_grid *grid, const uint32_t *prev, con
  *     GS_NOALLOC_SCRATCH_BYTES.
  *   - The first call on each device looks up the array's device address
  *     (with that device current) and caches it; make that first call before
- *     any stream capture.
+ *     any stream capture.  The cached address belongs to the device's primary
+ *     context: after cudaDeviceReset of that device, do not call this entry
+ *     point again in the same process.
  *   - All calls share the one array, which keeps the previous call's
  *     contents; the chain clears what must start at zero (counters, status).
  *     Calls that overlap on the GPU (other streams, other host threads) race
@@ -443,6 +446,27 @@ gs_status gs_voxel_new_free(const gs_voxel_grid *grid, const uint32_t *prev, con
 gs_status gs_render_fwd_noalloc(const gs_scene *scene, const gs_camera *cam, const gs_config *cfg, float *rgb,
                                 float *depth, float *sil, float *sem, gs_counters *counters_out,
                                 gs_stream_t stream);
+
+/* Testing hooks (host only; no device work).  Grid sizes of the grid-stride
+ * kernels follow the multiprocessor count of the current device, which the
+ * library queries once per device (cudaDevAttrMultiProcessorCount) and
+ * caches; one process may drive several devices.
+ *   gs_testing_set_sm_query  replaces that query by `query` (NULL restores
+ *                            the device query), so host tests can check the
+ *                            grids for any SM count without a GPU;
+ *   gs_testing_grid          the grid (CTAs) the library would launch for
+ *                            one of the kernels below on the current device
+ *                            (0 when the SM count is unknown, -1 for an
+ *                            unknown id). */
+enum {
+  GS_GRID_EMIT_CHUNKS = 0, /* chunks of the pair-emission count pass: 2 per SM, at most 1024 */
+  GS_GRID_EMIT_WRITE = 1,  /* pair-emission write pass: 8 per SM */
+  GS_GRID_SORT_RESET = 2,  /* radix-sort reset and digit histogram: 2 per SM */
+  GS_GRID_RANGES = 3,      /* tile-range marking: 4 per SM */
+  GS_GRID_ZERO_GRAD = 4    /* 2D-gradient clear of the adjoint: 2 per SM */
+};
+void gs_testing_set_sm_query(int (*query)(void));
+int64_t gs_testing_grid(int which);
 
 /* Synchronises `stream`, then copies the workspace counters to *out (host).
  * Returns the first device error recorded (GS_ERR_CAPACITY, GS_ERR_TIMEOUT)

@@ -20,7 +20,7 @@ EXPORTS = ["gs_workspace_size", "gs_workspace_layout", "gs_project", "gs_bin_sor
            "gs_render_bwd_objective", "gs_render_candidates", "gs_l1_loss", "gs_mapping_loss", "gs_render_fwd_noalloc",
            "gs_score_candidates", "gs_candidate_poses", "gs_candidate_positions", "gs_topk_init", "gs_topk_gather",
            "gs_voxel_words", "gs_voxel_scratch_words", "gs_voxel_update", "gs_voxel_new_free", "gs_read_counters",
-           "gs_status_string"]
+           "gs_status_string", "gs_testing_set_sm_query", "gs_testing_grid"]
 
 
 class GsScene(ctypes.Structure):
@@ -102,7 +102,13 @@ _SIGS = {
                                          c_void_p]),
     "gs_read_counters": (ctypes.c_int, [c_void_p, P(GsCounters), c_void_p]),
     "gs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "gs_testing_set_sm_query": (None, [c_void_p]),
+    "gs_testing_grid": (c_int64, [ctypes.c_int]),
 }
+
+# gs_testing_grid ids (include/gs.h)
+GS_GRID_EMIT_CHUNKS, GS_GRID_EMIT_WRITE, GS_GRID_SORT_RESET, GS_GRID_RANGES, GS_GRID_ZERO_GRAD = range(5)
+SM_QUERY = ctypes.CFUNCTYPE(ctypes.c_int)
 
 _LIB = None
 

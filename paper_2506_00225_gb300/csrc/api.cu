@@ -3,12 +3,59 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
+#include <mutex>
+#include <set>
+#include <utility>
 #include <vector>
 
 #include "gs_internal.cuh"
 #include "render_common.cuh"
 
 namespace gs {
+
+// ---------------------------------------------------------------------------
+// Device facts.  One process may drive several devices: the multiprocessor
+// count is cached per device index, and the dynamic shared-memory limit of a
+// kernel is raised once per (kernel, device), under a lock.
+// ---------------------------------------------------------------------------
+constexpr int kMaxDevices = 64;
+static std::atomic<int> g_sms[kMaxDevices];
+static std::atomic<int (*)(void)> g_sms_query{nullptr};  // replaces the device query (host tests)
+
+int device_sms() {
+  if (int (*q)(void) = g_sms_query.load()) return q();
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
+  int v = g_sms[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 0;
+  g_sms[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
+unsigned sm_grid(int ctas_per_sm) {
+  const int sms = device_sms();
+  return sms > 0 && ctas_per_sm > 0 ? (unsigned)sms * (unsigned)ctas_per_sm : 0u;
+}
+
+int emit_chunks() {
+  const int sms = device_sms();
+  return sms > 0 ? (2 * sms < kEmitCtasMax ? 2 * sms : kEmitCtasMax) : 0;
+}
+
+cudaError_t ensure_smem_limit(const void *func, int bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<const void *, int>> done;  // (kernel, device) pairs already raised
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({func, dev})) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.insert({func, dev});
+  return e;
+}
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -93,7 +140,7 @@ bool make_layout(const gs_scene *scene, const gs_camera *cams, int n_views, cons
   L->off_rec_sem = take(8 * (size_t)rcap * scene->k);
   for (int i = 0; i < 2; ++i) L->off_dkeys[i] = take(8 * (size_t)rcap);
   for (int i = 0; i < 2; ++i) L->off_dvals[i] = take(4 * (size_t)rcap);
-  L->off_epart = take(sizeof(uint32_t) * (kEmitCtas + 1));
+  L->off_epart = take(sizeof(uint32_t) * (kEmitCtasMax + 1));
   L->off_rloc = take(4 * (size_t)rcap);
   for (int i = 0; i < 2; ++i) L->off_pkeys[i] = take(4 * (size_t)pcap);
   for (int i = 0; i < 2; ++i) L->off_pvals[i] = take(4 * (size_t)pcap);
@@ -169,7 +216,7 @@ WsPtrs ws_ptrs(const Layout &L, void *ws) {
   return P;
 }
 
-static void fill_cam_table(const gs_camera *cams, int n_views, int tw, int th, CamTable *tab) {
+void fill_cam_table(const gs_camera *cams, int n_views, int tw, int th, CamTable *tab) {
   uint32_t off = 0;
   for (int v = 0; v < n_views; ++v) {
     const gs_camera &c = cams[v];
@@ -207,10 +254,8 @@ static bool shape_compiled(int tw, int th) {
     if (_e != cudaSuccess) return GS_ERR_CUDA;   \
   } while (0)
 
-static gs_status run_project(const Layout &L, const WsPtrs &P, const gs_scene &sc, const gs_camera *cams,
-                             cudaStream_t s) {
-  std::vector<unsigned char> buf(sizeof(CamTable));
-  CamTable *tab = reinterpret_cast<CamTable *>(buf.data());
+gs_status run_project_with(const Layout &L, const WsPtrs &P, const gs_scene &sc, const gs_camera *cams,
+                           CamTable *tab, cudaStream_t s) {
   memset(tab, 0, sizeof(CamTable));
   fill_cam_table(cams, L.n_views, L.tile_w, L.tile_h, tab);
   GS_CHECK_CUDA(launch_setup_views(*tab, L.n_views, P, (uint32_t)L.total_tiles, true, s));
@@ -218,7 +263,13 @@ static gs_status run_project(const Layout &L, const WsPtrs &P, const gs_scene &s
   return GS_OK;
 }
 
-static gs_status run_bin_sort(const Layout &L, const WsPtrs &P, cudaStream_t s) {
+static gs_status run_project(const Layout &L, const WsPtrs &P, const gs_scene &sc, const gs_camera *cams,
+                             cudaStream_t s) {
+  std::vector<unsigned char> buf(sizeof(CamTable));
+  return run_project_with(L, P, sc, cams, reinterpret_cast<CamTable *>(buf.data()), s);
+}
+
+gs_status run_bin_sort(const Layout &L, const WsPtrs &P, cudaStream_t s) {
   int dbuf = 0, pbuf = 0;
   GS_CHECK_CUDA(launch_radix_sort_u64(L, P, L.key_bits_depth, &dbuf, s));
   GS_CHECK_CUDA(launch_emit_pairs(L, P, dbuf, s));
@@ -428,6 +479,19 @@ gs_status gs_mapping_loss(int64_t npix, int m, int k, const float *rgb, const fl
   GS_CHECK_CUDA(launch_mapping_loss(npix, m, k, rgb, t_rgb, depth, t_depth, sil, sem, t_sem, d_rgb, d_depth, d_sem,
                                     loss, partial, (cudaStream_t)stream));
   return GS_OK;
+}
+
+void gs_testing_set_sm_query(int (*query)(void)) { g_sms_query.store(query); }
+
+int64_t gs_testing_grid(int which) {
+  switch (which) {
+    case GS_GRID_EMIT_CHUNKS: return emit_chunks();
+    case GS_GRID_EMIT_WRITE: return sm_grid(8);
+    case GS_GRID_SORT_RESET: return sm_grid(2);
+    case GS_GRID_RANGES: return sm_grid(4);
+    case GS_GRID_ZERO_GRAD: return sm_grid(2);
+    default: return -1;
+  }
 }
 
 gs_status gs_read_counters(void *ws, gs_counters *out, gs_stream_t stream) {

@@ -383,12 +383,9 @@ __global__ void k_zero_doubles(double *p, int n) {
 
 template <int TW, int TH>
 static cudaError_t launch_cand_shape(const CandArgs &a, uint32_t grid, size_t smem, cudaStream_t s) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_candidates<TW, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemBudget);
+  {
+    const cudaError_t e = ensure_smem_limit((const void *)k_candidates<TW, TH>, (int)kSmemBudget);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   k_candidates<TW, TH><<<grid, TW * TH, smem, s>>>(a);
   return cudaGetLastError();
@@ -396,12 +393,9 @@ static cudaError_t launch_cand_shape(const CandArgs &a, uint32_t grid, size_t sm
 
 template <int TW, int TH, int K>
 static cudaError_t launch_cand_sem(const CandArgs &a, uint32_t grid, size_t smem, cudaStream_t s) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_cand_sem<TW, TH, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemBudget);
+  {
+    const cudaError_t e = ensure_smem_limit((const void *)k_cand_sem<TW, TH, K>, (int)kSmemBudget);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   k_cand_sem<TW, TH, K><<<grid, TW * TH, smem, s>>>(a);
   return cudaGetLastError();

@@ -18,7 +18,7 @@ constexpr int kMaxRadixPasses = 8;       // 64-bit keys at most
 constexpr int kProjThreads = 256;
 constexpr int kProjItems = 4;
 constexpr int kProjBlock = kProjThreads * kProjItems;  // Gaussians per projection CTA
-constexpr int kEmitCtas = 2 * 152;
+constexpr int kEmitCtasMax = 1024;   // chunks of the pair emission (2 per SM, capped; sizes the chunk totals)
 constexpr int64_t kCandMaskBudget = 48ll << 30;  // contributor-bit bytes the candidate layout may hold
 constexpr int kEmitThreads = 256;
 
@@ -116,6 +116,26 @@ struct WsPtrs {
   double *lpart;   // [tiles of view 0][3] per-tile L1 sums
   float *semg;     // [n][k] d(semantic term)/d(sem_w) of the fused Sec. 3.1 objective, before dL/dloss
 };
+
+// Host side (api.cu): device facts, queried per device and cached
+// (thread-safe).  device_sms() is the multiprocessor count of the current
+// device (0 when it cannot be queried); sm_grid(c) is c CTAs per SM for a
+// grid-stride kernel (0 on failure); emit_chunks() is the chunk count of the
+// pair emission (2 per SM, at most kEmitCtasMax); ensure_smem_limit raises
+// the dynamic shared-memory limit of one kernel on the current device the
+// first time that device launches it.
+int device_sms();
+unsigned sm_grid(int ctas_per_sm);
+int emit_chunks();
+cudaError_t ensure_smem_limit(const void *func, int bytes);
+
+// Host side (api.cu): the camera table of a call (kernel parameter of the
+// view setup), and the launch chains of gs_project and gs_bin_sort; `tab` is
+// the caller's storage for the table (no heap use inside).
+void fill_cam_table(const gs_camera *cams, int n_views, int tw, int th, CamTable *tab);
+gs_status run_project_with(const Layout &L, const WsPtrs &P, const gs_scene &sc, const gs_camera *cams,
+                           CamTable *tab, cudaStream_t s);
+gs_status run_bin_sort(const Layout &L, const WsPtrs &P, cudaStream_t s);
 
 // Host side (api.cu).
 bool make_layout(const gs_scene *scene, const gs_camera *cams, int n_views, const gs_config *cfg, Layout *L);

@@ -6,7 +6,7 @@
 
 namespace gs {
 
-constexpr int kLossCtas = 2 * 152;
+constexpr int kLossMaxCtas = 2048;  // partial sums the caller's scratch holds (one per CTA)
 constexpr int kLossThreads = 256;
 
 __device__ __forceinline__ float l1_term(float x, float t, float scale, float &grad) {
@@ -98,11 +98,14 @@ __global__ void k_l1_final(const double *partial, int n, float *loss) {
 cudaError_t launch_l1_loss(int64_t npix, int m, const float *rgb, const float *t_rgb, const float *depth,
                            const float *t_depth, const float *sem, const float *t_sem, float *d_rgb, float *d_depth,
                            float *d_sem, float *loss, double *partial, cudaStream_t s) {
-  k_l1_partial<<<kLossCtas, kLossThreads, 0, s>>>(npix, m, rgb, t_rgb, depth, t_depth, sem, t_sem, d_rgb, d_depth,
-                                                  d_sem, partial);
+  // two CTAs per SM, within the caller's partial-sum scratch
+  const unsigned ctas = min(sm_grid(2), (unsigned)kLossMaxCtas);
+  if (ctas == 0) return cudaErrorInvalidDevice;
+  k_l1_partial<<<ctas, kLossThreads, 0, s>>>(npix, m, rgb, t_rgb, depth, t_depth, sem, t_sem, d_rgb, d_depth, d_sem,
+                                             partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_l1_final<<<1, 256, 0, s>>>(partial, kLossCtas, loss);
+  k_l1_final<<<1, 256, 0, s>>>(partial, (int)ctas, loss);
   return cudaGetLastError();
 }
 

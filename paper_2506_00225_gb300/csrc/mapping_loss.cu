@@ -23,7 +23,7 @@
 namespace gs {
 
 constexpr int kMlThreads = 256;
-constexpr int kMlCtas = 4 * 152;
+constexpr int kMlMaxCtas = GS_MAPPING_LOSS_PARTIALS / 2;  // two partial sums per CTA
 constexpr int kMlG = 4;  // pixels per warp round
 constexpr float kSilMin = 0.99f;
 constexpr float kWColour = 0.5f;
@@ -150,11 +150,14 @@ cudaError_t launch_mapping_loss(int64_t npix, int m, int k, const float *rgb, co
                                 const float *t_depth, const float *sil, const float *sem, const float *t_sem,
                                 float *d_rgb, float *d_depth, float *d_sem, float *loss, double *partial,
                                 cudaStream_t s) {
-  k_mapping_loss<<<kMlCtas, kMlThreads, 0, s>>>(npix, m, logf((float)k), rgb, t_rgb, depth, t_depth, sil, sem, t_sem,
+  // four CTAs per SM, within the caller's partial-sum scratch
+  const unsigned ctas = min(sm_grid(4), (unsigned)kMlMaxCtas);
+  if (ctas == 0) return cudaErrorInvalidDevice;
+  k_mapping_loss<<<ctas, kMlThreads, 0, s>>>(npix, m, logf((float)k), rgb, t_rgb, depth, t_depth, sil, sem, t_sem,
                                                 d_rgb, d_depth, d_sem, partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_mapping_loss_final<<<1, 256, 0, s>>>(partial, kMlCtas, (double)npix, loss);
+  k_mapping_loss_final<<<1, 256, 0, s>>>(partial, (int)ctas, (double)npix, loss);
   return cudaGetLastError();
 }
 

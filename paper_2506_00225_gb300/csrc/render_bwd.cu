@@ -276,12 +276,9 @@ __global__ void k_zero_grad2d(float4 *g, const Counters *cnt, uint32_t rcap) {
 
 template <int TW, int TH, bool CODES, int K, int PPT>
 static cudaError_t launch_bwd_shape(const BwdArgs &a, int grid, size_t smem, cudaStream_t s) {
-  static bool attr_set = false;
-  if (!attr_set) {  // the sign words of large class counts need more than 48 KB
-    cudaError_t e = cudaFuncSetAttribute(k_render_bwd<TW, TH, CODES, K, PPT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
+  {  // the sign words of large class counts need more than 48 KB
+    const cudaError_t e = ensure_smem_limit((const void *)k_render_bwd<TW, TH, CODES, K, PPT>, (int)kSmemBudget);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   k_render_bwd<TW, TH, CODES, K, PPT><<<grid, TW * TH / PPT, smem, s>>>(a);
   return cudaGetLastError();
@@ -318,7 +315,7 @@ cudaError_t launch_render_bwd(const Layout &L, const WsPtrs &P, int pbuf, const 
                               const float *d_depth, const float *d_sil, const float *d_sem, int sem_detach,
                               float *g_rgb, float *g_sem_w, cudaStream_t s, const float *loss_scale,
                               int objective) {
-  k_zero_grad2d<<<2 * 152, 256, 0, s>>>(P.grad2d, P.counters, (uint32_t)L.rcap);
+  k_zero_grad2d<<<sm_grid(2), 256, 0, s>>>(P.grad2d, P.counters, (uint32_t)L.rcap);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   BwdArgs a{};

@@ -488,12 +488,9 @@ __global__ void k_l1_tiles_final(const double *lpart, int ntiles, double npix, d
 
 template <int TW, int TH, bool L1, int K>
 static cudaError_t launch_semantic(const FwdArgs &a, int grid, size_t smem, cudaStream_t s) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_semantic<TW, TH, L1, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemBudget);
+  {
+    const cudaError_t e = ensure_smem_limit((const void *)k_semantic<TW, TH, L1, K>, (int)kSmemBudget);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   k_semantic<TW, TH, L1, K><<<grid, TW * TH, smem, s>>>(a);
   return cudaGetLastError();

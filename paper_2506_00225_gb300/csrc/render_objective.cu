@@ -262,19 +262,16 @@ __global__ void k_add_scaled(float *g, const float *src, const float *scale, siz
 }
 
 static unsigned elementwise_grid(size_t n) {
-  const size_t b = (n + 255) / 256;
-  return (unsigned)(b < 4 * 152 ? b : 4 * 152);
+  const size_t b = (n + 255) / 256, cap = sm_grid(4);
+  return (unsigned)(b < cap ? b : cap);
 }
 
 template <int TW, int TH, int K>
 static cudaError_t launch_sem_objective(const FwdArgs &a, int grid, size_t smem, float log_k, float inv_n,
                                         cudaStream_t s) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_sem_objective<TW, TH, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kSmemBudget);
+  {
+    const cudaError_t e = ensure_smem_limit((const void *)k_sem_objective<TW, TH, K>, (int)kSmemBudget);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   k_sem_objective<TW, TH, K><<<grid, TW * TH, smem, s>>>(a, log_k, inv_n);
   return cudaGetLastError();

@@ -32,7 +32,6 @@ constexpr int kOsWarps = kOsThreads / 32;
 // small tiles (more CTAs in flight, shorter per-tile latency), large ones
 // large tiles (fewer look-back steps, bounded look-back storage)
 inline int os_items(int64_t capacity) { return capacity <= (1 << 20) ? 8 : 16; }
-constexpr int kHistCtas = 2 * 152;
 constexpr unsigned long long kFlagA = 1ull << 62;   // tile aggregate published
 constexpr unsigned long long kFlagP = 2ull << 62;   // inclusive prefix published
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
@@ -219,11 +218,9 @@ static cudaError_t os_passes(K *keys[2], uint32_t *vals[2], const uint32_t *coun
                              uint32_t *tickets, uint32_t *ghist, unsigned long long *lookback, uint32_t lb_tiles,
                              Counters *counters, uint32_t spin_limit, cudaStream_t s) {
   const size_t smem = (size_t)kOsThreads * ITEMS * (sizeof(K) + sizeof(uint32_t));
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_os_pass<K, ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    const cudaError_t e = ensure_smem_limit((const void *)k_os_pass<K, ITEMS>, (int)smem);
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   for (int p = 0; p < passes; ++p) {
     const int src = p & 1, dst = src ^ 1;
@@ -243,7 +240,7 @@ static cudaError_t os_reset(const uint32_t *count_p, uint32_t cap, int passes, u
                             unsigned long long *lookback, cudaStream_t s) {
   const uint32_t lb_tiles = (uint32_t)sort_tiles(cap);
   if (passes < 1 || passes > kMaxRadixPasses || lb_tiles == 0) return cudaErrorInvalidValue;
-  k_os_reset<<<2 * 152, 256, 0, s>>>(count_p, cap, passes, tickets, ghist, lookback, lb_tiles,
+  k_os_reset<<<sm_grid(2), 256, 0, s>>>(count_p, cap, passes, tickets, ghist, lookback, lb_tiles,
                                      (uint32_t)(kOsThreads * os_items(cap)));
   return cudaGetLastError();
 }
@@ -261,7 +258,7 @@ static cudaError_t os_sort(K *keys[2], uint32_t *vals[2], const uint32_t *count_
   if (!hist_ready) {
     cudaError_t e = os_reset(count_p, cap, passes, tickets, ghist, lookback, s);
     if (e != cudaSuccess) return e;
-    k_os_hist<K><<<kHistCtas, 256, 0, s>>>(keys[0], count_p, cap, passes, ghist);
+    k_os_hist<K><<<sm_grid(2), 256, 0, s>>>(keys[0], count_p, cap, passes, ghist);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -329,9 +326,9 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_count(const uint32_t *__r
 // Record (position in the depth order) of pair p of the emission: the chunk
 // c (largest with epart[c] <= p), then the largest q of the chunk with
 // rloc[q] <= p - epart[c].  Records with no tile are never selected.
-__device__ __forceinline__ uint32_t find_record(uint32_t p, uint32_t count, uint32_t per, const uint32_t *s_epart,
-                                                const uint32_t *__restrict__ rloc) {
-  int lo = 0, hi = kEmitCtas - 1;
+__device__ __forceinline__ uint32_t find_record(uint32_t p, uint32_t count, uint32_t per, int n_chunks,
+                                                const uint32_t *s_epart, const uint32_t *__restrict__ rloc) {
+  int lo = 0, hi = n_chunks - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (s_epart[mid] <= p) lo = mid; else hi = mid - 1;
@@ -392,22 +389,22 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_write(const uint32_t *__r
                                                              const uint32_t *__restrict__ rloc,
                                                              uint32_t *__restrict__ pkeys,
                                                              uint32_t *__restrict__ pvals, int hist_passes,
-                                                             uint32_t *__restrict__ ghist) {
-  __shared__ uint32_t s_epart[kEmitCtas];
+                                                             uint32_t *__restrict__ ghist, int n_chunks) {
+  __shared__ uint32_t s_epart[kEmitCtasMax];
   __shared__ uint32_t s_hist[kEmitHistPasses * kRadix];
   __shared__ uint32_t s_start[kEmitBlock];  // first pair of records qa, qa + 1, ...
   __shared__ uint32_t s_q[2];
   if (cnt->status & kStatusTimeout) return;
-  for (int i = threadIdx.x; i < kEmitCtas; i += kEmitThreads) s_epart[i] = epart[i];
+  for (int i = threadIdx.x; i < n_chunks; i += kEmitThreads) s_epart[i] = epart[i];
   for (int i = threadIdx.x; i < kEmitHistPasses * kRadix; i += kEmitThreads) s_hist[i] = 0u;
   __syncthreads();
   const uint32_t count = min(cnt->n_records, rcap);
   const uint32_t npairs = min(cnt->n_pairs, pcap);
-  const uint32_t per = (count + kEmitCtas - 1) / kEmitCtas;
+  const uint32_t per = (count + n_chunks - 1) / n_chunks;
   const uint32_t lane = lane_id();
   for (uint32_t P0 = blockIdx.x * (uint32_t)kEmitBlock; P0 < npairs; P0 += gridDim.x * (uint32_t)kEmitBlock) {
     const uint32_t P1 = min(npairs, P0 + (uint32_t)kEmitBlock);
-    if (threadIdx.x < 2) s_q[threadIdx.x] = find_record(threadIdx.x ? P1 - 1 : P0, count, per, s_epart, rloc);
+    if (threadIdx.x < 2) s_q[threadIdx.x] = find_record(threadIdx.x ? P1 - 1 : P0, count, per, n_chunks, s_epart, rloc);
     __syncthreads();
     const uint32_t qa = s_q[0], nrec = s_q[1] - qa + 1;
     // more records than staging slots only with records of no tile
@@ -430,7 +427,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_write(const uint32_t *__r
           rec[it] = qa + (uint32_t)lo;
           jj[it] = p - s_start[lo];
         } else {
-          rec[it] = find_record(p, count, per, s_epart, rloc);
+          rec[it] = find_record(p, count, per, n_chunks, s_epart, rloc);
           jj[it] = p - pair_start(rec[it], per, s_epart, rloc);
         }
       }
@@ -475,11 +472,14 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit_write(const uint32_t *__r
 }
 
 cudaError_t launch_emit_pairs(const Layout &L, const WsPtrs &P, int dbuf, cudaStream_t s) {
-  k_emit_count<<<kEmitCtas, kEmitThreads, 0, s>>>(P.dvals[dbuf], P.rec_rect, P.counters, (uint32_t)L.rcap, L.tile_w,
+  // chunk count: the same in the count pass (its grid), the scan and the write pass
+  const int n_chunks = emit_chunks();
+  if (n_chunks < 1) return cudaErrorInvalidDevice;
+  k_emit_count<<<n_chunks, kEmitThreads, 0, s>>>(P.dvals[dbuf], P.rec_rect, P.counters, (uint32_t)L.rcap, L.tile_w,
                                                   L.tile_h, P.epart, P.rloc);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = launch_scan_single(P.epart, (uint32_t)kEmitCtas, &P.counters->n_pairs, (uint32_t)L.pcap, P.counters, s);
+  e = launch_scan_single(P.epart, (uint32_t)n_chunks, &P.counters->n_pairs, (uint32_t)L.pcap, P.counters, s);
   if (e != cudaSuccess) return e;
   // the tile sort's reset, then the emission counts its digits
   const int passes = radix_passes(L.key_bits_tile);
@@ -493,9 +493,9 @@ cudaError_t launch_emit_pairs(const Layout &L, const WsPtrs &P, int dbuf, cudaSt
             : tw == 8 && th == 8   ? k_emit_write<8, 8>
             : tw == 32 && th == 8  ? k_emit_write<32, 8>
                                    : k_emit_write<0, 0>;
-  kern<<<8 * 152, kEmitThreads, 0, s>>>(P.dvals[dbuf], P.rec_rect, P.rec_view, P.cams, P.counters, (uint32_t)L.rcap,
-                                        (uint32_t)L.pcap, tw, th, P.epart, P.rloc, P.pkeys[0], P.pvals[0], passes,
-                                        ghist);
+  kern<<<sm_grid(8), kEmitThreads, 0, s>>>(P.dvals[dbuf], P.rec_rect, P.rec_view, P.cams, P.counters,
+                                           (uint32_t)L.rcap, (uint32_t)L.pcap, tw, th, P.epart, P.rloc, P.pkeys[0],
+                                           P.pvals[0], passes, ghist, n_chunks);
   return cudaGetLastError();
 }
 
@@ -540,10 +540,12 @@ __global__ void k_ranges_mark(const uint32_t *__restrict__ pkeys, const Counters
 cudaError_t launch_tile_ranges(const Layout &L, const WsPtrs &P, int pbuf, cudaStream_t s) {
   const uint32_t T = (uint32_t)L.total_tiles;
   if (T == 0) return cudaSuccess;
-  k_ranges_clear<<<min((T + 255) / 256, 4u * 152u), 256, 0, s>>>(P.ranges, T);
+  const unsigned g4 = sm_grid(4);
+  if (g4 == 0) return cudaErrorInvalidDevice;
+  k_ranges_clear<<<min((T + 255) / 256, g4), 256, 0, s>>>(P.ranges, T);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_ranges_mark<<<4 * 152, 256, 0, s>>>(P.pkeys[pbuf], P.counters, (uint32_t)L.pcap, T, P.ranges);
+  k_ranges_mark<<<g4, 256, 0, s>>>(P.pkeys[pbuf], P.counters, (uint32_t)L.pcap, T, P.ranges);
   return cudaGetLastError();
 }
 

@@ -73,8 +73,8 @@ __global__ void k_topk_gather(int64_t n, int m, int k, const float *__restrict__
 }
 
 static unsigned grid_for(int64_t items, int per_cta) {
-  const int64_t b = (items + per_cta - 1) / per_cta;
-  return (unsigned)(b < 8 * 152 ? (b > 0 ? b : 1) : 8 * 152);
+  const int64_t b = (items + per_cta - 1) / per_cta, cap = sm_grid(8);
+  return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
 }  // namespace gs

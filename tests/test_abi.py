@@ -224,3 +224,39 @@ def test_noalloc_size_and_argument_checks_on_host(lib):
     assert call(sc, cams, cfg) == N.GS_ERR_ARG
     sc, cams, cfg = _structs(n=100, tile=(12, 12))
     assert call(with_pointers(sc), cams, cfg) == N.GS_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("sms", [1, 100, 152, 160, 600])
+def test_grids_follow_the_sm_count(lib, sms):
+    """The grid-stride kernels size their grids from the device's SM count
+    (queried per device), not a fixed GB300 figure: with the query stubbed,
+    every grid scales with the stubbed count."""
+    calls = []
+
+    def query():
+        calls.append(1)
+        return sms
+
+    cb = N.SM_QUERY(query)
+    lib.gs_testing_set_sm_query(ctypes.cast(cb, ctypes.c_void_p))
+    try:
+        assert lib.gs_testing_grid(N.GS_GRID_EMIT_CHUNKS) == min(2 * sms, 1024)
+        assert lib.gs_testing_grid(N.GS_GRID_EMIT_WRITE) == 8 * sms
+        assert lib.gs_testing_grid(N.GS_GRID_SORT_RESET) == 2 * sms
+        assert lib.gs_testing_grid(N.GS_GRID_RANGES) == 4 * sms
+        assert lib.gs_testing_grid(N.GS_GRID_ZERO_GRAD) == 2 * sms
+        assert lib.gs_testing_grid(99) == -1
+        assert calls
+    finally:
+        lib.gs_testing_set_sm_query(None)
+
+
+def test_grid_without_a_device_is_zero(lib):
+    """Without a device (this CPU container) the SM count is unknown and the
+    library reports a zero grid instead of a guessed one; launch chains then
+    fail with a CUDA error rather than running a wrong-sized grid."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    lib.gs_testing_set_sm_query(None)
+    assert lib.gs_testing_grid(N.GS_GRID_SORT_RESET) == 0
