@@ -29,7 +29,6 @@ struct BwdArgs {
   const float *tfinal;
   const uint32_t *nlast;
   const float *d_rgb, *d_depth, *d_sil, *d_sem;
-  int sem_detach;
   const Counters *counters;
   float4 *grad2d;
   float *g_rgb, *g_sem_w;
@@ -41,30 +40,92 @@ struct BwdArgs {
   double npix;
   const uint32_t *mask_off;  // contributor bitmasks of the forward pass
   const uint32_t *masks;
+  int warp_bytes;            // shared memory of one warp: staging slots + reduction rows
 };
 
 __device__ __forceinline__ float sign_code(uint32_t nz, uint32_t ng, int bit, float s) {
   return ((nz >> bit) & 1u) ? (((ng >> bit) & 1u) ? -s : s) : 0.f;
 }
 
-// Per contributing (pixel, Gaussian) the thread forms NV values
-//   0..6  du, dv, da, db, dc, dopacity, ddepth   (2D gradients of the record)
-//   7..9  drgb                                   (colour of the Gaussian)
-//   10..  dsem_w (k values)
-// which a transposed warp reduction sums over the warp's 32 pixels; each lane
-// then adds one of the totals with a single scalar atomic.
-// K > 0 fixes the top-k count at compile time (exact unrolling of the
-// per-class terms); the reduction width follows: 16 values for K <= 6,
-// else 32.
-template <int TW, int TH, bool CODES, int K, int PPT>
+// +w, -w or 0 for the class bit at left shift sh = 31 - bit of a (nonzero,
+// negative) sign-code word pair: all-ones / zero mask from the nonzero bit,
+// sign from the negative bit (a zero code may come out as -0.0, which adds
+// nothing).
+__device__ __forceinline__ float signed_weight(uint2 cw, uint32_t sh, float w) {
+  const uint32_t nzm = (uint32_t)((int32_t)(cw.x << sh) >> 31);
+  const uint32_t sg = (cw.y << sh) & 0x80000000u;
+  return __uint_as_float((__float_as_uint(w) & nzm) ^ sg);
+}
+
+// Per warp, the staged Gaussians of one half batch (32 pairs): the records
+// the warp's pixels visit, in pair order (mask mode: only the visited ones,
+// packed; recomputation: all of them, slot = position in the half), with
+// the base addresses of their gradient entries.
+constexpr int kSlots = 32;
+constexpr int kRedStride = 36;  // reduction row stride (floats): 16-byte rows, conflict-free reads and writes
+
+__host__ __device__ inline size_t warp_stage_bytes(int k) {
+  return (size_t)kSlots * (16 + 16 + 8 + 8 + 24 + 8 * k);
+}
+
+__host__ __device__ inline size_t bwd_warp_bytes(int k) {
+  return (warp_stage_bytes(k) + (size_t)(10 + k) * kRedStride * 4 + 15) & ~(size_t)15;
+}
+
+struct WarpStage {
+  float4 *co, *cd;   // conic + opacity; colour + depth
+  float2 *uv;
+  short4 *box;       // alpha box (recomputation mode)
+  float **dst;       // [slot][3]: 2D gradients of the record, colour and class-weight gradients of the Gaussian
+  int2 *sem;         // [slot][k] (class id, weight bits)
+};
+
+__device__ __forceinline__ WarpStage warp_stage(char *p, int k) {
+  WarpStage w;
+  w.co = reinterpret_cast<float4 *>(p); p += kSlots * 16;
+  w.cd = reinterpret_cast<float4 *>(p); p += kSlots * 16;
+  w.uv = reinterpret_cast<float2 *>(p); p += kSlots * 8;
+  w.box = reinterpret_cast<short4 *>(p); p += kSlots * 8;
+  w.dst = reinterpret_cast<float **>(p); p += kSlots * 24;
+  w.sem = reinterpret_cast<int2 *>(p);
+  return w;
+}
+
+// The adjoint of the tile blend, one CTA per tile.  Every warp owns an
+// 8 x (4 PPT) pixel block and works through the tile's pairs on its own
+// (no CTA barrier after the set-up): half batch by half batch, last to
+// first, it stages the Gaussians its pixels' contributor bits name, then
+// walks them back to front.  Per visited Gaussian every lane evaluates its
+// PPT pixels without branches (a pixel the Gaussian did not reach adds
+// exact zeros), forming
+//   0, 1   sum dpow dx, sum dpow dy   (-> du, dv with the conic)
+//   2..4   sum dpow dx dx, dx dy, dy dy (-> the conic gradient)
+//   5      dopacity,  6  ddepth,  7..9  drgb,  10..  dsem_w (k values)
+// with dpow = dalpha o G; the warp sums them through a transposed
+// shared-memory exchange (each lane writes its values as a column, a lane
+// per value reads its row back) and one lane per value adds the warp total
+// with a single atomic.  SEMG: the semantic upstream gradient also reaches
+// the geometry (sem_detach_geometry = 0).  K > 0 fixes the top-k count.
+template <int TW, int TH, bool CODES, int K, int PPT, bool SEMG>
 __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
-  constexpr int NV = (K > 0 && K <= 6) ? 16 : 32;
-  constexpr int NL = K > 0 ? K : NV - 10;  // per-class value slots walked
+  constexpr int NVMAX = 10 + (K > 0 ? K : kMaxK);
+  constexpr int KMAX = K > 0 ? K : kMaxK;
   using FP = Footprint<TW, TH, PPT>;
+  constexpr int THREADS = FP::kThreads;
+  constexpr int NPIX = FP::kPix;
   extern __shared__ float4 smem4[];
-  BatchSmem bs = batch_smem(smem4, a.k);
-  __shared__ uint32_t s_maxnl;
   if (a.counters->status & kStatusTimeout) return;  // the binning is incomplete
+
+  const int k = K > 0 ? K : a.k;
+  const int nv = 10 + k;
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  char *wbase = reinterpret_cast<char *>(smem4) + (size_t)warp * a.warp_bytes;
+  const WarpStage st = warp_stage(wbase, k);
+  float *red = reinterpret_cast<float *>(wbase + warp_stage_bytes(k));
+  // this thread's class sign words, [word][pixel i][thread] (conflict-free);
+  // word nwc is zero (invalid class ids point there)
+  uint2 *mycodes = reinterpret_cast<uint2 *>(reinterpret_cast<char *>(smem4) + (size_t)FP::kWarps * a.warp_bytes) +
+                   threadIdx.x;
 
   const int tile = blockIdx.x;
   const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
@@ -73,41 +134,46 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
   const int lx = FP::lx();
   const int px = ox + lx;
   const float fpx = (float)px + 0.5f;
-  const int k = a.k;
-  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-  // warp-uniform: every lane takes the same branches around the shuffles
+  // warp-uniform: every lane takes the same branches around the exchanges
   const bool has_dsem = (CODES && !a.objective) || a.d_sem != nullptr;
-  float s_sem = 0.f;
+  const bool recompute = a.masks == nullptr;
+  // fused-loss scales of the decoded signs (the class entries are scaled by
+  // the lane that issues their atomic)
+  float s_rgb = 0.f, s_d = 0.f, s_sem = 1.f;
+  if (CODES) {
+    const float ls = *a.loss_scale;
+    s_rgb = a.objective ? 0.5f * ls : (float)(ls / (3.0 * a.npix));
+    s_d = a.objective ? ls : (float)(ls / a.npix);
+    s_sem = (float)(ls / (a.npix * a.m));
+  }
 
-  int py[PPT];
+  int py[PPT], lp[PPT];
   float fpy[PPT], T[PPT], acc[PPT], dR[PPT], dG[PPT], dB[PPT], dD[PPT], dS[PPT];
   uint32_t nl[PPT];
   const float *dP[PPT];
-  uint2 *myc[PPT];  // CODES: this pixel's (nonzero, negative) class sign word pairs (odd stride)
+  bool ok[PPT];
   uint32_t my_max = 0;
 #pragma unroll
   for (int i = 0; i < PPT; ++i) {
     const int ly = FP::ly(i);
     py[i] = oy + ly;
+    lp[i] = ly * TW + lx;
     fpy[i] = (float)py[i] + 0.5f;
     T[i] = 1.f; acc[i] = 0.f; dR[i] = dG[i] = dB[i] = dD[i] = dS[i] = 0.f;
     nl[i] = 0;
-    dP[i] = nullptr;
-    myc[i] = reinterpret_cast<uint2 *>(bs.tail) + (ly * TW + lx) * (a.nwc | 1);
-    if (px < a.width && py[i] < a.height) {
+    dP[i] = a.d_sem;
+    ok[i] = px < a.width && py[i] < a.height;
+    if (CODES && has_dsem) mycodes[(a.nwc * PPT + i) * THREADS] = make_uint2(0u, 0u);
+    if (ok[i]) {
       const size_t pix = (size_t)py[i] * a.width + px;
       T[i] = a.tfinal[pix];
       nl[i] = a.nlast[pix];
       if (CODES) {
-        const float ls = *a.loss_scale;
-        const float s_rgb = a.objective ? 0.5f * ls : (float)(ls / (3.0 * a.npix));
-        const float s_d = a.objective ? ls : (float)(ls / a.npix);
-        s_sem = (float)(ls / (a.npix * a.m));
         const uint2 *cp = reinterpret_cast<const uint2 *>(a.codes + pix * code_words(a.nwc));
         const uint32_t nz = cp[0].x, ng = cp[0].y;
         dR[i] = sign_code(nz, ng, 0, s_rgb); dG[i] = sign_code(nz, ng, 1, s_rgb); dB[i] = sign_code(nz, ng, 2, s_rgb);
         dD[i] = sign_code(nz, ng, 3, s_d);
-        for (int wd = 0; wd < a.nwc; ++wd) myc[i][wd] = cp[1 + wd];
+        for (int wd = 0; wd < a.nwc; ++wd) mycodes[(wd * PPT + i) * THREADS] = cp[1 + wd];
       } else {
         if (a.d_rgb) { dR[i] = a.d_rgb[3 * pix]; dG[i] = a.d_rgb[3 * pix + 1]; dB[i] = a.d_rgb[3 * pix + 2]; }
         if (a.d_depth) dD[i] = a.d_depth[pix];
@@ -117,152 +183,219 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
       my_max = max(my_max, nl[i]);
     }
   }
-  if (threadIdx.x == 0) s_maxnl = 0;
-  __syncthreads();
-  if (my_max) atomicMax(&s_maxnl, my_max);
-  __syncthreads();
-  const uint32_t maxnl = s_maxnl;
-  const int my_idx = reduced_index<NV>();
+  // the warp's last contributor bounds its walk
+  const uint32_t wmax = __reduce_max_sync(0xffffffffu, my_max);
+  const uint32_t unit0 = recompute ? 0u : a.mask_off[tile];
+  // value q of this lane after the exchange (lane = q + 16 h for up to 16
+  // values, else lane = q) and its constant part of the final scaling
+  const bool narrow = NVMAX <= 16 || nv <= 16;
+  const int q = narrow ? (int)(lane & 15) : (int)lane;
+  const bool issue = narrow ? (lane < 16 && q < nv) : q < nv;
+  const int q_cls = q < 7 ? 0 : (q < 10 ? 1 : 2);
+  const int q_off = q < 7 ? q : (q < 10 ? q - 7 : q - 10);
+  const float q_scale = (q == 2 || q == 4) ? -0.5f : (q == 3 ? -1.f : (q >= 10 ? (CODES ? s_sem : 1.f) : 1.f));
 
-  // the forward's batches, last to first (batch bi covers rg.x + 64 bi ...)
-  for (int bi = maxnl ? (int)((maxnl - 1) / kBatch) : -1; bi >= 0; --bi) {
-    const uint32_t lo = rg.x + (uint32_t)bi * kBatch;
-    const int n = (int)min((uint32_t)kBatch, rg.y - lo);
-    __syncthreads();
-    for (int t = threadIdx.x; t < n; t += FP::kThreads)
-      stage_record<TW, TH, PPT>(a.rec, a.pvals[lo + t], t, k, ox, oy, bs, has_dsem, false);
-    __syncthreads();
-    // contributor bits of this batch: written by the forward pass 1, or
-    // re-tested (pairs up to the last contributor whose pixel box holds the
-    // pixel and whose alpha passes 1/255)
-    uint32_t mb[PPT][2];
-    if (a.masks) {
-      const uint32_t unit = a.mask_off[tile] + (uint32_t)bi;
-      const uint32_t *mw = a.masks + (size_t)unit * 2 * FP::kPix;
-#pragma unroll
-      for (int i = 0; i < PPT; ++i) {
-        const int lp = FP::ly(i) * TW + lx;
-        const bool ok = px < a.width && py[i] < a.height;
-        mb[i][0] = ok ? mw[lp] : 0u;
-        mb[i][1] = ok ? mw[FP::kPix + lp] : 0u;
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < PPT; ++i) {
-        mb[i][0] = mb[i][1] = 0u;
-        const uint32_t b0 = (uint32_t)bi * kBatch;
-        const int nj = nl[i] > b0 ? min(n, (int)(nl[i] - b0)) : 0;
-        for (int j = 0; j < nj; ++j) {
-          if (!((bs.wmask[j] >> warp) & 1u) || !box_holds(bs.box[j], px, py[i])) continue;
-          float al, G_, ar, dx_, dy_;
-          if (gauss_alpha(bs.uv[j], bs.co[j], fpx, fpy[i], al, G_, ar, dx_, dy_)) mb[i][j >> 5] |= 1u << (j & 31);
-        }
-      }
+  auto stage = [&](uint32_t r, int slot, bool use_box) {
+    st.uv[slot] = __ldg(a.rec.uv + r);
+    st.co[slot] = __ldg(a.rec.co + r);
+    st.cd[slot] = __ldg(a.rec.cd + r);
+    if (use_box) st.box[slot] = __ldg(a.rec.box + r);
+    const int gid = __ldg(a.rec.gid + r);
+    st.dst[3 * slot] = reinterpret_cast<float *>(a.grad2d) + 8 * (size_t)r;
+    st.dst[3 * slot + 1] = a.g_rgb ? a.g_rgb + 3 * (size_t)gid : nullptr;
+    st.dst[3 * slot + 2] = (has_dsem && a.g_sem_w) ? a.g_sem_w + (size_t)gid * k : nullptr;
+    if (has_dsem) {
+      const int2 *src = a.rec.sem + (size_t)r * k;
+      for (int l = 0; l < k; ++l) st.sem[slot * k + l] = __ldg(src + l);
     }
+  };
+
+  for (int bi = wmax ? (int)((wmax - 1) / kBatch) : -1; bi >= 0; --bi) {
+    const uint32_t b0 = (uint32_t)bi * kBatch;
+    const uint32_t lo = rg.x + b0;
+    const int n = (int)min((uint32_t)kBatch, rg.y - lo);
     for (int h = 1; h >= 0; --h) {
-      uint32_t mine = 0u;
-#pragma unroll
-      for (int i = 0; i < PPT; ++i) mine |= mb[i][h];
-      uint32_t vis = __reduce_or_sync(0xffffffffu, mine);
-      while (vis) {
-        const int bit = 31 - __clz(vis);
-        vis &= ~(1u << bit);
-        const int j = h * 32 + bit;
-        const float2 uv = bs.uv[j];
-        const float4 co = bs.co[j];
-        bool contrib[PPT];
-        float alpha[PPT], G[PPT], araw[PPT], dx[PPT], dy[PPT];
-        bool any = false;
+      const int nh = min(n - h * kSlots, kSlots);
+      if (nh <= 0) continue;
+      const uint32_t hb = b0 + (uint32_t)h * kSlots;  // first pair of the half, within the tile
+      // contributor bits of this half for the thread's pixels
+      uint32_t mine[PPT];
+      uint32_t any = 0u;
+      if (!recompute) {
+        const uint32_t *mw = a.masks + (size_t)(unit0 + (uint32_t)bi) * 2 * NPIX + (size_t)h * NPIX;
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
-          contrib[i] = (mb[i][h] >> bit) & 1u;
-          if (contrib[i]) gauss_alpha(uv, co, fpx, fpy[i], alpha[i], G[i], araw[i], dx[i], dy[i]);
-          any = any || contrib[i];
+          mine[i] = ok[i] ? mw[lp[i]] : 0u;
+          any |= mine[i];
         }
-        float v[NV];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) v[q] = 0.f;
-        const float4 cdp = bs.cd[j];
-        const int2 *sp = bs.sem + j * k;
+      } else {
+        // recomputation: stage every pair of the half, then each pixel
+        // re-tests the pairs before its last contributor (alpha box, alpha)
+        __syncwarp();
+        if ((int)lane < nh) stage(a.pvals[lo + h * kSlots + lane], lane, true);
+        __syncwarp();
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
-          if (!contrib[i]) continue;
-          const float om = 1.f - alpha[i];
-          const float inv_om = __fdividef(1.f, om);  // approximate: 2 ulp, well inside the gradient bar
+          mine[i] = 0u;
+          const int nj = nl[i] > hb ? min(nh, (int)(nl[i] - hb)) : 0;
+          for (int j = 0; j < nj; ++j) {
+            const short4 bx = st.box[j];
+            if (px < bx.x || px > bx.y || py[i] < bx.z || py[i] > bx.w) continue;
+            float al, G_, ar, dx_, dy_;
+            if (gauss_alpha(st.uv[j], st.co[j], fpx, fpy[i], al, G_, ar, dx_, dy_)) mine[i] |= 1u << j;
+          }
+          any |= mine[i];
+        }
+      }
+      const uint32_t vis = __reduce_or_sync(0xffffffffu, any);
+      if (!vis) continue;
+      if (!recompute) {
+        // stage the visited Gaussians, packed in pair order
+        __syncwarp();
+        if ((vis >> lane) & 1u) stage(a.pvals[lo + h * kSlots + lane], __popc(vis & lanemask_lt()), false);
+        __syncwarp();
+      }
+      int s = __popc(vis);
+      uint32_t rem = vis;
+      while (rem) {
+        const int bit = 31 - __clz(rem);
+        rem ^= 1u << bit;
+        --s;
+        const int slot = recompute ? bit : s;
+        const float2 uv = st.uv[slot];
+        const float4 co = st.co[slot];
+        const float4 cdp = st.cd[slot];
+        // per class: the sign-word address and shift (CODES) or the class id
+        const uint2 *cwp[KMAX];
+        uint32_t csh[KMAX];
+        int cid[KMAX];
+        float cw8[KMAX];
+        bool cvalid[KMAX];
+        if (has_dsem) {
+#pragma unroll
+          for (int l = 0; l < KMAX; ++l) {
+            if (K > 0 || l < k) {
+              const int2 e = st.sem[slot * k + l];
+              cvalid[l] = (unsigned)e.x < (unsigned)a.m;
+              cid[l] = cvalid[l] ? e.x : 0;
+              cwp[l] = mycodes + (cvalid[l] ? (e.x >> 5) : a.nwc) * (PPT * THREADS);
+              csh[l] = 31u - ((uint32_t)e.x & 31u);
+              cw8[l] = __int_as_float(e.y);
+            }
+          }
+        }
+        float v[NVMAX];
+        bool first = true, anyc = false;
+#pragma unroll
+        for (int i = 0; i < PPT; ++i) {
+          const bool c = (mine[i] >> bit) & 1u;
+          anyc = anyc || c;
+          if (!__any_sync(0xffffffffu, c)) continue;  // uniform: no pixel of this row group
+          // alpha at the pixel, with the forward's instructions; pixels the
+          // Gaussian did not reach get w = dalpha = 0 (all terms exact zeros)
+          const float dx = __fsub_rn(uv.x, fpx), dy = __fsub_rn(uv.y, fpy[i]);
+          const float qf = __fmaf_rn(co.x, __fmul_rn(dx, dx), __fmul_rn(co.z, __fmul_rn(dy, dy)));
+          const float power = __fmaf_rn(-0.5f, qf, -__fmul_rn(co.y, __fmul_rn(dx, dy)));
+          const float G = __expf(power);
+          const float araw = __fmul_rn(co.w, G);
+          const float alpha = araw < kAlphaMax ? araw : kAlphaMax;
+          const float inv_om = __fdividef(1.f, 1.f - alpha);  // approximate: 2 ulp, well inside the gradient bar
           const float Ti = T[i] * inv_om;
-          const float w = alpha[i] * Ti;
+          const float w = c ? alpha * Ti : 0.f;
+          T[i] = c ? Ti : T[i];
           float gi = dR[i] * cdp.x + dG[i] * cdp.y + dB[i] * cdp.z + dD[i] * cdp.w + dS[i];
+          float vs[KMAX];
           if (has_dsem) {
             float gs = 0.f;
 #pragma unroll
-            for (int l = 0; l < NL; ++l) {
+            for (int l = 0; l < KMAX; ++l) {
               if (K > 0 || l < k) {
-                const int2 e = sp[l];
-                float dp = 0.f;
-                if ((unsigned)e.x < (unsigned)a.m) {
-                  if (CODES) {
-                    const uint2 cw = myc[i][e.x >> 5];
-                    dp = sign_code(cw.x, cw.y, e.x & 31, s_sem);
-                  } else {
-                    dp = __ldg(dP[i] + e.x);
-                  }
+                if (CODES) {
+                  const uint2 cw = cwp[l][i * THREADS];
+                  vs[l] = signed_weight(cw, csh[l], w);
+                  if (SEMG) gs += signed_weight(cw, csh[l], cw8[l]);
+                } else {
+                  const float dp = cvalid[l] ? __ldg(dP[i] + cid[l]) : 0.f;
+                  vs[l] = dp * w;
+                  if (SEMG) gs = fmaf(dp, cw8[l], gs);
                 }
-                v[10 + l] = fmaf(dp, w, v[10 + l]);
-                gs = fmaf(dp, __int_as_float(e.y), gs);
               }
             }
-            if (!a.sem_detach) gi += gs;
+            if (SEMG) gi = CODES ? fmaf(s_sem, gs, gi) : gi + gs;
           }
-          v[7] = fmaf(dR[i], w, v[7]); v[8] = fmaf(dG[i], w, v[8]); v[9] = fmaf(dB[i], w, v[9]);
-          v[6] = fmaf(dD[i], w, v[6]);
-          const float dalpha = Ti * gi - acc[i] * inv_om;
+          const float dal = (c && araw < kAlphaMax) ? Ti * gi - acc[i] * inv_om : 0.f;
           acc[i] = fmaf(w, gi, acc[i]);
-          T[i] = Ti;
-          if (araw[i] < kAlphaMax) {
-            v[5] = fmaf(dalpha, G[i], v[5]);
-            const float dpow = dalpha * araw[i];
-            const float ddx = dx[i], ddy = dy[i];
-            v[2] = fmaf(dpow, -0.5f * ddx * ddx, v[2]);
-            v[3] = fmaf(dpow, -ddx * ddy, v[3]);
-            v[4] = fmaf(dpow, -0.5f * ddy * ddy, v[4]);
-            v[0] = fmaf(dpow, -(co.x * ddx + co.y * ddy), v[0]);
-            v[1] = fmaf(dpow, -(co.z * ddy + co.y * ddx), v[1]);
+          const float dpow = dal * araw;
+          const float ax = dpow * dx, ay = dpow * dy;
+          if (first) {
+            v[0] = ax; v[1] = ay; v[2] = ax * dx; v[3] = ax * dy; v[4] = ay * dy;
+            v[5] = dal * G; v[6] = dD[i] * w; v[7] = dR[i] * w; v[8] = dG[i] * w; v[9] = dB[i] * w;
+#pragma unroll
+            for (int l = 0; l < KMAX; ++l)
+              if (K > 0 || l < k) v[10 + l] = has_dsem ? vs[l] : 0.f;
+          } else {
+            v[0] += ax; v[1] += ay; v[2] = fmaf(ax, dx, v[2]); v[3] = fmaf(ax, dy, v[3]); v[4] = fmaf(ay, dy, v[4]);
+            v[5] = fmaf(dal, G, v[5]); v[6] = fmaf(dD[i], w, v[6]);
+            v[7] = fmaf(dR[i], w, v[7]); v[8] = fmaf(dG[i], w, v[8]); v[9] = fmaf(dB[i], w, v[9]);
+#pragma unroll
+            for (int l = 0; l < KMAX; ++l)
+              if ((K > 0 || l < k) && has_dsem) v[10 + l] += vs[l];
           }
+          first = false;
         }
-        if (NV == 32 && __popc(__ballot_sync(0xffffffffu, any)) <= 2) {
-          // with the wide (32-value) reduction, one or two lanes touched by
-          // this Gaussian add their values directly
-          if (any) {
-            float *g2 = reinterpret_cast<float *>(a.grad2d) + 8 * (size_t)bs.rec[j];
+        if (first) continue;  // unreachable: the Gaussian is a contributor of some pixel of the warp
+        if (NVMAX > 16 && __popc(__ballot_sync(0xffffffffu, anyc)) <= 2) {
+          // one or two lanes touched: they add their own values directly
+          if (anyc) {
 #pragma unroll
-            for (int q = 0; q < 7; ++q)
-              if (v[q] != 0.f) atomicAdd(g2 + q, v[q]);
-            if (a.g_rgb) {
-              float *gr = a.g_rgb + 3 * (size_t)bs.gid[j];
-#pragma unroll
-              for (int q = 0; q < 3; ++q)
-                if (v[7 + q] != 0.f) atomicAdd(gr + q, v[7 + q]);
-            }
-            if (has_dsem && a.g_sem_w) {
-              float *gw = a.g_sem_w + (size_t)bs.gid[j] * k;
-#pragma unroll
-              for (int l = 0; l < NL; ++l)
-                if ((K > 0 || l < k) && v[10 + l] != 0.f) atomicAdd(gw + l, v[10 + l]);
+            for (int qq = 0; qq < NVMAX; ++qq) {
+              if (qq >= nv) break;
+              const int cls = qq < 7 ? 0 : (qq < 10 ? 1 : 2);
+              const int off = qq < 7 ? qq : (qq < 10 ? qq - 7 : qq - 10);
+              float val = v[qq];
+              if (qq == 0) val = -(co.x * v[0] + co.y * v[1]);
+              else if (qq == 1) val = -(co.z * v[1] + co.y * v[0]);
+              else if (qq == 2 || qq == 4) val = -0.5f * v[qq];
+              else if (qq == 3) val = -v[qq];
+              else if (qq >= 10 && CODES) val = v[qq] * s_sem;
+              float *base = st.dst[3 * slot + cls];
+              if (base && val != 0.f) atomicAdd(base + off, val);
             }
           }
           continue;
         }
-        const float tot = warp_reduce_scatter<NV>(v);
-        if (my_idx == (int)lane || NV == 32) {
-          // lanes 0..15 (NV = 16) or all lanes (NV = 32) own one value each
-          if (my_idx < 7) {
-            if (tot != 0.f) atomicAdd(reinterpret_cast<float *>(a.grad2d) + 8 * (size_t)bs.rec[j] + my_idx, tot);
-          } else if (my_idx < 10) {
-            if (a.g_rgb && tot != 0.f) atomicAdd(a.g_rgb + 3 * (size_t)bs.gid[j] + (my_idx - 7), tot);
-          } else if (my_idx < 10 + k) {
-            if (has_dsem && a.g_sem_w && tot != 0.f) atomicAdd(a.g_sem_w + (size_t)bs.gid[j] * k + (my_idx - 10), tot);
+        // transposed exchange: value q of every lane in row q
+        __syncwarp();
+#pragma unroll
+        for (int qq = 0; qq < NVMAX; ++qq)
+          if (qq < nv) red[qq * kRedStride + lane] = v[qq];
+        __syncwarp();
+        float tot = 0.f;
+        if (narrow) {
+          if (q < nv) {
+            const float4 *r4 = reinterpret_cast<const float4 *>(red + q * kRedStride + 16 * (lane >> 4));
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float4 x = r4[u];
+              tot += (x.x + x.y) + (x.z + x.w);
+            }
+          }
+          tot += __shfl_xor_sync(0xffffffffu, tot, 16);
+        } else if (q < nv) {
+          const float4 *r4 = reinterpret_cast<const float4 *>(red + q * kRedStride);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const float4 x = r4[u];
+            tot += (x.x + x.y) + (x.z + x.w);
           }
         }
+        // lanes 0, 1 combine the two sums with the conic: du, dv
+        const float other = __shfl_xor_sync(0xffffffffu, tot, 1);
+        const float c1 = q == 0 ? -co.x : (q == 1 ? -co.z : q_scale);
+        const float c2 = q < 2 ? -co.y : 0.f;
+        const float val = fmaf(c1, tot, c2 * other);
+        float *base = st.dst[3 * slot + q_cls];
+        if (issue && base && val != 0.f) atomicAdd(base + q_off, val);
       }
     }
   }
@@ -274,41 +407,51 @@ __global__ void k_zero_grad2d(float4 *g, const Counters *cnt, uint32_t rcap) {
     g[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-template <int TW, int TH, bool CODES, int K, int PPT>
+constexpr int kBwdSmemMax = 227 * 1024;  // opt-in dynamic shared memory per CTA
+
+template <int TW, int TH, bool CODES, int K, int PPT, bool SEMG>
 static cudaError_t launch_bwd_shape(const BwdArgs &a, int grid, size_t smem, cudaStream_t s) {
-  {  // the sign words of large class counts need more than 48 KB
-    const cudaError_t e = ensure_smem_limit((const void *)k_render_bwd<TW, TH, CODES, K, PPT>, (int)kSmemBudget);
+  if (smem > (size_t)kBwdSmemMax) return cudaErrorInvalidConfiguration;
+  {
+    const cudaError_t e =
+        ensure_smem_limit((const void *)k_render_bwd<TW, TH, CODES, K, PPT, SEMG>, kBwdSmemMax);
     if (e != cudaSuccess) return e;
   }
-  k_render_bwd<TW, TH, CODES, K, PPT><<<grid, TW * TH / PPT, smem, s>>>(a);
+  k_render_bwd<TW, TH, CODES, K, PPT, SEMG><<<grid, TW * TH / PPT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <bool CODES, int K, int PPT>
+template <bool CODES, int K, int PPT, bool SEMG>
 static cudaError_t dispatch_bwd_shape(int tw, int th, const BwdArgs &a, int grid, size_t smem, cudaStream_t s) {
-  if (tw == 16 && th == 16) return launch_bwd_shape<16, 16, CODES, K, PPT>(a, grid, smem, s);
-  if (tw == 16 && th == 8) return launch_bwd_shape<16, 8, CODES, K, PPT>(a, grid, smem, s);
-  if (tw == 8 && th == 8) return launch_bwd_shape<8, 8, CODES, K, PPT>(a, grid, smem, s);
-  if (tw == 32 && th == 8) return launch_bwd_shape<32, 8, CODES, K, PPT>(a, grid, smem, s);
+  if (tw == 16 && th == 16) return launch_bwd_shape<16, 16, CODES, K, PPT, SEMG>(a, grid, smem, s);
+  if (tw == 16 && th == 8) return launch_bwd_shape<16, 8, CODES, K, PPT, SEMG>(a, grid, smem, s);
+  if (tw == 8 && th == 8) return launch_bwd_shape<8, 8, CODES, K, PPT, SEMG>(a, grid, smem, s);
+  if (tw == 32 && th == 8) return launch_bwd_shape<32, 8, CODES, K, PPT, SEMG>(a, grid, smem, s);
   return cudaErrorInvalidConfiguration;
 }
 
+template <bool CODES, int PPT>
+static cudaError_t dispatch_bwd_k(const Layout &L, const BwdArgs &a, bool semg, int grid, size_t smem,
+                                  cudaStream_t s) {
+  // semantics reaching the geometry (not the paper's setting) take the generic-k kernel
+  if (semg) return dispatch_bwd_shape<CODES, 0, PPT, true>(L.tile_w, L.tile_h, a, grid, smem, s);
+  if (a.k == 3) return dispatch_bwd_shape<CODES, 3, PPT, false>(L.tile_w, L.tile_h, a, grid, smem, s);
+  if (a.k == 8) return dispatch_bwd_shape<CODES, 8, PPT, false>(L.tile_w, L.tile_h, a, grid, smem, s);
+  return dispatch_bwd_shape<CODES, 0, PPT, false>(L.tile_w, L.tile_h, a, grid, smem, s);
+}
+
 template <bool CODES>
-static cudaError_t dispatch_bwd(const Layout &L, const BwdArgs &a, int grid, size_t smem, cudaStream_t s) {
+static cudaError_t dispatch_bwd(const Layout &L, const BwdArgs &a, bool semg, int grid, size_t smem,
+                                cudaStream_t s) {
   if (L.ppt == 4) {
     if (L.tile_w != 16 || L.tile_h != 16) return cudaErrorInvalidConfiguration;
-    if (a.k == 3) return launch_bwd_shape<16, 16, CODES, 3, 4>(a, grid, smem, s);
-    if (a.k == 8) return launch_bwd_shape<16, 16, CODES, 8, 4>(a, grid, smem, s);
-    return launch_bwd_shape<16, 16, CODES, 0, 4>(a, grid, smem, s);
+    if (semg) return launch_bwd_shape<16, 16, CODES, 0, 4, true>(a, grid, smem, s);
+    if (a.k == 3) return launch_bwd_shape<16, 16, CODES, 3, 4, false>(a, grid, smem, s);
+    if (a.k == 8) return launch_bwd_shape<16, 16, CODES, 8, 4, false>(a, grid, smem, s);
+    return launch_bwd_shape<16, 16, CODES, 0, 4, false>(a, grid, smem, s);
   }
-  if (L.ppt == 2) {
-    if (a.k == 3) return dispatch_bwd_shape<CODES, 3, 2>(L.tile_w, L.tile_h, a, grid, smem, s);
-    if (a.k == 8) return dispatch_bwd_shape<CODES, 8, 2>(L.tile_w, L.tile_h, a, grid, smem, s);
-    return dispatch_bwd_shape<CODES, 0, 2>(L.tile_w, L.tile_h, a, grid, smem, s);
-  }
-  if (a.k == 3) return dispatch_bwd_shape<CODES, 3, 1>(L.tile_w, L.tile_h, a, grid, smem, s);
-  if (a.k == 8) return dispatch_bwd_shape<CODES, 8, 1>(L.tile_w, L.tile_h, a, grid, smem, s);
-  return dispatch_bwd_shape<CODES, 0, 1>(L.tile_w, L.tile_h, a, grid, smem, s);
+  if (L.ppt == 2) return dispatch_bwd_k<CODES, 2>(L, a, semg, grid, smem, s);
+  return dispatch_bwd_k<CODES, 1>(L, a, semg, grid, smem, s);
 }
 
 cudaError_t launch_render_bwd(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc, const float *d_rgb,
@@ -328,25 +471,31 @@ cudaError_t launch_render_bwd(const Layout &L, const WsPtrs &P, int pbuf, const 
   const int tiles_y = (L.cam0_h + L.tile_h - 1) / L.tile_h;
   a.tfinal = P.tfinal; a.nlast = P.nlast;
   a.d_rgb = d_rgb; a.d_depth = d_depth; a.d_sil = d_sil; a.d_sem = d_sem;
-  a.sem_detach = sem_detach;
   a.counters = P.counters;
   a.grad2d = P.grad2d;
   a.g_rgb = g_rgb; a.g_sem_w = g_sem_w;
   a.mask_off = L.mask_units ? P.mask_off : nullptr;
   a.masks = L.mask_units ? P.masks : nullptr;
+  a.warp_bytes = (int)bwd_warp_bytes(sc.k);
   const int grid = a.tiles_x * tiles_y;
   if (grid == 0) return cudaSuccess;
+  const int threads = L.tile_w * L.tile_h / L.ppt;
+  const size_t warps_bytes = (size_t)(threads / 32) * a.warp_bytes;
+  // the semantic upstream gradient reaches the geometry only when asked for
+  // and when there is one
   if (loss_scale) {
     a.codes = P.codes;
     a.nwc = objective ? 0 : L.nwc;
     a.loss_scale = loss_scale;
     a.npix = (double)L.npix;
     a.objective = objective;
-    const size_t smem = batch_smem_bytes(sc.k) + (size_t)L.tile_w * L.tile_h * (a.nwc | 1) * 8;
-    return dispatch_bwd<true>(L, a, grid, smem, s);
+    const bool semg = !sem_detach && !objective;
+    // per thread and pixel: the class sign words plus one zero word
+    const size_t smem = warps_bytes + (a.nwc ? (size_t)threads * L.ppt * (a.nwc + 1) * 8 : 0);
+    return dispatch_bwd<true>(L, a, semg, grid, smem, s);
   }
-  const size_t smem = batch_smem_bytes(sc.k);
-  return dispatch_bwd<false>(L, a, grid, smem, s);
+  const bool semg = !sem_detach && d_sem != nullptr;
+  return dispatch_bwd<false>(L, a, semg, grid, warps_bytes, s);
 }
 
 // ---------------------------------------------------------------------------
