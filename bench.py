@@ -502,6 +502,53 @@ def main():
                                      "hbm_frac_of_" + peak_src: (bytes_front / t_front / 1e9) / hbm_peak}}
     roofline["phases_ms"] = {k_: round(v, 4) for k_, v in ph_ms.items()}
 
+    # the semantic pass on its own: the fused forward with and without the
+    # class target (the difference is k_semantic; the blend pass and the
+    # loss reduction run in both)
+    fwd_sem = phase_times_of(rast, lambda: rast.forward_l1(g, cam, t_rgb, t_depth, t_sem, check=False),
+                             ph_steps, flush)["render_fwd"]
+    fwd_nosem = phase_times_of(rast, lambda: rast.forward_l1(g, cam, t_rgb, t_depth, None, check=False),
+                               ph_steps, flush)["render_fwd"]
+    t_sem_pass = max(fwd_sem - fwd_nosem, 1e-6) * 1e-3
+    npx = H * W
+    # fused mean-L1 semantic pass: target map read once, sign codes written,
+    # last contributor and contributor bits read
+    bytes_sem = npx * m * 4 + npx * code_b + npx * 4 + n_pairs * 4 + n_contrib // 8
+    sem_roof = {"bound": "hbm", "kernel": "k_semantic<%d, %d, 1, %d>" % (best["tile"][0], best["tile"][1],
+                                                                         k if k in (3, 8) else 0),
+                "achieved": bytes_sem / t_sem_pass / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "frac": bytes_sem / t_sem_pass / 1e9 / hbm_peak, "peak_source": peak_src,
+                "traffic": ncu_traffic("k_semantic<%d, %d, 1, %d>" % (best["tile"][0], best["tile"][1],
+                                                                      k if k in (3, 8) else 0), "room300k"),
+                "algorithmic_bytes": bytes_sem, "ms": t_sem_pass * 1e3,
+                "ms_basis": "CUDA events: fused forward with the class target minus the same forward without it",
+                "fp32_frac": (10 + 2 * k) * n_contrib / t_sem_pass / 1e12 / fp32_peak}
+    roofline["forward"]["ms_without_semantic_pass"] = fwd_nosem
+    if t_sem_pass > t_bwd:
+        # the semantic pass is the longest kernel of the step: it heads the
+        # line, the adjoint's figures move under "adjoint"
+        adj = {k_: roofline.pop(k_) for k_ in list(roofline)
+               if k_ not in ("forward", "project_bin_sort", "phases_ms")}
+        roofline = dict(sem_roof, adjoint=adj, **roofline)
+    else:
+        roofline["semantic_pass"] = sem_roof
+
+    # a3 forward against FP32 and MUFU: the work counters of the same view
+    # (gs_count_work, outside the timed region) give N_eval and N_contrib
+    wc = rast.work_counts(g, [cam])
+    mufu_peak = n_sm * MUFU_PER_SM * clock_ghz / 1000.0  # T results/s
+    flops_fwd = 10 * wc["n_eval"] + (12 + 2 * k) * wc["n_contrib"]
+    roofline["forward"].update({
+        "work_counts": wc,
+        "fp32": {"achieved": flops_fwd / t_fwd / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                 "frac": flops_fwd / t_fwd / 1e12 / fp32_peak, "algorithmic_flops": flops_fwd,
+                 "formula": "10 n_eval + (12 + 2k) n_contrib"},
+        "mufu": {"achieved": wc["n_eval"] / t_fwd / 1e12, "peak": mufu_peak, "unit": "Tops/s",
+                 "frac": wc["n_eval"] / t_fwd / 1e12 / mufu_peak, "algorithmic_ops": wc["n_eval"],
+                 "formula": "one exponential per evaluated pair (n_eval); the kernels evaluate n_eval_box in "
+                            "the blend pass and recompute n_contrib in the semantic pass"},
+        "mufu_peak_source": f"{n_sm} SMs x {MUFU_PER_SM} results/clock x {clock_ghz:.3f} GHz (sampled SM clock)"})
+
     # ---- e2e through the public API with host buffers ------------------------
     # pipeline.MappingStream: every step copies its target frame from pinned
     # host memory into a free device slot on a copy stream (overlapping the
@@ -914,18 +961,14 @@ def bench_candidates(args, dev, flush):
     for _ in range(2):
         rast.candidates(g, cams, check=False, out=out)
     torch.cuda.synchronize()
-    ts = []
-    for _ in range(args.cand_steps):
-        flush.zero_()
-        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s.record()
-        rast.candidates(g, cams, check=False, out=out)
-        e.record()
-        ts.append((s, e))
-    torch.cuda.synchronize()
-    ms = statistics.mean(a.elapsed_time(b) for a, b in ts)
+    # the batched call captured as one CUDA graph, each replay timed on its own
+    graph = capture_graph(lambda: rast.candidates(g, cams, check=False, out=out))[0]
+    for _ in range(3):
+        graph.replay()
+    batch_ms = time_graph(graph, max(20, args.cand_steps), flush)
+    ms = statistics.mean(batch_ms)
     # the same views, one plain launch chain per view (one rasterizer per
-    # resolution, sized by a checked call first)
+    # resolution, sized by a checked call first), eager, >= 5 repetitions
     singles = {}
     for c in cams:
         key = (c.width, c.height)
@@ -933,15 +976,38 @@ def bench_candidates(args, dev, flush):
             singles[key] = raster.Rasterizer(tile=ctile, device=dev)
             singles[key].candidates(g, [c], check=True)
     torch.cuda.synchronize()
-    flush.zero_()
-    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s.record()
-    for c in cams:
-        singles[(c.width, c.height)].candidates(g, [c], check=False)
-    e.record()
-    torch.cuda.synchronize()
-    per_view_ms = s.elapsed_time(e)
+    per_view = []
+    for _ in range(5):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        for c in cams:
+            singles[(c.width, c.height)].candidates(g, [c], check=False)
+        e.record()
+        torch.cuda.synchronize()
+        per_view.append(s.elapsed_time(e))
+    per_view_ms = statistics.mean(per_view)
     npix = sum(c.width * c.height for c in cams)
+    # work of the batch (outside the timed region) and its FP32 / MUFU rooflines
+    wc = rast.work_counts(g, cams)
+    clock_ghz = 2.07
+    n_sm = device_sms(dev)
+    fp32_peak = n_sm * FP32_LANES_PER_SM * 2 * clock_ghz / 1000.0
+    mufu_peak = n_sm * MUFU_PER_SM * clock_ghz / 1000.0  # T ops/s
+    kk, mm = sc.k, sc.m
+    flops = 10 * wc["n_eval"] + (12 + 2 * kk) * wc["n_contrib"] + 4 * wc["n_touched"] + 12 * wc["n_pixels"]
+    mufu = wc["n_eval"] + wc["n_touched"] + 2 * wc["n_pixels"]
+    t_s = ms * 1e-3
+    cand_roof = {"kernels": "the whole batched call: projection, binning, k_cand_blend + k_cand_sem",
+                 "work_counts": wc,
+                 "fp32": {"achieved": flops / t_s / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                          "frac": flops / t_s / 1e12 / fp32_peak, "algorithmic_flops": flops,
+                          "formula": "10 n_eval + (12 + 2k) n_contrib + 4 n_touched + 12 n_pixels"},
+                 "mufu": {"achieved": mufu / t_s / 1e12, "peak": mufu_peak, "unit": "Tops/s",
+                          "frac": mufu / t_s / 1e12 / mufu_peak, "algorithmic_ops": mufu,
+                          "formula": "n_eval exponentials + n_touched logarithms + 2 n_pixels (log Z, 1/Z)"},
+                 "peak_source": f"{n_sm} SMs x (128 FP32 lanes x 2 flop | 16 MUFU results) x {clock_ghz} GHz "
+                                "(maximum SM clock)"}
     # the Eq. 6-8 scoring tail on the device after the batched render
     from paper_2506_00225_gb300 import explore
     npix_t = torch.tensor([c.width * c.height for c in cams], dtype=torch.int32, device=dev)
@@ -959,13 +1025,16 @@ def bench_candidates(args, dev, flush):
     score_us = s.elapsed_time(e) * 10.0
     return {"metric": "candidate views/s", "value": 1000.0 * len(cams) / ms, "unit": "views/s",
             "ms_per_batch": ms, "mpix_per_s": npix / (ms * 1e-3) / 1e6,
+            "timing": f"one CUDA graph of the batched call, {len(batch_ms)} replays (L2 flushed before each); "
+                      "per-view arm: 5 eager repetitions",
+            "roofline": cand_roof,
             "workload": ("cand96: the 300k room + Gamma(2,0.5) uncertainty, 96 poses (4x4 grid at 0.5 m x 6 yaws), "
                          "resolutions cycling 170x300 / 340x600 / 680x1200") if args.cand_workload == "cand96" else
                         ("mixed2m candidates: the 2M-Gaussian rooms (M=256, top-8) + Gamma(2,0.5) uncertainty, "
                          "128 views (64 @170x300, 48 @340x600, 16 @680x1200)"),
             "n_records": int(cnt.n_records), "n_pairs": int(cnt.n_pairs),
             "per_view_launches": {"value": 1000.0 * len(cams) / per_view_ms, "unit": "views/s",
-                                  "ms": per_view_ms},
+                                  "ms": per_view_ms, "ms_reps": [round(x, 3) for x in per_view]},
             "batched_speedup": per_view_ms / ms,
             "scoring_us": {"value": score_us, "what": "gs_score_candidates over all the views (Eq. 6-8 softmaxes, "
                                                       "motion cost, pruning, best index), mean of 100 calls"},

@@ -412,6 +412,28 @@ gs_status gs_voxel_update(const gs_voxel_grid *grid, uint32_t *state, const floa
 gs_status gs_voxel_new_free(const gs_voxel_grid *grid, const uint32_t *prev, const uint32_t *cur, uint32_t *scratch,
                             float *centres, int64_t capacity, uint32_t *count, gs_stream_t stream);
 
+/* Work counters of the blend passes over the views binned in `ws` (call
+ * after gs_project and gs_bin_sort with the same arguments), for roofline
+ * figures; not meant for the timed path.  Per pixel of every view:
+ *   n_eval      (pixel, Gaussian) pairs whose pixel rectangle holds the
+ *               pixel, up to and including the pair that stops the pixel's
+ *               compositing (T (1 - alpha) < 1e-4): the evaluations of the
+ *               per-pixel definition of Eq. 1;
+ *   n_eval_box  of those, the pairs inside the Gaussian's alpha box (the
+ *               pairs the blend kernels evaluate; outside, alpha < 1/255);
+ *   n_contrib   pairs blended (alpha >= 1/255, before the stop);
+ *   n_touched   (pixel, class) entries of the Eq. 3 distribution above the
+ *               0.001 clip floor of Eq. 7 (the logarithms of the entropy);
+ *   n_pixels    pixels inside the views.
+ * `out` is a DEVICE pointer (8-byte aligned), overwritten.  per_pixel
+ * (optional DEVICE uint32 [height][width][2], single view only, else
+ * GS_ERR_ARG) receives each pixel's (n_eval, n_contrib). */
+typedef struct gs_work_counts {
+  uint64_t n_eval, n_eval_box, n_contrib, n_touched, n_pixels;
+} gs_work_counts;
+gs_status gs_count_work(const gs_scene *scene, const gs_camera *cams, int n_views, const gs_config *cfg, void *ws,
+                        gs_work_counts *out, uint32_t *per_pixel, gs_stream_t stream);
+
 /* Bytes of the fixed device scratch array used by gs_render_fwd_noalloc. */
 #define GS_NOALLOC_SCRATCH_BYTES (32u << 20)
 

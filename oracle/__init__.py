@@ -142,7 +142,8 @@ def render(scene, cam, prec="f32", sem=True, unc=False, rows=None) -> dict:
     d = _dt(prec)
     W, H, m = cam.width, cam.height, scene.m
     out = dict(rgb=np.zeros((H, W, 3), d), depth=np.zeros((H, W), d), sil=np.zeros((H, W), d),
-               T=np.zeros((H, W), d), n_contrib=np.zeros((H, W), np.int32), flag=np.zeros((H, W), np.int32))
+               T=np.zeros((H, W), d), n_contrib=np.zeros((H, W), np.int32), n_eval_px=np.zeros((H, W), np.int32),
+               flag=np.zeros((H, W), np.int32))
     out["sem"] = np.zeros((H, W, m), d) if sem else None
     out["unc"] = np.zeros((H, W), d) if (unc and scene.geo_unc is not None) else None
     stats = np.zeros(2, np.int64)
@@ -152,7 +153,8 @@ def render(scene, cam, prec="f32", sem=True, unc=False, rows=None) -> dict:
        _ptr(a["opacity"]), _ptr(a["rgb"]), _ptr(a["sem_ids"]), _ptr(a["sem_w"]),
        _ptr(a["unc"]) if out["unc"] is not None else None, _ptr(cam_array(cam, prec)), _I(W), _I(H),
        _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["sil"]), _ptr(out["unc"]), _ptr(out["sem"]),
-       _ptr(out["T"]), _ptr(out["n_contrib"]), _ptr(out["flag"]), _ptr(stats), *_rows(rows, H))
+       _ptr(out["T"]), _ptr(out["n_contrib"]), _ptr(out["n_eval_px"]), _ptr(out["flag"]), _ptr(stats),
+       *_rows(rows, H))
     out["n_eval"], out["n_contrib_total"] = int(stats[0]), int(stats[1])
     return out
 

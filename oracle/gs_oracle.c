@@ -329,13 +329,14 @@ static void composite_pixel(const scene_t *sc, const view_t *vw, int x, int y, r
 /* Forward render of rows y_begin, y_begin + y_step, ... < y_end (the full
  * image for 0, H, 1).  Outputs: rgb[H,W,3], depth[H,W], sil[H,W]
  * (= 1 - T_final), unc_img[H,W] (if unc given and unc_img non-NULL),
- * sem[H,W,m] (if non-NULL), T_final[H,W], n_contrib[H,W], flag[H,W].
- * stats[2] = {N_eval, N_contrib} summed over pixels. */
+ * sem[H,W,m] (if non-NULL), T_final[H,W], n_contrib[H,W], n_eval[H,W],
+ * flag[H,W].  stats[2] = {N_eval, N_contrib} summed over pixels. */
 void SFX(orc_render)(int n, int k, int m, const real *means, const real *scales, const real *quats,
                      const real *opacity, const real *rgb, const int *sem_ids, const real *sem_w,
                      const real *unc, const real *cam, int W, int H,
                      real *out_rgb, real *out_depth, real *out_sil, real *out_unc, real *out_sem,
-                     real *out_T, int *out_nc, int *out_flag, long *stats, int y_begin, int y_end, int y_step) {
+                     real *out_T, int *out_nc, int *out_ne, int *out_flag, long *stats, int y_begin, int y_end,
+                     int y_step) {
   SCENE_FROM_ARGS
   view_t vw;
   view_build(&sc, cam, W, H, &vw);
@@ -356,6 +357,7 @@ void SFX(orc_render)(int n, int k, int m, const real *means, const real *scales,
       if (out_unc) out_unc[pid] = o.unc;
       if (out_T) out_T[pid] = o.T;
       if (out_nc) out_nc[pid] = o.n_contrib;
+      if (out_ne) out_ne[pid] = (int)o.n_eval;
       if (out_flag) out_flag[pid] = o.flag;
       ne += o.n_eval;
       ncs += o.n_contrib;

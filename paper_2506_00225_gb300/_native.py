@@ -20,7 +20,7 @@ EXPORTS = ["gs_workspace_size", "gs_workspace_layout", "gs_project", "gs_bin_sor
            "gs_render_bwd_objective", "gs_render_candidates", "gs_l1_loss", "gs_mapping_loss", "gs_render_fwd_noalloc",
            "gs_score_candidates", "gs_candidate_poses", "gs_candidate_positions", "gs_topk_init", "gs_topk_gather",
            "gs_voxel_words", "gs_voxel_scratch_words", "gs_voxel_update", "gs_voxel_new_free", "gs_read_counters",
-           "gs_status_string", "gs_testing_set_sm_query", "gs_testing_grid"]
+           "gs_status_string", "gs_testing_set_sm_query", "gs_testing_grid", "gs_count_work"]
 
 
 class GsScene(ctypes.Structure):
@@ -104,6 +104,8 @@ _SIGS = {
     "gs_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "gs_testing_set_sm_query": (None, [c_void_p]),
     "gs_testing_grid": (c_int64, [ctypes.c_int]),
+    "gs_count_work": (ctypes.c_int, [P(GsScene), P(GsCamera), ctypes.c_int, P(GsConfig), c_void_p, c_void_p,
+                                     c_void_p, c_void_p]),
 }
 
 # gs_testing_grid ids (include/gs.h)

@@ -41,6 +41,7 @@ SOURCES = {
     "voxel.cu": ["-fmad=false"],
     "api.cu": [],
     "noalloc.cu": [],
+    "stats.cu": ["-ftz=true"],
 }
 HEADERS = ["gs_internal.cuh", "render_common.cuh", "objective_math.cuh"]
 

@@ -192,6 +192,11 @@ cudaError_t launch_project_bwd(const Layout &L, const WsPtrs &P, const gs_scene 
                                float *g_scales, float *g_quats, float *g_opacity, cudaStream_t s);
 cudaError_t launch_candidates(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc, double *out,
                               cudaStream_t s);
+// Work counters of the binned views (stats.cu): out[5] = n_eval, n_eval_box,
+// n_contrib, n_touched, n_pixels; per_pixel (single view, or null): the
+// (n_eval, n_contrib) pair of every pixel.
+cudaError_t launch_work_stats(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc,
+                              unsigned long long *out, uint32_t *per_pixel, cudaStream_t s);
 cudaError_t launch_l1_loss(int64_t npix, int m, const float *rgb, const float *t_rgb, const float *depth,
                            const float *t_depth, const float *sem, const float *t_sem, float *d_rgb, float *d_depth,
                            float *d_sem, float *loss, double *partial, cudaStream_t s);

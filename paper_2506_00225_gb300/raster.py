@@ -385,6 +385,26 @@ class Rasterizer:
         self._last = None
         return out
 
+    def work_counts(self, g: Gaussians, cams, check=True, per_pixel=False) -> dict:
+        """Work counters of the blend passes for the views `cams` (project,
+        bin, then gs_count_work): n_eval (pixel-rectangle pairs up to each
+        pixel's stop), n_eval_box (those inside the alpha box), n_contrib,
+        n_touched (classes above the 0.001 clip floor) and n_pixels; with
+        per_pixel (one view) also "per_pixel": int32 [H, W, 2] of each
+        pixel's (n_eval, n_contrib)."""
+        cams = list(cams)
+        sc, cams_arr, cfg, ws = self._project_bin(g, cams, check)
+        out = torch.zeros(5, dtype=torch.int64, device=self.device)
+        pp = None
+        if per_pixel:
+            pp = torch.zeros((cams[0].height, cams[0].width, 2), dtype=torch.int32, device=self.device)
+        N.check(N.load().gs_count_work(ctypes.byref(sc), cams_arr, len(cams), ctypes.byref(cfg), ws, _ptr(out),
+                                       _ptr(pp), _stream()), "gs_count_work")
+        res = dict(zip(("n_eval", "n_eval_box", "n_contrib", "n_touched", "n_pixels"), out.cpu().tolist()))
+        if pp is not None:
+            res["per_pixel"] = pp.cpu().numpy()
+        return res
+
     def _fit_capacities(self, cnt, cfg):
         """After a checked candidate call: capacities far above the counts
         are cut to 1.25x the counts, and the workspace is re-laid at the

@@ -108,6 +108,9 @@ MUTANTS = [
     ('oracle/gs_oracle.c', 'sem grad w->T',
      'e[10 + j] += dpj * w;',
      'e[10 + j] += dpj * c->T;'),
+    ('oracle/gs_oracle.c', 'eval count before the column test',
+     '    if (x < p->x0 || x > p->x1) continue;\n    ++ne;',
+     '    ++ne;\n    if (x < p->x0 || x > p->x1) continue;'),
     ('oracle/gs_oracle.c', 'sem detach ignored',
      'if (!sem_detach) gi += gsem;',
      'gi += gsem;'),

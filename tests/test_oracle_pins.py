@@ -946,3 +946,34 @@ def test_voxel_off_centre_pixel_depth_limit_and_states():
     prev = np.array([[[2, 0, 1, 3]]], np.uint8)
     cur = np.array([[[1, 1, 1, 1]]], np.uint8)
     np.testing.assert_allclose(vx.new_free(prev, cur, (0.0, 0.0, 0.0), vs), [[1.5 * vs, 0.5 * vs, 0.5 * vs]])
+
+
+def test_evaluation_count_per_pixel():
+    """N_eval of the per-pixel definition (the work count of the forward
+    blend's roofline): a pixel whose final transmittance is at least 0.01
+    cannot have stopped (alpha <= 0.99 keeps T (1 - alpha) >= 1e-4), so it
+    tested every visible Gaussian whose pixel rectangle holds it -- a count
+    that the rectangles alone fix.  The stopped pixels tested a prefix of
+    that set, including the stopping pair; the per-pixel counts add up to
+    the oracle's total, and in the stack of the stop-rule example exactly
+    the 3 contributors and the stopping 4th Gaussian are tested."""
+    sc = scene_plain(5, n=10000, m=8, k=2)
+    cam = look_camera((0.0, 0.0, 1.5), 15.0, 61, 47, 40.0)
+    r = oracle.render(sc, cam, prec="f32")
+    p = oracle.project(sc, cam, prec="f32")
+    vis = np.nonzero(p["visible"])[0]
+    x0, x1, y0, y1 = (p["rect"][vis, i][:, None, None] for i in range(4))
+    ys, xs = np.mgrid[0:cam.height, 0:cam.width]
+    cover = ((xs[None] >= x0) & (xs[None] <= x1) & (ys[None] >= y0) & (ys[None] <= y1)).sum(axis=0)
+    open_px = r["T"] >= 0.01
+    assert open_px.sum() > 100 and (~open_px).sum() > 100
+    np.testing.assert_array_equal(r["n_eval_px"][open_px], cover[open_px])
+    assert (r["n_eval_px"][~open_px] <= cover[~open_px]).all()
+    assert (r["n_eval_px"] >= r["n_contrib"]).all()
+    assert int(r["n_eval_px"].sum()) == r["n_eval"]
+    # stop-rule stack: 3 contributors + the stopping Gaussian at the centre
+    cam3 = ident_cam(3, 3, 10.0)
+    means = [[0.0, 0.0, 1.0 + 0.1 * i] for i in range(6)]
+    st = mk_scene(means, [[1.0, 1.0, 1.0]] * 6, [[1, 0, 0, 0]] * 6, [0.95] * 6)
+    r3 = oracle.render(st, cam3, prec="f64")
+    assert r3["n_contrib"][1, 1] == 3 and r3["n_eval_px"][1, 1] == 4
