@@ -305,26 +305,26 @@ struct FwdArgs {
   uint32_t mask_units;
 };
 
-// The fused-loss semantic passes end with this: every CTA has written its
-// tile's three sums; the CTA that takes the last ticket adds all tiles'
-// sums (a fixed order: deterministic) and writes the loss, then leaves the
-// ticket counter at 0 for the next launch.  Mean-L1 mode: rgb / (3 npix) +
+// The fused-loss semantic passes end each tile with this: the tile's three
+// sums are written; the CTA that takes the last of the ntiles tickets adds
+// all tiles' sums (a fixed order: deterministic) and writes the loss, then
+// leaves the ticket counter at 0 for the next launch.  Mean-L1 mode: rgb / (3 npix) +
 // depth / npix + sem / (npix m); Sec. 3.1 objective mode: 0.5 rgb + depth
 // (sums over the silhouette mask) + sem / npix.  No CTA waits on another.
 template <int THREADS>
-__device__ __forceinline__ void finish_loss(const FwdArgs &a, int objective) {
+__device__ __forceinline__ void finish_loss(const FwdArgs &a, int objective, uint32_t ntiles) {
   constexpr int WARPS = THREADS / 32;
   __shared__ int s_last;
   __shared__ double s_red[3][WARPS];
   if (threadIdx.x == 0) {
     __threadfence();  // this tile's sums before the ticket
-    s_last = atomicAdd(&a.counters->tiles_done, 1u) == gridDim.x - 1;
+    s_last = atomicAdd(&a.counters->tiles_done, 1u) == ntiles - 1;
   }
   __syncthreads();
   if (!s_last) return;
   __threadfence();
   double s[3] = {0.0, 0.0, 0.0};
-  for (uint32_t t = threadIdx.x; t < gridDim.x; t += THREADS)
+  for (uint32_t t = threadIdx.x; t < ntiles; t += THREADS)
     for (int i = 0; i < 3; ++i) s[i] += __ldcg(a.lpart + 3 * (size_t)t + i);
   for (int i = 0; i < 3; ++i) {
 #pragma unroll

@@ -301,6 +301,14 @@ __global__ void __launch_bounds__(TW *TH, 2) k_semantic(FwdArgs a) {
     if (nbatch > 0 && t < batch_n(0)) issue(0, a.pvals[rg.x + t]);
     cp_async_commit();
     uint32_t pv = (nbatch > 1 && t < batch_n(1)) ? a.pvals[rg.x + kBatch + t] : 0u;
+    // contributor words of the next batch, loaded one batch ahead (their
+    // latency overlaps the walk of the current batch)
+    uint32_t mn0 = 0u, mn1 = 0u;
+    if (a.masks && nbatch > 0 && last > 0u) {
+      const uint32_t *mw = a.masks + (size_t)unit0 * 2 * NPIX;
+      mn0 = mw[lp];
+      mn1 = mw[NPIX + lp];
+    }
     cp_async_wait_all();
     __syncthreads();
     for (int bi = 0; bi < nbatch; ++bi) {
@@ -316,22 +324,26 @@ __global__ void __launch_bounds__(TW *TH, 2) k_semantic(FwdArgs a) {
       const float2 *suv = buf_uv(bi & 1);
       const float4 *sco = buf_co(bi & 1);
       const int2 *ssem = buf_sem(bi & 1);
-      if (b0 < last) {
-        if (a.masks) {
-          const uint32_t *mw = a.masks + (size_t)(unit0 + bi) * 2 * NPIX;
-          mine[0] = mw[lp];
-          mine[1] = mw[NPIX + lp];
-        } else {
-          // recomputation: contributors are the pairs up to the last one
-          // whose pixel box holds the pixel and whose alpha passes 1/255
-          const short4 *sbox = buf_box(bi & 1);
-          const int n = min(batch_n(bi), (int)(last - b0));
-          for (int j = 0; j < n; ++j) {
-            const short4 bx = sbox[j];
-            if (px < bx.x || px > bx.y || py < bx.z || py > bx.w) continue;
-            float alpha, G, araw, dx, dy;
-            if (gauss_alpha(suv[j], sco[j], fpx, fpy, alpha, G, araw, dx, dy)) mine[j >> 5] |= 1u << (j & 31);
-          }
+      if (a.masks) {
+        mine[0] = mn0;
+        mine[1] = mn1;
+        mn0 = mn1 = 0u;
+        if (bi + 1 < nbatch && b0 + kBatch < last) {
+          const uint32_t *mw = a.masks + (size_t)(unit0 + bi + 1) * 2 * NPIX;
+          mn0 = mw[lp];
+          mn1 = mw[NPIX + lp];
+        }
+      }
+      if (b0 < last && !a.masks) {
+        // recomputation: contributors are the pairs up to the last one
+        // whose pixel box holds the pixel and whose alpha passes 1/255
+        const short4 *sbox = buf_box(bi & 1);
+        const int n = min(batch_n(bi), (int)(last - b0));
+        for (int j = 0; j < n; ++j) {
+          const short4 bx = sbox[j];
+          if (px < bx.x || px > bx.y || py < bx.z || py > bx.w) continue;
+          float alpha, G, araw, dx, dy;
+          if (gauss_alpha(suv[j], sco[j], fpx, fpy, alpha, G, araw, dx, dy)) mine[j >> 5] |= 1u << (j & 31);
         }
       }
 #pragma unroll
@@ -341,8 +353,14 @@ __global__ void __launch_bounds__(TW *TH, 2) k_semantic(FwdArgs a) {
           const int jb = __ffs(un) - 1;
           un &= un - 1;
           const int j = h * 32 + jb;
-          float alpha = 0.f, G, araw, dx, dy;
-          gauss_alpha(suv[j], sco[j], fpx, fpy, alpha, G, araw, dx, dy);
+          // branch-free alpha (a contributor has power <= 0; other lanes get w = 0)
+          const float2 uv_ = suv[j];
+          const float4 co_ = sco[j];
+          const float dx = __fsub_rn(uv_.x, fpx), dy = __fsub_rn(uv_.y, fpy);
+          const float q_ = __fmaf_rn(co_.x, __fmul_rn(dx, dx), __fmul_rn(co_.z, __fmul_rn(dy, dy)));
+          const float power = __fmaf_rn(-0.5f, q_, -__fmul_rn(co_.y, __fmul_rn(dx, dy)));
+          const float araw = __fmul_rn(co_.w, __expf(power));
+          const float alpha = araw < kAlphaMax ? araw : kAlphaMax;
           const bool on = (mine[h] >> jb) & 1u;
           float w = on ? __fmul_rn(alpha, T) : 0.f;
           if (tmode) w = -w;
@@ -450,7 +468,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_semantic(FwdArgs a) {
       for (int w = 0; w < WARPS; ++w) s += red[w];
       a.lpart[3 * (size_t)tile + 2] = s;
     }
-    finish_loss<THREADS>(a, 0);
+    finish_loss<THREADS>(a, 0, gridDim.x);
   }
 }
 

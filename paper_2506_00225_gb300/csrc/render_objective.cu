@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_sem_objective(FwdArgs a, float lo
     for (int w = 0; w < WARPS; ++w) s += red[w];
     a.lpart[3 * (size_t)tile + 2] = s;
   }
-  finish_loss<TW * TH>(a, 1);
+  finish_loss<TW * TH>(a, 1, gridDim.x);
 
   // (3) d(objective)/d(weight l of Gaussian g) = sum_p w_gp dP_p[id_gl]:
   // lanes hold their pixel's products, a transposed warp sum leaves the

@@ -119,8 +119,12 @@ def test_unsupported_configurations_fall_back():
         l_d, g_d = _step(rast, g, cam, targets, fused=None)
         l_u, g_u = _step(rast, g, cam, targets, fused=False)
         assert l_d == l_u
+        # the same route twice: gradients differ only by the order in which
+        # float atomics add the warps' partial sums (the conic and quaternion
+        # entries sum cancelling terms), so a reassociation bound, well inside
+        # the 1e-3 bar against the oracle
         for a, b in zip(g_d, g_u):
-            _close(a, b, 1e-5, kw)
+            _close(a, b, 1e-4, kw)
 
 
 def test_fused_objective_matches_oracle():
