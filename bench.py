@@ -65,7 +65,8 @@ def parse():
     ap.add_argument("--cand-steps", type=int, default=5)
     ap.add_argument("--cand-workload", default="cand96", choices=["cand96", "mixed2m"],
                     help="candidate set of the candidates measurement")
-    ap.add_argument("--cand-tile", default="16x16", help="WxH tile of the candidate kernels")
+    ap.add_argument("--cand-tile", default=None, help="WxH tile of the candidate kernels (default: autotuned)")
+    ap.add_argument("--cand-batch", type=int, default=64, help="staged batch of the candidate kernels with --cand-tile")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 2M-Gaussian mapping and mixed-stream runs")
     ap.add_argument("--clocks-dir", default="/tmp",
@@ -898,7 +899,9 @@ def bench_large(args, dev, flush, wl):
 
     # ---- mixed stream: mapping step + 128 candidates, one graph ----------
     cams = wl["cand_cams"]
-    rc = raster.Rasterizer(tile=tile, device=dev)
+    from paper_2506_00225_gb300 import autotune
+    cbest, ctable = autotune.tune_candidates(g, cams)
+    rc = raster.Rasterizer(tile=cbest["tile"], cand_batch=cbest["cand_batch"], device=dev)
     cand_out = rc.candidates(g, cams, check=True)
     step = _mapping_step(rast_keep, g, cam, params_keep, t_rgb, t_depth, t_sem)
 
@@ -917,11 +920,11 @@ def bench_large(args, dev, flush, wl):
     for c in cams:
         key = (c.width, c.height)
         if key not in singles:
-            singles[key] = raster.Rasterizer(tile=tile, device=dev)
+            singles[key] = raster.Rasterizer(tile=cbest["tile"], cand_batch=cbest["cand_batch"], device=dev)
             singles[key].candidates(g, [c], check=True)
     torch.cuda.synchronize()
     plain = []
-    for _ in range(2):
+    for _ in range(5):
         flush.zero_()
         s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s_.record()
@@ -944,7 +947,9 @@ def bench_large(args, dev, flush, wl):
              "plain_per_view_launches": {"value": 1000.0 / ms_plain, "unit": "iters/s", "ms_per_iter": ms_plain},
              "graph_batched_speedup": ms_plain / ms_graph,
              "candidate_counts": {"visible_records": int(ccnt.n_records), "tile_gaussian_pairs": int(ccnt.n_pairs)},
-             "candidate_workspace_bytes": int(rc.ws.numel())}
+             "candidate_workspace_bytes": int(rc.ws.numel()),
+             "candidate_autotune": {"chosen": {"tile": "%dx%d" % cbest["tile"], "cand_batch": cbest["cand_batch"]},
+                                    "table": ctable}}
     return large, mixed
 
 
@@ -954,8 +959,16 @@ def bench_candidates(args, dev, flush):
     wl = scenes.workload(args.cand_workload)
     sc, cams = wl["scene"], wl.get("cand_cams", wl["cams"])
     g = raster.Gaussians.from_scene(sc, dev)
-    ctile = tuple(int(x) for x in args.cand_tile.lower().split("x"))
-    rast = raster.Rasterizer(tile=ctile, device=dev)
+    # launch configuration: the autotuner's (tile x staged batch) on these
+    # views, unless fixed on the command line
+    from paper_2506_00225_gb300 import autotune
+    if args.cand_tile:
+        ctile = tuple(int(x) for x in args.cand_tile.lower().split("x"))
+        cbest, ctable = {"tile": ctile, "cand_batch": args.cand_batch}, None
+    else:
+        cbest, ctable = autotune.tune_candidates(g, cams)
+        ctile = cbest["tile"]
+    rast = raster.Rasterizer(tile=ctile, cand_batch=cbest["cand_batch"], device=dev)
     out = rast.candidates(g, cams, check=True)
     cnt = rast.counters()
     for _ in range(2):
@@ -973,7 +986,7 @@ def bench_candidates(args, dev, flush):
     for c in cams:
         key = (c.width, c.height)
         if key not in singles:
-            singles[key] = raster.Rasterizer(tile=ctile, device=dev)
+            singles[key] = raster.Rasterizer(tile=ctile, cand_batch=cbest["cand_batch"], device=dev)
             singles[key].candidates(g, [c], check=True)
     torch.cuda.synchronize()
     per_view = []
@@ -1027,6 +1040,8 @@ def bench_candidates(args, dev, flush):
             "ms_per_batch": ms, "mpix_per_s": npix / (ms * 1e-3) / 1e6,
             "timing": f"one CUDA graph of the batched call, {len(batch_ms)} replays (L2 flushed before each); "
                       "per-view arm: 5 eager repetitions",
+            "autotune": {"chosen": {"tile": "%dx%d" % ctile, "cand_batch": cbest["cand_batch"]}, "table": ctable},
+            "workspace_bytes": int(rast.ws.numel()),
             "roofline": cand_roof,
             "workload": ("cand96: the 300k room + Gamma(2,0.5) uncertainty, 96 poses (4x4 grid at 0.5 m x 6 yaws), "
                          "resolutions cycling 170x300 / 340x600 / 680x1200") if args.cand_workload == "cand96" else

@@ -111,7 +111,14 @@ typedef struct gs_camera {
  *                        runs out raises GS_ERR_TIMEOUT in the device status,
  *                        later kernels of the chain skip their work, and
  *                        gs_read_counters reports it.  Small values exist to
- *                        exercise that path. */
+ *                        exercise that path.
+ *   cand_bits_bytes      candidate renders (n_views > 1): bytes of contributor
+ *                        bits the workspace keeps (0 = 4 GiB).  The views are
+ *                        rendered in waves whose bits fit; a tile whose bits
+ *                        still do not fit re-tests its pairs.  Results do not
+ *                        depend on it.
+ *   cand_batch           Gaussians staged per batch in the candidate kernels:
+ *                        32, 64 or 128 (0 = 64); results do not depend on it */
 typedef struct gs_config {
   int32_t tile_w, tile_h;
   int32_t sem_detach_geometry;
@@ -120,6 +127,8 @@ typedef struct gs_config {
   int64_t pair_capacity;
   int32_t recompute_bwd;
   int32_t spin_limit;
+  int64_t cand_bits_bytes;
+  int32_t cand_batch;
 } gs_config;
 
 /* Counters read back by gs_read_counters. */

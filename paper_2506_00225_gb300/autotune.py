@@ -64,3 +64,44 @@ def tune_mapping(g: raster.Gaussians, cam, t_rgb, t_depth, t_sem, reps: int = 5,
     res = ({"tile": (w, h), "px_per_thread": best["px_per_thread"], "ms": best["ms"]}, table)
     _CACHE[key] = res
     return res
+
+
+CAND_BATCHES = (32, 64, 128)
+_CAND_CACHE: dict = {}
+
+
+def tune_candidates(g: raster.Gaussians, cams, reps: int = 5, device=None):
+    """Times the batched candidate render of the caller's own views for
+    every compiled tile shape and staged batch size (32, 64, 128 Gaussians)
+    and returns (best {tile, cand_batch, ms}, table of all timings).  The
+    per-view sums do not depend on the choice.  Cached per (Gaussians,
+    view sizes, k, m)."""
+    key = (g.n, tuple((c.width, c.height) for c in cams), g.k, g.m)
+    if key in _CAND_CACHE:
+        return _CAND_CACHE[key]
+    device = device or g.means.device
+    table = []
+    for tile in SHAPES:
+        for batch in CAND_BATCHES:
+            rast = raster.Rasterizer(tile=tile, cand_batch=batch, device=device)
+            out = rast.candidates(g, cams, check=True)  # sizes and fits the workspace
+            rast.candidates(g, cams, check=False, out=out)
+            torch.cuda.synchronize()
+            times = []
+            for _ in range(reps):
+                s = torch.cuda.Event(enable_timing=True)
+                e = torch.cuda.Event(enable_timing=True)
+                torch.cuda._sleep(2_000_000)
+                s.record()
+                rast.candidates(g, cams, check=False, out=out)
+                e.record()
+                torch.cuda.synchronize()
+                times.append(s.elapsed_time(e))
+            table.append({"tile": f"{tile[0]}x{tile[1]}", "cand_batch": batch,
+                          "ms": round(statistics.median(times), 4)})
+            del rast
+    best = min(table, key=lambda r: r["ms"])
+    w, h = (int(x) for x in best["tile"].split("x"))
+    res = ({"tile": (w, h), "cand_batch": best["cand_batch"], "ms": best["ms"]}, table)
+    _CAND_CACHE[key] = res
+    return res

@@ -156,20 +156,43 @@ bool make_layout(const gs_scene *scene, const gs_camera *cams, int n_views, cons
   L->off_codes = take(n_views == 1 ? 4 * (size_t)L->npix * (2 * (1 + L->nwc)) : 32);
   L->off_lpart = take(n_views == 1 ? 3 * sizeof(double) * (size_t)(tiles > 0 ? tiles : 1) : 32);
   L->off_semg = take(n_views == 1 ? 4 * (size_t)scene->n * scene->k : 32);
-  // one unit = one staged batch of one tile: 2 words per tile pixel
-  // (none with recompute_bwd: pass 2 and the adjoint re-test the pairs;
-  // candidate views keep them only while they fit kCandMaskBudget, else the
-  // single-pass candidate kernel runs)
+  // Contributor bits: one unit = one staged batch of one tile, one bit per
+  // (tile pixel, pair) (none with recompute_bwd: the passes after the blend
+  // re-test the pairs).  The mapping view keeps every unit of 64 pairs; a
+  // candidate call keeps at most cand_bits_bytes and renders its views in
+  // waves whose units fit (a tile that still does not fit re-tests).
+  if (cfg.cand_batch != 0 && cfg.cand_batch != 32 && cfg.cand_batch != 64 && cfg.cand_batch != 128) return false;
+  if (cfg.cand_bits_bytes < 0) return false;
+  L->cand_batch = cfg.cand_batch ? cfg.cand_batch : 64;
   {
-    const int64_t units = pcap / kBatch + (int64_t)tiles + 1;
-    const int64_t bytes = 8 * units * cfg.tile_w * cfg.tile_h;
-    L->mask_units = cfg.recompute_bwd ? 0 : (n_views == 1 || bytes <= kCandMaskBudget) ? units : 0;
+    const int64_t tpx = (int64_t)cfg.tile_w * cfg.tile_h;
+    const int64_t map_units = pcap / kBatch + (int64_t)tiles + 1;
+    const int64_t cand_units = pcap / L->cand_batch + (int64_t)tiles + 1;
+    const int64_t unit_bytes = (int64_t)(L->cand_batch / 8) * tpx;  // cand_batch bits per tile pixel
+    int64_t bytes = cand_units * unit_bytes;
+    if (n_views == 1 && 8 * map_units * tpx > bytes) bytes = 8 * map_units * tpx;
+    const int64_t budget = cfg.cand_bits_bytes > 0 ? cfg.cand_bits_bytes : kCandBitsDefault;
+    if (n_views > 1 && bytes > budget) bytes = budget;
+    if (cfg.recompute_bwd) bytes = 0;
+    L->mask_units = n_views == 1 ? bytes / (8 * tpx) : 0;
+    L->cand_cap_units = bytes / unit_bytes;
+    if (L->cand_cap_units < 1) {
+      L->cand_cap_units = 0;
+      bytes = 0;
+    }
+    // waves: enough for the worst case of the capacities, twice over for the
+    // views that do not pack (at most one wave per view)
+    const int64_t need = cand_units;
+    int64_t waves = L->cand_cap_units > 0 ? 2 * ((need + L->cand_cap_units - 1) / L->cand_cap_units) : 1;
+    if (need <= L->cand_cap_units) waves = 1;
+    L->cand_waves = (int)(waves < n_views ? waves : n_views);
+    L->off_mask_off = take(sizeof(uint32_t) * (size_t)(tiles + 1));
+    L->off_masks = take(bytes > 0 ? (size_t)bytes : 32);
   }
-  L->off_mask_off = take(sizeof(uint32_t) * (size_t)(tiles + 1));
-  L->off_masks = take(L->mask_units ? 8 * (size_t)L->mask_units * cfg.tile_w * cfg.tile_h : 32);
   // last contributor of every (tile, pixel), written by the two-pass
   // candidate kernels (any number of views) whenever the bits exist
-  L->off_clast = take(L->mask_units ? 4 * (size_t)tiles * cfg.tile_w * cfg.tile_h : 32);
+  L->off_clast = take(L->cand_cap_units ? 4 * (size_t)tiles * cfg.tile_w * cfg.tile_h : 32);
+  L->off_cand_plan = take(sizeof(uint32_t) * (size_t)L->cand_waves * 5);
   L->total = off;
   return true;
 }
@@ -213,6 +236,7 @@ WsPtrs ws_ptrs(const Layout &L, void *ws) {
   P.mask_off = reinterpret_cast<uint32_t *>(b + L.off_mask_off);
   P.masks = reinterpret_cast<uint32_t *>(b + L.off_masks);
   P.clast = reinterpret_cast<uint32_t *>(b + L.off_clast);
+  P.cand_plan = reinterpret_cast<uint32_t *>(b + L.off_cand_plan);
   return P;
 }
 

@@ -18,12 +18,27 @@
 // mapping view): k_cand_blend composites U and S, records the last
 // contributor and one bit per (pixel, staged Gaussian) that contributed;
 // k_cand_sem walks only those bits to build the class distribution, class
-// chunk by class chunk, and reduces the entropy.  Otherwise the single-pass
-// k_candidates re-blends every chunk.
+// chunk by class chunk, and reduces the entropy.  Both are persistent: their
+// CTAs take (view, tile) work items by ticket, in tile order.
+// The bits are bounded: the views are rendered in waves whose bits fit the
+// workspace (planned on the device from the tile pair counts), and a tile
+// whose bits do not fit re-tests its pairs in the class pass.  The staged
+// batch size B (32, 64 or 128 Gaussians) is a template parameter chosen by
+// the autotuner.  Without bits (recompute_bwd) the single-pass k_candidates
+// re-blends every class chunk.
 #include "gs_internal.cuh"
 #include "render_common.cuh"
 
 namespace gs {
+
+// Candidate waves in the workspace: [waves][5] = first tile, end tile,
+// first bit unit, ticket of the blend pass, ticket of the class pass.
+struct CandPlan {
+  uint32_t *wave;
+  int waves;
+};
+
+inline CandPlan cand_plan(const Layout &L, const WsPtrs &P) { return CandPlan{P.cand_plan, L.cand_waves}; }
 
 struct CandArgs {
   const uint2 *ranges;
@@ -39,8 +54,9 @@ struct CandArgs {
   // two-pass mode
   const uint32_t *mask_off;
   uint32_t *masks;
-  uint32_t mask_units;
+  uint32_t cap_units;  // bit capacity of a wave in (tile, batch) units
   uint32_t *clast;
+  CandPlan plan;
 };
 
 // View of a global tile id: last v with tile_off[v] <= tile.
@@ -184,196 +200,298 @@ __global__ void __launch_bounds__(TW *TH) k_candidates(CandArgs a) {
   }
 }
 
+// Next tile of a persistent candidate pass: the CTA takes a ticket of the
+// wave's tile range (tile order: a view's tiles run together and share its
+// records in L2); false when the wave is exhausted.
+__device__ __forceinline__ bool next_tile(const CandPlan &p, int wave, int which, uint32_t *s_item,
+                                          uint32_t &tile, uint32_t &unit_base) {
+  __syncthreads();  // the previous tile's shared memory is no longer read
+  if (threadIdx.x == 0) *s_item = atomicAdd(p.wave + 5 * wave + 3 + which, 1u);
+  __syncthreads();
+  tile = p.wave[5 * wave] + *s_item;
+  if (tile >= p.wave[5 * wave + 1]) return false;
+  unit_base = p.wave[5 * wave + 2];
+  return true;
+}
+
 // Pass 1: U and S of Eq. 1 with the same per-pair rules as the mapping
 // blend (alpha box, 1/255 skip, 1e-4 stop); writes the last contributor and
-// the contributor bits of every staged batch; adds sum U and N_S per view.
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH) k_cand_blend(CandArgs a) {
+// the contributor bits of every staged batch of B pairs (when the tile's
+// bits fit the wave's capacity); adds sum U and N_S per view.
+template <int TW, int TH, int B>
+__global__ void __launch_bounds__(TW *TH) k_cand_blend(CandArgs a, int wave) {
   using FP = Footprint<TW, TH>;
   constexpr int THREADS = FP::kThreads;
   constexpr int WARPS = FP::kWarps;
   constexpr int NPIX = FP::kPix;
+  constexpr int NW = B / 32;  // contributor words per pixel and batch
   extern __shared__ float4 smem4[];
-  BatchSmem bs = batch_smem(smem4, 0);
-  __shared__ uint32_t lmask[kBatch * WARPS];  // per staged Gaussian: its lanes of each warp
+  float4 *s_co = smem4;
+  float4 *s_cd = smem4 + B;  // uncertainty in .x
+  float2 *s_uv = reinterpret_cast<float2 *>(smem4 + 2 * B);
+  uint32_t *lmask = reinterpret_cast<uint32_t *>(s_uv + B);  // per staged Gaussian: its lanes of each warp
+  __shared__ uint32_t s_item;
   if (a.counters->status & kStatusTimeout) return;
-  const uint32_t tile = blockIdx.x;
-  const int v = view_of(a.tile_off, a.n_views, tile);
-  const DevCam &c = a.cams[v];
-  const uint32_t local = tile - c.tile_off;
-  const int ox = (int)(local % (uint32_t)c.tiles_x) * TW, oy = (int)(local / (uint32_t)c.tiles_x) * TH;
-  const uint2 rg = a.ranges[tile];
-  const int lx = FP::lx(), ly = FP::ly(0);
-  const int px = ox + lx, py = oy + ly, lp = ly * TW + lx;
-  const bool inside = px < c.width && py < c.height;
-  const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+  const int lx = FP::lx(), ly = FP::ly(0), lp = ly * TW + lx;
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-  const uint32_t unit0 = a.mask_off[tile];
   const bool use_unc = a.unc != nullptr;
+  uint32_t tile, unit_base;
+  while (next_tile(a.plan, wave, 0, &s_item, tile, unit_base)) {
+    const int v = view_of(a.tile_off, a.n_views, tile);
+    const DevCam &c = a.cams[v];
+    const uint32_t local = tile - c.tile_off;
+    const int ox = (int)(local % (uint32_t)c.tiles_x) * TW, oy = (int)(local / (uint32_t)c.tiles_x) * TH;
+    const uint2 rg = a.ranges[tile];
+    const int px = ox + lx, py = oy + ly;
+    const bool inside = px < c.width && py < c.height;
+    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+    const uint32_t unit0 = a.mask_off[tile] - unit_base;
+    const bool store = unit0 + (rg.y - rg.x + B - 1) / B <= a.cap_units;
 
-  float T = 1.f, U = 0.f;
-  uint32_t last = 0;
-  bool done = !inside;
-  uint32_t bi = 0;
-  for (uint32_t b = rg.x; b < rg.y; b += kBatch, ++bi) {
-    const int n = (int)min((uint32_t)kBatch, rg.y - b);
-    __syncthreads();
-    for (int t = threadIdx.x; t < n; t += THREADS) {
-      const uint32_t r = a.pvals[b + t];
-      stage_record<TW, TH>(a.rec, r, t, 0, ox, oy, bs, false, use_unc);
-      lane_masks<TW, TH>(__ldg(a.rec.box + r), ox, oy, lmask + t * WARPS);
-    }
-    __syncthreads();
-    uint32_t bits[2] = {0u, 0u};
-    if (!__all_sync(0xffffffffu, done)) {
-      for (int base = 0; base < n; base += 32) {
-        const int jj = base + (int)lane;
-        uint32_t vis = __ballot_sync(0xffffffffu, jj < n && lmask[jj * WARPS + warp] != 0u);
-        while (vis) {
-          const int bit = __ffs(vis) - 1;
-          vis &= vis - 1;
-          const int j = base + bit;
-          if (done || !((lmask[j * WARPS + warp] >> lane) & 1u)) continue;
-          float alpha, G, araw, dx, dy;
-          if (!gauss_alpha(bs.uv[j], bs.co[j], fpx, fpy, alpha, G, araw, dx, dy)) continue;
-          const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
-          if (Tn < kTStop) { done = true; continue; }
-          const float w = __fmul_rn(alpha, T);
-          U = fmaf(w, bs.cd[j].x, U);
-          T = Tn;
-          bits[base >> 5] |= 1u << bit;
+    float T = 1.f, U = 0.f;
+    uint32_t last = 0;
+    bool done = !inside;
+    uint32_t bi = 0;
+    for (uint32_t b = rg.x; b < rg.y; b += B, ++bi) {
+      const int n = (int)min((uint32_t)B, rg.y - b);
+      __syncthreads();
+      for (int t = threadIdx.x; t < n; t += THREADS) {
+        const uint32_t r = a.pvals[b + t];
+        s_co[t] = __ldg(a.rec.co + r);
+        s_uv[t] = __ldg(a.rec.uv + r);
+        float4 cd = __ldg(a.rec.cd + r);
+        if (use_unc) cd.x = __ldg(a.rec.unc + r);
+        s_cd[t] = cd;
+        lane_masks<TW, TH>(__ldg(a.rec.box + r), ox, oy, lmask + t * WARPS);
+      }
+      __syncthreads();
+      uint32_t bits[NW];
+#pragma unroll
+      for (int h = 0; h < NW; ++h) bits[h] = 0u;
+      if (!__all_sync(0xffffffffu, done)) {
+#pragma unroll
+        for (int h = 0; h < NW; ++h) {
+          const int jj = h * 32 + (int)lane;
+          uint32_t vis = __ballot_sync(0xffffffffu, jj < n && lmask[jj * WARPS + warp] != 0u);
+          while (vis) {
+            const int bit = __ffs(vis) - 1;
+            vis &= vis - 1;
+            const int j = h * 32 + bit;
+            if (done || !((lmask[j * WARPS + warp] >> lane) & 1u)) continue;
+            float alpha, G, araw, dx, dy;
+            if (!gauss_alpha(s_uv[j], s_co[j], fpx, fpy, alpha, G, araw, dx, dy)) continue;
+            const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
+            if (Tn < kTStop) { done = true; continue; }
+            const float w = __fmul_rn(alpha, T);
+            U = fmaf(w, s_cd[j].x, U);
+            T = Tn;
+            bits[h] |= 1u << bit;
+          }
         }
       }
+#pragma unroll
+      for (int h = 0; h < NW; ++h)
+        if (bits[h]) last = b - rg.x + 32 * h + (32 - __clz(bits[h]));
+      if (store) {
+        uint32_t *mw = a.masks + (size_t)(unit0 + bi) * NW * NPIX;
+#pragma unroll
+        for (int h = 0; h < NW; ++h) mw[h * NPIX + lp] = bits[h];
+      }
+      if (__syncthreads_count(done) == THREADS) break;
     }
-    if (bits[1]) last = b - rg.x + 32 + (32 - __clz(bits[1]));
-    else if (bits[0]) last = b - rg.x + (32 - __clz(bits[0]));
-    if (unit0 + bi < a.mask_units) {
-      uint32_t *mw = a.masks + (size_t)(unit0 + bi) * 2 * NPIX;
-      mw[lp] = bits[0];
-      mw[NPIX + lp] = bits[1];
-    }
-    if (__syncthreads_count(done) == THREADS) break;
+    a.clast[(size_t)tile * NPIX + lp] = last;
+    add_view_sum<THREADS>(inside && use_unc ? U : 0.f, a.out + 3 * v);
+    add_view_sum<THREADS>(inside && T == 1.f ? 1.f : 0.f, a.out + 3 * v + 2);
   }
-  a.clast[(size_t)tile * NPIX + lp] = last;
-  add_view_sum<THREADS>(inside && use_unc ? U : 0.f, a.out + 3 * v);
-  add_view_sum<THREADS>(inside && T == 1.f ? 1.f : 0.f, a.out + 3 * v + 2);
 }
 
 // Pass 2: the class distribution from the contributor bits (warp-uniform
 // walk over the union of the warp's bits, alpha recomputed bit-identically,
 // k adds per contributor into per-thread rows), one class chunk at a time,
-// and the clipped, renormalised entropy per pixel.
-template <int TW, int TH, int K>
-__global__ void __launch_bounds__(TW *TH, 2) k_cand_sem(CandArgs a) {
+// and the clipped, renormalised entropy per pixel.  A tile without stored
+// bits re-tests its pairs up to each pixel's last contributor (alpha box,
+// alpha), which selects the same contributors.
+__host__ __device__ inline size_t cand_sem_batch_bytes(int k, int B) { return (size_t)B * (8 + 16 + 8 + 8 * k); }
+
+template <int TW, int TH, int K, int B>
+__global__ void __launch_bounds__(TW *TH, 2) k_cand_sem(CandArgs a, int wave) {
   using FP = Footprint<TW, TH>;
   constexpr int THREADS = FP::kThreads;
   constexpr int NPIX = FP::kPix;
+  constexpr int NW = B / 32;
   extern __shared__ float4 smem4[];
   const int k = a.k;
   char *sbase = reinterpret_cast<char *>(smem4);
-  const size_t bbytes = sem_batch_bytes(k);
+  const size_t bbytes = cand_sem_batch_bytes(k, B);
   float *sP = reinterpret_cast<float *>(sbase + 2 * bbytes);
-  __shared__ uint32_t s_maxlast;
+  __shared__ uint32_t s_maxlast, s_item;
   if (a.counters->status & kStatusTimeout) return;
-
-  const uint32_t tile = blockIdx.x;
-  const int v = view_of(a.tile_off, a.n_views, tile);
-  const DevCam &c = a.cams[v];
-  const uint32_t local = tile - c.tile_off;
-  const int ox = (int)(local % (uint32_t)c.tiles_x) * TW, oy = (int)(local / (uint32_t)c.tiles_x) * TH;
-  const uint2 rg = a.ranges[tile];
-  const int lx = FP::lx(), ly = FP::ly(0);
-  const int px = ox + lx, py = oy + ly, lp = ly * TW + lx;
-  const bool inside = px < c.width && py < c.height;
-  const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+  const int lx = FP::lx(), ly = FP::ly(0), lp = ly * TW + lx;
   float *myP = sP + threadIdx.x * a.mstride;
-  const uint32_t unit0 = a.mask_off[tile];
 
-  const uint32_t last = a.clast[(size_t)tile * NPIX + lp];
-  if (threadIdx.x == 0) s_maxlast = 0;
-  __syncthreads();
-  if (last) atomicMax(&s_maxlast, last);
-  __syncthreads();
-  const int nbatch = (int)((s_maxlast + kBatch - 1) / kBatch);
+  auto buf_co = [&](int q) { return reinterpret_cast<float4 *>(sbase + q * bbytes); };
+  auto buf_uv = [&](int q) { return reinterpret_cast<float2 *>(sbase + q * bbytes + B * 16); };
+  auto buf_box = [&](int q) { return reinterpret_cast<short4 *>(sbase + q * bbytes + B * 24); };
+  auto buf_sem = [&](int q) { return reinterpret_cast<int2 *>(sbase + q * bbytes + B * 32); };
 
-  auto buf_uv = [&](int q) { return reinterpret_cast<float2 *>(sbase + q * bbytes); };
-  auto buf_co = [&](int q) { return reinterpret_cast<float4 *>(sbase + q * bbytes + kBatch * 8); };
-  auto buf_sem = [&](int q) { return reinterpret_cast<int2 *>(sbase + q * bbytes + kBatch * 32); };
-  auto batch_n = [&](int bi) { return (int)min((uint32_t)kBatch, rg.y - (rg.x + (uint32_t)bi * kBatch)); };
-  auto issue = [&](int bi, uint32_t r) {
-    const int q = bi & 1, t = threadIdx.x;
-    cp_async8(buf_uv(q) + t, a.rec.uv + r);
-    cp_async16(buf_co(q) + t, a.rec.co + r);
-    const int2 *src = a.rec.sem + (size_t)r * k;
-    for (int l = 0; l < k; ++l) cp_async8(buf_sem(q) + t * k + l, src + l);
-  };
+  uint32_t tile, unit_base;
+  while (next_tile(a.plan, wave, 1, &s_item, tile, unit_base)) {
+    const int v = view_of(a.tile_off, a.n_views, tile);
+    const DevCam &c = a.cams[v];
+    const uint32_t local = tile - c.tile_off;
+    const int ox = (int)(local % (uint32_t)c.tiles_x) * TW, oy = (int)(local / (uint32_t)c.tiles_x) * TH;
+    const uint2 rg = a.ranges[tile];
+    const int px = ox + lx, py = oy + ly;
+    const bool inside = px < c.width && py < c.height;
+    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+    const uint32_t unit0 = a.mask_off[tile] - unit_base;
+    const bool stored = unit0 + (rg.y - rg.x + B - 1) / B <= a.cap_units;
 
-  float Z = 0.f, Aacc = 0.f;
-  uint32_t nfloor = 0;
-  for (int ch = 0; ch < a.nchunks; ++ch) {
-    const int c_lo = ch * a.mchunk, c_hi = min(a.m, c_lo + a.mchunk), mc = c_hi - c_lo;
-    for (int q = 0; q < mc; ++q) myP[q] = 0.f;
-    float T = 1.f;
-    const int t = threadIdx.x;
-    if (nbatch > 0 && t < batch_n(0)) issue(0, a.pvals[rg.x + t]);
-    cp_async_commit();
-    uint32_t pv = (nbatch > 1 && t < batch_n(1)) ? a.pvals[rg.x + kBatch + t] : 0u;
-    cp_async_wait_all();
+    const uint32_t last = a.clast[(size_t)tile * NPIX + lp];
+    if (threadIdx.x == 0) s_maxlast = 0;
     __syncthreads();
-    for (int bi = 0; bi < nbatch; ++bi) {
-      if (bi + 1 < nbatch && t < batch_n(bi + 1)) issue(bi + 1, pv);
-      cp_async_commit();
-      if (bi + 2 < nbatch && t < batch_n(bi + 2)) pv = a.pvals[rg.x + (uint32_t)(bi + 2) * kBatch + t];
-      const uint32_t b0 = (uint32_t)bi * kBatch;
-      uint32_t mine[2] = {0u, 0u};
-      if (b0 < last) {
-        const uint32_t *mw = a.masks + (size_t)(unit0 + bi) * 2 * NPIX;
-        mine[0] = mw[lp];
-        mine[1] = mw[NPIX + lp];
-      }
-      const float2 *suv = buf_uv(bi & 1);
-      const float4 *sco = buf_co(bi & 1);
-      const int2 *ssem = buf_sem(bi & 1);
+    if (last) atomicMax(&s_maxlast, last);
+    __syncthreads();
+    const int nbatch = (int)((s_maxlast + B - 1) / B);
+    auto batch_n = [&](int bi) { return (int)min((uint32_t)B, rg.y - (rg.x + (uint32_t)bi * B)); };
+    // thread t stages slots t, t + THREADS, ... (PER of them) of a batch
+    constexpr int PER = (B + THREADS - 1) / THREADS;
+    auto issue = [&](int bi, const uint32_t (&r)[PER]) {
+      const int q = bi & 1;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        uint32_t un = __reduce_or_sync(0xffffffffu, mine[h]);
-        while (un) {
-          const int jb = __ffs(un) - 1;
-          un &= un - 1;
-          const int j = h * 32 + jb;
-          float alpha = 0.f, G, araw, dx, dy;
-          gauss_alpha(suv[j], sco[j], fpx, fpy, alpha, G, araw, dx, dy);
-          const bool on = (mine[h] >> jb) & 1u;
-          const float w = on ? __fmul_rn(alpha, T) : 0.f;
-          if (on) T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-          scatter_classes<K>(myP, ssem + j * k, k, c_lo, mc, w);
-        }
+      for (int u = 0; u < PER; ++u) {
+        const int t = threadIdx.x + u * THREADS;
+        if (t >= batch_n(bi)) break;
+        cp_async16(buf_co(q) + t, a.rec.co + r[u]);
+        cp_async8(buf_uv(q) + t, a.rec.uv + r[u]);
+        if (!stored) cp_async8(buf_box(q) + t, a.rec.box + r[u]);
+        const int2 *src = a.rec.sem + (size_t)r[u] * k;
+        for (int l = 0; l < k; ++l) cp_async8(buf_sem(q) + t * k + l, src + l);
       }
+    };
+    // pair indices of batch bi for this thread's slots
+    auto fetch = [&](int bi, uint32_t (&r)[PER]) {
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const int t = threadIdx.x + u * THREADS;
+        r[u] = (bi < nbatch && t < batch_n(bi)) ? a.pvals[rg.x + (uint32_t)bi * B + t] : 0u;
+      }
+    };
+
+    float Z = 0.f, Aacc = 0.f;
+    uint32_t nfloor = 0;
+    for (int ch = 0; ch < a.nchunks; ++ch) {
+      const int c_lo = ch * a.mchunk, c_hi = min(a.m, c_lo + a.mchunk), mc = c_hi - c_lo;
+      for (int q = 0; q < mc; ++q) myP[q] = 0.f;
+      float T = 1.f;
+      uint32_t pv[PER];
+      fetch(0, pv);
+      if (nbatch > 0) issue(0, pv);
+      cp_async_commit();
+      fetch(1, pv);
       cp_async_wait_all();
       __syncthreads();
-    }
-    if (inside) {
-      for (int q = 0; q < mc; ++q) {
-        const float p = myP[q];
-        if (p > kClipLo) {
-          const float ph = p < 1.f ? p : 1.f;
-          Z += ph;
-          Aacc = fmaf(ph, __logf(ph), Aacc);  // hardware log2 approximation (ph in (0.001, 1])
-        } else {
-          ++nfloor;
+      for (int bi = 0; bi < nbatch; ++bi) {
+        if (bi + 1 < nbatch) issue(bi + 1, pv);
+        cp_async_commit();
+        fetch(bi + 2, pv);
+        const uint32_t b0 = (uint32_t)bi * B;
+        uint32_t mine[NW];
+#pragma unroll
+        for (int h = 0; h < NW; ++h) mine[h] = 0u;
+        const float2 *suv = buf_uv(bi & 1);
+        const float4 *sco = buf_co(bi & 1);
+        const int2 *ssem = buf_sem(bi & 1);
+        if (b0 < last) {
+          if (stored) {
+            const uint32_t *mw = a.masks + (size_t)(unit0 + bi) * NW * NPIX;
+#pragma unroll
+            for (int h = 0; h < NW; ++h) mine[h] = mw[h * NPIX + lp];
+          } else {
+            const short4 *sbox = buf_box(bi & 1);
+            const int n = min(batch_n(bi), (int)(last - b0));
+            for (int j = 0; j < n; ++j) {
+              const short4 bx = sbox[j];
+              if (px < bx.x || px > bx.y || py < bx.z || py > bx.w) continue;
+              float alpha, G, araw, dx, dy;
+              if (gauss_alpha(suv[j], sco[j], fpx, fpy, alpha, G, araw, dx, dy)) mine[j >> 5] |= 1u << (j & 31);
+            }
+          }
+        }
+#pragma unroll
+        for (int h = 0; h < NW; ++h) {
+          uint32_t un = __reduce_or_sync(0xffffffffu, mine[h]);
+          while (un) {
+            const int jb = __ffs(un) - 1;
+            un &= un - 1;
+            const int j = h * 32 + jb;
+            float alpha = 0.f, G, araw, dx, dy;
+            gauss_alpha(suv[j], sco[j], fpx, fpy, alpha, G, araw, dx, dy);
+            const bool on = (mine[h] >> jb) & 1u;
+            const float w = on ? __fmul_rn(alpha, T) : 0.f;
+            if (on) T = __fmul_rn(T, __fsub_rn(1.f, alpha));
+            scatter_classes<K>(myP, ssem + j * k, k, c_lo, mc, w);
+          }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+      }
+      if (inside) {
+        for (int q = 0; q < mc; ++q) {
+          const float p = myP[q];
+          if (p > kClipLo) {
+            const float ph = p < 1.f ? p : 1.f;
+            Z += ph;
+            Aacc = fmaf(ph, __logf(ph), Aacc);  // hardware log2 approximation (ph in (0.001, 1])
+          } else {
+            ++nfloor;
+          }
         }
       }
+      __syncthreads();  // the next chunk reuses the rows
     }
-    __syncthreads();  // the next chunk reuses the rows
+    float h = 0.f;
+    if (inside) {
+      const float zf = kClipLo * (float)nfloor;
+      Z += zf;
+      Aacc = fmaf(zf, logf(kClipLo), Aacc);
+      h = logf(Z) - Aacc / Z;
+    }
+    add_view_sum<THREADS>(h, a.out + 3 * v + 1);
   }
-  float h = 0.f;
-  if (inside) {
-    const float zf = kClipLo * (float)nfloor;
-    Z += zf;
-    Aacc = fmaf(zf, logf(kClipLo), Aacc);
-    h = logf(Z) - Aacc / Z;
+}
+
+// Plan of the candidate waves (one CTA): the bit units of every view (its
+// tiles' batch counts, from the exclusive scan mask_off), greedy waves of
+// consecutive views whose units fit the capacity (a view larger than the
+// capacity forms its own wave; its tiles that do not fit re-test), the
+// waves' tile ranges, first units and cleared tickets.
+__global__ void k_cand_plan(const uint32_t *__restrict__ mask_off, const uint32_t *__restrict__ tile_off,
+                            int n_views, uint32_t cap_units, CandPlan p) {
+  __shared__ uint32_t s_units[kMaxViews];
+  const int t = threadIdx.x;
+  if (t < n_views) s_units[t] = mask_off[tile_off[t + 1]] - mask_off[tile_off[t]];
+  __syncthreads();
+  if (t != 0) return;
+  int w = 0;
+  uint32_t used = 0;
+  const uint32_t total_tiles = tile_off[n_views];
+  p.wave[0] = 0u;
+  for (int v = 0; v < n_views; ++v) {
+    if (used > 0 && used + s_units[v] > cap_units && w + 1 < p.waves) {
+      p.wave[5 * w + 1] = tile_off[v];
+      ++w;
+      p.wave[5 * w] = tile_off[v];
+      used = 0;
+    }
+    used += s_units[v];
   }
-  add_view_sum<THREADS>(h, a.out + 3 * v + 1);
+  p.wave[5 * w + 1] = total_tiles;
+  for (int i = w + 1; i < p.waves; ++i) p.wave[5 * i] = p.wave[5 * i + 1] = total_tiles;
+  for (int i = 0; i < p.waves; ++i) {
+    p.wave[5 * i + 2] = mask_off[p.wave[5 * i]];
+    p.wave[5 * i + 3] = p.wave[5 * i + 4] = 0u;
+  }
 }
 
 __global__ void k_zero_doubles(double *p, int n) {
@@ -391,24 +509,50 @@ static cudaError_t launch_cand_shape(const CandArgs &a, uint32_t grid, size_t sm
   return cudaGetLastError();
 }
 
-template <int TW, int TH, int K>
-static cudaError_t launch_cand_sem(const CandArgs &a, uint32_t grid, size_t smem, cudaStream_t s) {
-  {
-    const cudaError_t e = ensure_smem_limit((const void *)k_cand_sem<TW, TH, K>, (int)kSmemBudget);
+// CTAs per SM of a persistent candidate pass (occupancy of the kernel with
+// its dynamic shared memory), cached per (kernel, shared memory, device).
+static int resident_ctas(const void *func, int threads, size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, func, threads, smem) != cudaSuccess || n < 1) n = 1;
+  return n;
+}
+
+template <int TW, int TH, int K, int B>
+static cudaError_t launch_cand_waves(const CandArgs &a, size_t smem_blend, size_t smem_sem, int waves,
+                                     cudaStream_t s) {
+  const void *fb = (const void *)k_cand_blend<TW, TH, B>;
+  const void *fs = (const void *)k_cand_sem<TW, TH, K, B>;
+  cudaError_t e = ensure_smem_limit(fs, (int)kSmemBudget);
+  if (e != cudaSuccess) return e;
+  const int sms = device_sms();
+  if (sms < 1) return cudaErrorInvalidDevice;
+  const unsigned gb = (unsigned)(sms * resident_ctas(fb, TW * TH, smem_blend));
+  const unsigned gs = (unsigned)(sms * resident_ctas(fs, TW * TH, smem_sem));
+  for (int w = 0; w < waves; ++w) {
+    k_cand_blend<TW, TH, B><<<gb, TW * TH, smem_blend, s>>>(a, w);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_cand_sem<TW, TH, K, B><<<gs, TW * TH, smem_sem, s>>>(a, w);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  k_cand_sem<TW, TH, K><<<grid, TW * TH, smem, s>>>(a);
-  return cudaGetLastError();
+  return cudaSuccess;
+}
+
+template <int TW, int TH, int B>
+static cudaError_t launch_cand_two_pass(const CandArgs &a, size_t smem_blend, size_t smem_sem, int waves,
+                                        cudaStream_t s) {
+  if (a.k == 3) return launch_cand_waves<TW, TH, 3, B>(a, smem_blend, smem_sem, waves, s);
+  if (a.k == 8) return launch_cand_waves<TW, TH, 8, B>(a, smem_blend, smem_sem, waves, s);
+  return launch_cand_waves<TW, TH, 0, B>(a, smem_blend, smem_sem, waves, s);
 }
 
 template <int TW, int TH>
-static cudaError_t launch_cand_two_pass(const CandArgs &a, uint32_t grid, size_t smem_sem, cudaStream_t s) {
-  k_cand_blend<TW, TH><<<grid, TW * TH, batch_smem_bytes(0), s>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  if (a.k == 3) return launch_cand_sem<TW, TH, 3>(a, grid, smem_sem, s);
-  if (a.k == 8) return launch_cand_sem<TW, TH, 8>(a, grid, smem_sem, s);
-  return launch_cand_sem<TW, TH, 0>(a, grid, smem_sem, s);
+static cudaError_t launch_cand_batch(int batch, const CandArgs &a, size_t smem_blend, size_t smem_sem, int waves,
+                                     cudaStream_t s) {
+  if (batch == 32) return launch_cand_two_pass<TW, TH, 32>(a, smem_blend, smem_sem, waves, s);
+  if (batch == 128) return launch_cand_two_pass<TW, TH, 128>(a, smem_blend, smem_sem, waves, s);
+  return launch_cand_two_pass<TW, TH, 64>(a, smem_blend, smem_sem, waves, s);
 }
 
 cudaError_t launch_candidates(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc, double *out,
@@ -428,21 +572,38 @@ cudaError_t launch_candidates(const Layout &L, const WsPtrs &P, int pbuf, const 
   const int threads = L.tile_w * L.tile_h;
   const uint32_t grid = (uint32_t)L.total_tiles;
   if (grid == 0) return cudaSuccess;
-  if (L.mask_units > 0) {
-    // two passes: batch offsets of every tile, blend + bits, classes + entropy
+  if (L.cand_cap_units > 0) {
+    // two passes over the waves: batch offsets of every tile, the wave
+    // plan, then blend + bits, classes + entropy
+    const int B = L.cand_batch;
     a.mask_off = P.mask_off;
     a.masks = P.masks;
-    a.mask_units = (uint32_t)L.mask_units;
+    a.cap_units = (uint32_t)L.cand_cap_units;
     a.clast = P.clast;
-    e = launch_tile_batch_offsets(P.ranges, grid, P.mask_off, P.counters, s);
+    a.plan = cand_plan(L, P);
+    e = launch_tile_batch_offsets(P.ranges, grid, P.mask_off, P.counters, s, B);
     if (e != cudaSuccess) return e;
-    const size_t fixed = 2 * sem_batch_bytes(sc.k), base = batch_smem_bytes(sc.k);
-    chunk_classes(sc.m, threads, sc.k, true, &a.mchunk, &a.mstride, &a.nchunks, fixed > base ? fixed - base : 0);
-    const size_t smem = fixed + (size_t)threads * a.mstride * sizeof(float);
-    if (L.tile_w == 16 && L.tile_h == 16) return launch_cand_two_pass<16, 16>(a, grid, smem, s);
-    if (L.tile_w == 16 && L.tile_h == 8) return launch_cand_two_pass<16, 8>(a, grid, smem, s);
-    if (L.tile_w == 8 && L.tile_h == 8) return launch_cand_two_pass<8, 8>(a, grid, smem, s);
-    if (L.tile_w == 32 && L.tile_h == 8) return launch_cand_two_pass<32, 8>(a, grid, smem, s);
+    k_cand_plan<<<1, kMaxViews, 0, s>>>(P.mask_off, P.tile_off, L.n_views, a.cap_units, a.plan);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t fixed = 2 * cand_sem_batch_bytes(sc.k, B);
+    {
+      // class rows beside the two batch buffers, within the two-CTAs budget
+      const int max_stride = (int)((kSmemBudget - fixed) / ((size_t)threads * sizeof(float)));
+      const int st = (sc.m & 1) ? sc.m : sc.m + 1;
+      if (st <= max_stride) {
+        a.mchunk = sc.m; a.mstride = st; a.nchunks = 1;
+      } else {
+        const int c = ((max_stride - 1) / 32) * 32;
+        a.mchunk = c; a.mstride = c + 1; a.nchunks = (sc.m + c - 1) / c;
+      }
+    }
+    const size_t smem_sem = fixed + (size_t)threads * a.mstride * sizeof(float);
+    const size_t smem_blend = (size_t)B * (16 + 16 + 8) + (size_t)B * (threads / 32) * 4;
+    if (L.tile_w == 16 && L.tile_h == 16) return launch_cand_batch<16, 16>(B, a, smem_blend, smem_sem, L.cand_waves, s);
+    if (L.tile_w == 16 && L.tile_h == 8) return launch_cand_batch<16, 8>(B, a, smem_blend, smem_sem, L.cand_waves, s);
+    if (L.tile_w == 8 && L.tile_h == 8) return launch_cand_batch<8, 8>(B, a, smem_blend, smem_sem, L.cand_waves, s);
+    if (L.tile_w == 32 && L.tile_h == 8) return launch_cand_batch<32, 8>(B, a, smem_blend, smem_sem, L.cand_waves, s);
     return cudaErrorInvalidConfiguration;
   }
   chunk_classes(sc.m, threads, sc.k, true, &a.mchunk, &a.mstride, &a.nchunks);

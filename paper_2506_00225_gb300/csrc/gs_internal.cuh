@@ -19,7 +19,7 @@ constexpr int kProjThreads = 256;
 constexpr int kProjItems = 4;
 constexpr int kProjBlock = kProjThreads * kProjItems;  // Gaussians per projection CTA
 constexpr int kEmitCtasMax = 1024;   // chunks of the pair emission (2 per SM, capped; sizes the chunk totals)
-constexpr int64_t kCandMaskBudget = 48ll << 30;  // contributor-bit bytes the candidate layout may hold
+constexpr int64_t kCandBitsDefault = 4ll << 30;  // contributor-bit bytes of a candidate layout (default)
 constexpr int kEmitThreads = 256;
 
 // Status bits in the workspace counters (1 << gs_status code).
@@ -76,7 +76,11 @@ struct Layout {
   size_t off_semg;                         // mapping view: [n][k] objective gradient of sem_w (unscaled)
   size_t off_mask_off, off_masks;          // contributor bitmasks (mapping view; candidate views when they fit)
   size_t off_clast;                        // candidate views: last contributor per (tile, pixel)
-  int64_t mask_units;                      // capacity in (tile, batch) units
+  int64_t mask_units;                      // capacity in (tile, 64-pair batch) units (mapping view)
+  int cand_batch;                          // Gaussians per batch of the candidate kernels (32, 64, 128)
+  int cand_waves;                          // candidate waves the launch chain provides for
+  int64_t cand_cap_units;                  // bit capacity in (tile, cand_batch) units (0: single pass)
+  size_t off_cand_plan;                    // candidate waves
   size_t total;
 };
 
@@ -115,6 +119,7 @@ struct WsPtrs {
   uint32_t *clast;     // [tiles][tile pixels] last contributor (candidate views)
   double *lpart;   // [tiles of view 0][3] per-tile L1 sums
   float *semg;     // [n][k] d(semantic term)/d(sem_w) of the fused Sec. 3.1 objective, before dL/dloss
+  uint32_t *cand_plan;  // candidate waves: [waves][5] (first tile, end tile, first unit, two tickets)
 };
 
 // Host side (api.cu): device facts, queried per device and cached
@@ -159,7 +164,7 @@ cudaError_t launch_radix_sort_u32(const Layout &L, const WsPtrs &P, int bits, in
 cudaError_t launch_emit_pairs(const Layout &L, const WsPtrs &P, int dbuf, cudaStream_t s);
 // first (tile, batch) unit of every tile: batches per tile, exclusive scan
 cudaError_t launch_tile_batch_offsets(const uint2 *ranges, uint32_t ntiles, uint32_t *mask_off, Counters *counters,
-                                      cudaStream_t s);
+                                      cudaStream_t s, int batch = 64);
 cudaError_t launch_tile_ranges(const Layout &L, const WsPtrs &P, int pbuf, cudaStream_t s);
 cudaError_t launch_render_fwd(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc, float *rgb,
                               float *depth, float *sil, float *sem, cudaStream_t s);

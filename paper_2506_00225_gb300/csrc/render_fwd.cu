@@ -40,10 +40,10 @@ __device__ __forceinline__ void prefetch_l2(const void *base, size_t total, cons
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((uint32_t)(hi - lo)) : "memory");
 }
 
-// Per tile: number of staged batches of its pair range.
-__global__ void k_tile_batches(const uint2 *__restrict__ ranges, uint32_t ntiles, uint32_t *units) {
+// Per tile: number of staged batches (of `batch` pairs) of its pair range.
+__global__ void k_tile_batches(const uint2 *__restrict__ ranges, uint32_t ntiles, uint32_t *units, uint32_t batch) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < ntiles) units[t] = (ranges[t].y - ranges[t].x + kBatch - 1) / kBatch;
+  if (t < ntiles) units[t] = (ranges[t].y - ranges[t].x + batch - 1) / batch;
 }
 
 template <int TW, int TH, bool L1, int PPT>
@@ -558,11 +558,12 @@ FwdArgs fwd_args(const Layout &L, const WsPtrs &P, int pbuf, const gs_scene &sc)
 
 // First (tile, batch) unit of every tile: batches per tile, exclusive scan.
 cudaError_t launch_tile_batch_offsets(const uint2 *ranges, uint32_t ntiles, uint32_t *mask_off, Counters *counters,
-                                      cudaStream_t s) {
-  k_tile_batches<<<(ntiles + 255) / 256, 256, 0, s>>>(ranges, ntiles, mask_off);
+                                      cudaStream_t s, int batch) {
+  k_tile_batches<<<(ntiles + 255) / 256, 256, 0, s>>>(ranges, ntiles, mask_off, (uint32_t)batch);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_scan_single(mask_off, ntiles, nullptr, 0xffffffffu, counters, s);
+  // mask_off[ntiles] receives the total
+  return launch_scan_single(mask_off, ntiles, mask_off + ntiles, 0xffffffffu, counters, s);
 }
 
 static cudaError_t launch_mask_offsets(const Layout &L, const WsPtrs &P, int grid, cudaStream_t s) {

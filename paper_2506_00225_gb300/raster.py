@@ -129,8 +129,11 @@ class Rasterizer:
     """
 
     def __init__(self, tile=(16, 16), sem_detach_geometry=True, record_capacity=0, pair_capacity=0,
-                 device=None, px_per_thread=0, recompute_bwd=False, spin_limit=0):
+                 device=None, px_per_thread=0, recompute_bwd=False, spin_limit=0, cand_batch=0,
+                 cand_bits_bytes=0):
         self.tile = tuple(tile)
+        self.cand_batch = int(cand_batch)            # Gaussians per staged batch of the candidate kernels (0: 64)
+        self.cand_bits_bytes = int(cand_bits_bytes)  # contributor-bit budget of candidate calls (0: 4 GiB)
         self.recompute_bwd = bool(recompute_bwd)
         self.spin_limit = int(spin_limit)  # 0: the library's bound on inter-CTA waits
         self.px_per_thread = int(px_per_thread)
@@ -159,6 +162,8 @@ class Rasterizer:
         c.px_per_thread = self.px_per_thread
         c.recompute_bwd = 1 if self.recompute_bwd else 0
         c.spin_limit = self.spin_limit
+        c.cand_batch = self.cand_batch
+        c.cand_bits_bytes = self.cand_bits_bytes
         # capacities start at a bound that never overflows for small problems
         # and grow on reported overflow (check=True)
         c.record_capacity = self.record_capacity if self.record_capacity > 0 else max(1, min(n_gauss * n_views,
@@ -172,7 +177,7 @@ class Rasterizer:
         need = N.load().gs_workspace_size(ctypes.byref(sc), cams_arr, n_views, ctypes.byref(cfg))
         if need == 0:
             raise ValueError("invalid scene / camera / config for the rasterizer")
-        if self.ws is None or self.ws.numel() < need or (self._shrink_ws and self.ws.numel() > 2 * need):
+        if self.ws is None or self.ws.numel() < need or (self._shrink_ws and self.ws.numel() > need + need // 8):
             self.ws = None
             self.ws = torch.empty(int(need), dtype=torch.uint8, device=self.device)
         self._shrink_ws = False
@@ -406,15 +411,15 @@ class Rasterizer:
         return res
 
     def _fit_capacities(self, cnt, cfg):
-        """After a checked candidate call: capacities far above the counts
-        are cut to 1.25x the counts, and the workspace is re-laid at the
+        """After a checked candidate call: capacities well above the counts
+        are cut to 1.15x the counts, and the workspace is re-laid at the
         next call (the default capacities are sized for the worst case; the
         fitted layout also lets the contributor bits of the two-pass
         candidate kernels fit).  Later calls whose counts exceed the fitted
         capacities report the capacity status and regrow under check=True."""
-        rc = int(cnt.n_records * 1.25) + 4096
-        pc = int(cnt.n_pairs * 1.25) + 65536
-        if cfg.pair_capacity > 2 * pc or cfg.record_capacity > 2 * rc:
+        rc = int(cnt.n_records * 1.15) + 4096
+        pc = int(cnt.n_pairs * 1.15) + 65536
+        if cfg.pair_capacity > pc + pc // 4 or cfg.record_capacity > rc + rc // 4:
             self.record_capacity, self.pair_capacity = rc, pc
             self._shrink_ws = True
 

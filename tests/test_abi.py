@@ -260,3 +260,26 @@ def test_grid_without_a_device_is_zero(lib):
         pytest.skip("a device is present")
     lib.gs_testing_set_sm_query(None)
     assert lib.gs_testing_grid(N.GS_GRID_SORT_RESET) == 0
+
+
+def test_candidate_config_checked_on_host(lib):
+    """Candidate batch sizes other than 32, 64, 128 and a negative bit
+    budget are refused; a budget bounds the workspace of a multi-view
+    layout (the bits of 8 large views would need far more)."""
+    sc, cams, cfg = _structs(n=2_000_000, views=8, w=1200, h=680)
+    for bad in (16, 48, 256, -1):
+        cfg.cand_batch = bad
+        assert lib.gs_workspace_size(ctypes.byref(sc), cams, 8, ctypes.byref(cfg)) == 0
+    cfg.cand_batch = 0
+    cfg.cand_bits_bytes = -5
+    assert lib.gs_workspace_size(ctypes.byref(sc), cams, 8, ctypes.byref(cfg)) == 0
+    cfg.cand_bits_bytes = 0
+    sizes = {}
+    for budget in (1 << 30, 4 << 30):
+        cfg.cand_bits_bytes = budget
+        sizes[budget] = lib.gs_workspace_size(ctypes.byref(sc), cams, 8, ctypes.byref(cfg))
+        assert sizes[budget] > 0
+    assert 2.5 * (1 << 30) < sizes[4 << 30] - sizes[1 << 30] <= 3 * (1 << 30) + (1 << 20)
+    for b in (32, 64, 128):
+        cfg.cand_batch = b
+        assert lib.gs_workspace_size(ctypes.byref(sc), cams, 8, ctypes.byref(cfg)) > 0
