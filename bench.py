@@ -67,6 +67,8 @@ def parse():
                     help="candidate set of the candidates measurement")
     ap.add_argument("--cand-tile", default=None, help="WxH tile of the candidate kernels (default: autotuned)")
     ap.add_argument("--cand-batch", type=int, default=64, help="staged batch of the candidate kernels with --cand-tile")
+    ap.add_argument("--cand-views", type=int, default=0, help="candidate benchmark on the first N views only (profiling)")
+    ap.add_argument("--no-mixed", action="store_true", help="--only large without the mixed stream (profiling)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 2M-Gaussian mapping and mixed-stream runs")
     ap.add_argument("--clocks-dir", default="/tmp",
@@ -851,8 +853,11 @@ def bench_large(args, dev, flush, wl):
         t_rgb, t_depth, _, t_sem = raster.Rasterizer(device=dev).forward(gt, cam, check=True)
         t_rgb, t_depth, t_sem = t_rgb.clone(), t_depth.clone(), t_sem.clone()
     del gt
-    best, _ = autotune.tune_mapping(g, cam, t_rgb, t_depth, t_sem)
-    tile, ppt = best["tile"], best["px_per_thread"]
+    if args.tile:
+        tile, ppt = tuple(int(x) for x in args.tile.lower().split("x")), args.ppt
+    else:
+        best, _ = autotune.tune_mapping(g, cam, t_rgb, t_depth, t_sem)
+        tile, ppt = best["tile"], best["px_per_thread"]
     steps = max(3, min(20, args.steps))
     modes = {}
     rast_keep = None
@@ -897,6 +902,8 @@ def bench_large(args, dev, flush, wl):
                         "contributions": int(cnt.n_contrib)},
              "modes": modes}
 
+    if args.no_mixed:
+        return large, None
     # ---- mixed stream: mapping step + 128 candidates, one graph ----------
     cams = wl["cand_cams"]
     from paper_2506_00225_gb300 import autotune
@@ -958,6 +965,8 @@ def bench_candidates(args, dev, flush):
     from paper_2506_00225_gb300 import raster, scenes
     wl = scenes.workload(args.cand_workload)
     sc, cams = wl["scene"], wl.get("cand_cams", wl["cams"])
+    if args.cand_views > 0:
+        cams = cams[:args.cand_views]
     g = raster.Gaussians.from_scene(sc, dev)
     # launch configuration: the autotuner's (tile x staged batch) on these
     # views, unless fixed on the command line
@@ -1036,7 +1045,7 @@ def bench_candidates(args, dev, flush):
     e.record()
     torch.cuda.synchronize()
     score_us = s.elapsed_time(e) * 10.0
-    return {"metric": "candidate views/s", "value": 1000.0 * len(cams) / ms, "unit": "views/s",
+    return {"metric": "candidate views/s", "value": 1000.0 * len(cams) / ms, "unit": "views/s", "n_views": len(cams),
             "ms_per_batch": ms, "mpix_per_s": npix / (ms * 1e-3) / 1e6,
             "timing": f"one CUDA graph of the batched call, {len(batch_ms)} replays (L2 flushed before each); "
                       "per-view arm: 5 eager repetitions",

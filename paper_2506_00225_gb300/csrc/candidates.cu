@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(TW *TH) k_cand_blend(CandArgs a, int wave) {
   float4 *s_co = smem4;
   float4 *s_cd = smem4 + B;  // uncertainty in .x
   float2 *s_uv = reinterpret_cast<float2 *>(smem4 + 2 * B);
-  uint32_t *lmask = reinterpret_cast<uint32_t *>(s_uv + B);  // per staged Gaussian: its lanes of each warp
+  uint32_t *lmask = reinterpret_cast<uint32_t *>(s_uv + B);  // [warp][staged Gaussian]: its lanes in the warp
   __shared__ uint32_t s_item;
   if (a.counters->status & kStatusTimeout) return;
   const int lx = FP::lx(), ly = FP::ly(0), lp = ly * TW + lx;
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(TW *TH) k_cand_blend(CandArgs a, int wave) {
         float4 cd = __ldg(a.rec.cd + r);
         if (use_unc) cd.x = __ldg(a.rec.unc + r);
         s_cd[t] = cd;
-        lane_masks<TW, TH>(__ldg(a.rec.box + r), ox, oy, lmask + t * WARPS);
+        lane_masks<TW, TH>(__ldg(a.rec.box + r), ox, oy, lmask + t, B);
       }
       __syncthreads();
       uint32_t bits[NW];
@@ -272,12 +272,12 @@ __global__ void __launch_bounds__(TW *TH) k_cand_blend(CandArgs a, int wave) {
 #pragma unroll
         for (int h = 0; h < NW; ++h) {
           const int jj = h * 32 + (int)lane;
-          uint32_t vis = __ballot_sync(0xffffffffu, jj < n && lmask[jj * WARPS + warp] != 0u);
+          uint32_t vis = __ballot_sync(0xffffffffu, jj < n && lmask[warp * B + jj] != 0u);
           while (vis) {
             const int bit = __ffs(vis) - 1;
             vis &= vis - 1;
             const int j = h * 32 + bit;
-            if (done || !((lmask[j * WARPS + warp] >> lane) & 1u)) continue;
+            if (done || !((lmask[warp * B + j] >> lane) & 1u)) continue;
             float alpha, G, araw, dx, dy;
             if (!gauss_alpha(s_uv[j], s_co[j], fpx, fpy, alpha, G, araw, dx, dy)) continue;
             const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));

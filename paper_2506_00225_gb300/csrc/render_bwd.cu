@@ -77,7 +77,7 @@ struct WarpStage {
   float2 *uv;
   short4 *box;       // alpha box (recomputation mode)
   float **dst;       // [slot][3]: 2D gradients of the record, colour and class-weight gradients of the Gaussian
-  int2 *sem;         // [slot][k] (class id, weight bits)
+  int2 *sem;         // [k][slot] (class id, weight bits)
 };
 
 __device__ __forceinline__ WarpStage warp_stage(char *p, int k) {
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
     st.dst[3 * slot + 2] = (has_dsem && a.g_sem_w) ? a.g_sem_w + (size_t)gid * k : nullptr;
     if (has_dsem) {
       const int2 *src = a.rec.sem + (size_t)r * k;
-      for (int l = 0; l < k; ++l) st.sem[slot * k + l] = __ldg(src + l);
+      for (int l = 0; l < k; ++l) st.sem[l * kSlots + slot] = __ldg(src + l);  // lanes: consecutive slots
     }
   };
 
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
 #pragma unroll
           for (int l = 0; l < KMAX; ++l) {
             if (K > 0 || l < k) {
-              const int2 e = st.sem[slot * k + l];
+              const int2 e = st.sem[l * kSlots + slot];
               cvalid[l] = (unsigned)e.x < (unsigned)a.m;
               cid[l] = cvalid[l] ? e.x : 0;
               cwp[l] = mycodes + (cvalid[l] ? (e.x >> 5) : a.nwc) * (PPT * THREADS);
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
               else if (qq == 3) val = -v[qq];
               else if (qq >= 10 && CODES) val = v[qq] * s_sem;
               float *base = st.dst[3 * slot + cls];
-              if (base && val != 0.f) atomicAdd(base + off, val);
+              if (base && val != 0.f) red_add_global(base + off, val);
             }
           }
           continue;
@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
         const float c2 = q < 2 ? -co.y : 0.f;
         const float val = fmaf(c1, tot, c2 * other);
         float *base = st.dst[3 * slot + q_cls];
-        if (issue && base && val != 0.f) atomicAdd(base + q_off, val);
+        if (issue && base && val != 0.f) red_add_global(base + q_off, val);
       }
     }
   }

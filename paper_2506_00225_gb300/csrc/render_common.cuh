@@ -46,6 +46,13 @@ struct Footprint {
   }
 };
 
+// Fire-and-forget float add to global memory through a generic pointer that
+// holds a global address (as staged in shared memory): the reduction the
+// compiler cannot emit for a generic atomicAdd without a returned value.
+__device__ __forceinline__ void red_add_global(float *p, float v) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "f"(v) : "memory");
+}
+
 struct RecPtrs {
   const float2 *uv;
   const float4 *co;    // conic a, b, c, opacity
@@ -117,11 +124,13 @@ __device__ __forceinline__ void stage_record(const RecPtrs &rec, uint32_t r, int
 }
 
 // Lane masks of a staged record for every warp of a tile: bit l of
-// masks[w PPT + i] is set when lane l's i-th pixel of warp w lies in the
-// record's alpha box (image pixels b; tile origin ox, oy).  A warp's lanes
-// hold an 8 x 4 PPT block, lane l at column l % 8 and rows l / 8 + 4 i.
+// masks[(w PPT + i) stride] is set when lane l's i-th pixel of warp w lies in
+// the record's alpha box (image pixels b; tile origin ox, oy).  A warp's lanes
+// hold an 8 x 4 PPT block, lane l at column l % 8 and rows l / 8 + 4 i.  With
+// the staged records consecutive (stride = batch size), the threads staging
+// consecutive records write consecutive words (no bank conflicts).
 template <int TW, int TH, int PPT = 1>
-__device__ __forceinline__ void lane_masks(short4 b, int ox, int oy, uint32_t *masks) {
+__device__ __forceinline__ void lane_masks(short4 b, int ox, int oy, uint32_t *masks, int stride) {
   using FP = Footprint<TW, TH, PPT>;
 #pragma unroll
   for (int w = 0; w < FP::kWarps; ++w) {
@@ -137,7 +146,7 @@ __device__ __forceinline__ void lane_masks(short4 b, int ox, int oy, uint32_t *m
         const uint32_t rows = (0xffffffffu >> (8 * (3 - rh))) & (0xffffffffu << (8 * rl));
         m = (cols * 0x01010101u) & rows;
       }
-      masks[w * PPT + i] = m;
+      masks[(w * PPT + i) * stride] = m;
     }
   }
 }

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_blend(FwdArgs a) {
   extern __shared__ float4 smem4[];
   BatchSmem bs = batch_smem(smem4, 0);
   __shared__ float red[2][WARPS];
-  // per staged Gaussian, warp and pixel row group i: its lanes
+  // per warp and pixel row group i, then staged Gaussian: its lanes
   __shared__ uint32_t lmask[kBatch * WARPS * PPT];
   if (a.counters->status & kStatusTimeout) return;  // the binning is incomplete
 
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_blend(FwdArgs a) {
     for (int t = threadIdx.x; t < n; t += THREADS) {
       const uint32_t r = a.pvals[b + t];
       stage_record<TW, TH, PPT>(a.rec, r, t, 0, ox, oy, bs, false, false);
-      lane_masks<TW, TH, PPT>(__ldg(a.rec.box + r), ox, oy, lmask + t * WARPS * PPT);
+      lane_masks<TW, TH, PPT>(__ldg(a.rec.box + r), ox, oy, lmask + t, kBatch);
     }
     __syncthreads();
     uint32_t bits[PPT][2];
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_blend(FwdArgs a) {
         bool any = false;
         if (jj < n)
 #pragma unroll
-          for (int i = 0; i < PPT; ++i) any = any || lmask[(jj * WARPS + warp) * PPT + i] != 0u;
+          for (int i = 0; i < PPT; ++i) any = any || lmask[(warp * PPT + i) * kBatch + jj] != 0u;
         uint32_t vis = __ballot_sync(0xffffffffu, any);
         while (vis) {
           const int bit = __ffs(vis) - 1;
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_blend(FwdArgs a) {
           const float4 co = bs.co[j];
 #pragma unroll
           for (int i = 0; i < PPT; ++i) {
-            if (done[i] || !((lmask[(j * WARPS + warp) * PPT + i] >> lane) & 1u)) continue;
+            if (done[i] || !((lmask[(warp * PPT + i) * kBatch + j] >> lane) & 1u)) continue;
             float alpha, G, araw, dx, dy;
             if (!gauss_alpha(uv, co, fpx, fpy[i], alpha, G, araw, dx, dy)) continue;
             const float Tn = __fmul_rn(T[i], __fsub_rn(1.f, alpha));
