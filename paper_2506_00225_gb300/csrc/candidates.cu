@@ -217,23 +217,30 @@ __device__ __forceinline__ bool next_tile(const CandPlan &p, int wave, int which
 // Pass 1: U and S of Eq. 1 with the same per-pair rules as the mapping
 // blend (alpha box, 1/255 skip, 1e-4 stop); writes the last contributor and
 // the contributor bits of every staged batch of B pairs (when the tile's
-// bits fit the wave's capacity); adds sum U and N_S per view.
+// bits fit the wave's capacity); adds sum U and N_S per view.  Each warp
+// works through the tile's pairs on its own, 32 at a time: a lane per pair
+// tests the pair's alpha box against the warp's 8 x 4 block, the pairs
+// that reach it are staged (packed) in the warp's shared memory and blended
+// in order.  A warp stops at a batch boundary once all its pixels are done,
+// so every batch a pixel can still read in pass 2 has its bits written.
+__host__ __device__ inline size_t cand_blend_warp_bytes() { return 32 * (16 + 16 + 8 + 4); }
+
 template <int TW, int TH, int B>
 __global__ void __launch_bounds__(TW *TH) k_cand_blend(CandArgs a, int wave) {
   using FP = Footprint<TW, TH>;
   constexpr int THREADS = FP::kThreads;
-  constexpr int WARPS = FP::kWarps;
   constexpr int NPIX = FP::kPix;
   constexpr int NW = B / 32;  // contributor words per pixel and batch
   extern __shared__ float4 smem4[];
-  float4 *s_co = smem4;
-  float4 *s_cd = smem4 + B;  // uncertainty in .x
-  float2 *s_uv = reinterpret_cast<float2 *>(smem4 + 2 * B);
-  uint32_t *lmask = reinterpret_cast<uint32_t *>(s_uv + B);  // [warp][staged Gaussian]: its lanes in the warp
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  char *wb = reinterpret_cast<char *>(smem4) + warp * cand_blend_warp_bytes();
+  float4 *w_co = reinterpret_cast<float4 *>(wb);
+  float4 *w_cd = w_co + 32;  // uncertainty in .x
+  float2 *w_uv = reinterpret_cast<float2 *>(w_co + 64);
+  uint32_t *w_lm = reinterpret_cast<uint32_t *>(w_uv + 32);  // lanes of the warp each staged pair reaches
   __shared__ uint32_t s_item;
   if (a.counters->status & kStatusTimeout) return;
   const int lx = FP::lx(), ly = FP::ly(0), lp = ly * TW + lx;
-  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   const bool use_unc = a.unc != nullptr;
   uint32_t tile, unit_base;
   while (next_tile(a.plan, wave, 0, &s_item, tile, unit_base)) {
@@ -241,6 +248,7 @@ __global__ void __launch_bounds__(TW *TH) k_cand_blend(CandArgs a, int wave) {
     const DevCam &c = a.cams[v];
     const uint32_t local = tile - c.tile_off;
     const int ox = (int)(local % (uint32_t)c.tiles_x) * TW, oy = (int)(local / (uint32_t)c.tiles_x) * TH;
+    const int bx0 = ox + (int)(warp % FP::kWX) * 8, by0 = oy + (int)(warp / FP::kWX) * 4;  // the warp's block
     const uint2 rg = a.ranges[tile];
     const int px = ox + lx, py = oy + ly;
     const bool inside = px < c.width && py < c.height;
@@ -251,53 +259,53 @@ __global__ void __launch_bounds__(TW *TH) k_cand_blend(CandArgs a, int wave) {
     float T = 1.f, U = 0.f;
     uint32_t last = 0;
     bool done = !inside;
-    uint32_t bi = 0;
-    for (uint32_t b = rg.x; b < rg.y; b += B, ++bi) {
-      const int n = (int)min((uint32_t)B, rg.y - b);
-      __syncthreads();
-      for (int t = threadIdx.x; t < n; t += THREADS) {
-        const uint32_t r = a.pvals[b + t];
-        s_co[t] = __ldg(a.rec.co + r);
-        s_uv[t] = __ldg(a.rec.uv + r);
-        float4 cd = __ldg(a.rec.cd + r);
-        if (use_unc) cd.x = __ldg(a.rec.unc + r);
-        s_cd[t] = cd;
-        lane_masks<TW, TH>(__ldg(a.rec.box + r), ox, oy, lmask + t, B);
+    // groups up to the end of the last batch: the empty groups of a partial
+    // batch still write their (zero) bits, which pass 2 reads
+    const uint32_t gend = rg.x + (rg.y - rg.x + B - 1) / B * B;
+    for (uint32_t g0 = rg.x; g0 < gend; g0 += 32) {
+      const uint32_t rel = g0 - rg.x, bi = rel / B, h = (rel % B) / 32;
+      const int n = g0 < rg.y ? (int)min(32u, rg.y - g0) : 0;
+      // the group's pairs that reach the warp's block
+      uint32_t r = 0u, lm = 0u;
+      if ((int)lane < n) {
+        r = a.pvals[g0 + lane];
+        lm = block_lane_mask(__ldg(a.rec.box + r), bx0, by0);
       }
-      __syncthreads();
-      uint32_t bits[NW];
-#pragma unroll
-      for (int h = 0; h < NW; ++h) bits[h] = 0u;
-      if (!__all_sync(0xffffffffu, done)) {
-#pragma unroll
-        for (int h = 0; h < NW; ++h) {
-          const int jj = h * 32 + (int)lane;
-          uint32_t vis = __ballot_sync(0xffffffffu, jj < n && lmask[warp * B + jj] != 0u);
-          while (vis) {
-            const int bit = __ffs(vis) - 1;
-            vis &= vis - 1;
-            const int j = h * 32 + bit;
-            if (done || !((lmask[warp * B + j] >> lane) & 1u)) continue;
-            float alpha, G, araw, dx, dy;
-            if (!gauss_alpha(s_uv[j], s_co[j], fpx, fpy, alpha, G, araw, dx, dy)) continue;
-            const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
-            if (Tn < kTStop) { done = true; continue; }
-            const float w = __fmul_rn(alpha, T);
-            U = fmaf(w, s_cd[j].x, U);
-            T = Tn;
-            bits[h] |= 1u << bit;
-          }
+      const uint32_t vis = __ballot_sync(0xffffffffu, lm != 0u);
+      uint32_t bits = 0u;
+      if (vis && !__all_sync(0xffffffffu, done)) {
+        __syncwarp();  // the previous group's slots are no longer read
+        if (lm) {
+          const int slot = __popc(vis & lanemask_lt());
+          w_co[slot] = __ldg(a.rec.co + r);
+          w_uv[slot] = __ldg(a.rec.uv + r);
+          float4 cd = __ldg(a.rec.cd + r);
+          if (use_unc) cd.x = __ldg(a.rec.unc + r);
+          w_cd[slot] = cd;
+          w_lm[slot] = lm;
+        }
+        __syncwarp();
+        uint32_t rem = vis;
+        int slot = 0;
+        while (rem) {
+          const int bit = __ffs(rem) - 1;
+          rem &= rem - 1;
+          const int sl = slot++;
+          if (done || !((w_lm[sl] >> lane) & 1u)) continue;
+          float alpha, G, araw, dx, dy;
+          if (!gauss_alpha(w_uv[sl], w_co[sl], fpx, fpy, alpha, G, araw, dx, dy)) continue;
+          const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
+          if (Tn < kTStop) { done = true; continue; }
+          const float w = __fmul_rn(alpha, T);
+          U = fmaf(w, w_cd[sl].x, U);
+          T = Tn;
+          bits |= 1u << bit;
         }
       }
-#pragma unroll
-      for (int h = 0; h < NW; ++h)
-        if (bits[h]) last = b - rg.x + 32 * h + (32 - __clz(bits[h]));
-      if (store) {
-        uint32_t *mw = a.masks + (size_t)(unit0 + bi) * NW * NPIX;
-#pragma unroll
-        for (int h = 0; h < NW; ++h) mw[h * NPIX + lp] = bits[h];
-      }
-      if (__syncthreads_count(done) == THREADS) break;
+      if (bits) last = rel + (32 - __clz(bits));
+      if (store) a.masks[((size_t)(unit0 + bi) * NW + h) * NPIX + lp] = bits;
+      // stop at a batch boundary once every pixel of the warp is done
+      if (h == NW - 1 && __all_sync(0xffffffffu, done)) break;
     }
     a.clast[(size_t)tile * NPIX + lp] = last;
     add_view_sum<THREADS>(inside && use_unc ? U : 0.f, a.out + 3 * v);
@@ -599,7 +607,7 @@ cudaError_t launch_candidates(const Layout &L, const WsPtrs &P, int pbuf, const 
       }
     }
     const size_t smem_sem = fixed + (size_t)threads * a.mstride * sizeof(float);
-    const size_t smem_blend = (size_t)B * (16 + 16 + 8) + (size_t)B * (threads / 32) * 4;
+    const size_t smem_blend = (size_t)(threads / 32) * cand_blend_warp_bytes();
     if (L.tile_w == 16 && L.tile_h == 16) return launch_cand_batch<16, 16>(B, a, smem_blend, smem_sem, L.cand_waves, s);
     if (L.tile_w == 16 && L.tile_h == 8) return launch_cand_batch<16, 8>(B, a, smem_blend, smem_sem, L.cand_waves, s);
     if (L.tile_w == 8 && L.tile_h == 8) return launch_cand_batch<8, 8>(B, a, smem_blend, smem_sem, L.cand_waves, s);

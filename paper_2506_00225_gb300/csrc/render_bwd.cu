@@ -225,7 +225,8 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
         const uint32_t *mw = a.masks + (size_t)(unit0 + (uint32_t)bi) * 2 * NPIX + (size_t)h * NPIX;
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
-          mine[i] = ok[i] ? mw[lp[i]] : 0u;
+          // pairs from the pixel's last contributor on are none of its own
+          mine[i] = (ok[i] && hb < nl[i]) ? mw[lp[i]] : 0u;
           any |= mine[i];
         }
       } else {

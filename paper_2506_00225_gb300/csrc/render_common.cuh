@@ -129,25 +129,26 @@ __device__ __forceinline__ void stage_record(const RecPtrs &rec, uint32_t r, int
 // hold an 8 x 4 PPT block, lane l at column l % 8 and rows l / 8 + 4 i.  With
 // the staged records consecutive (stride = batch size), the threads staging
 // consecutive records write consecutive words (no bank conflicts).
+// Lanes of an 8 x 4 pixel block at (x0, y0) (lane l at column l % 8, row
+// l / 8) whose pixel lies in the box b = (x_lo, x_hi, y_lo, y_hi).
+__device__ __forceinline__ uint32_t block_lane_mask(short4 b, int x0, int y0) {
+  const int cl = max((int)b.x - x0, 0), ch = min((int)b.y - x0, 7);
+  const int rl = max((int)b.z - y0, 0), rh = min((int)b.w - y0, 3);
+  if (cl > ch || rl > rh) return 0u;
+  const uint32_t cols = (0xffu >> (7 - ch)) & (0xffu << cl);
+  const uint32_t rows = (0xffffffffu >> (8 * (3 - rh))) & (0xffffffffu << (8 * rl));
+  return (cols * 0x01010101u) & rows;
+}
+
 template <int TW, int TH, int PPT = 1>
 __device__ __forceinline__ void lane_masks(short4 b, int ox, int oy, uint32_t *masks, int stride) {
   using FP = Footprint<TW, TH, PPT>;
 #pragma unroll
   for (int w = 0; w < FP::kWarps; ++w) {
 #pragma unroll
-    for (int i = 0; i < PPT; ++i) {
-      // rows 4 i .. 4 i + 3 of warp w's block
-      const int x0 = ox + (w % FP::kWX) * 8, y0 = oy + (w / FP::kWX) * FP::kBH + 4 * i;
-      const int cl = max((int)b.x - x0, 0), ch = min((int)b.y - x0, 7);
-      const int rl = max((int)b.z - y0, 0), rh = min((int)b.w - y0, 3);
-      uint32_t m = 0u;
-      if (cl <= ch && rl <= rh) {
-        const uint32_t cols = (0xffu >> (7 - ch)) & (0xffu << cl);
-        const uint32_t rows = (0xffffffffu >> (8 * (3 - rh))) & (0xffffffffu << (8 * rl));
-        m = (cols * 0x01010101u) & rows;
-      }
-      masks[(w * PPT + i) * stride] = m;
-    }
+    for (int i = 0; i < PPT; ++i)  // rows 4 i .. 4 i + 3 of warp w's block
+      masks[(w * PPT + i) * stride] =
+          block_lane_mask(b, ox + (w % FP::kWX) * 8, oy + (w / FP::kWX) * FP::kBH + 4 * i);
   }
 }
 

@@ -46,6 +46,11 @@ __global__ void k_tile_batches(const uint2 *__restrict__ ranges, uint32_t ntiles
   if (t < ntiles) units[t] = (ranges[t].y - ranges[t].x + batch - 1) / batch;
 }
 
+// Shared memory of one warp of the blend pass: 32 staging slots (conic +
+// opacity, colour + depth, mean, and per row group the lanes the Gaussian
+// reaches).
+__host__ __device__ inline size_t blend_warp_bytes(int ppt) { return 32 * (16 + 16 + 8 + 4 * (size_t)ppt); }
+
 template <int TW, int TH, bool L1, int PPT>
 __global__ void __launch_bounds__(TW *TH / PPT) k_blend(FwdArgs a) {
   using FP = Footprint<TW, TH, PPT>;
@@ -53,10 +58,13 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_blend(FwdArgs a) {
   constexpr int WARPS = FP::kWarps;
   constexpr int NPIX = FP::kPix;
   extern __shared__ float4 smem4[];
-  BatchSmem bs = batch_smem(smem4, 0);
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
+  char *wb = reinterpret_cast<char *>(smem4) + warp * blend_warp_bytes(PPT);
+  float4 *w_co = reinterpret_cast<float4 *>(wb);
+  float4 *w_cd = w_co + 32;
+  float2 *w_uv = reinterpret_cast<float2 *>(w_co + 64);
+  uint32_t *w_lm = reinterpret_cast<uint32_t *>(w_uv + 32);  // [row group][slot]
   __shared__ float red[2][WARPS];
-  // per warp and pixel row group i, then staged Gaussian: its lanes
-  __shared__ uint32_t lmask[kBatch * WARPS * PPT];
   if (a.counters->status & kStatusTimeout) return;  // the binning is incomplete
 
   const int tile = blockIdx.x;
@@ -66,8 +74,8 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_blend(FwdArgs a) {
   const int lx = FP::lx();
   const int px = ox + lx;
   const float fpx = (float)px + 0.5f;
-  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t unit0 = a.masks ? a.mask_off[tile] : 0u;
+  const int bx0 = ox + (int)(warp % FP::kWX) * 8, by0 = oy + (int)(warp / FP::kWX) * FP::kBH;  // the warp's block
 
   // PPT pixels per thread, one column, rows 4 apart: they share every
   // staged load and the x offset of every Gaussian
@@ -93,63 +101,77 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_blend(FwdArgs a) {
     for (int i = 0; i < PPT; ++i) d = d && done[i];
     return d;
   };
-  uint32_t bi = 0;
-  for (uint32_t b = rg.x; b < rg.y; b += kBatch, ++bi) {
-    const int n = (int)min((uint32_t)kBatch, rg.y - b);
-    __syncthreads();
-    for (int t = threadIdx.x; t < n; t += THREADS) {
-      const uint32_t r = a.pvals[b + t];
-      stage_record<TW, TH, PPT>(a.rec, r, t, 0, ox, oy, bs, false, false);
-      lane_masks<TW, TH, PPT>(__ldg(a.rec.box + r), ox, oy, lmask + t, kBatch);
+  // Every warp works through the tile's pairs on its own, 32 at a time: a
+  // lane per pair tests the pair's alpha box against the warp's block (per
+  // row group), the pairs that reach it are staged (packed) and composited in
+  // order.  The warp stops at a batch boundary once all its pixels are done;
+  // the groups up to the end of the last batch write their bits (zero when
+  // empty), so every batch a pixel can still read has its bits.
+  const uint32_t gend = rg.x + (rg.y - rg.x + kBatch - 1) / kBatch * kBatch;
+  for (uint32_t g0 = rg.x; g0 < gend; g0 += 32) {
+    const uint32_t rel = g0 - rg.x, bi = rel / kBatch, h = (rel % kBatch) / 32;
+    const int n = g0 < rg.y ? (int)min(32u, rg.y - g0) : 0;
+    uint32_t r = 0u, lm[PPT];
+    bool reach = false;
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) lm[i] = 0u;
+    if ((int)lane < n) {
+      r = a.pvals[g0 + lane];
+      const short4 bx = __ldg(a.rec.box + r);
+#pragma unroll
+      for (int i = 0; i < PPT; ++i) {
+        lm[i] = block_lane_mask(bx, bx0, by0 + 4 * i);
+        reach = reach || lm[i] != 0u;
+      }
     }
-    __syncthreads();
-    uint32_t bits[PPT][2];
+    const uint32_t vis = __ballot_sync(0xffffffffu, reach);
+    uint32_t bits[PPT];
 #pragma unroll
-    for (int i = 0; i < PPT; ++i) bits[i][0] = bits[i][1] = 0u;
-    if (!__all_sync(0xffffffffu, all_done())) {
-      for (int base = 0; base < n; base += 32) {
-        const int jj = base + (int)lane;
-        bool any = false;
-        if (jj < n)
+    for (int i = 0; i < PPT; ++i) bits[i] = 0u;
+    if (vis && !__all_sync(0xffffffffu, all_done())) {
+      __syncwarp();  // the previous group's slots are no longer read
+      if (reach) {
+        const int slot = __popc(vis & lanemask_lt());
+        w_co[slot] = __ldg(a.rec.co + r);
+        w_uv[slot] = __ldg(a.rec.uv + r);
+        w_cd[slot] = __ldg(a.rec.cd + r);
 #pragma unroll
-          for (int i = 0; i < PPT; ++i) any = any || lmask[(warp * PPT + i) * kBatch + jj] != 0u;
-        uint32_t vis = __ballot_sync(0xffffffffu, any);
-        while (vis) {
-          const int bit = __ffs(vis) - 1;
-          vis &= vis - 1;
-          const int j = base + bit;
-          const float2 uv = bs.uv[j];
-          const float4 co = bs.co[j];
+        for (int i = 0; i < PPT; ++i) w_lm[i * 32 + slot] = lm[i];
+      }
+      __syncwarp();
+      uint32_t rem = vis;
+      int slot = 0;
+      while (rem) {
+        const int bit = __ffs(rem) - 1;
+        rem &= rem - 1;
+        const int sl = slot++;
+        const float2 uv = w_uv[sl];
+        const float4 co = w_co[sl];
 #pragma unroll
-          for (int i = 0; i < PPT; ++i) {
-            if (done[i] || !((lmask[(warp * PPT + i) * kBatch + j] >> lane) & 1u)) continue;
-            float alpha, G, araw, dx, dy;
-            if (!gauss_alpha(uv, co, fpx, fpy[i], alpha, G, araw, dx, dy)) continue;
-            const float Tn = __fmul_rn(T[i], __fsub_rn(1.f, alpha));
-            if (Tn < kTStop) { done[i] = true; continue; }
-            const float w = __fmul_rn(alpha, T[i]);
-            const float4 cdp = bs.cd[j];
-            cr[i] = fmaf(w, cdp.x, cr[i]); cg[i] = fmaf(w, cdp.y, cg[i]); cb[i] = fmaf(w, cdp.z, cb[i]);
-            cd[i] = fmaf(w, cdp.w, cd[i]);
-            T[i] = Tn;
-            bits[i][base >> 5] |= 1u << bit;
-          }
+        for (int i = 0; i < PPT; ++i) {
+          if (done[i] || !((w_lm[i * 32 + sl] >> lane) & 1u)) continue;
+          float alpha, G, araw, dx, dy;
+          if (!gauss_alpha(uv, co, fpx, fpy[i], alpha, G, araw, dx, dy)) continue;
+          const float Tn = __fmul_rn(T[i], __fsub_rn(1.f, alpha));
+          if (Tn < kTStop) { done[i] = true; continue; }
+          const float w = __fmul_rn(alpha, T[i]);
+          const float4 cdp = w_cd[sl];
+          cr[i] = fmaf(w, cdp.x, cr[i]); cg[i] = fmaf(w, cdp.y, cg[i]); cb[i] = fmaf(w, cdp.z, cb[i]);
+          cd[i] = fmaf(w, cdp.w, cd[i]);
+          T[i] = Tn;
+          bits[i] |= 1u << bit;
         }
       }
     }
-    // last contributor and contribution count from the batch's bits
+    // last contributor, contribution count and this group's bits
 #pragma unroll
     for (int i = 0; i < PPT; ++i) {
-      if (bits[i][1]) last[i] = b - rg.x + 32 + (32 - __clz(bits[i][1]));
-      else if (bits[i][0]) last[i] = b - rg.x + (32 - __clz(bits[i][0]));
-      ncontrib += __popc(bits[i][0]) + __popc(bits[i][1]);
-      if (a.masks && unit0 + bi < a.mask_units) {
-        uint32_t *mw = a.masks + (size_t)(unit0 + bi) * 2 * NPIX;
-        mw[lp[i]] = bits[i][0];
-        mw[NPIX + lp[i]] = bits[i][1];
-      }
+      if (bits[i]) last[i] = rel + (32 - __clz(bits[i]));
+      ncontrib += __popc(bits[i]);
+      if (a.masks && unit0 + bi < a.mask_units)
+        a.masks[((size_t)(unit0 + bi) * 2 + h) * NPIX + lp[i]] = bits[i];
     }
-    if (__syncthreads_count(all_done()) == THREADS) break;
+    if (h == 1 && __all_sync(0xffffffffu, all_done())) break;
   }
   {
     uint32_t nc = ncontrib;
@@ -516,8 +538,8 @@ static cudaError_t launch_semantic(const FwdArgs &a, int grid, size_t smem, cuda
 
 template <int TW, int TH, bool L1>
 static cudaError_t launch_shape(const FwdArgs &a, int grid, size_t smem_sem, bool run_sem, cudaStream_t s) {
-  if (a.blend_ppt == 2) k_blend<TW, TH, L1, 2><<<grid, TW * TH / 2, batch_smem_bytes(0), s>>>(a);
-  else k_blend<TW, TH, L1, 1><<<grid, TW * TH, batch_smem_bytes(0), s>>>(a);
+  if (a.blend_ppt == 2) k_blend<TW, TH, L1, 2><<<grid, TW * TH / 2, (TW * TH / 64) * blend_warp_bytes(2), s>>>(a);
+  else k_blend<TW, TH, L1, 1><<<grid, TW * TH, (TW * TH / 32) * blend_warp_bytes(1), s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !run_sem) return e;
   // the common top-k sizes get an unrolled scatter
