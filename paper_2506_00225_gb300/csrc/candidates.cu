@@ -397,6 +397,18 @@ __global__ void __launch_bounds__(TW *TH, 2) k_cand_sem(CandArgs a, int wave) {
       if (nbatch > 0) issue(0, pv);
       cp_async_commit();
       fetch(1, pv);
+      // contributor words of the next batch, loaded one batch ahead
+      uint32_t mnext[NW];
+      auto load_bits = [&](int bi, uint32_t (&m)[NW]) {
+#pragma unroll
+        for (int h = 0; h < NW; ++h) m[h] = 0u;
+        if (stored && bi < nbatch && (uint32_t)bi * B < last) {
+          const uint32_t *mw = a.masks + (size_t)(unit0 + bi) * NW * NPIX;
+#pragma unroll
+          for (int h = 0; h < NW; ++h) m[h] = mw[h * NPIX + lp];
+        }
+      };
+      load_bits(0, mnext);
       cp_async_wait_all();
       __syncthreads();
       for (int bi = 0; bi < nbatch; ++bi) {
@@ -406,24 +418,20 @@ __global__ void __launch_bounds__(TW *TH, 2) k_cand_sem(CandArgs a, int wave) {
         const uint32_t b0 = (uint32_t)bi * B;
         uint32_t mine[NW];
 #pragma unroll
-        for (int h = 0; h < NW; ++h) mine[h] = 0u;
+        for (int h = 0; h < NW; ++h) mine[h] = mnext[h];
+        load_bits(bi + 1, mnext);
         const float2 *suv = buf_uv(bi & 1);
         const float4 *sco = buf_co(bi & 1);
         const int2 *ssem = buf_sem(bi & 1);
-        if (b0 < last) {
-          if (stored) {
-            const uint32_t *mw = a.masks + (size_t)(unit0 + bi) * NW * NPIX;
-#pragma unroll
-            for (int h = 0; h < NW; ++h) mine[h] = mw[h * NPIX + lp];
-          } else {
-            const short4 *sbox = buf_box(bi & 1);
-            const int n = min(batch_n(bi), (int)(last - b0));
-            for (int j = 0; j < n; ++j) {
-              const short4 bx = sbox[j];
-              if (px < bx.x || px > bx.y || py < bx.z || py > bx.w) continue;
-              float alpha, G, araw, dx, dy;
-              if (gauss_alpha(suv[j], sco[j], fpx, fpy, alpha, G, araw, dx, dy)) mine[j >> 5] |= 1u << (j & 31);
-            }
+        if (b0 < last && !stored) {
+          // no stored bits: re-test the pairs before the last contributor
+          const short4 *sbox = buf_box(bi & 1);
+          const int n = min(batch_n(bi), (int)(last - b0));
+          for (int j = 0; j < n; ++j) {
+            const short4 bx = sbox[j];
+            if (px < bx.x || px > bx.y || py < bx.z || py > bx.w) continue;
+            float alpha, G, araw, dx, dy;
+            if (gauss_alpha(suv[j], sco[j], fpx, fpy, alpha, G, araw, dx, dy)) mine[j >> 5] |= 1u << (j & 31);
           }
         }
 #pragma unroll
@@ -433,8 +441,14 @@ __global__ void __launch_bounds__(TW *TH, 2) k_cand_sem(CandArgs a, int wave) {
             const int jb = __ffs(un) - 1;
             un &= un - 1;
             const int j = h * 32 + jb;
-            float alpha = 0.f, G, araw, dx, dy;
-            gauss_alpha(suv[j], sco[j], fpx, fpy, alpha, G, araw, dx, dy);
+            // branch-free alpha (a contributor has power <= 0; other lanes get w = 0)
+            const float2 uv_ = suv[j];
+            const float4 co_ = sco[j];
+            const float dx = __fsub_rn(uv_.x, fpx), dy = __fsub_rn(uv_.y, fpy);
+            const float q_ = __fmaf_rn(co_.x, __fmul_rn(dx, dx), __fmul_rn(co_.z, __fmul_rn(dy, dy)));
+            const float power = __fmaf_rn(-0.5f, q_, -__fmul_rn(co_.y, __fmul_rn(dx, dy)));
+            const float araw = __fmul_rn(co_.w, __expf(power));
+            const float alpha = araw < kAlphaMax ? araw : kAlphaMax;
             const bool on = (mine[h] >> jb) & 1u;
             const float w = on ? __fmul_rn(alpha, T) : 0.f;
             if (on) T = __fmul_rn(T, __fsub_rn(1.f, alpha));
