@@ -484,8 +484,8 @@ def main():
     bytes_front = (sc.n * 44 + n_records * (112 + 8 * k) + n_records * 32 * dpass + n_pairs * 12
                    + n_pairs * 20 * tpass + n_pairs * 8)
     alu = flops_bwd / t_bwd / 1e12
-    bwd_kernel = "k_render_bwd<%d, %d, 1, %d, %d>" % (best["tile"][0], best["tile"][1], k if k in (3, 8) else 0,
-                                                      best["px_per_thread"])
+    bwd_kernel = "k_render_bwd<%d, %d, 1, %d, %d, 0>" % (best["tile"][0], best["tile"][1], k if k in (3, 8) else 0,
+                                                         best["px_per_thread"])
     roofline = {"bound": "alu", "kernel": bwd_kernel, "achieved": alu, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": alu / fp32_peak,
                 "peak_source": f"FP32 pipe: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 flop x {clock_ghz:.3f} GHz "
