@@ -118,7 +118,20 @@ typedef struct gs_camera {
  *                        still do not fit re-tests its pairs.  Results do not
  *                        depend on it.
  *   cand_batch           Gaussians staged per batch in the candidate kernels:
- *                        32, 64 or 128 (0 = 64); results do not depend on it */
+ *                        32, 64 or 128 (0 = 64); results do not depend on it
+ *   cand_group_pixels    0 (default): gs_render_candidates projects, bins
+ *                        and renders all its views at once.  P > 0: it does
+ *                        so for consecutive groups of views in turn, each
+ *                        group as many views as fit in P pixels (at least
+ *                        one), reusing one workspace, so records, pairs and
+ *                        contributor bits are sized for one group
+ *                        (record_capacity and pair_capacity then count per
+ *                        group; the default record capacity is n times the
+ *                        group's views).  Results do not depend on it.  When
+ *                        the views need more than one group only
+ *                        gs_render_candidates and gs_workspace_size (the
+ *                        largest group's bytes) accept the view list; the
+ *                        other entry points return GS_ERR_ARG. */
 typedef struct gs_config {
   int32_t tile_w, tile_h;
   int32_t sem_detach_geometry;
@@ -129,13 +142,15 @@ typedef struct gs_config {
   int32_t spin_limit;
   int64_t cand_bits_bytes;
   int32_t cand_batch;
+  int64_t cand_group_pixels;
 } gs_config;
 
 /* Counters read back by gs_read_counters. */
 typedef struct gs_counters {
   uint32_t status;      /* bit set of gs_status codes raised on the device (1 << code) */
-  uint32_t n_records;   /* visible (view, Gaussian) records (may exceed capacity) */
-  uint32_t n_pairs;     /* (tile, Gaussian) pairs (may exceed capacity) */
+  uint32_t n_records;   /* visible (view, Gaussian) records (may exceed capacity;
+                           the largest group's of a grouped candidate call) */
+  uint32_t n_pairs;     /* (tile, Gaussian) pairs (may exceed capacity; idem) */
   uint32_t n_contrib;   /* (pixel, Gaussian) contributions blended by the last forward render */
 } gs_counters;
 

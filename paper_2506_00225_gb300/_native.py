@@ -38,7 +38,8 @@ class GsCamera(ctypes.Structure):
 class GsConfig(ctypes.Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("sem_detach_geometry", c_int32), ("px_per_thread", c_int32),
                 ("record_capacity", c_int64), ("pair_capacity", c_int64), ("recompute_bwd", c_int32),
-                ("spin_limit", c_int32), ("cand_bits_bytes", c_int64), ("cand_batch", c_int32)]
+                ("spin_limit", c_int32), ("cand_bits_bytes", c_int64), ("cand_batch", c_int32),
+                ("cand_group_pixels", c_int64)]
 
 
 class GsVoxelGrid(ctypes.Structure):

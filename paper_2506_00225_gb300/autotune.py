@@ -105,3 +105,28 @@ def tune_candidates(g: raster.Gaussians, cams, reps: int = 5, device=None):
     res = ({"tile": (w, h), "cand_batch": best["cand_batch"], "ms": best["ms"]}, table)
     _CAND_CACHE[key] = res
     return res
+
+
+def fit_candidate_budget(g: raster.Gaussians, cams, ws_bytes: int, tile=(16, 16), cand_batch: int = 0,
+                         device=None):
+    """Largest pixel budget of the candidate view groups
+    (gs_config.cand_group_pixels) whose workspace stays within `ws_bytes`:
+    starts with all views in one group and halves the budget until the
+    workspace, laid out at the capacities fitted to a checked call's counts,
+    fits, or the budget reaches the largest view.  Returns (a Rasterizer
+    fitted to the views, the budget (0: one group), its workspace bytes).
+    The per-view sums do not depend on the budget."""
+    device = device or g.means.device
+    total = sum(c.width * c.height for c in cams)
+    floor = max(c.width * c.height for c in cams)
+    budget = total
+    while True:
+        gp = 0 if budget >= total else budget
+        rast = raster.Rasterizer(tile=tile, cand_batch=cand_batch, cand_group_pixels=gp, device=device)
+        out = rast.candidates(g, cams, check=True)  # counts -> fitted capacities
+        rast.candidates(g, cams, check=True, out=out)  # workspace re-laid at them
+        ws = int(rast.ws.numel())
+        if ws <= ws_bytes or budget <= floor:
+            return rast, gp, ws
+        del rast, out
+        budget = max(floor, budget // 2)

@@ -3,6 +3,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <set>
@@ -83,7 +84,9 @@ static gs_config default_config() {
   return c;
 }
 
-bool make_layout(const gs_scene *scene, const gs_camera *cams, int n_views, const gs_config *cfg_in, Layout *L) {
+// Layout of one call over all `n_views` views at once.
+static bool layout_views(const gs_scene *scene, const gs_camera *cams, int n_views, const gs_config *cfg_in,
+                         Layout *L) {
   if (!scene || !cams || n_views < 1 || n_views > kMaxViews) return false;
   const gs_config cfg = cfg_in ? *cfg_in : default_config();
   if (scene->n < 0 || scene->n >= (1 << 28) || scene->k < 1 || scene->k > kMaxK || scene->m < 1 ||
@@ -279,18 +282,18 @@ static bool shape_compiled(int tw, int th) {
   } while (0)
 
 gs_status run_project_with(const Layout &L, const WsPtrs &P, const gs_scene &sc, const gs_camera *cams,
-                           CamTable *tab, cudaStream_t s) {
+                           CamTable *tab, cudaStream_t s, bool first) {
   memset(tab, 0, sizeof(CamTable));
   fill_cam_table(cams, L.n_views, L.tile_w, L.tile_h, tab);
-  GS_CHECK_CUDA(launch_setup_views(*tab, L.n_views, P, (uint32_t)L.total_tiles, true, s));
+  GS_CHECK_CUDA(launch_setup_views(*tab, L.n_views, P, (uint32_t)L.total_tiles, first, s));
   GS_CHECK_CUDA(launch_project(L, P, sc, s));
   return GS_OK;
 }
 
 static gs_status run_project(const Layout &L, const WsPtrs &P, const gs_scene &sc, const gs_camera *cams,
-                             cudaStream_t s) {
+                             cudaStream_t s, bool first = true) {
   std::vector<unsigned char> buf(sizeof(CamTable));
-  return run_project_with(L, P, sc, cams, reinterpret_cast<CamTable *>(buf.data()), s);
+  return run_project_with(L, P, sc, cams, reinterpret_cast<CamTable *>(buf.data()), s, first);
 }
 
 gs_status run_bin_sort(const Layout &L, const WsPtrs &P, cudaStream_t s) {
@@ -302,6 +305,49 @@ gs_status run_bin_sort(const Layout &L, const WsPtrs &P, cudaStream_t s) {
   return GS_OK;
 }
 
+// End (exclusive) of the view group that starts at view v0: views are
+// added while the group's pixels stay within `budget` (at least one view);
+// budget <= 0 puts every view in one group.
+static int group_end(const gs_camera *views, int n_views, int v0, int64_t budget) {
+  if (budget <= 0) return n_views;
+  int v1 = v0;
+  int64_t px = 0;
+  while (v1 < n_views) {
+    const int64_t p = (int64_t)views[v1].width * views[v1].height;
+    if (v1 > v0 && px + p > budget) break;
+    px += p;
+    ++v1;
+  }
+  return v1;
+}
+
+static int64_t group_pixels(const gs_config *cfg) { return cfg ? cfg->cand_group_pixels : 0; }
+
+// A view list that needs more than one group (only gs_render_candidates runs
+// those).
+static bool grouped(const gs_camera *views, int n_views, const gs_config *cfg) {
+  return views && n_views > 0 && n_views <= kMaxViews && group_end(views, n_views, 0, group_pixels(cfg)) < n_views;
+}
+
+bool make_layout(const gs_scene *scene, const gs_camera *cams, int n_views, const gs_config *cfg, Layout *L) {
+  if (group_pixels(cfg) < 0 || grouped(cams, n_views, cfg)) return false;
+  return layout_views(scene, cams, n_views, cfg, L);
+}
+
+// Grouped candidate call: checks every group of views and returns the
+// largest group's workspace bytes (0 if a group is invalid).
+static size_t grouped_total(const gs_scene *scene, const gs_camera *cams, int n_views, const gs_config *cfg) {
+  if (!cams || n_views < 1 || n_views > kMaxViews || group_pixels(cfg) < 0) return 0;
+  size_t total = 0;
+  for (int v0 = 0, v1; v0 < n_views; v0 = v1) {
+    v1 = group_end(cams, n_views, v0, group_pixels(cfg));
+    Layout L;
+    if (!layout_views(scene, cams + v0, v1 - v0, cfg, &L)) return 0;
+    total = std::max(total, L.total);
+  }
+  return total;
+}
+
 }  // namespace gs
 
 using namespace gs;
@@ -309,6 +355,7 @@ using namespace gs;
 extern "C" {
 
 size_t gs_workspace_size(const gs_scene *scene, const gs_camera *cams, int n_views, const gs_config *cfg) {
+  if (grouped(cams, n_views, cfg)) return grouped_total(scene, cams, n_views, cfg);
   Layout L;
   if (!make_layout(scene, cams, n_views, cfg, &L)) return 0;
   return L.total;
@@ -470,17 +517,24 @@ gs_status gs_render_bwd_objective(const gs_scene *scene, const gs_camera *cam, c
 
 gs_status gs_render_candidates(const gs_scene *scene, const gs_camera *views, int n_views, const gs_config *cfg,
                                void *ws, double *out, gs_stream_t stream) {
-  Layout L;
-  if (!ws || !aligned(ws, 256) || !out || !make_layout(scene, views, n_views, cfg, &L)) return GS_ERR_ARG;
+  if (!ws || !aligned(ws, 256) || !out || grouped_total(scene, views, n_views, cfg) == 0) return GS_ERR_ARG;
   if (!scene_ptrs_ok(scene, true)) return GS_ERR_ARG;
-  if (!shape_compiled(L.tile_w, L.tile_h)) return GS_ERR_UNSUPPORTED;
-  WsPtrs P = ws_ptrs(L, ws);
   cudaStream_t s = (cudaStream_t)stream;
-  gs_status st = run_project(L, P, *scene, views, s);
-  if (st != GS_OK) return st;
-  st = run_bin_sort(L, P, s);
-  if (st != GS_OK) return st;
-  GS_CHECK_CUDA(launch_candidates(L, P, pair_sort_buffer(L), *scene, out, s));
+  // one projection, binning and candidate chain per group of views, each in
+  // its own layout of the same workspace; the device status and the largest
+  // counts carry over from group to group
+  for (int v0 = 0, v1; v0 < n_views; v0 = v1) {
+    v1 = group_end(views, n_views, v0, group_pixels(cfg));
+    Layout L;
+    if (!layout_views(scene, views + v0, v1 - v0, cfg, &L)) return GS_ERR_ARG;
+    if (!shape_compiled(L.tile_w, L.tile_h)) return GS_ERR_UNSUPPORTED;
+    WsPtrs P = ws_ptrs(L, ws);
+    gs_status st = run_project(L, P, *scene, views + v0, s, v0 == 0);
+    if (st != GS_OK) return st;
+    st = run_bin_sort(L, P, s);
+    if (st != GS_OK) return st;
+    GS_CHECK_CUDA(launch_candidates(L, P, pair_sort_buffer(L), *scene, out + 3 * (size_t)v0, s));
+  }
   return GS_OK;
 }
 
@@ -524,8 +578,8 @@ gs_status gs_read_counters(void *ws, gs_counters *out, gs_stream_t stream) {
   Counters c;
   if (cudaMemcpy(&c, ws, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return GS_ERR_CUDA;
   out->status = c.status;
-  out->n_records = c.n_records;
-  out->n_pairs = c.n_pairs;
+  out->n_records = std::max(c.n_records, c.grp_records);
+  out->n_pairs = std::max(c.n_pairs, c.grp_pairs);
   out->n_contrib = c.n_contrib;
   if (c.status & kStatusTimeout) return GS_ERR_TIMEOUT;  // first: later counts may be meaningless
   if (c.status & kStatusCapacity) return GS_ERR_CAPACITY;

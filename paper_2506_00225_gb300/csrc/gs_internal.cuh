@@ -49,6 +49,7 @@ struct Counters {
   uint32_t n_pairs;
   uint32_t n_contrib;  // (pixel, Gaussian) contributions of the last forward render
   uint32_t tiles_done; // tickets of the tile pass that finishes the loss (0 between launches)
+  uint32_t grp_records, grp_pairs;  // largest counts of the earlier view groups of a grouped call
 };
 
 // Host-computed workspace layout (offsets in bytes from the base pointer).
@@ -138,8 +139,10 @@ cudaError_t ensure_smem_limit(const void *func, int bytes);
 // view setup), and the launch chains of gs_project and gs_bin_sort; `tab` is
 // the caller's storage for the table (no heap use inside).
 void fill_cam_table(const gs_camera *cams, int n_views, int tw, int th, CamTable *tab);
+// `first` = false continues a grouped call: the device status is kept and
+// the previous group's counts are folded into the group maxima.
 gs_status run_project_with(const Layout &L, const WsPtrs &P, const gs_scene &sc, const gs_camera *cams,
-                           CamTable *tab, cudaStream_t s);
+                           CamTable *tab, cudaStream_t s, bool first = true);
 gs_status run_bin_sort(const Layout &L, const WsPtrs &P, cudaStream_t s);
 
 // Host side (api.cu).

@@ -133,7 +133,14 @@ __global__ void k_setup_views(CamTable tab, int n_views, DevCam *cams, uint32_t 
   }
   if (i == 0) {
     tile_off[n_views] = total_tiles;
-    if (reset_status) counters->status = 0u;
+    if (reset_status) {
+      counters->status = 0u;
+      counters->grp_records = 0u;
+      counters->grp_pairs = 0u;
+    } else {
+      counters->grp_records = max(counters->grp_records, counters->n_records);
+      counters->grp_pairs = max(counters->grp_pairs, counters->n_pairs);
+    }
     counters->n_records = 0u;
     counters->n_pairs = 0u;
     counters->n_contrib = 0u;

@@ -115,6 +115,22 @@ def _stream():
 # rasterizer: owns a workspace
 # ---------------------------------------------------------------------------
 
+def largest_group(cams, budget: int) -> int:
+    """Views in the largest group of a candidate call whose views are
+    grouped by `budget` pixels (gs_config.cand_group_pixels: consecutive
+    views while their pixels fit, at least one; budget <= 0: one group)."""
+    if budget <= 0:
+        return len(cams)
+    best = n = px = 0
+    for c in cams:
+        p = c.width * c.height
+        if n and px + p > budget:
+            n = px = 0
+        n, px = n + 1, px + p
+        best = max(best, n)
+    return best
+
+
 class Rasterizer:
     """Owns one device workspace and a launch configuration.
 
@@ -130,10 +146,11 @@ class Rasterizer:
 
     def __init__(self, tile=(16, 16), sem_detach_geometry=True, record_capacity=0, pair_capacity=0,
                  device=None, px_per_thread=0, recompute_bwd=False, spin_limit=0, cand_batch=0,
-                 cand_bits_bytes=0):
+                 cand_bits_bytes=0, cand_group_pixels=0):
         self.tile = tuple(tile)
         self.cand_batch = int(cand_batch)            # Gaussians per staged batch of the candidate kernels (0: 64)
         self.cand_bits_bytes = int(cand_bits_bytes)  # contributor-bit budget of candidate calls (0: 4 GiB)
+        self.cand_group_pixels = int(cand_group_pixels)  # pixels of a candidate view group (0: all views at once)
         self.recompute_bwd = bool(recompute_bwd)
         self.spin_limit = int(spin_limit)  # 0: the library's bound on inter-CTA waits
         self.px_per_thread = int(px_per_thread)
@@ -164,6 +181,7 @@ class Rasterizer:
         c.spin_limit = self.spin_limit
         c.cand_batch = self.cand_batch
         c.cand_bits_bytes = self.cand_bits_bytes
+        c.cand_group_pixels = self.cand_group_pixels
         # capacities start at a bound that never overflows for small problems
         # and grow on reported overflow (check=True)
         c.record_capacity = self.record_capacity if self.record_capacity > 0 else max(1, min(n_gauss * n_views,
@@ -370,7 +388,7 @@ class Rasterizer:
         if out is None:
             out = torch.empty((V, 3), dtype=torch.float64, device=self.device)
         for _ in range(8):
-            cfg = self.config(g.n, V)
+            cfg = self.config(g.n, largest_group(cams, self.cand_group_pixels))
             ws = self._ensure_ws(sc, cams_arr, V, cfg)
             N.check(lib.gs_render_candidates(ctypes.byref(sc), cams_arr, V, ctypes.byref(cfg), ws, _ptr(out),
                                              _stream()), "gs_render_candidates")

@@ -283,3 +283,43 @@ def test_candidate_config_checked_on_host(lib):
     for b in (32, 64, 128):
         cfg.cand_batch = b
         assert lib.gs_workspace_size(ctypes.byref(sc), cams, 8, ctypes.byref(cfg)) > 0
+
+
+def test_grouped_candidate_workspace(lib):
+    """cand_group_pixels: a grouped candidate call is laid out one group of
+    consecutive views at a time (views added while their pixels fit the
+    budget, at least one), so its workspace is the largest group's
+    (computed here group by group), well below the whole list's; a negative
+    budget is refused, a budget covering every view changes nothing, and
+    the entry points that run all views at once refuse a list that needs
+    several groups."""
+    sc = N.GsScene()
+    sc.n, sc.k, sc.m = 500_000, 3, 16
+    sizes = [(300, 170, 150.0), (600, 340, 300.0), (1200, 680, 600.0)] * 3
+    cams = raster.cameras_array([scenes.look_camera((0, 0, 1.5), 40.0 * i, w, h, f)
+                                 for i, (w, h, f) in enumerate(sizes)])
+    cfg = N.GsConfig()
+    cfg.tile_w, cfg.tile_h = 16, 16
+    nv, budget = len(sizes), 900_000
+    # 51k, 204k, 816k pixels: groups [0, 1], [2, 3], [4], [5, 6], [7], [8]
+    groups = [(0, 2), (2, 4), (4, 5), (5, 7), (7, 8), (8, 9)]
+    whole = lib.gs_workspace_size(ctypes.byref(sc), cams, nv, ctypes.byref(cfg))
+    per = [lib.gs_workspace_size(ctypes.byref(sc), ctypes.cast(ctypes.addressof(cams) + a * ctypes.sizeof(N.GsCamera),
+                                                               ctypes.POINTER(N.GsCamera)), b - a, ctypes.byref(cfg))
+           for a, b in groups]
+    cfg.cand_group_pixels = budget
+    grouped = lib.gs_workspace_size(ctypes.byref(sc), cams, nv, ctypes.byref(cfg))
+    assert grouped == max(per) and 0 < grouped < 0.5 * whole, (grouped, per, whole)
+    assert raster.largest_group([scenes.look_camera((0, 0, 1.5), 0.0, w, h, f) for w, h, f in sizes], budget) == 2
+    cfg.cand_group_pixels = 3 * (51_000 + 204_000 + 816_000)
+    assert lib.gs_workspace_size(ctypes.byref(sc), cams, nv, ctypes.byref(cfg)) == whole
+    cfg.cand_group_pixels = -1
+    assert lib.gs_workspace_size(ctypes.byref(sc), cams, nv, ctypes.byref(cfg)) == 0
+    fake = ctypes.c_void_p(1 << 40)  # never dereferenced: the calls fail on the host
+    out = ctypes.c_void_p(1 << 41)
+    assert lib.gs_render_candidates(ctypes.byref(sc), cams, nv, ctypes.byref(cfg), fake, out, None) == N.GS_ERR_ARG
+    cfg.cand_group_pixels = budget
+    assert lib.gs_project(ctypes.byref(sc), cams, nv, ctypes.byref(cfg), fake, None) == N.GS_ERR_ARG
+    mp = N.GsWorkspaceMap()
+    assert lib.gs_workspace_layout(ctypes.byref(sc), cams, nv, ctypes.byref(cfg), fake,
+                                   ctypes.byref(mp)) == N.GS_ERR_ARG

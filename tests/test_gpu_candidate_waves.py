@@ -95,3 +95,53 @@ def test_bits_stay_within_the_budget_at_the_128_view_workload():
         su, sh, ns, nf = oracle.candidate(sc, cams[v])
         assert abs(out[v, 1] - sh) <= 1e-5 * abs(sh), (v, out[v, 1], sh)
         assert abs(out[v, 2] - ns) <= nf, (v, out[v, 2], ns, nf)
+
+
+# (pixel budget, groups of views it makes); the views have 3150, 12750,
+# 51000, 3150, 12750 and 1551 pixels
+GROUPINGS = [(1, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5), (5, 6)]),
+             (16_000, [(0, 2), (2, 3), (3, 5), (5, 6)]),
+             (60_000, [(0, 2), (2, 4), (4, 6)])]
+
+
+@pytest.mark.parametrize("budget,groups", GROUPINGS)
+def test_grouped_views_match_the_whole_call(case, budget, groups):
+    """Views projected, binned and rendered in pixel-bounded groups within
+    one workspace: the same sums as the call over all views at once and as
+    the oracle; the counters report the largest group's records and pairs
+    (each group's own counts taken from separate calls), so the capacities
+    fitted from them hold every group and the refitted call agrees."""
+    sc, cams, refs = case
+    g = raster.Gaussians.from_scene(sc)
+    free = raster.Rasterizer().candidates(g, cams).cpu().numpy()
+    rast = raster.Rasterizer(cand_group_pixels=budget)
+    out = rast.candidates(g, cams).cpu().numpy()
+    np.testing.assert_allclose(out, free, rtol=1e-9, atol=1e-6)
+    _check(out, refs)
+    cnt = rast.counters()
+    recs, pairs = [], []
+    for a, b in groups:
+        r1 = raster.Rasterizer()
+        r1.candidates(g, cams[a:b])
+        c1 = r1.counters()
+        recs.append(c1.n_records)
+        pairs.append(c1.n_pairs)
+    assert (cnt.n_records, cnt.n_pairs) == (max(recs), max(pairs)), (cnt.n_records, cnt.n_pairs, recs, pairs)
+    out2 = rast.candidates(g, cams).cpu().numpy()
+    np.testing.assert_allclose(out2, free, rtol=1e-9, atol=1e-6)
+
+
+def test_grouped_128_view_workload_fits_8_gib():
+    """The 2M-Gaussian 128-view set (66M records, 717M pairs at once): the
+    largest pixel budget whose fitted workspace fits 8 GiB renders the same
+    per-view sums as the call over all views at once, within 8 GiB."""
+    from paper_2506_00225_gb300 import autotune
+    wl = scenes.workload("mixed2m")
+    sc, cams = wl["scene"], wl["cand_cams"]
+    g = raster.Gaussians.from_scene(sc)
+    whole = raster.Rasterizer().candidates(g, cams).cpu().numpy()
+    rast, budget, ws = autotune.fit_candidate_budget(g, cams, 8 << 30)
+    assert 0 < budget and ws <= (8 << 30), (budget, ws)
+    out = rast.candidates(g, cams).cpu().numpy()
+    np.testing.assert_allclose(out, whole, rtol=1e-9, atol=1e-6)
+    assert rast.counters().status == 0
