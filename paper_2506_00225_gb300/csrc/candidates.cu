@@ -377,6 +377,17 @@ __global__ void __launch_bounds__(TW *TH, 2) k_cand_sem(CandArgs a, int wave) {
         for (int l = 0; l < k; ++l) cp_async8(buf_sem(q) + t * k + l, src + l);
       }
     };
+    // repeated-id marks of this thread's slots of batch bi, once they landed
+    auto mark = [&](int bi) {
+      if constexpr (K >= 4) {
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+          const int t = threadIdx.x + u * THREADS;
+          if (bi >= nbatch || t >= batch_n(bi)) break;
+          mark_repeated_ids<K>(buf_sem(bi & 1) + t * k);
+        }
+      }
+    };
     // pair indices of batch bi for this thread's slots
     auto fetch = [&](int bi, uint32_t (&r)[PER]) {
 #pragma unroll
@@ -410,6 +421,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_cand_sem(CandArgs a, int wave) {
       };
       load_bits(0, mnext);
       cp_async_wait_all();
+      mark(0);
       __syncthreads();
       for (int bi = 0; bi < nbatch; ++bi) {
         if (bi + 1 < nbatch) issue(bi + 1, pv);
@@ -452,10 +464,11 @@ __global__ void __launch_bounds__(TW *TH, 2) k_cand_sem(CandArgs a, int wave) {
             const bool on = (mine[h] >> jb) & 1u;
             const float w = on ? __fmul_rn(alpha, T) : 0.f;
             if (on) T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-            scatter_classes<K>(myP, ssem + j * k, k, c_lo, mc, w);
+            scatter_classes_marked<K>(myP, ssem + j * k, k, c_lo, mc, w);
           }
         }
         cp_async_wait_all();
+        mark(bi + 1);
         __syncthreads();
       }
       if (inside) {

@@ -289,6 +289,81 @@ __device__ __forceinline__ void scatter_classes(float *row, const int2 *e, int k
   }
 }
 
+// The same adds with the k = 3 read-modify-writes in flight together: all
+// three slots are read before any is written, and an id repeated within the
+// Gaussian takes the earlier entry's result as its input, so every slot ends
+// with the roundings and the order of scatter_classes.  Straight-line code
+// (no branch on the ids).  Other k take scatter_classes.
+template <int K>
+__device__ __forceinline__ void scatter_classes_ilp(float *row, const int2 *e, int k, int c_lo, int mc, float w) {
+  if constexpr (K == 3) {
+    const int2 e0 = e[0], e1 = e[1], e2 = e[2];
+    const int i0 = e0.x - c_lo, i1 = e1.x - c_lo, i2 = e2.x - c_lo;
+    const bool k0 = (unsigned)i0 < (unsigned)mc, k1 = (unsigned)i1 < (unsigned)mc, k2 = (unsigned)i2 < (unsigned)mc;
+    const float o0 = k0 ? row[i0] : 0.f, o1 = k1 ? row[i1] : 0.f, o2 = k2 ? row[i2] : 0.f;
+    const float n0 = fmaf(w, __int_as_float(e0.y), o0);
+    const float n1 = fmaf(w, __int_as_float(e1.y), i1 == i0 ? n0 : o1);
+    const float n2 = fmaf(w, __int_as_float(e2.y), i2 == i1 ? n1 : (i2 == i0 ? n0 : o2));
+    if (k0) row[i0] = n0;
+    if (k1) row[i1] = n1;
+    if (k2) row[i2] = n2;
+  } else {
+    scatter_classes<K>(row, e, k, c_lo, mc, w);
+  }
+}
+
+// Staged-entry mark for k >= 4: the thread that staged a Gaussian's k
+// (class, weight) entries, once its copies have landed, sets bit 31 of the
+// first id when two of the ids are equal (valid ids are non-negative, so the
+// bit is free).  scatter_classes_marked reads it.
+template <int K>
+__device__ __forceinline__ void mark_repeated_ids(int2 *e) {
+  if constexpr (K >= 4) {
+    bool rep = false;
+#pragma unroll
+    for (int a = 1; a < K; ++a)
+#pragma unroll
+      for (int b = 0; b < a; ++b) rep |= e[a].x == e[b].x;
+    if (rep) e[0].x = (int)((uint32_t)e[0].x | 0x80000000u);
+  }
+}
+
+// scatter_classes over entries marked by mark_repeated_ids: a Gaussian
+// without repeated ids (the warp-uniform common case) has all K
+// read-modify-writes in flight together; one with repeated ids takes them
+// one after another.  Either way each slot ends as in scatter_classes.
+// k = 3 takes scatter_classes_ilp (needs no mark).
+template <int K>
+__device__ __forceinline__ void scatter_classes_marked(float *row, const int2 *e, int k, int c_lo, int mc, float w) {
+  if constexpr (K >= 4) {
+    int2 v[K];
+#pragma unroll
+    for (int l = 0; l < K; ++l) v[l] = e[l];
+    if (v[0].x >= 0) {
+      float o[K];
+#pragma unroll
+      for (int l = 0; l < K; ++l) {
+        const int id = v[l].x - c_lo;
+        o[l] = (unsigned)id < (unsigned)mc ? row[id] : 0.f;
+      }
+#pragma unroll
+      for (int l = 0; l < K; ++l) {
+        const int id = v[l].x - c_lo;
+        if ((unsigned)id < (unsigned)mc) row[id] = fmaf(w, __int_as_float(v[l].y), o[l]);
+      }
+    } else {
+      v[0].x = (int)((uint32_t)v[0].x & 0x7fffffffu);
+#pragma unroll
+      for (int l = 0; l < K; ++l) {
+        const int id = v[l].x - c_lo;
+        if ((unsigned)id < (unsigned)mc) row[id] = fmaf(w, __int_as_float(v[l].y), row[id]);
+      }
+    }
+  } else {
+    scatter_classes_ilp<K>(row, e, k, c_lo, mc, w);
+  }
+}
+
 struct FwdArgs {
   const uint2 *ranges;
   const uint32_t *pvals;

@@ -332,6 +332,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_semantic(FwdArgs a) {
       mn1 = mw[NPIX + lp];
     }
     cp_async_wait_all();
+    if (nbatch > 0 && t < batch_n(0)) mark_repeated_ids<K>(buf_sem(0) + t * k);
     __syncthreads();
     for (int bi = 0; bi < nbatch; ++bi) {
       if (bi + 1 < nbatch && t < batch_n(bi + 1)) issue(bi + 1, pv);
@@ -387,10 +388,11 @@ __global__ void __launch_bounds__(TW *TH, 2) k_semantic(FwdArgs a) {
           float w = on ? __fmul_rn(alpha, T) : 0.f;
           if (tmode) w = -w;
           if (on) T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-          scatter_classes<K>(myP, ssem + j * k, k, c_lo, mc, w);
+          scatter_classes_marked<K>(myP, ssem + j * k, k, c_lo, mc, w);
         }
       }
       cp_async_wait_all();
+      if (bi + 1 < nbatch && t < batch_n(bi + 1)) mark_repeated_ids<K>(buf_sem((bi + 1) & 1) + t * k);
       __syncthreads();
     }
     __syncthreads();

@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_sem_objective(FwdArgs a, float lo
 
   // (1) the rendered class distribution P of this thread's pixel
   for (int c = 0; c < m; ++c) myP[c] = 0.f;
-  walk(true, [&](int, bool, float w, const int2 *e) { scatter_classes<K>(myP, e, k, 0, m, w); });
+  walk(true, [&](int, bool, float w, const int2 *e) { scatter_classes_ilp<K>(myP, e, k, 0, m, w); });
 
   // (2) per pixel: the semantic term, and d term / d P (over the pixel
   // count) in place of P.  Thread per pixel: its own row (shared memory,
