@@ -86,6 +86,32 @@ __device__ __forceinline__ void add_view_sum(float v, double *dst) {
   }
 }
 
+// add_view_sum over the pixels of a tile as the one-pixel-per-thread
+// kernels add them (same 32-pixel groups, same butterfly, same order of the
+// group sums), whatever the thread mapping of the caller: px[p] is the
+// value of tile pixel p (raster order).  Every thread of the CTA calls it.
+template <int TW, int TH, int THREADS>
+__device__ __forceinline__ void add_view_sum_pixels(const float *px, double *dst) {
+  using F1 = Footprint<TW, TH, 1>;
+  constexpr int G = F1::kWarps;  // 32-pixel groups
+  __shared__ float red[G];
+  __syncthreads();  // px is complete
+  for (int w = threadIdx.x >> 5; w < G; w += THREADS / 32) {
+    const int l = (int)lane_id();
+    const int lx = (w % F1::kWX) * 8 + (l & 7), ly = (w / F1::kWX) * 4 + (l >> 3);
+    float v = px[ly * TW + lx];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (l == 0) red[w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < G; ++w) s += red[w];
+    atomicAdd(dst, s);
+  }
+}
+
 constexpr float kClipLo = 0.001f;
 
 template <int TW, int TH>
@@ -223,24 +249,30 @@ __device__ __forceinline__ bool next_tile(const CandPlan &p, int wave, int which
 // that reach it are staged (packed) in the warp's shared memory and blended
 // in order.  A warp stops at a batch boundary once all its pixels are done,
 // so every batch a pixel can still read in pass 2 has its bits written.
-__host__ __device__ inline size_t cand_blend_warp_bytes() { return 32 * (16 + 16 + 8 + 4); }
+// Shared memory of one warp of the candidate blend: 32 staging slots (conic
+// + opacity, uncertainty, mean, and per row group the lanes the pair reaches).
+__host__ __device__ inline size_t cand_blend_warp_bytes(int ppt) { return 32 * (16 + 16 + 8 + 4 * (size_t)ppt); }
+constexpr int kCandBlendPpt = 2;  // pixels per thread of the candidate blend
 
-template <int TW, int TH, int B>
-__global__ void __launch_bounds__(TW *TH) k_cand_blend(CandArgs a, int wave) {
-  using FP = Footprint<TW, TH>;
+// PPT pixels per thread, one column, rows 4 apart: they share every staged
+// load and the x offset of every Gaussian (as in the mapping blend pass).
+template <int TW, int TH, int B, int PPT>
+__global__ void __launch_bounds__(TW *TH / PPT) k_cand_blend(CandArgs a, int wave) {
+  using FP = Footprint<TW, TH, PPT>;
   constexpr int THREADS = FP::kThreads;
   constexpr int NPIX = FP::kPix;
   constexpr int NW = B / 32;  // contributor words per pixel and batch
   extern __shared__ float4 smem4[];
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
-  char *wb = reinterpret_cast<char *>(smem4) + warp * cand_blend_warp_bytes();
+  char *wb = reinterpret_cast<char *>(smem4) + warp * cand_blend_warp_bytes(PPT);
   float4 *w_co = reinterpret_cast<float4 *>(wb);
   float4 *w_cd = w_co + 32;  // uncertainty in .x
   float2 *w_uv = reinterpret_cast<float2 *>(w_co + 64);
-  uint32_t *w_lm = reinterpret_cast<uint32_t *>(w_uv + 32);  // lanes of the warp each staged pair reaches
+  uint32_t *w_lm = reinterpret_cast<uint32_t *>(w_uv + 32);  // [row group][slot]: lanes each staged pair reaches
   __shared__ uint32_t s_item;
+  __shared__ float s_px[2][NPIX];  // per-pixel uncertainty sum and empty flag of the current tile
   if (a.counters->status & kStatusTimeout) return;
-  const int lx = FP::lx(), ly = FP::ly(0), lp = ly * TW + lx;
+  const int lx = FP::lx();
   const bool use_unc = a.unc != nullptr;
   uint32_t tile, unit_base;
   while (next_tile(a.plan, wave, 0, &s_item, tile, unit_base)) {
@@ -248,41 +280,68 @@ __global__ void __launch_bounds__(TW *TH) k_cand_blend(CandArgs a, int wave) {
     const DevCam &c = a.cams[v];
     const uint32_t local = tile - c.tile_off;
     const int ox = (int)(local % (uint32_t)c.tiles_x) * TW, oy = (int)(local / (uint32_t)c.tiles_x) * TH;
-    const int bx0 = ox + (int)(warp % FP::kWX) * 8, by0 = oy + (int)(warp / FP::kWX) * 4;  // the warp's block
+    const int bx0 = ox + (int)(warp % FP::kWX) * 8, by0 = oy + (int)(warp / FP::kWX) * FP::kBH;  // the warp's block
     const uint2 rg = a.ranges[tile];
-    const int px = ox + lx, py = oy + ly;
-    const bool inside = px < c.width && py < c.height;
-    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+    const int px = ox + lx;
+    const float fpx = (float)px + 0.5f;
     const uint32_t unit0 = a.mask_off[tile] - unit_base;
     const bool store = unit0 + (rg.y - rg.x + B - 1) / B <= a.cap_units;
 
-    float T = 1.f, U = 0.f;
-    uint32_t last = 0;
-    bool done = !inside;
+    int lp[PPT];
+    float fpy[PPT], T[PPT], U[PPT];
+    uint32_t last[PPT];
+    bool inside[PPT], done[PPT];
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+      const int ly = FP::ly(i);
+      lp[i] = ly * TW + lx;
+      fpy[i] = (float)(oy + ly) + 0.5f;
+      inside[i] = px < c.width && oy + ly < c.height;
+      done[i] = !inside[i];
+      T[i] = 1.f; U[i] = 0.f;
+      last[i] = 0;
+    }
+    auto all_done = [&]() {
+      bool d = true;
+#pragma unroll
+      for (int i = 0; i < PPT; ++i) d = d && done[i];
+      return d;
+    };
     // groups up to the end of the last batch: the empty groups of a partial
     // batch still write their (zero) bits, which pass 2 reads
     const uint32_t gend = rg.x + (rg.y - rg.x + B - 1) / B * B;
     for (uint32_t g0 = rg.x; g0 < gend; g0 += 32) {
       const uint32_t rel = g0 - rg.x, bi = rel / B, h = (rel % B) / 32;
       const int n = g0 < rg.y ? (int)min(32u, rg.y - g0) : 0;
-      // the group's pairs that reach the warp's block
-      uint32_t r = 0u, lm = 0u;
+      // the group's pairs that reach the warp's block, per row group
+      uint32_t r = 0u, lm[PPT];
+      bool reach = false;
+#pragma unroll
+      for (int i = 0; i < PPT; ++i) lm[i] = 0u;
       if ((int)lane < n) {
         r = a.pvals[g0 + lane];
-        lm = block_lane_mask(__ldg(a.rec.box + r), bx0, by0);
+        const short4 bx = __ldg(a.rec.box + r);
+#pragma unroll
+        for (int i = 0; i < PPT; ++i) {
+          lm[i] = block_lane_mask(bx, bx0, by0 + 4 * i);
+          reach = reach || lm[i] != 0u;
+        }
       }
-      const uint32_t vis = __ballot_sync(0xffffffffu, lm != 0u);
-      uint32_t bits = 0u;
-      if (vis && !__all_sync(0xffffffffu, done)) {
+      const uint32_t vis = __ballot_sync(0xffffffffu, reach);
+      uint32_t bits[PPT];
+#pragma unroll
+      for (int i = 0; i < PPT; ++i) bits[i] = 0u;
+      if (vis && !__all_sync(0xffffffffu, all_done())) {
         __syncwarp();  // the previous group's slots are no longer read
-        if (lm) {
+        if (reach) {
           const int slot = __popc(vis & lanemask_lt());
           w_co[slot] = __ldg(a.rec.co + r);
           w_uv[slot] = __ldg(a.rec.uv + r);
           float4 cd = __ldg(a.rec.cd + r);
           if (use_unc) cd.x = __ldg(a.rec.unc + r);
           w_cd[slot] = cd;
-          w_lm[slot] = lm;
+#pragma unroll
+          for (int i = 0; i < PPT; ++i) w_lm[i * 32 + slot] = lm[i];
         }
         __syncwarp();
         uint32_t rem = vis;
@@ -291,25 +350,38 @@ __global__ void __launch_bounds__(TW *TH) k_cand_blend(CandArgs a, int wave) {
           const int bit = __ffs(rem) - 1;
           rem &= rem - 1;
           const int sl = slot++;
-          if (done || !((w_lm[sl] >> lane) & 1u)) continue;
-          float alpha, G, araw, dx, dy;
-          if (!gauss_alpha(w_uv[sl], w_co[sl], fpx, fpy, alpha, G, araw, dx, dy)) continue;
-          const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
-          if (Tn < kTStop) { done = true; continue; }
-          const float w = __fmul_rn(alpha, T);
-          U = fmaf(w, w_cd[sl].x, U);
-          T = Tn;
-          bits |= 1u << bit;
+          const float2 uv = w_uv[sl];
+          const float4 co = w_co[sl];
+#pragma unroll
+          for (int i = 0; i < PPT; ++i) {
+            if (done[i] || !((w_lm[i * 32 + sl] >> lane) & 1u)) continue;
+            float alpha, G, araw, dx, dy;
+            if (!gauss_alpha(uv, co, fpx, fpy[i], alpha, G, araw, dx, dy)) continue;
+            const float Tn = __fmul_rn(T[i], __fsub_rn(1.f, alpha));
+            if (Tn < kTStop) { done[i] = true; continue; }
+            const float w = __fmul_rn(alpha, T[i]);
+            U[i] = fmaf(w, w_cd[sl].x, U[i]);
+            T[i] = Tn;
+            bits[i] |= 1u << bit;
+          }
         }
       }
-      if (bits) last = rel + (32 - __clz(bits));
-      if (store) a.masks[((size_t)(unit0 + bi) * NW + h) * NPIX + lp] = bits;
+#pragma unroll
+      for (int i = 0; i < PPT; ++i) {
+        if (bits[i]) last[i] = rel + (32 - __clz(bits[i]));
+        if (store) a.masks[((size_t)(unit0 + bi) * NW + h) * NPIX + lp[i]] = bits[i];
+      }
       // stop at a batch boundary once every pixel of the warp is done
-      if (h == NW - 1 && __all_sync(0xffffffffu, done)) break;
+      if (h == NW - 1 && __all_sync(0xffffffffu, all_done())) break;
     }
-    a.clast[(size_t)tile * NPIX + lp] = last;
-    add_view_sum<THREADS>(inside && use_unc ? U : 0.f, a.out + 3 * v);
-    add_view_sum<THREADS>(inside && T == 1.f ? 1.f : 0.f, a.out + 3 * v + 2);
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+      a.clast[(size_t)tile * NPIX + lp[i]] = last[i];
+      s_px[0][lp[i]] = inside[i] && use_unc ? U[i] : 0.f;
+      s_px[1][lp[i]] = inside[i] && T[i] == 1.f ? 1.f : 0.f;
+    }
+    add_view_sum_pixels<TW, TH, THREADS>(s_px[0], a.out + 3 * v);
+    add_view_sum_pixels<TW, TH, THREADS>(s_px[1], a.out + 3 * v + 2);
   }
 }
 
@@ -555,16 +627,16 @@ static int resident_ctas(const void *func, int threads, size_t smem) {
 template <int TW, int TH, int K, int B>
 static cudaError_t launch_cand_waves(const CandArgs &a, size_t smem_blend, size_t smem_sem, int waves,
                                      cudaStream_t s) {
-  const void *fb = (const void *)k_cand_blend<TW, TH, B>;
+  const void *fb = (const void *)k_cand_blend<TW, TH, B, kCandBlendPpt>;
   const void *fs = (const void *)k_cand_sem<TW, TH, K, B>;
   cudaError_t e = ensure_smem_limit(fs, (int)kSmemBudget);
   if (e != cudaSuccess) return e;
   const int sms = device_sms();
   if (sms < 1) return cudaErrorInvalidDevice;
-  const unsigned gb = (unsigned)(sms * resident_ctas(fb, TW * TH, smem_blend));
+  const unsigned gb = (unsigned)(sms * resident_ctas(fb, TW * TH / kCandBlendPpt, smem_blend));
   const unsigned gs = (unsigned)(sms * resident_ctas(fs, TW * TH, smem_sem));
   for (int w = 0; w < waves; ++w) {
-    k_cand_blend<TW, TH, B><<<gb, TW * TH, smem_blend, s>>>(a, w);
+    k_cand_blend<TW, TH, B, kCandBlendPpt><<<gb, TW * TH / kCandBlendPpt, smem_blend, s>>>(a, w);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_cand_sem<TW, TH, K, B><<<gs, TW * TH, smem_sem, s>>>(a, w);
@@ -634,7 +706,7 @@ cudaError_t launch_candidates(const Layout &L, const WsPtrs &P, int pbuf, const 
       }
     }
     const size_t smem_sem = fixed + (size_t)threads * a.mstride * sizeof(float);
-    const size_t smem_blend = (size_t)(threads / 32) * cand_blend_warp_bytes();
+    const size_t smem_blend = (size_t)(threads / kCandBlendPpt / 32) * cand_blend_warp_bytes(kCandBlendPpt);
     if (L.tile_w == 16 && L.tile_h == 16) return launch_cand_batch<16, 16>(B, a, smem_blend, smem_sem, L.cand_waves, s);
     if (L.tile_w == 16 && L.tile_h == 8) return launch_cand_batch<16, 8>(B, a, smem_blend, smem_sem, L.cand_waves, s);
     if (L.tile_w == 8 && L.tile_h == 8) return launch_cand_batch<8, 8>(B, a, smem_blend, smem_sem, L.cand_waves, s);
