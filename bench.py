@@ -997,7 +997,12 @@ def bench_candidates(args, dev, flush):
     else:
         cbest, ctable = autotune.tune_candidates(g, cams)
         ctile = cbest["tile"]
-    rast = raster.Rasterizer(tile=ctile, cand_batch=cbest["cand_batch"], device=dev)
+    # consecutive views in pixel-bounded groups: the largest group budget
+    # whose fitted workspace stays within 4 GiB (the per-view sums do not
+    # depend on it; smaller groups also keep the tile ids of a group short,
+    # so the tile sort takes fewer digit passes)
+    rast, cgroup, _ = autotune.fit_candidate_budget(g, cams, 4 << 30, tile=ctile, cand_batch=cbest["cand_batch"],
+                                                    device=dev)
     out = rast.candidates(g, cams, check=True)
     cnt = rast.counters()
     for _ in range(2):
@@ -1031,7 +1036,8 @@ def bench_candidates(args, dev, flush):
     per_view_ms = statistics.mean(per_view)
     npix = sum(c.width * c.height for c in cams)
     # work of the batch (outside the timed region) and its FP32 / MUFU rooflines
-    wc = rast.work_counts(g, cams)
+    # (counted by an ungrouped rasterizer: the counting call takes all views at once)
+    wc = raster.Rasterizer(tile=ctile, cand_batch=cbest["cand_batch"], device=dev).work_counts(g, cams)
     clock_ghz = 2.07
     n_sm = device_sms(dev)
     fp32_peak = n_sm * FP32_LANES_PER_SM * 2 * clock_ghz / 1000.0
@@ -1071,12 +1077,15 @@ def bench_candidates(args, dev, flush):
                       "per-view arm: 5 eager repetitions",
             "autotune": {"chosen": {"tile": "%dx%d" % ctile, "cand_batch": cbest["cand_batch"]}, "table": ctable},
             "workspace_bytes": int(rast.ws.numel()),
+            "candidate_group_pixels": cgroup,
             "roofline": cand_roof,
             "workload": ("cand96: the 300k room + Gamma(2,0.5) uncertainty, 96 poses (4x4 grid at 0.5 m x 6 yaws), "
                          "resolutions cycling 170x300 / 340x600 / 680x1200") if args.cand_workload == "cand96" else
                         ("mixed2m candidates: the 2M-Gaussian rooms (M=256, top-8) + Gamma(2,0.5) uncertainty, "
                          "128 views (64 @170x300, 48 @340x600, 16 @680x1200)"),
-            "n_records": int(cnt.n_records), "n_pairs": int(cnt.n_pairs),
+            # with view groups the counters hold the largest group's counts
+            ("largest_group_records" if cgroup else "n_records"): int(cnt.n_records),
+            ("largest_group_pairs" if cgroup else "n_pairs"): int(cnt.n_pairs),
             "per_view_launches": {"value": 1000.0 * len(cams) / per_view_ms, "unit": "views/s",
                                   "ms": per_view_ms, "ms_reps": [round(x, 3) for x in per_view]},
             "batched_speedup": per_view_ms / ms,

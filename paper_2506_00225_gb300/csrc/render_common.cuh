@@ -252,6 +252,18 @@ inline void chunk_classes(int m, int threads, int k, bool has_sem, int *mchunk, 
   *nchunks = (m + c - 1) / c;
 }
 
+// L2 prefetch of [p, p + bytes) clipped to 16-byte granules inside
+// [base, base + total).
+__device__ __forceinline__ void prefetch_l2(const void *base, size_t total, const void *p, size_t bytes) {
+  const uintptr_t b = reinterpret_cast<uintptr_t>(base);
+  const uintptr_t lo = (reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15;
+  uintptr_t hi = (reinterpret_cast<uintptr_t>(p) + bytes) & ~(uintptr_t)15;
+  const uintptr_t end = (b + total) & ~(uintptr_t)15;
+  if (hi > end) hi = end;
+  if (lo < b || hi <= lo) return;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((uint32_t)(hi - lo)) : "memory");
+}
+
 // Asynchronous global -> shared copies (sm_80+ cp.async), used to stage the
 // next batch while the current one is processed.
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {

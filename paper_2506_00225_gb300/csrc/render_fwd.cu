@@ -28,18 +28,6 @@
 
 namespace gs {
 
-// L2 prefetch of [p, p + bytes) clipped to 16-byte granules inside
-// [base, base + total).
-__device__ __forceinline__ void prefetch_l2(const void *base, size_t total, const void *p, size_t bytes) {
-  const uintptr_t b = reinterpret_cast<uintptr_t>(base);
-  const uintptr_t lo = (reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15;
-  uintptr_t hi = (reinterpret_cast<uintptr_t>(p) + bytes) & ~(uintptr_t)15;
-  const uintptr_t end = (b + total) & ~(uintptr_t)15;
-  if (hi > end) hi = end;
-  if (lo < b || hi <= lo) return;
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((uint32_t)(hi - lo)) : "memory");
-}
-
 // Per tile: number of staged batches (of `batch` pairs) of its pair range.
 __global__ void k_tile_batches(const uint2 *__restrict__ ranges, uint32_t ntiles, uint32_t *units, uint32_t batch) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;

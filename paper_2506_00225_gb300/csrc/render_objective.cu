@@ -10,11 +10,12 @@
 //   (1) accumulates each pixel's class distribution P from the contributor
 //       bits of pass 1 (Eq. 3), in a per-pixel shared-memory row, exactly as
 //       the plain semantic pass does;
-//   (2) one warp per pixel, lanes over the classes: reads the target
-//       distribution Q (coalesced), forms the entropy mask, the Hellinger
-//       distance, the cosine and the pixel's term, and overwrites the row
-//       with d term / d P_m divided by the pixel count (the same arithmetic
-//       and summation order as the objective on rendered maps);
+//   (2) one thread per pixel: reads its target distribution Q (warmed into
+//       L2 for the whole tile when the CTA starts), forms the entropy mask,
+//       the Hellinger distance, the cosine and the pixel's term, and
+//       overwrites its row with d term / d P_m divided by the pixel count
+//       (the same arithmetic and summation order as the objective on
+//       rendered maps);
 //   (3) walks the contributors again, recomputing w = alpha T, and adds
 //       sum_p w * dP_p[id] into the objective's gradient of every (Gaussian,
 //       entry) weight: a transposed warp sum, one atomic per entry and warp.
@@ -58,6 +59,15 @@ __global__ void __launch_bounds__(TW *TH, 2) k_sem_objective(FwdArgs a, float lo
   const uint32_t lane = lane_id(), warp = threadIdx.x >> 5;
   const uint32_t unit0 = a.mask_off[tile];
 
+  if ((int)threadIdx.x < TH) {
+    // warm L2 with the tile's target rows while the class accumulation runs
+    const int y = oy + (int)threadIdx.x;
+    if (y < a.height) {
+      const int vw = min(TW, a.width - ox);
+      prefetch_l2(a.t_sem, (size_t)a.width * a.height * m * 4, a.t_sem + ((size_t)y * a.width + ox) * m,
+                  (size_t)vw * m * 4);
+    }
+  }
   const uint32_t last = inside ? a.nlast[(size_t)py * a.width + px] : 0u;
   if (threadIdx.x == 0) s_maxlast = 0;
   __syncthreads();
