@@ -35,6 +35,7 @@ inline int os_items(int64_t capacity) { return capacity <= (1 << 20) ? 8 : 16; }
 constexpr unsigned long long kFlagA = 1ull << 62;   // tile aggregate published
 constexpr unsigned long long kFlagP = 2ull << 62;   // inclusive prefix published
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
+constexpr int kLookWindow = 8;                       // predecessors read per look-back step
 
 int sort_tiles(int64_t capacity) {
   const int64_t tile = (int64_t)kOsThreads * os_items(capacity);
@@ -172,19 +173,38 @@ __global__ void __launch_bounds__(kOsThreads) k_os_pass(const K *__restrict__ ke
   }
   unsigned long long excl = 0ull;
   if (t > 0) {
+    // the look-back reads kLookWindow predecessors at a time (their loads in
+    // flight together) and walks them newest first: aggregates are added,
+    // an inclusive prefix ends the walk, and an unpublished word (flag 0)
+    // stops the window there to be read again (a bounded wait)
     int j = (int)t - 1;
     uint32_t spins = 0;
-    while (j >= 0) {
-      const unsigned long long v = *reinterpret_cast<volatile unsigned long long *>(lookback + (size_t)j * kRadix + d);
-      const unsigned long long flag = v & ~kValMask;
-      if (flag == 0ull) {
+    bool done = false;
+    while (!done) {
+      unsigned long long v[kLookWindow];
+#pragma unroll
+      for (int i = 0; i < kLookWindow; ++i)
+        v[i] = j - i >= 0 ? *reinterpret_cast<volatile unsigned long long *>(lookback + (size_t)(j - i) * kRadix + d)
+                          : (unsigned long long)kFlagP;  // before tile 0: an empty inclusive prefix
+      int taken = 0;
+      bool blocked = false;
+#pragma unroll
+      for (int i = 0; i < kLookWindow; ++i) {
+        if (done || blocked) continue;
+        const unsigned long long flag = v[i] & ~kValMask;
+        if (flag == 0ull) {
+          blocked = true;
+          continue;
+        }
+        excl += v[i] & kValMask;
+        ++taken;
+        if (flag == kFlagP) done = true;
+      }
+      j -= taken;
+      if (blocked && !done) {
         if (++spins > spin_limit) { set_status(counters, kStatusTimeout); break; }
         __nanosleep(32);
-        continue;
       }
-      excl += v & kValMask;
-      if (flag == kFlagP) break;
-      --j;
     }
     atomicExch(lb + d, kFlagP | (excl + tile_count));
   }
