@@ -295,32 +295,49 @@ __global__ void __launch_bounds__(kProjThreads) k_project_single(gs_scene sc, co
   }
   uint32_t total;
   const uint32_t ex = block_exclusive_scan(cnt, tmp, &total);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
+    // warp 0 looks back 32 blocks at a time (lane i reads block j - i):
+    // the newest blocks' counts are added up to the first inclusive prefix;
+    // an unpublished word stops the step there and is read again (a bounded
+    // wait).  Blocks before block 0 read as an empty prefix.
+    const uint32_t lane = threadIdx.x;
     uint32_t excl = 0u;
     if (b == 0) {
-      atomicExch(lookback, kPjFlagP | total);
+      if (lane == 0) atomicExch(lookback, kPjFlagP | total);
     } else {
-      atomicExch(lookback + b, kPjFlagA | total);
+      if (lane == 0) atomicExch(lookback + b, kPjFlagA | total);
       int j = b - 1;
       uint32_t spins = 0;
-      while (j >= 0) {
-        const uint32_t w = *reinterpret_cast<volatile uint32_t *>(lookback + j);
+      while (true) {
+        const int idx = j - (int)lane;
+        const uint32_t w = idx >= 0 ? *reinterpret_cast<volatile uint32_t *>(lookback + idx) : (uint32_t)kPjFlagP;
         const uint32_t flag = w & ~kPjVal;
-        if (flag == 0u) {
-          if (++spins > spin_limit) { set_status(P.counters, kStatusTimeout); break; }
+        const uint32_t zero = __ballot_sync(0xffffffffu, flag == 0u);
+        const uint32_t pre = __ballot_sync(0xffffffffu, flag == kPjFlagP);
+        const int first_zero = zero ? __ffs(zero) - 1 : 32, first_p = pre ? __ffs(pre) - 1 : 32;
+        const int upto = first_p < first_zero ? first_p + 1 : first_zero;  // lanes whose counts are taken
+        uint32_t v = (int)lane < upto ? (w & kPjVal) : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        excl += v;
+        if (first_p < first_zero) break;
+        j -= upto;
+        if (first_zero < 32) {
+          if (++spins > spin_limit) {
+            if (lane == 0) set_status(P.counters, kStatusTimeout);
+            break;
+          }
           __nanosleep(32);
-          continue;
         }
-        excl += w & kPjVal;
-        if (flag == kPjFlagP) break;
-        --j;
       }
-      atomicExch(lookback + b, kPjFlagP | ((excl + total) & kPjVal));
+      if (lane == 0) atomicExch(lookback + b, kPjFlagP | ((excl + total) & kPjVal));
     }
-    s_off = excl;
-    if (b == nb - 1) {
-      P.counters->n_records = excl + total;
-      if (excl + total > rcap) set_status(P.counters, kStatusCapacity);
+    if (lane == 0) {
+      s_off = excl;
+      if (b == nb - 1) {
+        P.counters->n_records = excl + total;
+        if (excl + total > rcap) set_status(P.counters, kStatusCapacity);
+      }
     }
   }
   __syncthreads();
