@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(256) k_os_hist(const K *__restrict__ keys, con
 }
 
 template <typename K, int ITEMS>
-__global__ void __launch_bounds__(kOsThreads) k_os_pass(const K *__restrict__ keys_in,
+__global__ void __launch_bounds__(kOsThreads, sizeof(K) == 4 ? 3 : 2) k_os_pass(const K *__restrict__ keys_in,
                                                         const uint32_t *__restrict__ vals_in,
                                                         K *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
                                                         const uint32_t *count_p, uint32_t cap, int shift,
@@ -134,24 +134,28 @@ __global__ void __launch_bounds__(kOsThreads) k_os_pass(const K *__restrict__ ke
 
   // stable ranking: warp-striped items, in index order within each warp
   const uint32_t lt = lanemask_lt();
+  // per item one word: its digit (kRadix past the tile's end) in the high
+  // half and its rank among the warp's equal digits in the low half (fewer
+  // live registers: more CTAs per SM)
   K key[ITEMS];
-  uint32_t val[ITEMS], dig[ITEMS], loc[ITEMS];
+  uint32_t val[ITEMS], dl[ITEMS];
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
     const uint32_t off = warp * (32 * ITEMS) + i * 32 + lane;
     const bool ok = off < n_tile;
     key[i] = ok ? keys_in[base + off] : (K)0;
     val[i] = ok ? vals_in[base + off] : 0u;
-    dig[i] = ok ? digit_of(key[i], shift) : (uint32_t)kRadix;
+    dl[i] = (ok ? digit_of(key[i], shift) : (uint32_t)kRadix) << 16;
   }
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
-    const uint32_t peers = __match_any_sync(0xffffffffu, dig[i]);
+    const uint32_t di = dl[i] >> 16;
+    const uint32_t peers = __match_any_sync(0xffffffffu, di);
     uint32_t b = 0;
-    if (dig[i] < (uint32_t)kRadix) b = wcnt[warp][dig[i]];
-    loc[i] = b + __popc(peers & lt);
+    if (di < (uint32_t)kRadix) b = wcnt[warp][di];
+    dl[i] |= b + __popc(peers & lt);
     __syncwarp();
-    if ((peers & lt) == 0u && dig[i] < (uint32_t)kRadix) wcnt[warp][dig[i]] = b + __popc(peers);
+    if ((peers & lt) == 0u && di < (uint32_t)kRadix) wcnt[warp][di] = b + __popc(peers);
     __syncwarp();
   }
   __syncthreads();
@@ -217,8 +221,9 @@ __global__ void __launch_bounds__(kOsThreads) k_os_pass(const K *__restrict__ ke
   // local reorder by digit (stable), then contiguous global writes
 #pragma unroll
   for (int i = 0; i < ITEMS; ++i) {
-    if (dig[i] < (uint32_t)kRadix) {
-      const uint32_t lp = tile_pre[dig[i]] + wcnt[warp][dig[i]] + loc[i];
+    const uint32_t di = dl[i] >> 16;
+    if (di < (uint32_t)kRadix) {
+      const uint32_t lp = tile_pre[di] + wcnt[warp][di] + (dl[i] & 0xffffu);
       skey[lp] = key[i];
       sval[lp] = val[i];
     }
