@@ -168,9 +168,13 @@ constexpr int kViewsPerCta = 16;
 // Pass 1: count visible Gaussians per (view, projection block).
 __global__ void __launch_bounds__(kProjThreads) k_project_count(gs_scene sc, const DevCam *cams, int nb, int n_views,
                                                                 uint32_t *blockcnt) {
-  __shared__ uint32_t tmp[33];
+  // per view: a warp sum, then one shared-memory add per warp (the counts
+  // are totals, so no scan and no barrier per view)
+  __shared__ uint32_t s_cnt[kViewsPerCta];
   const int b = blockIdx.x;
   const int v0 = blockIdx.y * kViewsPerCta, v1 = min(n_views, v0 + kViewsPerCta);
+  if ((int)threadIdx.x < kViewsPerCta) s_cnt[threadIdx.x] = 0u;
+  __syncthreads();
   const int g0 = b * kProjBlock + threadIdx.x * kProjItems;
   GIn in[kProjItems];
 #pragma unroll
@@ -187,10 +191,11 @@ __global__ void __launch_bounds__(kProjThreads) k_project_count(gs_scene sc, con
                                                                                                           : 0u;
       }
     }
-    uint32_t total;
-    block_exclusive_scan(cnt, tmp, &total);
-    if (threadIdx.x == 0) blockcnt[v * nb + b] = total;
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if (lane_id() == 0 && cnt) atomicAdd(&s_cnt[v - v0], cnt);
   }
+  __syncthreads();
+  if ((int)threadIdx.x < v1 - v0) blockcnt[(v0 + threadIdx.x) * nb + b] = s_cnt[threadIdx.x];
 }
 
 // Writes visible record r (Gaussian g projected into view v) and its
