@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_sem_objective(FwdArgs a, float lo
     const int m2 = pairs ? (m & ~3) : 0;  // classes read as 8-byte pairs, four per step
     float st[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     if (inside) {
+#pragma unroll 4
       for (int c = 0; c < m2; c += 4) {
         const float2 q0 = __ldg(reinterpret_cast<const float2 *>(q + c));
         const float2 q1 = __ldg(reinterpret_cast<const float2 *>(q + c + 2));
@@ -177,6 +178,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_sem_objective(FwdArgs a, float lo
     s_keep[lp] = t.keep;
     if (t.keep) {
       term_sum = (double)t.value;
+#pragma unroll 4
       for (int c = 0; c < m2; c += 4) {
         const float2 q0 = __ldg(reinterpret_cast<const float2 *>(q + c));
         const float2 q1 = __ldg(reinterpret_cast<const float2 *>(q + c + 2));
