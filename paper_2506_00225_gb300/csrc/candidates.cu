@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_cand_sem(CandArgs a, int wave) {
         cp_async8(buf_uv(q) + t, a.rec.uv + r[u]);
         if (!stored) cp_async8(buf_box(q) + t, a.rec.box + r[u]);
         const int2 *src = a.rec.sem + (size_t)r[u] * k;
-        for (int l = 0; l < k; ++l) cp_async8(buf_sem(q) + t * k + l, src + l);
+        for (int l = 0; l < k; ++l) cp_async8(buf_sem(q) + l * B + t, src + l);  // entry-major
       }
     };
     // repeated-id marks of this thread's slots of batch bi, once they landed
@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_cand_sem(CandArgs a, int wave) {
         for (int u = 0; u < PER; ++u) {
           const int t = threadIdx.x + u * THREADS;
           if (bi >= nbatch || t >= batch_n(bi)) break;
-          mark_repeated_ids<K>(buf_sem(bi & 1) + t * k);
+          mark_repeated_ids<K>(buf_sem(bi & 1) + t, B);
         }
       }
     };
@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_cand_sem(CandArgs a, int wave) {
             const bool on = (mine[h] >> jb) & 1u;
             const float w = on ? __fmul_rn(alpha, T) : 0.f;
             if (on) T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-            scatter_classes_marked<K>(myP, ssem + j * k, k, c_lo, mc, w);
+            scatter_classes_marked<K>(myP, ssem + j, k, c_lo, mc, w, B);
           }
         }
         cp_async_wait_all();

@@ -289,13 +289,16 @@ __host__ __device__ inline size_t sem_batch_bytes(int k) {
 
 // Adds w * weight to the accumulator slot of each of the Gaussian's k
 // (class, weight) entries that falls in the class chunk [c_lo, c_lo + mc).
-// K > 0 fixes k at compile time.
+// Entry l of the Gaussian is e[l * es] (staged entry-major: the threads that
+// stage consecutive Gaussians write consecutive words).  K > 0 fixes k at
+// compile time.
 template <int K>
-__device__ __forceinline__ void scatter_classes(float *row, const int2 *e, int k, int c_lo, int mc, float w) {
+__device__ __forceinline__ void scatter_classes(float *row, const int2 *e, int k, int c_lo, int mc, float w,
+                                                int es) {
   const int n = K > 0 ? K : k;
 #pragma unroll
   for (int l = 0; l < n; ++l) {
-    const int2 v = e[l];
+    const int2 v = e[l * es];
     const int id = v.x - c_lo;
     if ((unsigned)id < (unsigned)mc) row[id] = fmaf(w, __int_as_float(v.y), row[id]);
   }
@@ -307,9 +310,10 @@ __device__ __forceinline__ void scatter_classes(float *row, const int2 *e, int k
 // with the roundings and the order of scatter_classes.  Straight-line code
 // (no branch on the ids).  Other k take scatter_classes.
 template <int K>
-__device__ __forceinline__ void scatter_classes_ilp(float *row, const int2 *e, int k, int c_lo, int mc, float w) {
+__device__ __forceinline__ void scatter_classes_ilp(float *row, const int2 *e, int k, int c_lo, int mc, float w,
+                                                    int es) {
   if constexpr (K == 3) {
-    const int2 e0 = e[0], e1 = e[1], e2 = e[2];
+    const int2 e0 = e[0], e1 = e[es], e2 = e[2 * es];
     const int i0 = e0.x - c_lo, i1 = e1.x - c_lo, i2 = e2.x - c_lo;
     const bool k0 = (unsigned)i0 < (unsigned)mc, k1 = (unsigned)i1 < (unsigned)mc, k2 = (unsigned)i2 < (unsigned)mc;
     const float o0 = k0 ? row[i0] : 0.f, o1 = k1 ? row[i1] : 0.f, o2 = k2 ? row[i2] : 0.f;
@@ -320,7 +324,7 @@ __device__ __forceinline__ void scatter_classes_ilp(float *row, const int2 *e, i
     if (k1) row[i1] = n1;
     if (k2) row[i2] = n2;
   } else {
-    scatter_classes<K>(row, e, k, c_lo, mc, w);
+    scatter_classes<K>(row, e, k, c_lo, mc, w, es);
   }
 }
 
@@ -329,13 +333,16 @@ __device__ __forceinline__ void scatter_classes_ilp(float *row, const int2 *e, i
 // first id when two of the ids are equal (valid ids are non-negative, so the
 // bit is free).  scatter_classes_marked reads it.
 template <int K>
-__device__ __forceinline__ void mark_repeated_ids(int2 *e) {
+__device__ __forceinline__ void mark_repeated_ids(int2 *e, int es) {
   if constexpr (K >= 4) {
+    int id[K];
+#pragma unroll
+    for (int a = 0; a < K; ++a) id[a] = e[a * es].x;
     bool rep = false;
 #pragma unroll
     for (int a = 1; a < K; ++a)
 #pragma unroll
-      for (int b = 0; b < a; ++b) rep |= e[a].x == e[b].x;
+      for (int b = 0; b < a; ++b) rep |= id[a] == id[b];
     if (rep) e[0].x = (int)((uint32_t)e[0].x | 0x80000000u);
   }
 }
@@ -346,11 +353,12 @@ __device__ __forceinline__ void mark_repeated_ids(int2 *e) {
 // one after another.  Either way each slot ends as in scatter_classes.
 // k = 3 takes scatter_classes_ilp (needs no mark).
 template <int K>
-__device__ __forceinline__ void scatter_classes_marked(float *row, const int2 *e, int k, int c_lo, int mc, float w) {
+__device__ __forceinline__ void scatter_classes_marked(float *row, const int2 *e, int k, int c_lo, int mc, float w,
+                                                       int es) {
   if constexpr (K >= 4) {
     int2 v[K];
 #pragma unroll
-    for (int l = 0; l < K; ++l) v[l] = e[l];
+    for (int l = 0; l < K; ++l) v[l] = e[l * es];
     if (v[0].x >= 0) {
       float o[K];
 #pragma unroll
@@ -372,7 +380,7 @@ __device__ __forceinline__ void scatter_classes_marked(float *row, const int2 *e
       }
     }
   } else {
-    scatter_classes_ilp<K>(row, e, k, c_lo, mc, w);
+    scatter_classes_ilp<K>(row, e, k, c_lo, mc, w, es);
   }
 }
 

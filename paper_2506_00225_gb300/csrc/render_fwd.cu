@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_semantic(FwdArgs a) {
     cp_async16(buf_co(q) + t, a.rec.co + r);
     if (!a.masks) cp_async8(buf_box(q) + t, a.rec.box + r);
     const int2 *src = a.rec.sem + (size_t)r * k;
-    for (int l = 0; l < k; ++l) cp_async8(buf_sem(q) + t * k + l, src + l);
+    for (int l = 0; l < k; ++l) cp_async8(buf_sem(q) + l * kBatch + t, src + l);  // entry-major
   };
 
   for (int c = 0; c < a.nchunks; ++c) {
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_semantic(FwdArgs a) {
       mn1 = mw[NPIX + lp];
     }
     cp_async_wait_all();
-    if (nbatch > 0 && t < batch_n(0)) mark_repeated_ids<K>(buf_sem(0) + t * k);
+    if (nbatch > 0 && t < batch_n(0)) mark_repeated_ids<K>(buf_sem(0) + t, kBatch);
     __syncthreads();
     for (int bi = 0; bi < nbatch; ++bi) {
       if (bi + 1 < nbatch && t < batch_n(bi + 1)) issue(bi + 1, pv);
@@ -376,11 +376,11 @@ __global__ void __launch_bounds__(TW *TH, 2) k_semantic(FwdArgs a) {
           float w = on ? __fmul_rn(alpha, T) : 0.f;
           if (tmode) w = -w;
           if (on) T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-          scatter_classes_marked<K>(myP, ssem + j * k, k, c_lo, mc, w);
+          scatter_classes_marked<K>(myP, ssem + j, k, c_lo, mc, w, kBatch);
         }
       }
       cp_async_wait_all();
-      if (bi + 1 < nbatch && t < batch_n(bi + 1)) mark_repeated_ids<K>(buf_sem((bi + 1) & 1) + t * k);
+      if (bi + 1 < nbatch && t < batch_n(bi + 1)) mark_repeated_ids<K>(buf_sem((bi + 1) & 1) + t, kBatch);
       __syncthreads();
     }
     __syncthreads();

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_sem_objective(FwdArgs a, float lo
     cp_async16(buf_co(q) + t, a.rec.co + r);
     cp_async4(buf_gid(q) + t, a.rec.gid + r);
     const int2 *src = a.rec.sem + (size_t)r * k;
-    for (int l = 0; l < k; ++l) cp_async8(buf_sem(q) + t * k + l, src + l);
+    for (int l = 0; l < k; ++l) cp_async8(buf_sem(q) + l * kBatch + t, src + l);  // entry-major
   };
   // One front-to-back walk over the tile's batches (copies of batch bi + 1
   // in flight while bi is processed); a thread that is not live takes no
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_sem_objective(FwdArgs a, float lo
           const bool on = (mine[h] >> jb) & 1u;
           const float w = on ? __fmul_rn(alpha, T) : 0.f;
           if (on) T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-          f(sgid[j], on, w, ssem + j * k);
+          f(sgid[j], on, w, ssem + j);  // entry l at [l * kBatch]
         }
       }
       cp_async_wait_all();
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_sem_objective(FwdArgs a, float lo
 
   // (1) the rendered class distribution P of this thread's pixel
   for (int c = 0; c < m; ++c) myP[c] = 0.f;
-  walk(true, [&](int, bool, float w, const int2 *e) { scatter_classes_ilp<K>(myP, e, k, 0, m, w); });
+  walk(true, [&](int, bool, float w, const int2 *e) { scatter_classes_ilp<K>(myP, e, k, 0, m, w, kBatch); });
 
   // (2) per pixel: the semantic term, and d term / d P (over the pixel
   // count) in place of P.  Thread per pixel: its own row (shared memory,
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_sem_objective(FwdArgs a, float lo
 #pragma unroll
         for (int l = 0; l < (K > 0 ? K : 16); ++l) {
           if (K == 0 && l >= nl) break;
-          const int2 en = e[l];
+          const int2 en = e[l * kBatch];
           const float v = (unsigned)en.x < (unsigned)m ? w * myP[en.x] : 0.f;
           if (v != 0.f) atomicAdd(a.semg + (size_t)gid * k + l, v);
         }
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_sem_objective(FwdArgs a, float lo
       float v[K];
 #pragma unroll
       for (int l = 0; l < K; ++l) {
-        const int2 en = e[l];
+        const int2 en = e[l * kBatch];
         v[l] = (unsigned)en.x < (unsigned)m ? w * myP[en.x] : 0.f;
       }
 #pragma unroll
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(TW *TH, 2) k_sem_objective(FwdArgs a, float lo
 #pragma unroll
       for (int l = 0; l < (K > 0 ? K : 16); ++l) {
         if (K == 0 && l >= nl) break;
-        const int2 en = e[l];
+        const int2 en = e[l * kBatch];
         if ((unsigned)en.x < (unsigned)m) v[l] = w * myP[en.x];
       }
       const float tot = warp_reduce_scatter<16>(v);
