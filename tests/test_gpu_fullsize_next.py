@@ -26,6 +26,7 @@ import torch
 import oracle
 from oracle import mapping_loss as ml
 from oracle import voxel as ovx
+from gradtol import WIDE, grad_close
 from voxel_ties import tie_cells
 from paper_2506_00225_gb300 import explore, raster, scenes
 
@@ -58,9 +59,8 @@ def _targets(seed, H, W, m):
 
 
 def _grad_close(a, b, rtol, name):
-    scale = np.abs(b).max() + 1e-30
-    err = np.abs(a - b) / (np.abs(b) + 0.01 * scale)
-    assert err.max() <= rtol, (name, err.max())
+    """Full-size images: the wide floor (gradtol.WIDE)."""
+    grad_close(a, b, rtol, name, WIDE)
 
 
 def test_mapping_loss_gradients_fullsize_rows(room300k):

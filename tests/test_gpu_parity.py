@@ -5,7 +5,8 @@ records bit-exact; rendered images and semantic maps within 1e-5 max abs
 (pixels where the oracle saw a threshold decision within a relative 1e-5 of
 its threshold are excluded and counted -- the two sides may round exp()
 differently by an ulp or two); gradients within 1e-3 relative of the oracle's
-float32 adjoint (scaled per tensor, see _grad_close); per-view candidate sums
+float32 adjoint (floored at 1e-4 of the tensor's largest entry, see
+gradtol); per-view candidate sums
 within 1e-5 relative, N_S within the number of flagged pixels.
 """
 import numpy as np
@@ -14,6 +15,7 @@ import torch
 
 import oracle
 from paper_2506_00225_gb300 import raster, scenes
+from gradtol import FLOOR, WIDE, grad_close
 
 pytestmark = pytest.mark.gpu
 
@@ -194,7 +196,7 @@ def test_backward_independent_of_mapping():
         res.append({k: v.cpu().numpy() for k, v in rast.backward(g, cam, *ups).items()})
     for other in res[1:]:
         for name in res[0]:
-            _grad_close(other[name], res[0][name], rtol=1e-4, name=name)
+            _grad_close(other[name], res[0][name], rtol=1e-4, name=name, floor=WIDE)
 
 
 def test_autotune_picks_a_compiled_config():
@@ -241,13 +243,9 @@ def test_forward_deterministic():
 # backward
 # ---------------------------------------------------------------------------
 
-def _grad_close(a, b, rtol=1e-3, name=""):
-    """|a - b| <= rtol * (|b| + 0.01 * max|b|): relative error, with a floor
-    at 1 % of the tensor's largest magnitude for entries that are sums of
-    cancelling per-pixel terms (float32 accumulation in a different order)."""
-    scale = np.abs(b).max() + 1e-30
-    err = np.abs(a - b) / (np.abs(b) + 0.01 * scale)
-    assert err.max() <= rtol, (name, err.max(), np.unravel_index(err.argmax(), err.shape))
+def _grad_close(a, b, rtol=1e-3, name="", floor=FLOOR):
+    """|a - b| <= rtol * (|b| + floor * max|b|) (gradtol.grad_close)."""
+    grad_close(a, b, rtol, name, floor)
 
 
 def _mask_flagged(up, flag):
@@ -307,7 +305,7 @@ def test_backward_semantic_block():
     g0 = rast.backward(g, cam, d_rgb=d_rgb, d_sem=torch.zeros_like(d_sem))
     # equal up to the order of float atomics (run-to-run reordering ~1e-5)
     for name in ["means", "scales", "quats", "opacity", "rgb"]:
-        _grad_close(g1[name].cpu().numpy(), g0[name].cpu().numpy(), rtol=1e-4, name=name)
+        _grad_close(g1[name].cpu().numpy(), g0[name].cpu().numpy(), rtol=1e-4, name=name, floor=WIDE)
     assert g1["sem_w"].abs().max() > 0 and g0["sem_w"].abs().max() == 0
     # contrast: without the block the semantic term changes geometric gradients
     rast2 = raster.Rasterizer(sem_detach_geometry=False)
@@ -438,7 +436,7 @@ def test_fused_l1_loss_and_gradients(m, k):
     unf = rast3.backward(g, cam, 2.0 * d_rgb, 2.0 * d_depth, None, 2.0 * d_sem)
     for p, name in zip(params, ["means", "scales", "quats", "opacity", "rgb", "sem_w"]):
         a, b = p.grad.cpu().numpy(), unf[name].cpu().numpy()
-        _grad_close(a, b, rtol=1e-4, name=name)
+        _grad_close(a, b, rtol=1e-4, name=name, floor=WIDE)
 
 
 def test_fused_l1_without_semantic_term():
