@@ -1,15 +1,17 @@
 """gs_render_fwd_noalloc: the forward render for callers that cannot
 allocate device memory (graph capture, real-time loops, hosts that own all
 device memory).  Its workspace is a fixed device array inside the library;
-these checks compare it, through the C ABI, with the regular entry points
-(gs_project + gs_bin_sort + gs_render_fwd on a caller-allocated workspace)
-on two calls in a row, with the image tolerance of the parity tests."""
+these checks compare it, through the C ABI, with the CPU oracle and with the
+regular entry points (gs_project + gs_bin_sort + gs_render_fwd on a
+caller-allocated workspace) on two calls in a row, with the image tolerance
+of the parity tests."""
 import ctypes
 
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2506_00225_gb300 import _native as N
 from paper_2506_00225_gb300 import raster, scenes
 
@@ -74,6 +76,26 @@ def test_noalloc_matches_regular_entry_points_twice():
         for a, b in zip(got, ref):
             assert a.shape == b.shape
             assert np.abs(a - b).max() <= IMG_TOL
+
+
+def test_noalloc_matches_oracle():
+    """Eq. 1 colour, depth, silhouette and Eq. 3 class map against the
+    oracle, element by element, on a ragged 123 x 77 view (pixels whose
+    threshold decision the oracle flags as within rounding are excluded and
+    counted, as in the parity tests)."""
+    sc = scenes.scene_plain(2, n=6000, m=16, k=3)
+    cam = scenes.look_camera((0.0, 0.0, 1.5), 10.0, 123, 77, 60.0, pitch_deg=-5.0)
+    g = raster.Gaussians.from_scene(sc)
+    got, cnt = _noalloc(g, cam, _cfg(sc.n, 1 << 19))
+    assert cnt[0] == 0
+    r = oracle.render(sc, cam, prec="f32")
+    ok = r["flag"] & 1 == 0
+    assert (~ok).sum() <= max(2, ok.size // 1000)
+    for x, name in zip(got, ("rgb", "depth", "sil", "sem")):
+        err = np.abs(x - r[name])
+        if err.ndim > ok.ndim:
+            err = err.reshape(ok.shape + (-1,)).max(-1)
+        assert err[ok].max(initial=0.0) <= IMG_TOL, (name, err[ok].max())
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
