@@ -235,11 +235,24 @@ __global__ void __launch_bounds__(TW *TH / PPT) k_render_bwd(BwdArgs a) {
         __syncwarp();
         if ((int)lane < nh) stage(a.pvals[lo + h * kSlots + lane], lane, true);
         __syncwarp();
+        // pairs whose pixel box meets the warp's pixel block (one test per
+        // lane); the others fail every pixel's box test below
+        int bx0 = px, bx1 = px, by0 = py[0], by1 = py[0];
+#pragma unroll
+        for (int i = 1; i < PPT; ++i) { by0 = min(by0, py[i]); by1 = max(by1, py[i]); }
+        bx0 = __reduce_min_sync(0xffffffffu, bx0); bx1 = __reduce_max_sync(0xffffffffu, bx1);
+        by0 = __reduce_min_sync(0xffffffffu, by0); by1 = __reduce_max_sync(0xffffffffu, by1);
+        const short4 lb = st.box[lane];  // slots past nh hold stale boxes: masked out
+        const uint32_t meets = __ballot_sync(0xffffffffu, (int)lane < nh && lb.x <= bx1 && lb.y >= bx0 &&
+                                                               lb.z <= by1 && lb.w >= by0);
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
           mine[i] = 0u;
           const int nj = nl[i] > hb ? min(nh, (int)(nl[i] - hb)) : 0;
-          for (int j = 0; j < nj; ++j) {
+          uint32_t cand = nj >= 32 ? meets : meets & ((1u << nj) - 1u);
+          while (cand) {
+            const int j = __ffs(cand) - 1;
+            cand &= cand - 1u;
             const short4 bx = st.box[j];
             if (px < bx.x || px > bx.y || py[i] < bx.z || py[i] > bx.w) continue;
             float al, G_, ar, dx_, dy_;

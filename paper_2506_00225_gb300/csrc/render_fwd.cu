@@ -345,16 +345,38 @@ __global__ void __launch_bounds__(TW *TH, 2) k_semantic(FwdArgs a) {
           mn1 = mw[NPIX + lp];
         }
       }
-      if (b0 < last && !a.masks) {
+      if (!a.masks) {
         // recomputation: contributors are the pairs up to the last one
-        // whose pixel box holds the pixel and whose alpha passes 1/255
+        // whose pixel box holds the pixel and whose alpha passes 1/255.
+        // First the pairs whose box meets the warp's pixel block (two slots
+        // per lane); the others fail every pixel's box test.
         const short4 *sbox = buf_box(bi & 1);
-        const int n = min(batch_n(bi), (int)(last - b0));
-        for (int j = 0; j < n; ++j) {
-          const short4 bx = sbox[j];
-          if (px < bx.x || px > bx.y || py < bx.z || py > bx.w) continue;
-          float alpha, G, araw, dx, dy;
-          if (gauss_alpha(suv[j], sco[j], fpx, fpy, alpha, G, araw, dx, dy)) mine[j >> 5] |= 1u << (j & 31);
+        const int nb = batch_n(bi);
+        const int bx0 = __reduce_min_sync(0xffffffffu, px), bx1 = __reduce_max_sync(0xffffffffu, px);
+        const int by0 = __reduce_min_sync(0xffffffffu, py), by1 = __reduce_max_sync(0xffffffffu, py);
+        uint32_t meets[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int j = h * 32 + (int)lane;
+          const short4 bx = sbox[j];  // slots past nb hold stale boxes: masked out
+          meets[h] = __ballot_sync(0xffffffffu, j < nb && bx.x <= bx1 && bx.y >= bx0 && bx.z <= by1 && bx.w >= by0);
+        }
+        if (b0 < last) {
+          const int n = min(nb, (int)(last - b0));
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int lim = n - 32 * h;
+            uint32_t cand = lim >= 32 ? meets[h] : (lim > 0 ? meets[h] & ((1u << lim) - 1u) : 0u);
+            while (cand) {
+              const int jb = __ffs(cand) - 1;
+              cand &= cand - 1u;
+              const short4 bx = sbox[h * 32 + jb];
+              if (px < bx.x || px > bx.y || py < bx.z || py > bx.w) continue;
+              float alpha, G, araw, dx, dy;
+              if (gauss_alpha(suv[h * 32 + jb], sco[h * 32 + jb], fpx, fpy, alpha, G, araw, dx, dy))
+                mine[h] |= 1u << jb;
+            }
+          }
         }
       }
 #pragma unroll
