@@ -259,8 +259,8 @@ def _mask_flagged(up, flag):
     return int(bad.sum())
 
 
-def _bwd_case(sem_detach, seed=0, w=48, h=40):
-    sc, cam = small_case(n=2500, w=w, h=h, seed=seed)
+def _bwd_case(sem_detach, seed=0, w=48, h=40, m=16, k=3, ppt=0, recompute=False):
+    sc, cam = small_case(n=2500, w=w, h=h, seed=seed, m=m, k=k)
     rng = np.random.default_rng(seed + 10)
     H, W, m = cam.height, cam.width, sc.m
     up = dict(d_rgb=rng.normal(size=(H, W, 3)).astype(np.float32), d_depth=rng.normal(size=(H, W)).astype(np.float32),
@@ -268,9 +268,9 @@ def _bwd_case(sem_detach, seed=0, w=48, h=40):
     nbad = _mask_flagged(up, oracle.render(sc, cam, prec="f32")["flag"])
     assert nbad <= max(2, H * W // 1000)
     g = raster.Gaussians.from_scene(sc)
-    rast = raster.Rasterizer(sem_detach_geometry=sem_detach)
+    rast = raster.Rasterizer(sem_detach_geometry=sem_detach, px_per_thread=ppt, recompute_bwd=recompute)
     rast.forward(g, cam)
-    t = {k: torch.from_numpy(v).cuda() for k, v in up.items()}
+    t = {key: torch.from_numpy(v).cuda() for key, v in up.items()}
     grads = rast.backward(g, cam, t["d_rgb"], t["d_depth"], t["d_sil"], t["d_sem"])
     ref = oracle.render_bwd(sc, cam, **up, sem_detach=sem_detach, prec="f32")
     return {k: v.cpu().numpy() for k, v in grads.items()}, ref, sc, cam
@@ -290,6 +290,29 @@ def test_backward_parity_ragged_edges():
         grads, ref, sc, cam = _bwd_case(sem_detach, seed=1, w=45, h=37)
         for name in ["means", "scales", "quats", "opacity", "rgb", "sem_w"]:
             _grad_close(grads[name], ref[name], name=name)
+
+
+@pytest.mark.parametrize("ppt,m,k", [(1, 16, 3), (2, 16, 3), (4, 40, 8)])
+def test_recompute_mode_ragged(ppt, m, k):
+    """recompute_bwd re-derives each pixel's contributors (pairs whose box
+    meets the warp's pixel block, then the pixel's box and alpha tests).  On
+    a ragged 45 x 37 view, where warps straddle the image edge: its forward
+    maps equal the stored-bits forward bit for bit (same contributors, same
+    order), and its adjoint equals the oracle's, for 1, 2 and 4 pixels per
+    thread and k = 3 and 8."""
+    sc, cam = small_case(n=2500, w=45, h=37, seed=7, m=m, k=k)
+    g = raster.Gaussians.from_scene(sc)
+    outs = []
+    for rec in (False, True):
+        rast = raster.Rasterizer(px_per_thread=ppt, recompute_bwd=rec)
+        with torch.no_grad():
+            outs.append([t.cpu().numpy() for t in rast.forward(g, cam)])
+    for a, b, name in zip(*outs, ("rgb", "depth", "sil", "sem")):
+        np.testing.assert_array_equal(a, b, err_msg=name)
+    for sem_detach in (True, False):
+        grads, ref, _, _ = _bwd_case(sem_detach, seed=7, w=45, h=37, m=m, k=k, ppt=ppt, recompute=True)
+        for name in ["means", "scales", "quats", "opacity", "rgb", "sem_w"]:
+            _grad_close(grads[name], ref[name], name=(name, sem_detach))
 
 
 def test_backward_semantic_block():
