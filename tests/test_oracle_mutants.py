@@ -183,6 +183,18 @@ MUTANTS = [
     ('oracle/sparse.py', 'gather invalid',
      'if 0 <= ids[i, l] < m:',
      'if 0 <= ids[i, l] <= m - 1 and ids[i, l] != 0:'),
+    ('oracle/sparse.py', 'lowest kept',
+     'order = np.lexsort((np.broadcast_to(np.arange(m), key.shape), -key), axis=1)[:, :k]',
+     'order = np.lexsort((np.broadcast_to(np.arange(m), key.shape), key), axis=1)[:, :k]'),
+    ('oracle/sparse.py', 'largest skipped',
+     'order = np.lexsort((np.broadcast_to(np.arange(m), key.shape), -key), axis=1)[:, :k]',
+     'order = np.lexsort((np.broadcast_to(np.arange(m), key.shape), -key), axis=1)[:, 1:k + 1]'),
+    ('oracle/sparse.py', 'init rows ignored',
+     'sel = p[r].astype(np.float64)',
+     'sel = p[np.arange(len(r))].astype(np.float64)'),
+    ('oracle/sparse.py', 'gather rows ignored',
+     'out[i, l] = p[r[i], ids[i, l]]',
+     'out[i, l] = p[i, ids[i, l]]'),
     # oracle/voxel.py
     ('oracle/voxel.py', 'pixel centre',
      'xc = (u + 0.5 - float(np.float32(cam.cx))) / float(np.float32(cam.fx)) * de',
@@ -199,6 +211,27 @@ MUTANTS = [
     ('oracle/voxel.py', 'zero depth kept',
      'if not (d > 0.0) or not math.isfinite(d):',
      'if not (d >= 0.0) or not math.isfinite(d):'),
+    ('oracle/voxel.py', 'camera centre sign',
+     'return -r.T @ t, r',
+     'return r.T @ t, r'),
+    ('oracle/voxel.py', 'rotation not transposed',
+     'p = r.T @ np.array([xc, yc, de]) + o',
+     'p = r @ np.array([xc, yc, de]) + o'),
+    ('oracle/voxel.py', 'pixel centre y',
+     'yc = (v + 0.5 - float(np.float32(cam.cy)))',
+     'yc = (v - float(np.float32(cam.cy)))'),
+    ('oracle/voxel.py', 'ray instead of segment',
+     't1 = np.ones(lo.shape[0])',
+     't1 = np.full(lo.shape[0], np.inf)'),
+    ('oracle/voxel.py', 'end voxel rounded',
+     'end = np.floor(b).astype(np.int64)',
+     'end = np.round(b).astype(np.int64)'),
+    ('oracle/voxel.py', 'slab entry',
+     't0 = np.maximum(t0, np.minimum(ta, tb))',
+     't0 = np.maximum(t0, np.maximum(ta, tb))'),
+    ('oracle/voxel.py', 'new free centre',
+     'org[0] + (x + 0.5) * voxel',
+     'org[0] + x * voxel'),
 ]
 
 

@@ -844,6 +844,10 @@ def test_topk_hand_examples():
     # gather with fixed ids; an invalid id keeps its value
     g = sp.topk_gather(probs, np.array([[4, 0, -1]], np.int32), np.array([[9.0, 9.0, 9.0]], np.float32), rows=[0])
     np.testing.assert_array_equal(g, np.float32([[0.0, 0.1, 9.0]]))
+    # Gaussian i reads its own observation row rows[i], not row i
+    g = sp.topk_gather(probs, np.array([[4, 0, 1], [3, 4, 7]], np.int32), np.full((2, 3), 9.0, np.float32),
+                       rows=[2, 1])
+    np.testing.assert_array_equal(g, np.float32([[1.0, 0.0, 0.0], [0.3, 0.1, 9.0]]))
 
 
 def test_topk_matches_python_selection():
