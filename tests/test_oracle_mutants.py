@@ -142,6 +142,42 @@ MUTANTS = [
     ('oracle/mapping_loss.py', 'dcos sign',
      'grad = mask[..., None] * (LAM_HD * dhd - LAM_COS * dcos)',
      'grad = mask[..., None] * (LAM_HD * dhd + LAM_COS * dcos)'),
+    ('oracle/mapping_loss.py', 'dhd sign',
+     '(sp - sq) / (2.0 * sp)',
+     '(sq - sp) / (2.0 * sp)'),
+    ('oracle/mapping_loss.py', 'dhd sqrt factor',
+     '(sp - sq) / (2.0 * sp)',
+     '(sp - sq) / sp'),
+    ('oracle/mapping_loss.py', 'dcos second term sign',
+     '- (cos / np.maximum(npn * npn, EPS_DIV))[..., None] * p',
+     '+ (cos / np.maximum(npn * npn, EPS_DIV))[..., None] * p'),
+    ('oracle/mapping_loss.py', 'dcos norm not squared',
+     'np.maximum(npn * npn, EPS_DIV)',
+     'np.maximum(npn, EPS_DIV)'),
+    ('oracle/mapping_loss.py', 'entropy sign',
+     'h = -qlogq.sum(-1)',
+     'h = qlogq.sum(-1)'),
+    ('oracle/mapping_loss.py', 'depth grad unmasked',
+     'd_depth = mg * np.sign(e_d)',
+     'd_depth = np.sign(e_d)'),
+    ('oracle/mapping_loss.py', 'colour grad weight',
+     'd_rgb = W_COLOUR * mg[..., None] * np.sign(e_c)',
+     'd_rgb = mg[..., None] * np.sign(e_c)'),
+    ('oracle/mapping_loss.py', 'sem grad not mean',
+     'd_sem = g / npix',
+     'd_sem = g'),
+    ('oracle/mapping_loss.py', 'cos norm q twice',
+     'den = nq * npn',
+     'den = nq * nq'),
+    ('oracle/mapping_loss.py', 'negative P as |P|',
+     'pc = np.maximum(p, 0.0)',
+     'pc = np.abs(p)'),
+    ('oracle/mapping_loss.py', 'geometry mean',
+     'loss_geo = (mg * (np.abs(e_d) + W_COLOUR * np.abs(e_c).sum(-1))).sum()',
+     'loss_geo = (mg * (np.abs(e_d) + W_COLOUR * np.abs(e_c).sum(-1))).mean()'),
+    ('oracle/mapping_loss.py', 'colour channel mean',
+     'W_COLOUR * np.abs(e_c).sum(-1))).sum()',
+     'W_COLOUR * np.abs(e_c).mean(-1))).sum()'),
     # oracle/explore.py
     ('oracle/explore.py', 'prune >',
      'keep = ns >= prune_frac * np.asarray(npix, np.float64)',

@@ -688,6 +688,11 @@ def test_mapping_loss_semantic_closed_forms():
     assert -(qs[qs > 0] * np.log(qs[qs > 0])).sum() < math.log(k)
     t, _ = ml.semantic_terms(qs, np.array([[0.0, 0.0, 0.0, 1.0]]), k)
     assert t[0] > 0.5
+    # a negative rendered entry counts as 0 under the square roots (the
+    # module's reading): P = (1, -0.5) against Q = (1, 0) is at Hellinger
+    # distance 0, and the cosine sees the raw P: 1 / sqrt(1.25)
+    t, _ = ml.semantic_terms(np.array([[1.0, 0.0]]), np.array([[1.0, -0.5]]), k)
+    assert abs(t[0] - 0.2 * (1.0 - 1.0 / math.sqrt(1.25))) < 1e-9
 
 
 def test_mapping_loss_geometric_closed_form_and_mask():
