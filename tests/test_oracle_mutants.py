@@ -209,6 +209,39 @@ MUTANTS = [
     ('oracle/explore.py', 'band <',
      'if abs(z - h) <= band:',
      'if abs(z - h) < band:'),
+    ('oracle/explore.py', 'semantic factor from U',
+     'ns, sh = sums[:, 2], sums[:, 1]',
+     'ns, sh = sums[:, 2], sums[:, 0]'),
+    ('oracle/explore.py', 'N_S from column 0',
+     'ns, sh = sums[:, 2], sums[:, 1]',
+     'ns, sh = sums[:, 0], sums[:, 1]'),
+    ('oracle/explore.py', 'no N_S: uniform',
+     'igeo = np.zeros_like(ns)',
+     'igeo = np.full_like(ns, 1.0 / len(ns))'),
+    ('oracle/explore.py', 'distance squared',
+     'dist = np.linalg.norm(np.asarray(positions, np.float64) - np.asarray(current, np.float64), axis=1)',
+     'dist = ((np.asarray(positions, np.float64) - np.asarray(current, np.float64)) ** 2).sum(1)'),
+    ('oracle/explore.py', 'best ignores pruning',
+     'if keep[v] and (best < 0 or iv[v] > iv[best]):',
+     'if (best < 0 or iv[v] > iv[best]):'),
+    ('oracle/explore.py', 'down axis flip',
+     'down = np.cross(d, right)',
+     'down = np.cross(right, d)'),
+    ('oracle/explore.py', 'translation sign',
+     '(-r @ np.asarray(position, np.float64))',
+     '(r @ np.asarray(position, np.float64))'),
+    ('oracle/explore.py', 'fib radius',
+     'r = np.sqrt(np.maximum(0.0, 1.0 - z * z))',
+     'r = np.maximum(0.0, 1.0 - z * z)'),
+    ('oracle/explore.py', 'height index as height',
+     'out = [(i * step, j * step, hs[hi]) for i, j, hi in sorted(pts)]',
+     'out = [(i * step, j * step, float(hi)) for i, j, hi in sorted(pts)]'),
+    ('oracle/explore.py', 'score without motion',
+     'iv = mov * igeo * isem',
+     'iv = igeo * isem'),
+    ('oracle/explore.py', 'lattice y floor',
+     'pts.add((math.floor(x / step + 0.5), math.floor(y / step + 0.5), hi))',
+     'pts.add((math.floor(x / step + 0.5), math.floor(y / step), hi))'),
     # oracle/sparse.py
     ('oracle/sparse.py', 'ties high id',
      'order = np.lexsort((np.broadcast_to(np.arange(m), key.shape), -key), axis=1)[:, :k]',
