@@ -138,36 +138,44 @@ def test_projection_matches_numeric_jacobian():
 
 def test_frustum_clamp_of_the_jacobian():
     """A Gaussian beyond 1.3 tan(half field of view) of the optical axis is
-    linearised at the clamped point (x/z clamped to +-1.3 (W/2)/f): its
-    conic equals the EWA form with a numerically differentiated pinhole map
-    at that point, and differs from the one at its own mean."""
-    W = H = 41
+    linearised at the clamped point (x/z clamped to +-1.3 (W/2)/f, y/z to
+    +-1.3 (H/2)/f): its conic equals the EWA form with a numerically
+    differentiated pinhole map at that point, and differs from the one at its
+    own mean; one within the limit is linearised at its mean.  A square and
+    a wide view, offsets along x and along y, inside and beyond each axis's
+    limit."""
     f, z, s = 40.0, 2.0, 0.5
-    cam = ident_cam(W, H, f)
-    lim = 1.3 * (W / 2.0) / f
-    for sign in (1.0, -1.0):
-        mean = np.array([sign * 0.8 * z, 0.1, z])
-        sc = mk_scene([mean], [[s, s, s]], [[1, 0, 0, 0]], [0.9])
-        p = oracle.project(sc, cam, prec="f64")
-        assert p["visible"][0]
-        m32 = np.asarray(sc.means[0], np.float64)
-        s32 = float(sc.scales[0, 0])
+    for W, H in ((41, 41), (61, 31)):
+        cam = ident_cam(W, H, f)
+        lims = (1.3 * (W / 2.0) / f, 1.3 * (H / 2.0) / f)
+        for axis in (0, 1):
+            for off in (0.3, 0.8, 1.2):
+                for sign in (1.0, -1.0):
+                    mean = np.array([0.1, 0.1, z])
+                    mean[axis] = sign * off * z
+                    sc = mk_scene([mean], [[s, s, s]], [[1, 0, 0, 0]], [0.9])
+                    p = oracle.project(sc, cam, prec="f64")
+                    assert p["visible"][0], (W, H, axis, off, sign)
+                    m32 = np.asarray(sc.means[0], np.float64)
+                    s32 = float(sc.scales[0, 0])
 
-        def pix(X):
-            return np.array([f * X[0] / X[2] + W / 2.0, f * X[1] / X[2] + H / 2.0])
+                    def pix(X):
+                        return np.array([f * X[0] / X[2] + W / 2.0, f * X[1] / X[2] + H / 2.0])
 
-        def ewa_conic(X):
-            J = np.zeros((2, 3))
-            for i in range(3):
-                e = np.zeros(3); e[i] = 1e-6
-                J[:, i] = (pix(X + e) - pix(X - e)) / 2e-6
-            S2 = J @ (s32 ** 2 * np.eye(3)) @ J.T + 0.3 * np.eye(2)
-            inv = np.linalg.inv(S2)
-            return np.array([inv[0, 0], inv[0, 1], inv[1, 1]])
+                    def ewa_conic(X):
+                        J = np.zeros((2, 3))
+                        for i in range(3):
+                            e = np.zeros(3); e[i] = 1e-6
+                            J[:, i] = (pix(X + e) - pix(X - e)) / 2e-6
+                        S2 = J @ (s32 ** 2 * np.eye(3)) @ J.T + 0.3 * np.eye(2)
+                        inv = np.linalg.inv(S2)
+                        return np.array([inv[0, 0], inv[0, 1], inv[1, 1]])
 
-        clamped = np.array([np.clip(m32[0] / m32[2], -lim, lim) * m32[2], m32[1], m32[2]])
-        np.testing.assert_allclose(p["conic"][0], ewa_conic(clamped), rtol=1e-6)
-        assert np.abs(p["conic"][0] - ewa_conic(m32)).max() > 1e-3 * np.abs(p["conic"][0]).max()
+                    clamped = np.array([np.clip(m32[0] / m32[2], -lims[0], lims[0]) * m32[2],
+                                        np.clip(m32[1] / m32[2], -lims[1], lims[1]) * m32[2], m32[2]])
+                    np.testing.assert_allclose(p["conic"][0], ewa_conic(clamped), rtol=1e-6)
+                    if abs(m32[axis] / m32[2]) > lims[axis]:
+                        assert np.abs(p["conic"][0] - ewa_conic(m32)).max() > 1e-3 * np.abs(p["conic"][0]).max()
 
 
 def test_near_plane_culls_at_and_before_it():
