@@ -263,6 +263,35 @@ def test_tile_lists_bruteforce_and_tiebreak():
         assert list(gids[s:e]) == members
 
 
+def test_tile_lists_several_ragged_views():
+    """Two views, one of them ragged (57 x 41 with 16 x 16 tiles: the last
+    column and row of tiles are partial): view v's tiles follow all tiles
+    of the views before it, each view has ceil(W / 16) x ceil(H / 16) tiles
+    numbered row-major, and each tile holds its view's Gaussians whose tile
+    rectangle contains it, front to back, ties by gid."""
+    rng = np.random.default_rng(4)
+    n = 200
+    cams = [ident_cam(64, 48, 50.0), ident_cam(57, 41, 45.0)]
+    z = rng.choice([1.5, 2.0, 2.5], size=n)
+    means = np.stack([rng.uniform(-0.7, 0.7, n) * z, rng.uniform(-0.55, 0.55, n) * z, z], 1)
+    sc = mk_scene(means, np.exp(rng.normal(-3, 0.4, (n, 3))), rand_quat(rng, n), np.full(n, 0.5))
+    projs = [oracle.project(sc, cam, prec="f32") for cam in cams]
+    ranges, gids, offs = oracle.tile_lists(projs, cams)
+    counts = [((c.width + 15) // 16) * ((c.height + 15) // 16) for c in cams]
+    assert counts == [12, 12] and offs.tolist() == [0, 12, 24] and len(ranges) == 24
+    for v, (p, cam) in enumerate(zip(projs, cams)):
+        gx = (cam.width + 15) // 16
+        for t in range(counts[v]):
+            tx, ty = t % gx, t // gx
+            members = [g for g in range(n) if p["visible"][g] and p["trect"][g][0] <= tx <= p["trect"][g][1]
+                       and p["trect"][g][2] <= ty <= p["trect"][g][3]]
+            members.sort(key=lambda g: (float(p["depth"][g]), g))
+            s_, e = ranges[offs[v] + t]
+            assert list(gids[s_:e]) == members, (v, t)
+    # the ragged view's partial tiles are reached
+    assert any(projs[1]["trect"][g][1] == 3 for g in range(n) if projs[1]["visible"][g])
+
+
 # --------------------------------------------------------------------------
 # compositing (Eq. 1, Eq. 3)
 # --------------------------------------------------------------------------
