@@ -83,6 +83,51 @@ def test_isotropic_on_axis_closed_form():
         np.testing.assert_allclose(r["depth"], z32 * expect, rtol=1e-12, atol=1e-14)
 
 
+def test_isotropic_on_axis_anisotropic_focal_lengths():
+    """The same Gaussian seen through fx != fy renders the axis-aligned
+    ellipse alpha(p) = o exp(-(dx^2 / var_x + dy^2 / var_y) / 2), var_x =
+    (fx s / z)^2 + 0.3, var_y = (fy s / z)^2 + 0.3, inside the square of half
+    size ceil(3 sqrt(lambda_max)) (lambda_max = var_x: the eigenvalue gap
+    exceeds the floor)."""
+    W = H = 41
+    fx, fy, z, s, o = 40.0, 24.0, 2.0, 0.15, 0.8
+    w2c = np.zeros((3, 4), np.float32)
+    w2c[:, :3] = np.eye(3, dtype=np.float32)
+    cam = Camera(W, H, fx, fy, W / 2.0, H / 2.0, 0.2, w2c)
+    sc = mk_scene([[0.0, 0.0, z]], [[s, s, s]], [[1.0, 0, 0, 0]], [o])
+    r = oracle.render(sc, cam, prec="f64")
+    s32, z32, o32 = float(np.float32(s)), float(np.float32(z)), float(np.float32(o))
+    vx, vy = (fx * s32 / z32) ** 2 + 0.3, (fy * s32 / z32) ** 2 + 0.3
+    assert ((vx - vy) / 2) ** 2 > 0.1
+    rad = math.ceil(3 * math.sqrt(vx))
+    ys, xs = np.mgrid[0:H, 0:W]
+    dx = xs + 0.5 - W / 2.0
+    dy = ys + 0.5 - H / 2.0
+    a = np.minimum(0.99, o32 * np.exp(-0.5 * (dx ** 2 / vx + dy ** 2 / vy)))
+    inside = (np.abs(dx) <= rad) & (np.abs(dy) <= rad) & (a >= 1 / 255)
+    np.testing.assert_allclose(r["sil"], np.where(inside, a, 0.0), rtol=1e-12, atol=1e-14)
+
+
+def test_row_sample_renders_exactly_its_rows():
+    """rows = (begin, end, step) renders rows begin, begin + step, ... below
+    end, each equal to the full render's row, and leaves every other row
+    (including those past end on the same stride) at zero."""
+    rng = np.random.default_rng(12)
+    cam = ident_cam(24, 20, 18.0)
+    n = 60
+    z = rng.uniform(1.0, 3.0, n)
+    means = np.stack([rng.uniform(-0.5, 0.5, n) * z, rng.uniform(-0.5, 0.5, n) * z, z], 1)
+    sc = mk_scene(means, np.exp(rng.normal(-1.8, 0.3, (n, 3))), rand_quat(rng, n), rng.uniform(0.3, 0.9, n))
+    full = oracle.render(sc, cam, prec="f32")
+    part = oracle.render(sc, cam, prec="f32", rows=(2, 10, 3))
+    sel = np.zeros(cam.height, bool)
+    sel[[2, 5, 8]] = True
+    for key in ("rgb", "depth", "sil", "sem"):
+        np.testing.assert_array_equal(part[key][sel], full[key][sel], err_msg=key)
+        assert not part[key][~sel].any(), key
+    assert full["sil"][[11, 14, 17]].any()  # rows the sample must leave out are not empty
+
+
 def _proj_numeric(mean, scale, q, cam):
     """EWA linearisation by numerical differentiation of the pinhole map
     (world point -> pixel) at the mean, in float64."""
