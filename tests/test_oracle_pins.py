@@ -128,6 +128,35 @@ def test_row_sample_renders_exactly_its_rows():
     assert full["sil"][[11, 14, 17]].any()  # rows the sample must leave out are not empty
 
 
+def test_near_threshold_flags():
+    """A pixel is flagged when a threshold decision lies within a relative
+    1e-5 of its threshold: bit 1 for alpha at the 1/255 skip or the
+    transmittance at the 1e-4 stop, bit 2 for alpha at the 0.99 cap.  On a
+    1 x 1 view a Gaussian centred on the pixel has G = 1, so alpha is its
+    opacity."""
+    w2c = np.zeros((3, 4), np.float32)
+    w2c[:, :3] = np.eye(3, dtype=np.float32)
+    cam = Camera(1, 1, 10.0, 10.0, 0.5, 0.5, 0.2, w2c)
+
+    def flag(opacities, depths):
+        n = len(opacities)
+        sc = mk_scene([[0.0, 0.0, d] for d in depths], [[0.2, 0.2, 0.2]] * n, [[1.0, 0, 0, 0]] * n, opacities)
+        return int(oracle.render(sc, cam, prec="f32")["flag"][0, 0])
+
+    assert flag([0.5], [2.0]) == 0
+    assert flag([(1 / 255) * (1 + 1e-7)], [2.0]) & 1
+    assert flag([(1 / 255) * (1 - 1e-7)], [2.0]) & 1
+    assert flag([(1 / 255) * 1.01], [2.0]) == 0
+    assert flag([(1 / 255) * 1.001], [2.0]) == 0  # the margin is relative: 1e-5 of 1/255
+    assert flag([(1 / 255) * 1.0005], [2.0]) == 0
+    assert flag([0.99 * (1 + 1e-6)], [2.0]) == 2
+    assert flag([0.99 * (1 - 1e-6)], [2.0]) == 2
+    assert flag([0.98], [2.0]) == 0
+    # two capped Gaussians: T = 0.01, then 1e-4 within rounding of the stop
+    assert flag([0.995, 0.995], [2.0, 3.0]) & 1
+    assert flag([0.9, 0.9], [2.0, 3.0]) == 0
+
+
 def _proj_numeric(mean, scale, q, cam):
     """EWA linearisation by numerical differentiation of the pinhole map
     (world point -> pixel) at the mean, in float64."""
