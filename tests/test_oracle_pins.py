@@ -487,9 +487,15 @@ def test_pixel_list_equals_full_image():
     xs = rng.integers(0, 40, 50)
     ys = rng.integers(0, 30, 50)
     rp = oracle.render_pixels(sc, cam, xs, ys, prec="f32")
-    np.testing.assert_array_equal(rp["rgb"], r["rgb"][ys, xs])
-    np.testing.assert_array_equal(rp["sem"], r["sem"][ys, xs])
-    np.testing.assert_array_equal(rp["sil"], r["sil"][ys, xs])
+    for key in ("rgb", "sem", "sil", "depth", "T", "n_contrib", "flag"):
+        np.testing.assert_array_equal(rp[key], r[key][ys, xs], err_msg=key)
+    # a flagged pixel: alpha at the skip threshold on a 1 x 1 view
+    w2c = np.zeros((3, 4), np.float32)
+    w2c[:, :3] = np.eye(3, dtype=np.float32)
+    cam1 = Camera(1, 1, 10.0, 10.0, 0.5, 0.5, 0.2, w2c)
+    sc1 = mk_scene([[0.0, 0.0, 2.0]], [[0.2, 0.2, 0.2]], [[1.0, 0, 0, 0]], [(1 / 255) * (1 + 1e-7)])
+    rp1 = oracle.render_pixels(sc1, cam1, np.array([0]), np.array([0]), prec="f32")
+    assert rp1["flag"][0] & 1 and rp1["flag"][0] == oracle.render(sc1, cam1, prec="f32")["flag"][0, 0]
 
 
 # --------------------------------------------------------------------------
