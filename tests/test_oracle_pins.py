@@ -812,6 +812,30 @@ def test_mapping_loss_semantic_closed_forms():
     assert abs(t[0] - 0.2 * (1.0 - 1.0 / math.sqrt(1.25))) < 1e-9
 
 
+def test_mapping_loss_semantic_degenerate_cases():
+    """The module's readings at its degenerate points, in closed form:
+    an uncovered pixel (P = 0) against a one-hot Q has cosine 0 and a zero
+    cosine gradient, so its term is 0.8 D + 0.2 and its gradient the
+    Hellinger one alone; distributions within 1e-12 in Hellinger distance
+    have a zero Hellinger gradient."""
+    from oracle import mapping_loss as ml
+    k = 3
+    eps = 1e-12
+    q = np.array([[1.0, 0.0, 0.0]])
+    t, g = ml.semantic_terms(q, np.zeros((1, 3)), k)
+    sq0, s0 = math.sqrt(1.0 + eps), math.sqrt(eps)
+    d = math.sqrt(0.5 * (sq0 - s0) ** 2)
+    assert abs(t[0] - (0.8 * d + 0.2)) < 1e-12
+    expect = np.array([[0.8 * (s0 - sq0) / (2.0 * s0) / (2.0 * d), 0.0, 0.0]])
+    np.testing.assert_allclose(g, expect, rtol=1e-9, atol=0)
+    # P within 1e-13 of Q: Hellinger distance below 1e-12, so only the
+    # cosine part (of the order of the difference) is left in the gradient
+    qh = np.array([[0.5, 0.5, 0.0]])
+    ph = np.array([[0.5 + 1e-13, 0.5 - 1e-13, 0.0]])
+    t, g = ml.semantic_terms(qh, ph, k)
+    assert abs(t[0]) < 1e-12 and np.abs(g).max() < 1e-11
+
+
 def test_mapping_loss_geometric_closed_form_and_mask():
     from oracle import mapping_loss as ml
     rgb = np.array([[[0.6, 0.3, 0.55]], [[0.2, 0.2, 0.2]]])
