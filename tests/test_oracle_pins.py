@@ -984,6 +984,9 @@ def test_topk_hand_examples():
     ids, w = sp.topk_init(probs, 3)
     assert ids.tolist() == [[1, 2, 3], [1, 2, 3], [4, 0, 1]]
     np.testing.assert_array_equal(w, np.float32([[0.5, 0.2, 0.2], [0.3, 0.3, 0.3], [1.0, 0.0, 0.0]]))
+    # NaN ranks below every number, zero included
+    ids, _ = sp.topk_init(np.array([[np.nan, 0.0, 0.2]], np.float32), 3)
+    assert ids.tolist() == [[2, 1, 0]]
     # rows select observations; k = m returns a full descending order
     ids, w = sp.topk_init(probs, 5, rows=[2, 0])
     assert ids.tolist() == [[4, 0, 1, 2, 3], [1, 2, 3, 0, 4]]
@@ -1030,6 +1033,22 @@ def test_voxel_axis_aligned_ray_closed_form():
     for bad in (0.0, -1.0, np.nan, np.inf):
         s_, m_ = vx.integrate((0, 0, 0), vs, (8, 5, 5), np.array([[bad]], np.float32), cam)
         assert not s_.any() and not m_.any()
+
+
+def test_voxel_ray_on_a_face_is_undecided():
+    """The same ray moved onto the face between voxel rows y = 1 and y = 2
+    (y = 2.0 voxels, exact in float): it touches both rows' cubes on their
+    shared face only, so those voxels are near ties, in `maybe` but not in
+    `sure`; the rows beside them are untouched."""
+    from oracle import voxel as vx
+    vs = 0.25
+    cam = _axis_cam((0.5 * vs, 2.0 * vs, 2.5 * vs), 0.0, 1, 1, 10.0)
+    depth = np.array([[5.0 * vs]], np.float32)
+    sure, maybe = vx.integrate((0, 0, 0), vs, (8, 5, 5), depth, cam)
+    for x in range(4):  # away from the end point's cells (x = 4..6)
+        for y in (1, 2):
+            assert sure[2, y, x] & 1 == 0 and maybe[2, y, x] & 1 == 1, (x, y)
+    assert not sure[:, (0, 3, 4), :].any() and not maybe[:, (0, 3, 4), :].any()
 
 
 def test_voxel_ray_entering_from_outside_and_sampling():
