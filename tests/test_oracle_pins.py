@@ -959,6 +959,17 @@ def test_look_along_pose():
     cam = scenes.look_camera((1.0, 2.0, 1.5), 30.0, 64, 48, 50.0)
     d = np.array([math.cos(math.radians(30)), math.sin(math.radians(30)), 0.0])
     np.testing.assert_allclose(ex.look_along((1.0, 2.0, 1.5), d), cam.w2c, atol=1e-6)
+    # straight up and straight down (d parallel to z): still a proper pose,
+    # right = d x y normalised (the module's reading), forward = d
+    for dz in (1.0, -1.0):
+        d = np.array([0.0, 0.0, dz])
+        w = ex.look_along((0.5, -0.5, 1.0), d)
+        r = w[:, :3]
+        assert np.isfinite(w).all()
+        np.testing.assert_allclose(r @ r.T, np.eye(3), atol=1e-14)
+        assert abs(np.linalg.det(r) - 1.0) < 1e-12
+        np.testing.assert_allclose(r[2], d, atol=1e-15)
+        np.testing.assert_allclose(r[0], np.cross(d, [0.0, 1.0, 0.0]), atol=1e-15)
 
 
 def test_candidate_positions_closed_form():
@@ -969,6 +980,9 @@ def test_candidate_positions_closed_form():
     np.testing.assert_allclose(p, [[0, 0, 1.5], [1, 0, 1.5], [3, 1, 1.5]], atol=1e-7)
     p2 = ex.candidate_positions(centres, 0.5, [0.8, 1.5], 0.1)
     assert len(p2) == 5 and set(np.round(p2[:, 2], 5)) == {0.8, 1.5}
+    # a centre within the band of two heights gives a position at each
+    p3 = ex.candidate_positions(np.array([[0.1, 0.1, 1.1]]), 1.0, [1.0, 1.2], 0.15)
+    np.testing.assert_allclose(p3, [[0, 0, 1.0], [0, 0, 1.2]], atol=1e-7)
 
 
 # ---------------------------------------------------------------------------
